@@ -1,0 +1,152 @@
+"""Exact-integer CDF sampling and proportional non-degenerate batched sampling.
+TEST INFRASTRUCTURE (see the package docstring).
+
+Paper, Sec. III-B (NBS, proportional case): at each batch B_j the m_i shots of a
+trajectory are drawn from conditional marginal distributions; block B_1 needs
+one contraction per trajectory, and for j > 1 each *distinct* prefix
+(s_1..s_{j-1}) already drawn is contracted once and all shots sharing it are
+drawn from its conditional marginal.  Shots are carried as (prefix, count)
+pairs, so no contraction is repeated for a repeated prefix.
+
+Conventions (readings of points the paper leaves open, listed in the design doc):
+
+* a marginal row p[0 .. 2^b) (unnormalised, FP32 or FP64, negatives clamped to
+  zero) is quantised to integers P_x = rint(p_x * 2^sigma) held exactly in FP64,
+  sigma = 52 - bits - e where max p = f * 2^e, f in [0.5, 1), and bits =
+  ceil(log2(#bins)); the running sum C of P is then exact in any order;
+* a draw takes the 64-bit word a = (x0 << 32) | x1 of one Philox4x32-10 call,
+  r = floor(a * T / 2^64) with T = C[last], and returns the smallest x with
+  r < C[x] (entries with P_x = 0 are never returned);
+* shot rank r of trajectory i in block j (0-based) uses the counter
+  (r_lo, r_hi, i, tag(SAMPLE, circuit, j)); the c shots of a parent take the
+  ranks R .. R+c-1, R the sum of the counts of the trajectory's earlier
+  parents in canonical order;
+* canonical order: trajectories in their listed order, then prefixes
+  lexicographic by (x_1, x_2, ...), block 1 most significant; a child's bits
+  are prefix | (x << start_j);
+* proportional shot allocation draws the M shots of the whole run over the
+  trajectory weights a_i = c_i * w_i (multiplicity times norm) with shot t using
+  the counter (t_lo, t_hi, 0, tag(ALLOC, circuit)).
+"""
+import math
+
+import numpy as np
+
+from . import philox
+
+
+def quantise(p):
+    """Integer-valued FP64 weights and their running sum for one row p."""
+    p = np.asarray(p, dtype=np.float64)
+    p = np.where(p > 0.0, p, 0.0)
+    n_bins = p.shape[-1]
+    bits = int(math.ceil(math.log2(n_bins))) if n_bins > 1 else 0
+    m = float(p.max())
+    if m <= 0.0:
+        raise ValueError("all-zero probability row")
+    _, e = math.frexp(m)
+    sigma = 52 - bits - e
+    P = np.rint(np.ldexp(p, sigma))
+    C = np.empty_like(P)
+    acc = 0.0
+    for i, v in enumerate(P):
+        acc = acc + v
+        C[i] = acc
+    return P, C
+
+
+def inverse_cdf(C, a):
+    """Smallest x with floor(a * T / 2^64) < C[x], T = C[-1]; a uint64 array."""
+    T = np.uint64(int(C[-1]))
+    r = philox.mulhi64(a, T).astype(np.float64)     # < T <= 2^52: exact
+    return np.searchsorted(C, r, side="right")
+
+
+def draw_words(ranks, traj, tagw, seed):
+    k0, k1 = philox.key_of(seed)
+    ranks = np.asarray(ranks, dtype=np.uint64)
+    x0, x1, _, _ = philox.philox4x32_10(ranks & philox.MASK32, ranks >> philox.S32,
+                                        traj, tagw, k0, k1)
+    return philox.word64(x0, x1)
+
+
+def sample_block(p_rows, traj, counts, rank0, seed, block, circuit=0):
+    """Draw counts[n] shots from row n of p_rows for every parent n.
+
+    Returns the list of child bins: (parent index, x, count) in canonical order."""
+    tagw = philox.tag(philox.STREAM_SAMPLE, circuit, block)
+    out_parent, out_x, out_c = [], [], []
+    for n in range(len(counts)):
+        c = int(counts[n])
+        if c == 0:
+            continue
+        _, C = quantise(p_rows[n])
+        ranks = np.arange(int(rank0[n]), int(rank0[n]) + c, dtype=np.uint64)
+        a = draw_words(ranks, np.uint64(int(traj[n])), tagw, seed)
+        xs = inverse_cdf(C, a)
+        hist = np.bincount(xs, minlength=len(C))
+        nz = np.nonzero(hist)[0]
+        out_parent.extend([n] * len(nz))
+        out_x.extend(nz.tolist())
+        out_c.extend(hist[nz].tolist())
+    return (np.array(out_parent, dtype=np.int64), np.array(out_x, dtype=np.int64),
+            np.array(out_c, dtype=np.int64))
+
+
+def rank_offsets(traj, counts):
+    """Exclusive running sum of counts within each trajectory (canonical order)."""
+    r0 = np.zeros(len(counts), dtype=np.int64)
+    acc = {}
+    for n in range(len(counts)):
+        t = int(traj[n])
+        r0[n] = acc.get(t, 0)
+        acc[t] = r0[n] + int(counts[n])
+    return r0
+
+
+def allocate_shots(weights, total, seed, circuit=0):
+    """m_i: one multinomial draw of ``total`` shots over the trajectory weights."""
+    _, C = quantise(weights)
+    tagw = philox.tag(philox.STREAM_ALLOC, circuit, 0)
+    m = np.zeros(len(weights), dtype=np.int64)
+    chunk = 1 << 20
+    for t0 in range(0, total, chunk):
+        t = np.arange(t0, min(total, t0 + chunk), dtype=np.uint64)
+        a = draw_words(t, np.uint64(0), tagw, seed)
+        m += np.bincount(inverse_cdf(C, a), minlength=len(weights))
+    return m
+
+
+def nbs_proportional(marginal_fn, blocks, seed, n_traj, circuit=0, shots=None,
+                     total_shots=None, mult=None):
+    """Proportional NBS over all blocks.
+
+    marginal_fn(j, traj[], prefix[]) -> unnormalised marginal rows [n, 2^{b_j}]
+    (FP64 or FP32), blocks = [(start_j, b_j)].  ``shots`` gives m_i per
+    trajectory (fixed allocation); otherwise ``total_shots`` are allocated over
+    a_i = mult_i * Z_i, Z_i the sum of trajectory i's block-1 marginal.
+
+    Returns (traj, bits, count) of the final level in canonical order, the
+    per-block numbers of parents D_j and the allocation m."""
+    all_traj = np.arange(n_traj, dtype=np.int64)
+    rows0 = marginal_fn(0, all_traj, np.zeros(n_traj, dtype=np.uint64))
+    if shots is None:
+        z = np.asarray(rows0, dtype=np.float64).sum(axis=1)
+        w = z * (np.ones(n_traj) if mult is None else np.asarray(mult, np.float64))
+        m = allocate_shots(w, int(total_shots), seed, circuit)
+    else:
+        m = np.asarray(shots, dtype=np.int64)
+    keep = m > 0
+    traj = all_traj[keep]
+    prefix = np.zeros(len(traj), dtype=np.uint64)
+    counts = m[keep]
+    levels = []
+    for j, (start, b) in enumerate(blocks):
+        levels.append(len(traj))
+        rows = rows0[keep] if j == 0 else marginal_fn(j, traj, prefix)
+        r0 = rank_offsets(traj, counts)
+        par, xs, cs = sample_block(rows, traj, counts, r0, seed, j, circuit)
+        traj = traj[par]
+        prefix = prefix[par] | (xs.astype(np.uint64) << np.uint64(start))
+        counts = cs
+    return traj, prefix, counts, levels, m

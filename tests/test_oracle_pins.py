@@ -1,0 +1,359 @@
+"""Pins of the CPU oracle to facts fixed outside the oracle itself: published
+known-answer vectors, closed forms, brute force on tiny inputs, invariants and
+special cases.  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import densmat, mps, philox, pts, sampling, statevector as sv
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox ----
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox.philox4x32_10(*v[0:4], *v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_mulhi64_exact():
+    rng = np.random.default_rng(1)
+    a = rng.integers(0, 2**63, size=2000, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, size=2000, dtype=np.uint64)
+    t = rng.integers(1, 2**53, size=2000, dtype=np.uint64)
+    got = philox.mulhi64(a, t)
+    want = [(int(x) * int(y)) >> 64 for x, y in zip(a, t)]
+    assert [int(g) for g in got] == want
+    assert int(philox.mulhi64(np.uint64(2**64 - 1), np.uint64(2**53))) == 2**53 - 1
+
+
+def test_uniform53_range():
+    u = philox.uniform53(np.array([0, 0xFFFFFFFF], np.uint64), np.array([0, 0xFFFFFFFF], np.uint64))
+    assert u[0] == 0.0 and u[1] < 1.0 and u[1] == 1.0 - 2.0**-53
+
+
+# ------------------------------------------------------- Kraus channels ----
+
+@pytest.mark.parametrize("p", [0.0, 0.003, 0.01, 0.2, 0.75])
+def test_depolarizing_completeness_and_action(p):
+    ch = W.depolarizing_kraus(p)
+    assert pts.completeness_error(ch.kraus) < 1e-14
+    q = pts.kraus_probs(ch.kraus)
+    assert abs(q.sum() - 1) < 1e-15
+    np.testing.assert_allclose(q, [1 - p, p / 3, p / 3, p / 3], atol=1e-15)
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    rho = a @ a.conj().T
+    rho /= np.trace(rho)
+    x = np.array([[0, 1], [1, 0]]); y = np.array([[0, -1j], [1j, 0]]); z = np.diag([1, -1])
+    closed = (1 - p) * rho + p / 3 * (x @ rho @ x + y @ rho @ y + z @ rho @ z)
+    got = sum(k @ rho @ k.conj().T for k in ch.kraus)
+    np.testing.assert_allclose(got, closed, atol=1e-14)
+    if p == 0.75:   # fully depolarising: maps every state to I/2
+        np.testing.assert_allclose(got, np.eye(2) / 2, atol=1e-14)
+
+
+@pytest.mark.parametrize("g", [0.0, 0.002, 0.3, 1.0])
+def test_amplitude_damping_closed_form(g):
+    ch = W.amplitude_damping_kraus(g)
+    assert pts.completeness_error(ch.kraus) < 1e-14
+    one = np.diag([0.0, 1.0]).astype(complex)
+    got = sum(k @ one @ k.conj().T for k in ch.kraus)
+    np.testing.assert_allclose(got, np.diag([g, 1 - g]), atol=1e-15)
+    plus = np.full((2, 2), 0.5, dtype=complex)
+    got = sum(k @ plus @ k.conj().T for k in ch.kraus)
+    want = np.array([[0.5 + 0.5 * g, 0.5 * math.sqrt(1 - g)], [0.5 * math.sqrt(1 - g), 0.5 - 0.5 * g]])
+    np.testing.assert_allclose(got, want, atol=1e-15)
+    np.testing.assert_allclose(pts.kraus_probs(ch.kraus), [1 - g / 2, g / 2], atol=1e-15)
+
+
+def test_cdf_last_entry_is_one():
+    for ch in (W.depolarizing_kraus(0.01), W.amplitude_damping_kraus(0.002)):
+        c = pts.kraus_cdf(ch.kraus)
+        assert c[-1] == 1.0 and np.all(np.diff(c) >= 0)
+
+
+def test_haar_u2_unitary():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        u = W.haar_u2(rng)
+        np.testing.assert_allclose(u @ u.conj().T, np.eye(2), atol=1e-14)
+
+
+# ---------------------------------------------------------- pre-sampling ----
+
+def test_presample_frequencies_match_q():
+    rng = np.random.default_rng(5)
+    circ = W.attach_noise(W.brickwork_1d(4, 2, rng), [W.depolarizing_kraus(0.2)])
+    k, logq = pts.presample(circ, 4000, seed=123)
+    counts = np.bincount(k.reshape(-1), minlength=4)
+    n = k.size
+    exp = n * np.array([0.8, 0.2 / 3, 0.2 / 3, 0.2 / 3])
+    chi2 = float(np.sum((counts - exp) ** 2 / exp))
+    assert chi2 < 16.3            # chi2(3) at p = 1e-3
+    q = pts.kraus_probs(circ.channels[0].kraus)
+    np.testing.assert_allclose(logq, np.log(q)[k].sum(axis=1), rtol=1e-13)
+
+
+def test_presample_counter_addressing():
+    """Draws depend only on (seed, site, trajectory): a subset reproduces."""
+    circ = W.config_c1()["circuit"]
+    k_all, _ = pts.presample(circ, 16, seed=99)
+    k_few, _ = pts.presample(circ, 4, seed=99)
+    assert np.array_equal(k_all[:4], k_few)
+    k_other, _ = pts.presample(circ, 4, seed=100)
+    assert not np.array_equal(k_other, k_few)
+
+
+def test_dedup_first_occurrence():
+    k = np.array([[0, 1], [0, 0], [0, 1], [2, 0], [0, 0]], dtype=np.uint8)
+    lq = np.arange(5, dtype=float)
+    ku, lu, mult, first = pts.dedup(k, lq)
+    assert first.tolist() == [0, 1, 3]
+    assert mult.tolist() == [2, 2, 1]
+    assert np.array_equal(ku, k[[0, 1, 3]])
+
+
+# ---------------------------------------------------------- state vector ----
+
+def _full_operator(n, qubits, m):
+    """Brute force: the 2^n x 2^n matrix of a gate, built element by element."""
+    d = 1 << n
+    out = np.zeros((d, d), dtype=np.complex128)
+    for col in range(d):
+        for row in range(d):
+            rest_ok = all(((row >> q) & 1) == ((col >> q) & 1) for q in range(n) if q not in qubits)
+            if not rest_ok:
+                continue
+            if len(qubits) == 1:
+                q = qubits[0]
+                out[row, col] = m[(row >> q) & 1, (col >> q) & 1]
+            else:
+                a, b = qubits
+                r = (((row >> a) & 1) << 1) | ((row >> b) & 1)
+                c = (((col >> a) & 1) << 1) | ((col >> b) & 1)
+                out[row, col] = m[r, c]
+    return out
+
+
+@pytest.mark.parametrize("qubits", [(0,), (2,), (0, 1), (1, 0), (3, 1), (0, 3)])
+def test_apply_gate_brute_force(qubits):
+    n = 4
+    rng = np.random.default_rng(7)
+    d = 1 << len(qubits)
+    m = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    got = sv.apply_gate(psi, n, qubits, m)
+    np.testing.assert_allclose(got, _full_operator(n, qubits, m) @ psi, atol=1e-12)
+
+
+def test_bell_state_distribution():
+    h = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    circ = W.Circuit(2, [W.Gate((0,), h.astype(complex)), W.Gate((1,), h.astype(complex)),
+                         W.Gate((0, 1), W.CZ.copy()), W.Gate((1,), h.astype(complex))])
+    p = np.abs(sv.pure_state(circ)) ** 2
+    np.testing.assert_allclose(p, [0.5, 0, 0, 0.5], atol=1e-15)   # H(0) then CNOT(0->1)
+
+
+def test_hadamard_layer_uniform_marginals():
+    h = np.array([[1, 1], [1, -1]], dtype=complex) / np.sqrt(2)
+    n = 6
+    circ = W.Circuit(n, [W.Gate((q,), h) for q in range(n)])
+    p = np.abs(sv.pure_state(circ)) ** 2
+    for start, b in [(0, 4), (4, 2)]:
+        m = sv.block_marginals(p, n, start, b)
+        np.testing.assert_allclose(m, np.full(m.shape, 1.0 / (1 << n) * (1 << (n - start - b))), atol=1e-15)
+
+
+def test_zero_noise_is_pure_circuit():
+    rng = np.random.default_rng(11)
+    circ = W.attach_noise(W.brickwork_1d(6, 4, rng),
+                          [W.depolarizing_kraus(0.0), W.amplitude_damping_kraus(0.0)])
+    k, logq = pts.presample(circ, 3, seed=5)
+    assert np.all(k == 0) and np.all(logq == 0.0)
+    np.testing.assert_allclose(sv.trajectory_state(circ, k[0]), sv.pure_state(circ), atol=1e-14)
+
+
+def test_depolarizing_trajectories_unit_norm():
+    circ = W.config_c1()["circuit"]
+    k, _ = pts.presample(circ, 4, seed=7)
+    for i in range(4):
+        assert abs(np.linalg.norm(sv.trajectory_state(circ, k[i])) - 1) < 1e-12
+
+
+def test_trajectory_average_converges_to_density_matrix():
+    """mean_i |psi_i><psi_i| -> rho at rate O(1/sqrt(E)) (unbiased estimator)."""
+    rng = np.random.default_rng(13)
+    circ = W.attach_noise(W.brickwork_1d(3, 3, rng),
+                          [W.depolarizing_kraus(0.15), W.amplitude_damping_kraus(0.3)])
+    rho = densmat.density_matrix(circ)
+    assert abs(np.trace(rho) - 1) < 1e-12
+    errs = []
+    for e in (250, 4000):
+        k, _ = pts.presample(circ, e, seed=77)
+        acc = np.zeros_like(rho)
+        for i in range(e):
+            psi = sv.trajectory_state(circ, k[i])
+            acc += np.outer(psi, psi.conj())
+        errs.append(np.linalg.norm(acc / e - rho))
+    assert errs[1] < 3.0 / math.sqrt(4000)
+    assert errs[1] < errs[0]
+
+
+def test_dropped_kraus_scale_breaks_convergence():
+    """Planted mistake: inserting K_k without the 1/sqrt(q_k) factor biases the
+    average away from rho, which the convergence pin detects."""
+    rng = np.random.default_rng(13)
+    circ = W.attach_noise(W.brickwork_1d(3, 3, rng), [W.depolarizing_kraus(0.15)])
+    rho = densmat.density_matrix(circ)
+    k, _ = pts.presample(circ, 2000, seed=77)
+    acc = np.zeros_like(rho)
+    for i in range(2000):
+        psi = np.zeros(8, complex); psi[0] = 1
+        for l, g in enumerate(circ.gates):
+            m = g.matrix
+            for s, site in enumerate(circ.sites):
+                if site.gate == l:
+                    kk = circ.channels[site.channel].kraus[k[i, s]]     # unscaled
+                    m = (np.kron(kk, np.eye(2)) if g.arity == 2 and site.qubit == g.qubits[0]
+                         else np.kron(np.eye(2), kk) if g.arity == 2 else kk) @ m
+            psi = sv.apply_gate(psi, 3, g.qubits, m)
+        acc += np.outer(psi, psi.conj())
+    assert np.linalg.norm(acc / 2000 - rho) > 3 * 3.0 / math.sqrt(2000)
+
+
+def test_block_marginals_parent_child_identity():
+    circ = W.config_c1()["circuit"]
+    k, _ = pts.presample(circ, 2, seed=3)
+    psi = sv.trajectory_state(circ, k[1])
+    p = np.abs(psi) ** 2
+    m1 = sv.block_marginals(p, 12, 0, 10)      # [1, 1024]
+    m2 = sv.block_marginals(p, 12, 10, 2)      # [1024, 4]
+    np.testing.assert_allclose(m2.sum(axis=1), m1[0], rtol=1e-12, atol=1e-18)
+    assert abs(m1.sum() - np.linalg.norm(psi) ** 2) < 1e-12
+
+
+# ------------------------------------------------------------------- MPS ----
+
+def test_mps_matches_statevector():
+    cfg = W.config_c2(n_traj=4)
+    rng = np.random.default_rng(21)
+    circ = W.attach_noise(W.brickwork_1d(12, 12, rng), cfg["circuit"].channels)
+    k, _ = pts.presample(circ, 3, seed=cfg["seed"])
+    for i in range(3):
+        psi = sv.trajectory_state(circ, k[i])
+        p = np.abs(psi) ** 2
+        m = mps.trajectory_mps(circ, k[i])
+        for start, b in [(0, 4), (4, 4), (8, 4)]:
+            ref = sv.block_marginals(p, 12, start, b)
+            for prefix in (0, 5, (1 << start) - 1):
+                if prefix >= (1 << start) and start > 0:
+                    continue
+                got = m.block_marginal(start, b, prefix if start else 0)
+                np.testing.assert_allclose(got, ref[prefix if start else 0], rtol=1e-10, atol=1e-15)
+
+
+# -------------------------------------------------------------- sampling ----
+
+def test_quantise_is_exact_integer_cdf():
+    rows = W.synthetic_marginals(20, 10, seed=4)
+    for r in rows:
+        P, C = sampling.quantise(r)
+        assert np.all(P == np.floor(P)) and C[-1] <= 2.0**52
+        assert C[-1] == float(sum(int(x) for x in P))
+        assert np.all((P == 0) == (r <= 0))   # scale keeps every nonzero entry
+
+
+def test_inverse_cdf_never_picks_zero_bins_and_matches_law():
+    p = np.array([0.0, 1.0, 0.0, 2.0, 5.0, 0.0, 0.0, 2.0])
+    _, C = sampling.quantise(p)
+    a = sampling.draw_words(np.arange(200000, dtype=np.uint64), np.uint64(0), 77, seed=1)
+    x = sampling.inverse_cdf(C, a)
+    cnt = np.bincount(x, minlength=8)
+    assert cnt[[0, 2, 5, 6]].sum() == 0
+    exp = 200000 * p / p.sum()
+    nz = exp > 0
+    assert float(np.sum((cnt[nz] - exp[nz]) ** 2 / exp[nz])) < 16.3
+
+
+def test_inverse_cdf_boundaries():
+    """r = 0 picks the first positive bin; the largest word picks the last positive bin."""
+    C = np.array([0.0, 3.0, 3.0, 10.0])
+    a = np.array([0, 2**64 - 1], dtype=np.uint64)
+    assert sampling.inverse_cdf(C, a).tolist() == [1, 3]
+
+
+def test_single_block_is_plain_sampling():
+    """One block covering all qubits reduces NBS to plain sampling of |psi|^2."""
+    rng = np.random.default_rng(31)
+    circ = W.attach_noise(W.brickwork_1d(5, 4, rng), [W.depolarizing_kraus(0.05)])
+    k, _ = pts.presample(circ, 2, seed=9)
+    probs = [np.abs(sv.trajectory_state(circ, k[i])) ** 2 for i in range(2)]
+
+    def marg(j, traj, prefix):
+        return np.stack([probs[t] for t in traj])
+
+    traj, bits, cnt, levels, m = sampling.nbs_proportional(marg, [(0, 5)], seed=3, n_traj=2,
+                                                           shots=[50000, 50000])
+    for t in range(2):
+        h = np.zeros(32)
+        h[bits[traj == t].astype(int)] = cnt[traj == t]
+        exp = 50000 * probs[t] / probs[t].sum()
+        nz = exp > 5
+        assert float(np.sum((h[nz] - exp[nz]) ** 2 / exp[nz])) < 2 * nz.sum() + 30
+
+
+def test_nbs_law_equals_joint_distribution():
+    """Block-by-block conditional sampling draws from the joint |psi|^2 law, and
+    carries every shot (sum of counts = m_i) in canonical order."""
+    rng = np.random.default_rng(41)
+    circ = W.attach_noise(W.brickwork_1d(6, 5, rng), [W.depolarizing_kraus(0.05)])
+    k, _ = pts.presample(circ, 3, seed=2)
+    probs = [np.abs(sv.trajectory_state(circ, k[i])) ** 2 for i in range(3)]
+    blocks = [(0, 2), (2, 3), (5, 1)]
+
+    def marg(j, traj, prefix):
+        start, b = blocks[j]
+        return np.stack([sv.block_marginals(probs[t], 6, start, b)[int(s)]
+                         for t, s in zip(traj, prefix)])
+
+    shots = [40000, 1, 30000]
+    traj, bits, cnt, levels, m = sampling.nbs_proportional(marg, blocks, seed=5, n_traj=3,
+                                                           shots=shots)
+    for t in range(3):
+        assert cnt[traj == t].sum() == shots[t]
+    keys = list(zip(traj.tolist(), bits.tolist()))
+    assert len(set(keys)) == len(keys)
+    # canonical: per trajectory, sorted by (x1, x2, x3) with block 1 most significant
+    def lex(bt):
+        return tuple(((bt >> s) & ((1 << b) - 1)) for s, b in blocks)
+    for t in range(3):
+        bt = bits[traj == t].tolist()
+        assert bt == sorted(bt, key=lex)
+    for t in (0, 2):
+        h = np.zeros(64)
+        h[bits[traj == t].astype(int)] = cnt[traj == t]
+        exp = shots[t] * probs[t] / probs[t].sum()
+        nz = exp > 5
+        assert float(np.sum((h[nz] - exp[nz]) ** 2 / exp[nz])) < 2 * nz.sum() + 30
+
+
+def test_allocation_sums_and_proportionality():
+    w = np.array([1.0, 3.0, 0.0, 6.0])
+    m = sampling.allocate_shots(w, 100000, seed=8)
+    assert m.sum() == 100000 and m[2] == 0
+    exp = 100000 * w / w.sum()
+    nz = exp > 0
+    assert float(np.sum((m[nz] - exp[nz]) ** 2 / exp[nz])) < 13.8
+
+
+def test_rank_offsets():
+    assert sampling.rank_offsets([0, 0, 1, 1, 1], [3, 2, 1, 4, 2]).tolist() == [0, 3, 0, 1, 5]

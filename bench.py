@@ -1,0 +1,320 @@
+"""Benchmark: noisy-circuit shots/s of the tensor-network PTSBE hot path on GB300.
+
+Workload (one "step"): the 30-qubit 1D brickwork circuit of depth 12 with
+depolarizing (p = 0.005) then amplitude damping (gamma = 0.002) after every
+gate; 4096 pre-sampled trajectories; 10^6 shots allocated in proportion to
+trajectory weight; sampling in blocks of 10 qubits through conditional
+marginals over the distinct prefixes.  A step = pre-sampling + UPV merge +
+batched contraction + NBS sampling of all blocks (path planning is done once,
+outside the timed region, as the paper's throughput definition excludes it).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank runs the full workload on its own
+trajectory seeds (weak scaling, no collective on the data path); value is the
+shots of all ranks over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "noisy-circuit shots/sec on 1 GB300, batched vs plain path, at stated error vs FP64"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        rows = [r for r in rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def c2_config():
+    return W.config_c2()
+
+
+# ----------------------------------------------------------- CPU oracle ----
+
+def oracle_sample_run(cfg, n_traj_sample, shots_per_traj, seed_offset=0):
+    """The oracle's pipeline (exact MPS contraction + NBS replay) for a bounded
+    sample of trajectories of the workload; returns (shots, seconds)."""
+    from oracle import mps, pts, sampling
+    circ = cfg["circuit"]
+    blocks = []
+    s = 0
+    for b in cfg["block_sizes"]:
+        blocks.append((s, b))
+        s += b
+    t0 = time.perf_counter()
+    kraus, _ = pts.presample(circ, n_traj_sample, cfg["seed"] + seed_offset)
+    states = [mps.trajectory_mps(circ, kraus[i]) for i in range(n_traj_sample)]
+    renv = {}
+
+    def marg(j, traj, prefix):
+        start, b = blocks[j]
+        rows = []
+        for t, p in zip(traj, prefix):
+            key = (int(t), start + b)
+            if key not in renv:
+                renv[key] = states[int(t)].right_env(start + b)
+            rows.append(states[int(t)].block_marginal(start, b, int(p), renv=renv[key]))
+        return np.array(rows)
+
+    tr, bits, cnt, levels, m = sampling.nbs_proportional(marg, blocks, cfg["seed"], n_traj_sample,
+                                                         shots=[shots_per_traj] * n_traj_sample)
+    return int(cnt.sum()), time.perf_counter() - t0
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank):
+    """--impl reference: the CPU oracle as it stands, on bounded samples."""
+    if rank != 0:
+        return
+    cfg = c2_config()
+    shots_per_traj = cfg["total_shots"] // cfg["n_traj"]
+    n_sample = 2
+    for w in range(args.warmup):
+        oracle_sample_run(cfg, 1, shots_per_traj, seed_offset=1000 + w)
+    times, shots = [], 0
+    for k in range(args.steps):
+        s, t = oracle_sample_run(cfg, n_sample, shots_per_traj, seed_offset=k)
+        times.append(t)
+        shots += s
+    value = shots / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic",
+            "config": {"workload": "c2_brickwork30_d12 (30 qubits, depth 12, dep 0.005 + AD 0.002, blocks 10/10/10)",
+                       "sample": f"{n_sample} trajectories x {shots_per_traj} shots per step"},
+            "cpu_baseline": {"value": value, "unit": "shots/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": f"{n_sample} trajectories x {shots_per_traj} shots per step, exact MPS + NBS"},
+            "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------- our arm ----
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--hypersamples", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-traj", type=int, default=64,
+                    help="trajectories timed on the plain per-trajectory path")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2604_08467_gb300 import ptn
+
+    cfg = c2_config()
+    E, M = cfg["n_traj"], cfg["total_shots"]
+    t_plan = time.perf_counter()
+    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=args.hypersamples, est_traj=E,
+                             est_shots=M)
+    t_plan = time.perf_counter() - t_plan
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def step(k):
+        tr = ptn.ptn_presample_trajectories(plan, cfg["seed"] + 7919 * (rank * 1000 + k), E)
+        res = ptn.ptn_sample_shots(plan, tr, cfg["seed"] + k, total_shots=M)
+        return tr, res
+
+    for w in range(args.warmup):
+        tr, res = step(10_000 + w)
+        del tr, res
+    torch.cuda.synchronize()
+
+    nets = None
+    times = []
+    ptn.ptn_stats_reset()
+    ptn.ptn_stats_enable(True)
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tr, res = step(k)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b) / 1e3)
+            nets = res.nets_per_block
+            del tr, res
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+    ptn.ptn_stats_enable(False)
+    stats = ptn.ptn_stats_read()
+    clocks = clk.summary()
+    t_step = float(np.mean(times))
+    if dist:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = M * world / t_step
+
+    # ---- end to end through the public API, result copied to pinned host memory
+    e2e_times = []
+    d2h = 0
+    h2d = 0
+    for k in range(max(2, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tr, res = step(100 + k)
+        t, bits, cnt = res.to_torch()
+        ht = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+        hb = torch.empty(bits.shape, dtype=bits.dtype, pin_memory=True)
+        hc = torch.empty(cnt.shape, dtype=cnt.dtype, pin_memory=True)
+        ht.copy_(t, non_blocking=True)
+        hb.copy_(bits, non_blocking=True)
+        hc.copy_(cnt, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = t.numel() * 4 + bits.numel() * 8 + cnt.numel() * 8
+        # host->device per step: the chunk index tables the runtime uploads per block
+        h2d = 8 * E + sum(4 * n for n in res.nets_per_block) + 4 * E
+        del tr, res
+    e2e = {"value": M * world / float(np.mean(e2e_times)), "unit": "shots/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h)}
+
+    # ---- plain per-trajectory path on a subset (same kernels, one trajectory per launch)
+    plain = None
+    if args.plain_traj > 0:
+        tr = ptn.ptn_presample_trajectories(plan, cfg["seed"] + 5, args.plain_traj)
+        m_pt = M // E
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ptn.ptn_sample_shots(plan, tr, cfg["seed"], shots_per_traj=m_pt, max_traj_per_chunk=1)
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - t0
+        plain = {"value": args.plain_traj * m_pt / tp, "unit": "shots/s",
+                 "sample": f"{args.plain_traj} trajectories x {m_pt} shots, one trajectory per chunk"}
+        del tr, res
+
+    # ---- roofline of the dominant kernel (from the library's per-launch events)
+    peaks, peak_src = load_peaks()
+    top = max(stats.items(), key=lambda kv: kv[1]["ms"]) if stats else (None, None)
+    roof = None
+    if top[0]:
+        s = top[1]
+        achieved = s["alg_bytes"] / (s["ms"] / 1e3) / 1e9 if s["ms"] > 0 else 0.0
+        peak = peaks["hbm_gbs"]
+        roof = {"kernel": top[0], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "launches_per_step": s["timed_launches"] / max(args.steps, 1),
+                "ms_per_step": s["ms"] / max(args.steps, 1),
+                "share_of_step": s["ms"] / 1e3 / max(sum(times), 1e-12)}
+    launches = sum(v["launches"] for v in stats.values())
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        shots, sec = oracle_sample_run(cfg, 2, M // E)
+        cpu = {"value": shots / sec, "unit": "shots/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"2 trajectories x {M // E} shots (exact MPS contraction + NBS replay, complex128)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+                "config": {"workload": "c2_brickwork30_d12: 30-qubit 1D brickwork depth 12, Haar U(2) + CZ, "
+                                       "depolarizing 0.005 + amplitude damping 0.002 after every gate, "
+                                       "4096 trajectories, 1e6 shots proportional, blocks 10/10/10",
+                           "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)",
+                           "nets_per_block": nets, "plan_seconds": t_plan,
+                           "precision": "fp32 complex (c64), fp64 CDF / log-probabilities"},
+                "e2e": e2e, "plain_path": plain, "roofline": roof, "cpu_baseline": cpu,
+                "gpu_launches": int(launches), "clocks": clocks,
+                "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items()}}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

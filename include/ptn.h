@@ -1,0 +1,298 @@
+/*
+ * ptn.h — C ABI of the GB300-native tensor-network PTSBE hot path.
+ *
+ * The method (arxiv 2604.08467) samples shots of a noisy quantum circuit by
+ *   1. pre-sampling E Kraus error sets K_i (pre-trajectory sampling, Sec. II-C),
+ *   2. merging every sampled error operator into the gate it follows, so every
+ *      error set yields a network with the structure of the error-free one and
+ *      one contraction path per qubit block serves all of them (unified path
+ *      variations, Sec. III-A, Fig. 2c),
+ *   3. contracting, block by block, one network per (trajectory, distinct
+ *      prefix of already-sampled bits) and drawing all shots that share a
+ *      prefix from its conditional marginal, carrying repeated outcomes as
+ *      counts (non-degenerate batched sampling, proportional case, Sec. III-B).
+ *
+ * Conventions used by every call:
+ *   - qubit q is bit q of a bitstring (uint64, n <= 64 qubits);
+ *   - block j covers qubits [start_j, start_j + b_j), start_0 = 0, ascending;
+ *     a block-local outcome x has bit t = qubit start_j + t;
+ *   - complex numbers are (re, im) pairs; host inputs are complex128, device
+ *     data is complex64 unless a precision mode says otherwise;
+ *   - "device" pointers are CUDA device (or managed) memory on the current
+ *     device; "host" pointers are ordinary host memory;
+ *   - every call returns a ptn_status and never aborts the process; the text
+ *     of the last error of the calling thread is available from
+ *     ptn_last_error();
+ *   - calls that take a stream enqueue their GPU work on it; the ones that
+ *     must read a size back to the host say so and synchronise that stream.
+ *
+ * Ownership: handles (ptn_plan, ptn_traj, ptn_shots) are created and owned by
+ * the library and released only by the matching *_destroy call.  Host input
+ * arrays are copied during the call.  Device output arrays named *_out are
+ * allocated by the caller.
+ */
+#ifndef PTN_H
+#define PTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PTN_OK = 0,
+    PTN_ERR_INVALID_ARG = 1,   /* malformed argument (sizes, indices, null pointers) */
+    PTN_ERR_NOT_CPTP = 2,      /* a channel fails sum_k K_k^dagger K_k = I to 1e-10 */
+    PTN_ERR_TOO_LARGE = 3,     /* a plan or batch exceeds the memory cap (the failures counted in Sec. IV-D) */
+    PTN_ERR_OOM = 4,           /* device or host allocation failed */
+    PTN_ERR_CUDA = 5,          /* a CUDA runtime call failed (message has the CUDA error) */
+    PTN_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+    PTN_ERR_UNSUPPORTED = 7    /* option or shape not supported by this build */
+} ptn_status;
+
+typedef struct ptn_plan ptn_plan;
+typedef struct ptn_traj ptn_traj;
+typedef struct ptn_shots ptn_shots;
+typedef void* ptn_stream;      /* a cudaStream_t; NULL is the legacy default stream */
+
+/* ---------------------------------------------------------------- inputs -- */
+
+enum { PTN_PARAM_NONE = 0, PTN_PARAM_RY = 1, PTN_PARAM_RZ = 2 };
+
+/* One coherent gate d_l (Sec. II-B: the deterministic gates D = {d_l}).
+ * 1-qubit: mat[0..7] holds M[out][in] row-major as (re, im) pairs.
+ * 2-qubit on (q0, q1): mat[0..31] holds the 4x4 matrix
+ *   M[(o0 << 1) | o1][(i0 << 1) | i1], q0 being the high bit.
+ * param_kind marks RY(angle) = exp(-i angle Y / 2) / RZ(angle) =
+ * exp(-i angle Z / 2) gates whose angle theta[param_index] is differentiated
+ * by ptn_expval_grad; mat must hold the gate at its current angle. */
+typedef struct {
+    int32_t arity;
+    int32_t q0, q1;
+    int32_t param_kind;
+    int32_t param_index;
+    int32_t reserved;
+    double  mat[32];
+} ptn_gate;
+
+typedef struct {
+    int32_t n_qubits;          /* 1 .. 64 */
+    int32_t n_gates;
+    const ptn_gate* gates;     /* host, n_gates entries, in circuit order */
+} ptn_circuit;
+
+/* A single-qubit noise channel given by its Kraus operators (Sec. II-A).
+ * kraus holds n_kraus 2x2 complex128 matrices K[out][in], row-major (re, im). */
+typedef struct {
+    int32_t n_kraus;           /* 1 .. 16 */
+    const double* kraus;       /* host, n_kraus * 8 doubles */
+} ptn_channel;
+
+/* A noise site: channel `channel` acts on qubit `qubit` right after gate `gate`
+ * (the paper couples channels to every coherent gate, Sec. IV-B).  Sites are
+ * listed in application order: grouped by gate in circuit order; within a
+ * gate, the sites of one qubit act in list order.  Site s is column s of the
+ * Kraus-index matrix. */
+typedef struct {
+    int32_t gate;
+    int32_t qubit;             /* must be one of the gate's qubits */
+    int32_t channel;
+} ptn_site;
+
+typedef struct {
+    int32_t n_channels;
+    const ptn_channel* channels;
+    int32_t n_sites;
+    const ptn_site* sites;
+} ptn_noise;
+
+/* Path-planner options (Sec. III-A: one path set P^j found once for the
+ * error-free network; Sec. IV-C: 100 hypersamples by default). */
+typedef struct {
+    int32_t  hypersamples;     /* randomised greedy restarts; 0 -> 100 */
+    int32_t  split_gates;      /* 1: split 2-qubit gates by operator-Schmidt decomposition
+                                  (bond padded to a power of two); 0: keep 4-leg tensors */
+    uint64_t seed;             /* planner randomness */
+    double   est_traj;         /* expected trajectories E for the cost model; 0 -> 1024 */
+    double   est_shots;        /* expected shots for the cost model (bounds the number of
+                                  distinct prefixes per block); 0 -> 1e6 */
+    double   mem_cap_bytes;    /* device memory one execution chunk may use; 0 -> 40% of
+                                  the device's free memory at first use */
+} ptn_plan_opts;
+
+/* ------------------------------------------------------------- planning -- */
+
+/* Build the plan: validates the channels (PTN_ERR_NOT_CPTP), builds the UPV
+ * variant tables (every merged gate (N_a (x) N_b) d_l for every combination of
+ * Kraus choices of its sites, N_q = product of K_k / sqrt(q_k), q_k =
+ * Tr(K_k^dagger K_k) / 2), the double-layer marginal network of every block
+ * (prefix qubits projected, block qubits open, later qubits traced), and one
+ * contraction path per block (Sec. III-A), lowered to a list of batched
+ * pairwise contractions.  Host only: needs no GPU (device tables are uploaded
+ * on first use).  block_sizes may be NULL (then b = 10 blocks, the last one
+ * taking the remainder); otherwise they must be >= 1, <= 24 and sum to
+ * n_qubits. */
+ptn_status ptn_plan_path(const ptn_circuit* circuit, const ptn_noise* noise,
+                         const int32_t* block_sizes, int32_t n_blocks,
+                         const ptn_plan_opts* opts, ptn_plan** plan_out);
+
+/* JSON description of the plan: per block the number of steps by storage
+ * class, arena sizes and modelled work.  detail = 1 adds every lowered step
+ * (operand descriptors, stride tables), the block roots, the variant-selecting
+ * sites of every merged-gate leaf and the complex64 variant table, so the
+ * lowering can be inspected or replayed on the host.  Writes at most cap bytes
+ * (NUL-terminated) to buf and the full length to *len (host). */
+ptn_status ptn_plan_describe(const ptn_plan* plan, int32_t detail, char* buf, size_t cap, size_t* len);
+
+void ptn_plan_destroy(ptn_plan* plan);
+
+/* --------------------------------------------------------- pre-sampling -- */
+
+/* Draw E Kraus error sets on the GPU (pre-trajectory sampling, Sec. II-C).
+ * Site s of trajectory i takes the Philox4x32-10 counter
+ * (s, 0, i, (1 << 24) | (circuit_id << 8)) with key (seed_lo, seed_hi); u =
+ * ((x0 << 32 | x1) >> 11) * 2^-53; the Kraus index is the smallest k with
+ * u < C_s[k], C_s the running sum of q_{s,.} (last entry 1.0).  log q_i, the
+ * sum over sites in site order of log q_{s,k}, is kept in FP64.
+ * dedup != 0 merges identical error sets (first-occurrence order) and keeps
+ * their multiplicities; this synchronises the stream once to read the number
+ * of distinct sets.  Also computes, per trajectory, the variant index of every
+ * merged tensor (the UPV merge as a table gather).  n_traj in 1 .. 2^24. */
+ptn_status ptn_presample_trajectories(const ptn_plan* plan, uint64_t seed, int32_t circuit_id,
+                                      int64_t n_traj, int32_t dedup, ptn_traj** traj_out,
+                                      ptn_stream stream);
+
+/* Device views of a ptn_traj (valid until ptn_traj_destroy): kraus [n][S]
+ * uint8 row-major, logq [n] double, mult [n] int64 (1 without dedup), first
+ * [n] int64 (index of the error set in the original draw order). */
+ptn_status ptn_traj_info(const ptn_traj* traj, int64_t* n_unique, int32_t* n_sites,
+                         const uint8_t** kraus, const double** logq,
+                         const int64_t** mult, const int64_t** first);
+
+/* Copy the trajectory set into caller-allocated device arrays of n_unique
+ * (x n_sites for kraus) entries; any pointer may be NULL. */
+ptn_status ptn_traj_copy(const ptn_traj* traj, uint8_t* kraus_out, double* logq_out, int64_t* mult_out,
+                         int64_t* first_out, ptn_stream stream);
+
+void ptn_traj_destroy(ptn_traj* traj);
+
+/* ---------------------------------------------------------- contraction -- */
+
+enum { PTN_PREC_FP32 = 0, PTN_PREC_BF16X3 = 1, PTN_PREC_FP16X3 = 2 };
+
+/* Contract n_net block-`block` networks with the block's shared path
+ * (Sec. III-A) and write their unnormalised marginals (Sec. II-B):
+ *   marg_out[n][x] = <psi_i| P_s (x) |x><x| (x) I |psi_i>,  i = net_traj[n],
+ *   s = the bits of net_prefix[n] below start_block (higher bits ignored),
+ *   Z_out[n] = sum_x marg_out[n][x] accumulated in FP64.
+ * net_traj (device int32, indices into the ptn_traj's distinct error sets) must
+ * be non-decreasing.  marg_out: device float [n_net][2^b_block]; Z_out: device
+ * double [n_net].  Copies net_traj to the host (one synchronisation) to split
+ * the batch into chunks that fit the memory cap. */
+ptn_status ptn_contract_batch(const ptn_plan* plan, const ptn_traj* traj, int32_t block,
+                              const int32_t* net_traj, const uint64_t* net_prefix, int64_t n_net,
+                              int32_t precision, float* marg_out, double* Z_out,
+                              ptn_stream stream);
+
+/* ------------------------------------------------------------- sampling -- */
+
+/* One block of proportional NBS (Sec. III-B) for n_parent networks whose
+ * marginals are given: parent n (trajectory parent_traj[n], prefix bits
+ * parent_prefix[n], count parent_count[n] >= 0) draws its count shots from row
+ * n of marg (device float [n_parent][2^b]) with the exact-integer FP64 CDF:
+ * P_x = rint(max(p_x, 0) * 2^sigma), sigma = 52 - b - e, max p = f 2^e with f
+ * in [0.5, 1); shot rank r (the ranks of a parent continue the ranks of the
+ * trajectory's earlier parents) uses the Philox4x32-10 counter
+ * (r_lo, r_hi, traj, (3 << 24) | (circuit_id << 8) | block), a = x0 << 32 | x1,
+ * and picks the smallest x with floor(a T / 2^64) < C[x].  The distinct
+ * outcomes are written, in canonical order (parents in order, x ascending), as
+ * children (traj, prefix | x << start, count) to the device arrays child_*
+ * (capacity child_cap >= sum_n min(count_n, 2^b)).  Parents must be grouped by
+ * trajectory.  Writes the number of children to *n_child (host); synchronises
+ * the stream. */
+ptn_status ptn_sample_block(const float* marg, int32_t b, int32_t start,
+                            const int32_t* parent_traj, const uint64_t* parent_prefix,
+                            const int64_t* parent_count, int64_t n_parent,
+                            uint64_t seed, int32_t circuit_id, int32_t block,
+                            int32_t* child_traj, uint64_t* child_prefix, int64_t* child_count,
+                            int64_t child_cap, int64_t* n_child, ptn_stream stream);
+
+/* Proportional shot allocation (Sec. II-C "shots m_i assigned by the rule"):
+ * one multinomial draw of `total` shots over the device weights w[n] (FP64,
+ * >= 0, not all zero), quantised like the marginals (b = ceil(log2 n)); shot t
+ * uses the counter (t_lo, t_hi, 0, (2 << 24) | (circuit_id << 8)).  Writes
+ * m_out (device int64 [n]). */
+ptn_status ptn_allocate_shots(const double* weights, int64_t n, int64_t total, uint64_t seed,
+                              int32_t circuit_id, int64_t* m_out, ptn_stream stream);
+
+enum { PTN_PROPORTIONAL_FIXED = 0, PTN_PROPORTIONAL_TOTAL = 1 };
+
+typedef struct {
+    int32_t  mode;               /* PTN_PROPORTIONAL_FIXED or PTN_PROPORTIONAL_TOTAL */
+    int32_t  circuit_id;         /* goes into every Philox counter */
+    int64_t  shots_per_traj;     /* FIXED: m_i = shots_per_traj * multiplicity_i */
+    int64_t  total_shots;        /* TOTAL: M allocated over a_i = mult_i * w_i, w_i = Z of block 1 */
+    uint64_t seed;               /* Philox key for allocation and sampling */
+    int32_t  precision;          /* PTN_PREC_* */
+    int32_t  max_traj_per_chunk; /* 0: as many as the memory cap allows; 1: the plain
+                                    per-trajectory path (one trajectory per launch) */
+    int32_t  use_graphs;         /* capture each chunk's step list in a CUDA graph */
+    int32_t  reserved;
+} ptn_sample_opts;
+
+/* Full proportional NBS over all blocks (Sec. III-B): block 1 contracts one
+ * network per distinct error set; every later block contracts one network per
+ * distinct (trajectory, prefix) and draws all its shots from it.  The final
+ * (trajectory, bitstring, count) list is in canonical order (trajectories in
+ * order, then bitstrings lexicographic by block outcome, block 1 most
+ * significant).  Synchronises the stream once per block to size the next
+ * level. */
+ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const ptn_sample_opts* opts,
+                            ptn_shots** shots_out, ptn_stream stream);
+
+/* Device views of the result (valid until ptn_shots_destroy) and, per block,
+ * the number of networks contracted (host array of n_blocks, may be NULL). */
+ptn_status ptn_shots_info(const ptn_shots* shots, int64_t* n_out, const int32_t** traj,
+                          const uint64_t** bits, const int64_t** count,
+                          int64_t* nets_per_block, int32_t cap_blocks);
+
+/* Copy the result into caller-allocated device arrays of n_out entries. */
+ptn_status ptn_shots_copy(const ptn_shots* shots, int32_t* traj_out, uint64_t* bits_out, int64_t* count_out,
+                          ptn_stream stream);
+
+void ptn_shots_destroy(ptn_shots* shots);
+
+/* ----------------------------------------------------------- statistics -- */
+
+/* Per-kernel launch statistics (instrumentation for roofline reporting).
+ * Launch counts are always kept.  While timing is enabled every launch of the
+ * library's kernels is bracketed by CUDA events on its stream and charged its
+ * algorithmic bytes (distinct operand elements read + output written) and
+ * flops (8 per complex multiply-add).  ptn_stats_read synchronises the device,
+ * resolves the events and fills up to cap records; ptn_stats_reset clears. */
+typedef struct {
+    char    name[32];
+    int64_t launches;
+    int64_t timed_launches;
+    double  ms;             /* summed event time of the timed launches */
+    double  alg_bytes;      /* summed algorithmic bytes of the timed launches */
+    double  alg_flops;
+} ptn_kernel_stat;
+
+ptn_status ptn_stats_enable(int32_t timing_on);
+ptn_status ptn_stats_reset(void);
+ptn_status ptn_stats_read(ptn_kernel_stat* out, int32_t cap, int32_t* n_out);
+
+/* ------------------------------------------------------------- utilities -- */
+
+const char* ptn_status_string(ptn_status status);
+const char* ptn_last_error(void);
+const char* ptn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTN_H */

@@ -21,6 +21,9 @@ Conventions (readings of points the paper leaves open, listed in the design doc):
   (r_lo, r_hi, i, tag(SAMPLE, circuit, j)); the c shots of a parent take the
   ranks R .. R+c-1, R the sum of the counts of the trajectory's earlier
   parents in canonical order;
+* a network whose marginal row is all zero (a zero-norm trajectory, possible
+  with non-unitary Kraus operators) has zero probability; its shots cannot be
+  drawn and are dropped, as proportional allocation gives it none;
 * canonical order: trajectories in their listed order, then prefixes
   lexicographic by (x_1, x_2, ...), block 1 most significant; a child's bits
   are prefix | (x << start_j);
@@ -78,8 +81,8 @@ def sample_block(p_rows, traj, counts, rank0, seed, block, circuit=0):
     out_parent, out_x, out_c = [], [], []
     for n in range(len(counts)):
         c = int(counts[n])
-        if c == 0:
-            continue
+        if c == 0 or not np.any(np.asarray(p_rows[n]) > 0):
+            continue        # no shots, or a zero-norm network whose shots cannot be drawn
         _, C = quantise(p_rows[n])
         ranks = np.arange(int(rank0[n]), int(rank0[n]) + c, dtype=np.uint64)
         a = draw_words(ranks, np.uint64(int(traj[n])), tagw, seed)
@@ -105,7 +108,10 @@ def rank_offsets(traj, counts):
 
 
 def allocate_shots(weights, total, seed, circuit=0):
-    """m_i: one multinomial draw of ``total`` shots over the trajectory weights."""
+    """m_i: one multinomial draw of ``total`` shots over the trajectory weights
+    (no shot is allocated when every weight is zero)."""
+    if not np.any(np.asarray(weights) > 0):
+        return np.zeros(len(weights), dtype=np.int64)
     _, C = quantise(weights)
     tagw = philox.tag(philox.STREAM_ALLOC, circuit, 0)
     m = np.zeros(len(weights), dtype=np.int64)

@@ -1,0 +1,99 @@
+// Device helpers and kernel launchers shared by the runtime's .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ptn_internal.h"
+
+namespace ptn {
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
+// multiplies mixed with the key, the key bumped by the Weyl constants between
+// rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint64_t word64(uint4 x) {
+    return ((uint64_t)x.x << 32) | (uint64_t)x.y;
+}
+
+// Counter word 3: (stream << 24) | (circuit << 8) | block.
+enum { STREAM_KRAUS = 1, STREAM_ALLOC = 2, STREAM_SAMPLE = 3 };
+__host__ __device__ __forceinline__ uint32_t philox_tag(int stream, int circuit, int block) {
+    return ((uint32_t)(stream & 0xFF) << 24) | ((uint32_t)(circuit & 0xFFFF) << 8) | (uint32_t)(block & 0xFF);
+}
+
+// Per-chunk execution context of a block's step list.
+struct ChunkCtx {
+    const float2* vtab;         // merged-gate variant table
+    const int32_t* var_ids;     // [traj][n_var_cols] variant of every multi-variant leaf
+    int32_t n_var_cols;
+    int32_t pad;
+    const int32_t* chunk_traj;  // local trajectory -> global (index into var_ids)
+    const int32_t* net_tl;      // network -> local trajectory
+    const uint64_t* net_prefix; // network -> prefix bits
+    float2* arena[3];           // CONST, TRAJ, NET arenas
+    int64_t arena_inst[3];      // instances of each arena in this chunk
+};
+
+// ---- launchers (kernels_contract.cu)
+void launch_contract_step(const StepDesc* d_step, const StepDesc& h_step, const ChunkCtx& ctx,
+                          int64_t n_inst, cudaStream_t s);
+void launch_finalize(const RootRef* d_root, const ChunkCtx& ctx, int b, int64_t n_net,
+                     float* marg, double* Z, cudaStream_t s);
+
+// ---- launchers (kernels_sample.cu)
+void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, uint64_t seed,
+                      int32_t circuit, uint8_t* kraus, double* logq, cudaStream_t s);
+void launch_row_hash(const uint8_t* kraus, int64_t n, int32_t S, uint64_t* h, cudaStream_t s);
+void launch_first_occurrence(const uint8_t* kraus, const uint64_t* h, int64_t n, int32_t S,
+                             int64_t* first, cudaStream_t s);
+void launch_dedup_compact(const uint8_t* kraus, const double* logq, const int64_t* first,
+                          const int64_t* uid, int64_t n, int32_t S, uint8_t* kraus_u,
+                          double* logq_u, int64_t* mult_u, int64_t* first_u, cudaStream_t s);
+void launch_var_ids(const uint8_t* kraus, int64_t n, int32_t S, const int32_t* ptr,
+                    const int32_t* idx, const int32_t* mul, int32_t n_cols, int32_t* var_ids,
+                    cudaStream_t s);
+void launch_flags_first(const int64_t* first, int64_t n, int64_t* flags, cudaStream_t s);
+// exclusive prefix sum of int64 (in may equal out); tmp must hold scan_tmp_elems(n) int64
+int64_t scan_tmp_elems(int64_t n);
+void launch_exclusive_scan(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
+void launch_alloc_shots(const double* w, int64_t n, int64_t total, uint64_t seed, int32_t circuit,
+                        double* cdf_tmp, int64_t* m, cudaStream_t s);
+void launch_mult_times_z(const int64_t* mult, const double* Z, int64_t n, double* w, cudaStream_t s);
+void launch_fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s);
+void launch_iota_i32(int32_t* p, int64_t n, cudaStream_t s);
+void launch_scale_i64(const int64_t* a, int64_t k, int64_t n, int64_t* out, cudaStream_t s);
+
+struct SampleScratch {
+    int64_t* cap;        // [n_parent] min(count, 2^b)
+    int64_t* tmp_off;    // [n_parent]
+    int64_t* rank0;      // [n_parent]
+    int64_t* excl;       // [n_parent]
+    int64_t* first;      // [n_traj_max]
+    int64_t* ndist;      // [n_parent]
+    int64_t* out_off;    // [n_parent]
+    int32_t* tmp_x;      // [cap total]
+    int64_t* tmp_c;      // [cap total]
+    int64_t* scan_tmp;
+};
+// NBS sampling of one block; returns the number of children (synchronises).
+int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptraj,
+                         const uint64_t* pprefix, const int64_t* pcount, int64_t n_parent,
+                         int64_t n_traj_max, uint64_t seed, int circuit, int block,
+                         int32_t* ctraj, uint64_t* cprefix, int64_t* ccount, int64_t child_cap,
+                         const SampleScratch& sc, int64_t* host_tmp, cudaStream_t s, ptn_status* st);
+
+}  // namespace ptn

@@ -1,0 +1,1177 @@
+// Host planner: unified-path-variation networks, one contraction path per
+// qubit block, lowered to batched pairwise contraction steps.
+//
+// Paper, Sec. III-A (UPV): every sampled error operator is merged into the
+// gate it follows, so all error sets share the error-free network's structure
+// and one path set P^j (one path per qubit block B_j) serves every error set
+// and every shot.  Here the merge is precomputed for every combination of
+// Kraus choices of a gate's sites ("variants"); executing a trajectory's
+// network then only selects variants.
+//
+// Paper, Sec. II-B / III-B: the network of block j measures the block's qubits
+// (open outputs), projects the earlier qubits onto the sampled prefix and
+// traces the later ones.  It is built as a double layer <psi| . |psi>: the bra
+// layer is the mirror image of the ket layer with conjugated tensors.
+//
+// Paper, Sec. IV-C: paths come from a randomised search with 100
+// hypersamples.  The search here is a randomised greedy over pairwise
+// contractions whose objective counts every step's work times the number of
+// copies the batch needs: once per trajectory for tensors built from gates
+// only, once per network (trajectory, prefix) for tensors that depend on
+// projected prefix bits.  Projected bits are carried as open "slice" indices
+// until a slice move fixes them from each network's prefix, so work shared by
+// all prefixes of a trajectory is done once per trajectory.  Work on the ket
+// layer is mirrored on the bra layer for free (its result is the complex
+// conjugate), so mirrored pairs are contracted in lockstep.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <array>
+#include <functional>
+#include <queue>
+#include <random>
+#include <unordered_map>
+
+#include "ptn_internal.h"
+
+namespace ptn {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ errors --
+static thread_local std::string g_last_error;
+
+ptn_status set_error(ptn_status s, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+const char* last_error_text() { return g_last_error.c_str(); }
+void clear_error() { g_last_error.clear(); }
+
+// --------------------------------------------------- small linear algebra --
+using M2 = std::array<cd, 4>;    // row-major 2x2
+using M4 = std::array<cd, 16>;   // row-major 4x4
+
+static M2 mul2(const M2& a, const M2& b) {
+    M2 r;
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++) r[i * 2 + j] = a[i * 2] * b[j] + a[i * 2 + 1] * b[2 + j];
+    return r;
+}
+static M2 eye2() { return M2{cd(1), cd(0), cd(0), cd(1)}; }
+
+// q_k = Tr(K^dagger K) / 2 with the entries summed as re*re + im*im in
+// row-major order (a fixed order so every implementation gets the same bits).
+static double kraus_prob(const double* k) {
+    double acc = 0.0;
+    for (int e = 0; e < 4; e++) {
+        double re = k[2 * e], im = k[2 * e + 1];
+        double sq = re * re;
+        sq = sq + im * im;
+        acc = acc + sq;
+    }
+    return acc / 2.0;
+}
+
+// One-sided (Hestenes) Jacobi SVD of a complex 4x4 matrix X = sum_r u_r s_r v_r^H.
+// Returns singular values (descending) with X*V columns and V.
+static void svd4(const M4& x_in, double s[4], cd xv[4][4], cd v[4][4]) {
+    cd x[4][4];
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            x[i][j] = x_in[i * 4 + j];
+            v[i][j] = (i == j) ? cd(1) : cd(0);
+        }
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < 3; p++)
+            for (int q = p + 1; q < 4; q++) {
+                double a = 0, b = 0;
+                cd g = 0;
+                for (int i = 0; i < 4; i++) {
+                    a += std::norm(x[i][p]);
+                    b += std::norm(x[i][q]);
+                    g += std::conj(x[i][p]) * x[i][q];
+                }
+                double ag = std::abs(g);
+                if (ag <= 1e-300 || ag <= 1e-16 * std::sqrt(a * b)) continue;
+                off = std::max(off, ag / std::sqrt(a * b + 1e-300));
+                cd ph = g / ag;   // rotate column q by conj(phase) to make <p,q> real
+                double zeta = (b - a) / (2.0 * ag);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                for (int i = 0; i < 4; i++) {
+                    cd xp = x[i][p], xq = x[i][q] * std::conj(ph);
+                    x[i][p] = c * xp - sn * xq;
+                    x[i][q] = sn * xp + c * xq;
+                    cd vp = v[i][p], vq = v[i][q] * std::conj(ph);
+                    v[i][p] = c * vp - sn * vq;
+                    v[i][q] = sn * vp + c * vq;
+                }
+            }
+        if (off < 1e-15) break;
+    }
+    int order[4] = {0, 1, 2, 3};
+    double nrm[4];
+    for (int j = 0; j < 4; j++) {
+        double a = 0;
+        for (int i = 0; i < 4; i++) a += std::norm(x[i][j]);
+        nrm[j] = std::sqrt(a);
+    }
+    std::sort(order, order + 4, [&](int a, int b) { return nrm[a] > nrm[b]; });
+    cd x2[4][4], v2[4][4];
+    for (int j = 0; j < 4; j++) {
+        s[j] = nrm[order[j]];
+        for (int i = 0; i < 4; i++) {
+            x2[i][j] = x[i][order[j]];
+            v2[i][j] = v[i][order[j]];
+        }
+    }
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            xv[i][j] = x2[i][j];
+            v[i][j] = v2[i][j];
+        }
+}
+
+// ------------------------------------------------------------- leaf roles --
+enum Role : int32_t { R_IN_A = 0, R_OUT_A = 1, R_IN_B = 2, R_OUT_B = 3, R_BOND = 4 };
+
+// --------------------------------------------------------------- network --
+enum IdxKind : int32_t { IX_INT = 0, IX_OPEN = 1, IX_TRACED = 2, IX_SLICE = 3 };
+
+struct NetIdx {
+    int32_t kind;
+    int32_t qubit;     // end indices and slices
+    int32_t mirror;    // id on the other layer (itself for open / traced)
+};
+
+struct BlockNet {
+    std::vector<NetIdx> idx;
+    std::vector<std::vector<int32_t>> tidx;   // per tensor: index ids in leaf storage order
+    std::vector<int32_t> tleaf;               // per tensor: leaf id
+    std::vector<int32_t> tbra;                // per tensor: 1 for the bra layer
+    std::vector<int32_t> tcls;
+    int32_t n_leaf_tensors = 0;               // ket tensors; bra tensor i + n is the mirror of i
+};
+
+// ------------------------------------------------------------ path search --
+struct GT {
+    std::vector<int32_t> idx;   // sorted index ids
+    int32_t cls;
+    int32_t side;               // 0 ket, 1 bra, 2 mixed
+    int32_t mirror;             // live mirror partner or -1
+    int32_t nslice;
+    bool alive;
+};
+
+enum MoveType : int32_t { MV_CONTRACT = 0, MV_SLICE = 1 };
+struct Move {
+    int32_t type;
+    int32_t a, b, c;            // operands and result (b = -1 for a slice)
+    int32_t ma, mb, mc;         // lockstep mirror operands / result, -1 if none
+};
+
+struct CostModel {
+    double mult[3];             // CONST, TRAJ, NET copies
+    double flops_rate = 6.0e13; // complex-MAC work in real flops/s (8 flops per MAC)
+    double bw = 5.0e12;         // bytes/s
+    double launch = 3.0e-6;     // per step
+};
+
+struct Searcher {
+    const BlockNet* net;
+    const CostModel* cm;
+    std::vector<GT> t;
+    std::vector<std::vector<int32_t>> occ;   // index id -> live tensors holding it
+    std::vector<Move> moves;
+    double time = 0, macs[3] = {0, 0, 0}, bytes[3] = {0, 0, 0};
+    int64_t max_rank = 0;
+
+    Searcher(const BlockNet& n, const CostModel& c) : net(&n), cm(&c) {}
+
+    bool is_slice(int32_t i) const { return net->idx[i].kind == IX_SLICE; }
+    bool is_open(int32_t i) const { return net->idx[i].kind == IX_OPEN; }
+
+    void init() {
+        t.clear();
+        occ.assign(net->idx.size(), {});
+        moves.clear();
+        time = 0;
+        for (int k = 0; k < 3; k++) macs[k] = bytes[k] = 0;
+        max_rank = 0;
+        int nl = net->n_leaf_tensors;
+        for (size_t i = 0; i < net->tidx.size(); i++) {
+            GT g;
+            g.idx = net->tidx[i];
+            std::sort(g.idx.begin(), g.idx.end());
+            g.cls = net->tcls[i];
+            g.side = net->tbra[i];
+            g.mirror = (int32_t)((i < (size_t)nl) ? i + nl : i - nl);
+            g.nslice = 0;
+            for (int32_t x : g.idx) g.nslice += is_slice(x);
+            g.alive = true;
+            t.push_back(g);
+            for (int32_t x : g.idx) occ[x].push_back((int32_t)i);
+        }
+    }
+
+    // Result of contracting a and b (without applying it).
+    void result(int32_t a, int32_t b, std::vector<int32_t>& out, int32_t& nsum, int32_t& cls,
+                int32_t& nslice) const {
+        const GT &A = t[a], &B = t[b];
+        cls = std::max(A.cls, B.cls);
+        out.clear();
+        nsum = 0;
+        nslice = 0;
+        size_t i = 0, j = 0;
+        auto keep = [&](int32_t x) {
+            if (is_slice(x)) {
+                if (cls == CLS_NET) return;   // fixed from the network's prefix
+                nslice++;
+            }
+            out.push_back(x);
+        };
+        while (i < A.idx.size() || j < B.idx.size()) {
+            if (j == B.idx.size() || (i < A.idx.size() && A.idx[i] < B.idx[j])) {
+                keep(A.idx[i++]);
+            } else if (i == A.idx.size() || B.idx[j] < A.idx[i]) {
+                keep(B.idx[j++]);
+            } else {
+                int32_t x = A.idx[i];
+                if (!is_open(x) && occ[x].size() == 2) nsum++;
+                else keep(x);
+                i++;
+                j++;
+            }
+        }
+    }
+
+    double size_of(const GT& g, bool sliced) const {
+        return std::ldexp(1.0, (int)g.idx.size() - (sliced ? g.nslice : 0));
+    }
+
+    // Cost of one step (count once for a lockstep mirror pair).
+    void account(int32_t cls, int64_t rank_out, int32_t nsum, const GT& A, const GT* B) {
+        double m = cm->mult[cls];
+        double mac = std::ldexp(1.0, (int)(rank_out + nsum));
+        double by = 8.0 * std::ldexp(1.0, (int)rank_out) * m;
+        auto rd = [&](const GT& g) {
+            if (cls == CLS_NET && g.cls != CLS_NET) return 8.0 * size_of(g, false) * cm->mult[g.cls];
+            return 8.0 * size_of(g, false) * cm->mult[g.cls];
+        };
+        by += rd(A);
+        if (B) by += rd(*B);
+        macs[cls] += mac * m;
+        bytes[cls] += by;
+        time += std::max(8.0 * mac * m / cm->flops_rate, by / cm->bw) + cm->launch;
+        max_rank = std::max<int64_t>(max_rank, rank_out);
+    }
+
+    int32_t add_tensor(GT&& g) {
+        int32_t id = (int32_t)t.size();
+        for (int32_t x : g.idx) occ[x].push_back(id);
+        t.push_back(std::move(g));
+        return id;
+    }
+    void kill(int32_t a) {
+        t[a].alive = false;
+        for (int32_t x : t[a].idx) {
+            auto& v = occ[x];
+            v.erase(std::find(v.begin(), v.end(), a));
+        }
+        if (t[a].mirror >= 0 && t[t[a].mirror].mirror == a) t[t[a].mirror].mirror = -1;
+    }
+
+    int32_t do_contract(int32_t a, int32_t b, bool count) {
+        std::vector<int32_t> out;
+        int32_t nsum, cls, nslice;
+        result(a, b, out, nsum, cls, nslice);
+        if (count) account(cls, (int64_t)out.size(), nsum, t[a], &t[b]);
+        GT g;
+        g.idx = std::move(out);
+        g.cls = cls;
+        g.side = (t[a].side == t[b].side) ? t[a].side : 2;
+        g.mirror = -1;
+        g.nslice = nslice;
+        g.alive = true;
+        int32_t keep_ma = t[a].mirror, keep_mb = t[b].mirror;
+        (void)keep_ma;
+        (void)keep_mb;
+        kill(a);
+        kill(b);
+        return add_tensor(std::move(g));
+    }
+
+    int32_t do_slice(int32_t a, bool count) {
+        GT g;
+        for (int32_t x : t[a].idx)
+            if (!is_slice(x)) g.idx.push_back(x);
+        g.cls = CLS_NET;
+        g.side = t[a].side;
+        g.mirror = -1;
+        g.nslice = 0;
+        g.alive = true;
+        (void)count;   // a slice is a view: no work
+        kill(a);
+        return add_tensor(std::move(g));
+    }
+
+    bool lockstep_pair(int32_t a, int32_t b) const {
+        const GT &A = t[a], &B = t[b];
+        return A.side == 0 && B.side == 0 && A.mirror >= 0 && B.mirror >= 0 &&
+               t[A.mirror].alive && t[B.mirror].alive;
+    }
+    bool skip_pair(int32_t a, int32_t b) const {   // bra-side twin of a lockstep ket pair
+        const GT &A = t[a], &B = t[b];
+        return A.side == 1 && B.side == 1 && A.mirror >= 0 && B.mirror >= 0;
+    }
+
+    // Apply a contraction, with its mirror when in lockstep; returns result id.
+    int32_t apply_contract(int32_t a, int32_t b) {
+        Move mv{MV_CONTRACT, a, b, -1, -1, -1, -1};
+        if (lockstep_pair(a, b)) {
+            int32_t ma = t[a].mirror, mb = t[b].mirror;
+            int32_t c = do_contract(a, b, true);
+            int32_t mc = do_contract(ma, mb, false);
+            t[c].mirror = mc;
+            t[mc].mirror = c;
+            mv.c = c;
+            mv.ma = ma;
+            mv.mb = mb;
+            mv.mc = mc;
+        } else {
+            mv.c = do_contract(a, b, true);
+        }
+        moves.push_back(mv);
+        return mv.c;
+    }
+    int32_t apply_slice(int32_t a) {
+        Move mv{MV_SLICE, a, -1, -1, -1, -1, -1};
+        int32_t m = t[a].mirror;
+        bool lock = t[a].side == 0 && m >= 0 && t[m].alive && t[m].cls == CLS_TRAJ && t[m].nslice > 0;
+        mv.c = do_slice(a, true);
+        if (lock) {
+            mv.ma = m;
+            mv.mc = do_slice(m, false);
+            t[mv.c].mirror = mv.mc;
+            t[mv.mc].mirror = mv.c;
+        }
+        moves.push_back(mv);
+        return mv.c;
+    }
+
+    struct Cand {
+        double score;
+        int32_t a, b;   // b = -1: slice move
+        bool operator<(const Cand& o) const { return score > o.score; }   // min-heap
+    };
+
+    double pair_score(int32_t a, int32_t b, double costmod) const {
+        std::vector<int32_t> out;
+        int32_t nsum, cls, nslice;
+        result(a, b, out, nsum, cls, nslice);
+        double so = std::ldexp(1.0, (int)out.size()) * cm->mult[cls];
+        double sa = size_of(t[a], false) * cm->mult[t[a].cls];
+        double sb = size_of(t[b], false) * cm->mult[t[b].cls];
+        return so - costmod * (sa + sb);
+    }
+    double slice_score(int32_t a, double costmod) const {
+        double so = size_of(t[a], true) * cm->mult[CLS_NET];
+        double sa = size_of(t[a], false) * cm->mult[t[a].cls];
+        return so - costmod * sa;
+    }
+
+    void run(double temperature, double costmod, std::mt19937_64& rng) {
+        init();
+        std::priority_queue<Cand> heap;
+        std::uniform_real_distribution<double> U(1e-12, 1.0);
+        auto noisy = [&](double s) {
+            double v = (s >= 0 ? 1.0 : -1.0) * std::log1p(std::fabs(s));
+            if (temperature > 0) v -= temperature * (-std::log(-std::log(U(rng))));
+            return v;
+        };
+        auto push_pairs = [&](int32_t a) {
+            if (!t[a].alive) return;
+            std::vector<int32_t> nb;
+            for (int32_t x : t[a].idx)
+                for (int32_t o : occ[x])
+                    if (o != a) nb.push_back(o);
+            std::sort(nb.begin(), nb.end());
+            nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+            for (int32_t o : nb) {
+                if (skip_pair(a, o)) continue;
+                heap.push({noisy(pair_score(a, o, costmod)), std::min(a, o), std::max(a, o)});
+            }
+            if (t[a].cls == CLS_TRAJ && t[a].nslice > 0 && cm->mult[CLS_NET] > 0 &&
+                !(t[a].side == 1 && t[a].mirror >= 0))
+                heap.push({noisy(slice_score(a, costmod)), a, -1});
+        };
+        for (size_t i = 0; i < t.size(); i++) push_pairs((int32_t)i);
+        while (!heap.empty()) {
+            Cand c = heap.top();
+            heap.pop();
+            if (!t[c.a].alive || (c.b >= 0 && !t[c.b].alive)) continue;
+            if (c.b >= 0 && skip_pair(c.a, c.b)) continue;
+            if (c.b < 0 && !(t[c.a].cls == CLS_TRAJ && t[c.a].nslice > 0)) continue;
+            int32_t r;
+            if (c.b < 0) {
+                int32_t m = t[c.a].mirror;
+                r = apply_slice(c.a);
+                push_pairs(r);
+                if (t[r].mirror >= 0) push_pairs(t[r].mirror);
+                (void)m;
+            } else {
+                r = apply_contract(c.a, c.b);
+                push_pairs(r);
+                if (t[r].mirror >= 0) push_pairs(t[r].mirror);
+            }
+        }
+        // disconnected remainder: outer products, smallest first
+        for (;;) {
+            std::vector<int32_t> live;
+            for (size_t i = 0; i < t.size(); i++)
+                if (t[i].alive) live.push_back((int32_t)i);
+            if (live.size() <= 1) break;
+            std::sort(live.begin(), live.end(), [&](int32_t x, int32_t y) {
+                return size_of(t[x], false) * cm->mult[t[x].cls] < size_of(t[y], false) * cm->mult[t[y].cls];
+            });
+            apply_contract(live[0], live[1]);
+        }
+        // the root must hold no unresolved slice index
+        for (size_t i = 0; i < t.size(); i++)
+            if (t[i].alive && t[i].cls == CLS_TRAJ && t[i].nslice > 0) apply_slice((int32_t)i);
+    }
+
+    int32_t root() const {
+        for (size_t i = 0; i < t.size(); i++)
+            if (t[i].alive) return (int32_t)i;
+        return -1;
+    }
+};
+
+// -------------------------------------------------------------- lowering --
+struct TRef {
+    int32_t mode;               // OP_LEAF / OP_BUF
+    int32_t id;                 // leaf id / buffer id
+    int32_t conj;
+    int32_t cls;                // storage class
+    std::vector<int32_t> layout;   // index ids, position = log2(stride)
+};
+
+struct Arena {
+    std::vector<std::pair<int64_t, int64_t>> live;   // (offset, size)
+    int64_t peak = 0;
+    int64_t alloc(int64_t size) {
+        std::sort(live.begin(), live.end());
+        int64_t off = 0;
+        for (auto& b : live) {
+            if (b.first - off >= size) break;
+            off = std::max(off, b.first + b.second);
+        }
+        live.push_back({off, size});
+        peak = std::max(peak, off + size);
+        return off;
+    }
+    void release(int64_t off) {
+        for (size_t i = 0; i < live.size(); i++)
+            if (live[i].first == off) {
+                live.erase(live.begin() + i);
+                return;
+            }
+    }
+};
+
+static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const Searcher& s,
+                              int32_t start, int32_t b, BlockPlan& bp) {
+    const auto& idx = net.idx;
+    std::vector<TRef> ref(s.t.size());
+    int nl = net.n_leaf_tensors;
+    for (size_t i = 0; i < net.tidx.size(); i++) {
+        const LeafInfo& L = plan->leaves[net.tleaf[i]];
+        TRef r;
+        r.mode = OP_LEAF;
+        r.id = net.tleaf[i];
+        r.conj = net.tbra[i];
+        r.cls = L.n_var > 1 ? CLS_TRAJ : CLS_CONST;
+        r.layout = net.tidx[i];
+        ref[i] = r;
+    }
+    (void)nl;
+    struct BufInfo {
+        int32_t arena;
+        int64_t off;
+        int32_t refs;
+    };
+    std::vector<BufInfo> bufs;
+    Arena arenas[3];
+    auto pos_in = [](const std::vector<int32_t>& lay, int32_t x) -> int {
+        for (size_t p = 0; p < lay.size(); p++)
+            if (lay[p] == x) return (int)p;
+        return -1;
+    };
+    auto make_op = [&](const TRef& r, int32_t step_cls, OperandDesc& d) -> ptn_status {
+        memset(&d, 0, sizeof d);
+        d.mode = r.mode;
+        d.cls = r.cls;
+        d.conj = r.conj;
+        d.inst_size = (int64_t)1 << r.layout.size();
+        if (r.mode == OP_LEAF) {
+            const LeafInfo& L = plan->leaves[r.id];
+            d.leaf_base = L.var_base;
+            d.leaf_col = L.var_col;
+            d.arena = -1;
+        } else {
+            d.arena = bufs[r.id].arena;
+            d.arena_off = bufs[r.id].off;
+            d.leaf_col = -1;
+        }
+        d.n_slice = 0;
+        if (step_cls == CLS_NET && r.cls != CLS_NET) {
+            for (size_t p = 0; p < r.layout.size(); p++) {
+                const NetIdx& x = idx[r.layout[p]];
+                if (x.kind != IX_SLICE) continue;
+                if (d.n_slice >= kMaxSlice)
+                    return set_error(PTN_ERR_UNSUPPORTED, "too many projected bits on one operand");
+                d.slice_qubit[d.n_slice] = x.qubit;
+                d.slice_stride[d.n_slice] = (int64_t)1 << p;
+                d.n_slice++;
+            }
+        }
+        return PTN_OK;
+    };
+    auto consume = [&](const TRef& r) {
+        if (r.mode != OP_BUF) return;
+        BufInfo& bi = bufs[r.id];
+        if (--bi.refs == 0) arenas[bi.arena].release(bi.off);
+    };
+
+    int32_t root_id = s.root();
+    // find the move that produces the root (or the tensor the root is a slice of)
+    int32_t root_src = root_id;
+    for (auto it = s.moves.rbegin(); it != s.moves.rend(); ++it)
+        if (it->c == root_src && it->type == MV_SLICE) root_src = it->a;
+
+    std::string summary;
+    for (const Move& mv : s.moves) {
+        if (mv.type == MV_SLICE) {
+            ref[mv.c] = ref[mv.a];       // a view: same storage, NET addressing when consumed
+            if (mv.mc >= 0) ref[mv.mc] = ref[mv.ma];
+            continue;
+        }
+        const GT& C = s.t[mv.c];
+        const TRef& A = ref[mv.a];
+        const TRef& B = ref[mv.b];
+        StepDesc st;
+        memset(&st, 0, sizeof st);
+        st.out_cls = C.cls;
+        // output layout: A's kept bits in A's order, then B's
+        std::vector<int32_t> out;
+        auto keep_from = [&](const TRef& r) {
+            for (int32_t x : r.layout)
+                if (std::binary_search(C.idx.begin(), C.idx.end(), x) &&
+                    std::find(out.begin(), out.end(), x) == out.end())
+                    out.push_back(x);
+        };
+        if (mv.c == root_src) {
+            // canonical: open bits by qubit (block bit t = qubit start + t), then the rest
+            std::vector<int32_t> open, rest;
+            for (int32_t x : C.idx) (idx[x].kind == IX_OPEN ? open : rest).push_back(x);
+            std::sort(open.begin(), open.end(), [&](int32_t u, int32_t v) { return idx[u].qubit < idx[v].qubit; });
+            out = open;
+            out.insert(out.end(), rest.begin(), rest.end());
+        } else {
+            keep_from(A);
+            keep_from(B);
+        }
+        if (out.size() != C.idx.size())
+            return set_error(PTN_ERR_INVALID_ARG, "internal: output layout mismatch");
+        if ((int)out.size() > kMaxOut)
+            return set_error(PTN_ERR_TOO_LARGE, "a contraction step has %d output bits (max %d)",
+                             (int)out.size(), kMaxOut);
+        // summed bits: in both operands' layouts, not in the output, not a slice
+        std::vector<int32_t> sum;
+        for (int32_t x : A.layout)
+            if (pos_in(B.layout, x) >= 0 && pos_in(out, x) < 0 && idx[x].kind != IX_SLICE) sum.push_back(x);
+        if ((int)sum.size() > kMaxSum)
+            return set_error(PTN_ERR_TOO_LARGE, "a contraction step sums %d bits (max %d)",
+                             (int)sum.size(), kMaxSum);
+        st.n_out = (int32_t)out.size();
+        st.n_sum = (int32_t)sum.size();
+        st.out_size = (int64_t)1 << out.size();
+        ptn_status e = make_op(A, C.cls, st.op[0]);
+        if (e) return e;
+        e = make_op(B, C.cls, st.op[1]);
+        if (e) return e;
+        const TRef* ops[2] = {&A, &B};
+        for (int o = 0; o < 2; o++) {
+            for (size_t p = 0; p < out.size(); p++) {
+                int q = pos_in(ops[o]->layout, out[p]);
+                st.out_stride[o][p] = q >= 0 ? ((int64_t)1 << q) : 0;
+            }
+            for (size_t p = 0; p < sum.size(); p++) {
+                int q = pos_in(ops[o]->layout, sum[p]);
+                st.sum_stride[o][p] = (int64_t)1 << q;
+            }
+        }
+        // output buffer: allocate before releasing the operands
+        BufInfo bi;
+        bi.arena = C.cls;
+        bi.off = arenas[C.cls].alloc(st.out_size);
+        bi.refs = mv.mc >= 0 ? 2 : 1;
+        int32_t bid = (int32_t)bufs.size();
+        bufs.push_back(bi);
+        st.out_arena = C.cls;
+        st.out_off = bi.off;
+        consume(A);
+        consume(B);
+        if (mv.ma >= 0) {
+            consume(ref[mv.ma]);
+            consume(ref[mv.mb]);
+        }
+        TRef rc;
+        rc.mode = OP_BUF;
+        rc.id = bid;
+        rc.conj = 0;
+        rc.cls = C.cls;
+        rc.layout = out;
+        ref[mv.c] = rc;
+        if (mv.mc >= 0) {
+            TRef rm = rc;
+            rm.conj = 1;
+            for (auto& x : rm.layout) x = idx[x].mirror;
+            ref[mv.mc] = rm;
+        }
+        bp.steps.push_back(st);
+    }
+    // root descriptor
+    const TRef& R = ref[root_id];
+    if (R.mode != OP_BUF) return set_error(PTN_ERR_UNSUPPORTED, "degenerate block network");
+    ptn_status e = make_op(R, CLS_NET, bp.root.op);
+    if (e) return e;
+    for (int tb = 0; tb < b; tb++) bp.root.x_stride[tb] = -1;
+    for (size_t p = 0; p < R.layout.size(); p++) {
+        const NetIdx& x = idx[R.layout[p]];
+        if (x.kind == IX_OPEN) bp.root.x_stride[x.qubit - start] = (int64_t)1 << p;
+    }
+    for (int tb = 0; tb < b; tb++)
+        if (bp.root.x_stride[tb] < 0) return set_error(PTN_ERR_INVALID_ARG, "internal: root misses an open bit");
+    for (int k = 0; k < 3; k++) bp.arena_peak[k] = arenas[k].peak;
+    return PTN_OK;
+}
+
+// ------------------------------------------------------------ build plan --
+static void cd_from(const double* p, cd* out, int n) {
+    for (int i = 0; i < n; i++) out[i] = cd(p[2 * i], p[2 * i + 1]);
+}
+
+ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* block_sizes,
+                      int32_t n_blocks, const ptn_plan_opts* o, ptn_plan* plan) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!c || !c->gates || c->n_qubits < 1 || c->n_qubits > 64 || c->n_gates < 0)
+        return set_error(PTN_ERR_INVALID_ARG, "invalid circuit");
+    const int n = c->n_qubits;
+    plan->n_qubits = n;
+    ptn_plan_opts opts{};
+    if (o) opts = *o;
+    if (opts.hypersamples <= 0) opts.hypersamples = 100;
+    if (opts.est_traj <= 0) opts.est_traj = 1024;
+    if (opts.est_shots <= 0) opts.est_shots = 1e6;
+    plan->opts = opts;
+    plan->mem_cap = opts.mem_cap_bytes;
+
+    // ---- validate gates and noise
+    for (int l = 0; l < c->n_gates; l++) {
+        const ptn_gate& g = c->gates[l];
+        if (g.arity != 1 && g.arity != 2) return set_error(PTN_ERR_INVALID_ARG, "gate %d: arity %d", l, g.arity);
+        if (g.q0 < 0 || g.q0 >= n || (g.arity == 2 && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)))
+            return set_error(PTN_ERR_INVALID_ARG, "gate %d: bad qubits", l);
+    }
+    int n_sites = nz ? nz->n_sites : 0;
+    int n_ch = nz ? nz->n_channels : 0;
+    plan->n_sites = n_sites;
+    for (int k = 0; k < n_ch; k++) {
+        const ptn_channel& ch = nz->channels[k];
+        if (ch.n_kraus < 1 || ch.n_kraus > kMaxKraus || !ch.kraus)
+            return set_error(PTN_ERR_INVALID_ARG, "channel %d: n_kraus %d", k, ch.n_kraus);
+        cd s[4] = {0, 0, 0, 0};
+        for (int a = 0; a < ch.n_kraus; a++) {
+            cd m[4];
+            cd_from(ch.kraus + 8 * a, m, 4);
+            for (int i = 0; i < 2; i++)
+                for (int j = 0; j < 2; j++)
+                    s[i * 2 + j] += std::conj(m[i]) * m[j] + std::conj(m[2 + i]) * m[2 + j];
+        }
+        double err = std::max({std::abs(s[0] - 1.0), std::abs(s[1]), std::abs(s[2]), std::abs(s[3] - 1.0)});
+        if (err > 1e-10) return set_error(PTN_ERR_NOT_CPTP, "channel %d: |sum K^dag K - I| = %.3g", k, err);
+    }
+    int prev_gate = -1;
+    for (int s = 0; s < n_sites; s++) {
+        const ptn_site& st = nz->sites[s];
+        if (st.gate < 0 || st.gate >= c->n_gates || st.channel < 0 || st.channel >= n_ch)
+            return set_error(PTN_ERR_INVALID_ARG, "site %d: bad gate or channel", s);
+        const ptn_gate& g = c->gates[st.gate];
+        if (st.qubit != g.q0 && !(g.arity == 2 && st.qubit == g.q1))
+            return set_error(PTN_ERR_INVALID_ARG, "site %d: qubit not on its gate", s);
+        if (st.gate < prev_gate) return set_error(PTN_ERR_INVALID_ARG, "sites must be grouped by gate in order");
+        prev_gate = st.gate;
+    }
+
+    // ---- site tables (Kraus CDF and log q)
+    plan->site_tables.assign(n_sites, SiteTable{});
+    std::vector<std::vector<double>> qtab(n_ch);
+    for (int k = 0; k < n_ch; k++) {
+        const ptn_channel& ch = nz->channels[k];
+        for (int a = 0; a < ch.n_kraus; a++) qtab[k].push_back(kraus_prob(ch.kraus + 8 * a));
+    }
+    for (int s = 0; s < n_sites; s++) {
+        SiteTable& T = plan->site_tables[s];
+        const auto& q = qtab[nz->sites[s].channel];
+        T.n_kraus = (int32_t)q.size();
+        double acc = 0.0;
+        for (int a = 0; a < kMaxKraus; a++) {
+            if (a < T.n_kraus) {
+                acc = acc + q[a];
+                T.cdf[a] = acc;
+                T.logq[a] = q[a] > 0 ? std::log(q[a]) : -INFINITY;
+            } else {
+                T.cdf[a] = 2.0;
+                T.logq[a] = 0.0;
+            }
+        }
+        T.cdf[T.n_kraus - 1] = 1.0;
+    }
+    std::vector<std::vector<int32_t>> gsites(c->n_gates);
+    for (int s = 0; s < n_sites; s++) gsites[nz->sites[s].gate].push_back(s);
+
+    // scaled Kraus operator K_k / sqrt(q_k) of a site
+    auto scaled_kraus = [&](int s, int k) {
+        const ptn_channel& ch = nz->channels[nz->sites[s].channel];
+        cd m[4];
+        cd_from(ch.kraus + 8 * k, m, 4);
+        double q = qtab[nz->sites[s].channel][k];
+        double sc = q > 0 ? 1.0 / std::sqrt(q) : 0.0;
+        M2 r;
+        for (int i = 0; i < 4; i++) r[i] = m[i] * sc;
+        return r;
+    };
+
+    // ---- leaves and their variant tables
+    std::vector<bool> touched(n, false);
+    plan->leaves.clear();
+    std::vector<float>& vt = plan->var_table;
+    vt.clear();
+    auto finish_leaf = [&](LeafInfo& L, const std::function<cd(int64_t var, const int32_t* role_bits)>& val) {
+        L.size = (int64_t)1 << L.legs.size();
+        L.n_var = 1;
+        for (int32_t r : L.radix) L.n_var *= r;
+        L.var_base = (int64_t)vt.size() / 2;
+        for (int64_t v = 0; v < L.n_var; v++)
+            for (int64_t e = 0; e < L.size; e++) {
+                int32_t rb[5] = {0, 0, 0, 0, 0};
+                for (size_t p = 0; p < L.legs.size(); p++) rb[L.legs[p]] = (int32_t)((e >> p) & 1);
+                cd z = val(v, rb);
+                vt.push_back((float)z.real());
+                vt.push_back((float)z.imag());
+            }
+        L.var_col = L.n_var > 1 ? plan->n_var_cols++ : -1;
+        plan->leaves.push_back(L);
+    };
+    // decode the Kraus choices of a variant and build N_q for one qubit
+    auto noise_op = [&](const LeafInfo& L, int64_t var, int qubit) {
+        M2 N = eye2();
+        int64_t v = var;
+        for (size_t i = 0; i < L.sites.size(); i++) {
+            int k = (int)(v % L.radix[i]);
+            v /= L.radix[i];
+            if (nz->sites[L.sites[i]].qubit == qubit) N = mul2(scaled_kraus(L.sites[i], k), N);
+        }
+        return N;
+    };
+    plan->n_var_cols = 0;
+    for (int l = 0; l < c->n_gates; l++) {
+        const ptn_gate& g = c->gates[l];
+        if (g.arity == 1) {
+            LeafInfo L;
+            L.gate = l;
+            L.part = 0;
+            L.qubit0 = g.q0;
+            L.qubit1 = -1;
+            for (int32_t s : gsites[l]) {
+                L.sites.push_back(s);
+                L.radix.push_back((int32_t)qtab[nz->sites[s].channel].size());
+            }
+            bool fixed = !touched[g.q0];
+            touched[g.q0] = true;
+            if (!fixed) L.legs.push_back(R_IN_A);
+            L.legs.push_back(R_OUT_A);
+            M2 M;
+            cd_from(g.mat, M.data(), 4);
+            finish_leaf(L, [&](int64_t v, const int32_t* rb) {
+                M2 NM = mul2(noise_op(L, v, g.q0), M);
+                return NM[rb[R_OUT_A] * 2 + rb[R_IN_A]];
+            });
+        } else {
+            M4 M;
+            cd_from(g.mat, M.data(), 16);
+            bool fa = !touched[g.q0], fb = !touched[g.q1];
+            touched[g.q0] = touched[g.q1] = true;
+            // operator-Schmidt rank: X[(oa ia)][(ob ib)] = M[(oa ob)][(ia ib)]
+            M4 X;
+            for (int oa = 0; oa < 2; oa++)
+                for (int ob = 0; ob < 2; ob++)
+                    for (int ia = 0; ia < 2; ia++)
+                        for (int ib = 0; ib < 2; ib++)
+                            X[(oa * 2 + ia) * 4 + ob * 2 + ib] = M[(oa * 2 + ob) * 4 + ia * 2 + ib];
+            double sv[4];
+            cd xv[4][4], vv[4][4];
+            svd4(X, sv, xv, vv);
+            int rank = 0;
+            for (int r = 0; r < 4; r++)
+                if (sv[r] > 1e-12 * std::max(sv[0], 1e-300)) rank++;
+            if (opts.split_gates && rank <= 2) {
+                int bond_bits = rank == 2 ? 1 : 0;
+                // left factor A_r[oa][ia] = (X V)[(oa ia), r] / sqrt(s_r); right B_r[ob][ib] = sqrt(s_r) conj(V[(ob ib), r])
+                for (int part = 1; part <= 2; part++) {
+                    LeafInfo L;
+                    L.gate = l;
+                    L.part = part;
+                    L.qubit0 = g.q0;
+                    L.qubit1 = g.q1;
+                    int q = part == 1 ? g.q0 : g.q1;
+                    for (int32_t s : gsites[l])
+                        if (nz->sites[s].qubit == q) {
+                            L.sites.push_back(s);
+                            L.radix.push_back((int32_t)qtab[nz->sites[s].channel].size());
+                        }
+                    bool fixed = part == 1 ? fa : fb;
+                    if (!fixed) L.legs.push_back(R_IN_A);
+                    L.legs.push_back(R_OUT_A);
+                    if (bond_bits) L.legs.push_back(R_BOND);
+                    finish_leaf(L, [&, part, q](int64_t v, const int32_t* rb) {
+                        int r = rb[R_BOND];
+                        M2 F;
+                        for (int oo = 0; oo < 2; oo++)
+                            for (int ii = 0; ii < 2; ii++) {
+                                double sr = std::sqrt(sv[r]);
+                                F[oo * 2 + ii] = part == 1 ? xv[oo * 2 + ii][r] / sr : sr * std::conj(vv[oo * 2 + ii][r]);
+                            }
+                        M2 NF = mul2(noise_op(L, v, q), F);
+                        return NF[rb[R_OUT_A] * 2 + rb[R_IN_A]];
+                    });
+                }
+            } else {
+                LeafInfo L;
+                L.gate = l;
+                L.part = 0;
+                L.qubit0 = g.q0;
+                L.qubit1 = g.q1;
+                for (int32_t s : gsites[l]) {
+                    L.sites.push_back(s);
+                    L.radix.push_back((int32_t)qtab[nz->sites[s].channel].size());
+                }
+                if (!fb) L.legs.push_back(R_IN_B);
+                if (!fa) L.legs.push_back(R_IN_A);
+                L.legs.push_back(R_OUT_B);
+                L.legs.push_back(R_OUT_A);
+                finish_leaf(L, [&](int64_t v, const int32_t* rb) {
+                    M2 Na = noise_op(L, v, g.q0), Nb = noise_op(L, v, g.q1);
+                    int ro = rb[R_OUT_A] * 2 + rb[R_OUT_B];
+                    int ci = rb[R_IN_A] * 2 + rb[R_IN_B];
+                    // ((Na (x) Nb) M)[ro][ci] = sum_{a,b} Na[oa][a] Nb[ob][b] M[(a b)][ci]
+                    cd z = 0;
+                    for (int a = 0; a < 2; a++)
+                        for (int bb = 0; bb < 2; bb++)
+                            z += Na[rb[R_OUT_A] * 2 + a] * Nb[rb[R_OUT_B] * 2 + bb] * M[(a * 2 + bb) * 4 + ci];
+                    (void)ro;
+                    return z;
+                });
+            }
+        }
+    }
+    for (int q = 0; q < n; q++)
+        if (!touched[q]) {
+            LeafInfo L;
+            L.gate = -1;
+            L.part = 0;
+            L.qubit0 = q;
+            L.qubit1 = -1;
+            L.legs.push_back(R_OUT_A);
+            finish_leaf(L, [](int64_t, const int32_t* rb) { return rb[R_OUT_A] ? cd(0) : cd(1); });
+        }
+    // CSR of variant-selecting sites per var column
+    plan->leaf_site_ptr.assign(plan->n_var_cols + 1, 0);
+    plan->leaf_site_idx.clear();
+    plan->leaf_site_mul.clear();
+    {
+        std::vector<const LeafInfo*> bycol(plan->n_var_cols, nullptr);
+        for (auto& L : plan->leaves)
+            if (L.var_col >= 0) bycol[L.var_col] = &L;
+        for (int col = 0; col < plan->n_var_cols; col++) {
+            const LeafInfo& L = *bycol[col];
+            int64_t mul = 1;
+            for (size_t i = 0; i < L.sites.size(); i++) {
+                plan->leaf_site_idx.push_back(L.sites[i]);
+                plan->leaf_site_mul.push_back((int32_t)mul);
+                mul *= L.radix[i];
+            }
+            plan->leaf_site_ptr[col + 1] = (int32_t)plan->leaf_site_idx.size();
+        }
+    }
+
+    // ---- blocks
+    std::vector<int32_t> bs;
+    if (block_sizes && n_blocks > 0) {
+        bs.assign(block_sizes, block_sizes + n_blocks);
+    } else {
+        int f = (n + 9) / 10;
+        for (int j = 0; j < f - 1; j++) bs.push_back(10);
+        bs.push_back(n - 10 * (f - 1));
+    }
+    if ((int)bs.size() > kMaxBlocks) return set_error(PTN_ERR_INVALID_ARG, "too many blocks");
+    int tot = 0;
+    for (int32_t v : bs) {
+        if (v < 1 || v > 14) return set_error(PTN_ERR_INVALID_ARG, "block sizes must be in 1..14");
+        tot += v;
+    }
+    if (tot != n) return set_error(PTN_ERR_INVALID_ARG, "block sizes sum to %d, circuit has %d qubits", tot, n);
+
+    std::mt19937_64 rng(opts.seed ^ 0x9E3779B97F4A7C15ull);
+    int start = 0;
+    plan->blocks.clear();
+    for (size_t j = 0; j < bs.size(); j++) {
+        int b = bs[j];
+        BlockNet net;
+        // ket layer: walk the leaves in circuit order
+        std::vector<int32_t> cur(n, -1);
+        auto new_idx = [&](int32_t kind, int32_t q) {
+            net.idx.push_back({kind, q, -1});
+            return (int32_t)net.idx.size() - 1;
+        };
+        std::vector<std::vector<int32_t>> ket_idx;
+        std::vector<int32_t> ket_leaf;
+        int32_t bond = -1;
+        for (size_t li = 0; li < plan->leaves.size(); li++) {
+            const LeafInfo& L = plan->leaves[li];
+            std::vector<int32_t> ids;
+            int qa = L.qubit0, qb = L.qubit1;
+            int qA = (L.part == 2) ? qb : qa;   // the factor's own qubit
+            if (L.part == 1) bond = -1;
+            int32_t in_a = cur[qA], in_b = (L.part == 0 && L.qubit1 >= 0) ? cur[qb] : -1;
+            int32_t out_a = new_idx(IX_INT, qA), out_b = (L.part == 0 && L.qubit1 >= 0) ? new_idx(IX_INT, qb) : -1;
+            for (int32_t role : L.legs) {
+                switch (role) {
+                    case R_IN_A: ids.push_back(in_a); break;
+                    case R_OUT_A: ids.push_back(out_a); break;
+                    case R_IN_B: ids.push_back(in_b); break;
+                    case R_OUT_B: ids.push_back(out_b); break;
+                    case R_BOND:
+                        if (bond < 0) bond = new_idx(IX_INT, -1);
+                        ids.push_back(bond);
+                        break;
+                }
+            }
+            cur[qA] = out_a;
+            if (out_b >= 0) cur[qb] = out_b;
+            ket_idx.push_back(ids);
+            ket_leaf.push_back((int32_t)li);
+        }
+        // end kinds
+        for (int q = 0; q < n; q++) {
+            NetIdx& x = net.idx[cur[q]];
+            x.qubit = q;
+            x.kind = q < start ? IX_SLICE : (q < start + b ? IX_OPEN : IX_TRACED);
+        }
+        // mirrors
+        size_t n_ket_idx = net.idx.size();
+        for (size_t i = 0; i < n_ket_idx; i++) {
+            NetIdx& x = net.idx[i];
+            if (x.kind == IX_OPEN || x.kind == IX_TRACED) {
+                x.mirror = (int32_t)i;
+            } else {
+                NetIdx m{x.kind, x.qubit, (int32_t)i};
+                net.idx.push_back(m);
+                net.idx[i].mirror = (int32_t)net.idx.size() - 1;
+            }
+        }
+        int nl = (int)ket_idx.size();
+        net.n_leaf_tensors = nl;
+        for (int side = 0; side < 2; side++)
+            for (int i = 0; i < nl; i++) {
+                std::vector<int32_t> ids = ket_idx[i];
+                if (side)
+                    for (auto& x : ids) x = net.idx[x].mirror;
+                net.tidx.push_back(ids);
+                net.tleaf.push_back(ket_leaf[i]);
+                net.tbra.push_back(side);
+                net.tcls.push_back(plan->leaves[ket_leaf[i]].n_var > 1 ? CLS_TRAJ : CLS_CONST);
+            }
+
+        CostModel cm;
+        double E = opts.est_traj;
+        double D = j == 0 ? E : std::min(E * std::ldexp(1.0, start), opts.est_shots);
+        D = std::max(D, E);
+        cm.mult[CLS_CONST] = 1.0;
+        cm.mult[CLS_TRAJ] = E;
+        cm.mult[CLS_NET] = j == 0 ? E : D;
+
+        Searcher best(net, cm), cur_s(net, cm);
+        double best_time = INFINITY;
+        std::uniform_real_distribution<double> U(0.0, 1.0);
+        for (int h = 0; h < opts.hypersamples; h++) {
+            double temp = h == 0 ? 0.0 : 0.02 + 1.0 * U(rng);
+            double costmod = h == 0 ? 1.0 : 0.5 + 1.5 * U(rng);
+            cur_s.run(temp, costmod, rng);
+            if (cur_s.root() < 0) continue;
+            if (cur_s.max_rank > kMaxOut) continue;
+            if (cur_s.time < best_time) {
+                best_time = cur_s.time;
+                best = cur_s;
+            }
+        }
+        if (!std::isfinite(best_time))
+            return set_error(PTN_ERR_TOO_LARGE, "block %d: no path with at most %d open bits per tensor", (int)j, kMaxOut);
+        BlockPlan bp;
+        bp.start = start;
+        bp.b = b;
+        for (int k = 0; k < 3; k++) {
+            bp.est_macs[k] = best.macs[k];
+            bp.est_bytes[k] = best.bytes[k];
+        }
+        bp.est_time = best.time;
+        bp.est_mult_traj = E;
+        bp.est_mult_net = cm.mult[CLS_NET];
+        ptn_status e = lower_block(plan, net, best, start, b, bp);
+        if (e) return e;
+        char buf[256];
+        snprintf(buf, sizeof buf, "steps=%zu max_rank=%lld est_time=%.3es", bp.steps.size(),
+                 (long long)best.max_rank, best.time);
+        bp.path_summary = buf;
+        plan->blocks.push_back(std::move(bp));
+        start += b;
+    }
+    plan->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return PTN_OK;
+}
+
+static void json_op(std::string& s, const OperandDesc& d) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "{\"mode\":%d,\"cls\":%d,\"conj\":%d,\"arena\":%d,\"inst_size\":%lld,\"arena_off\":%lld,"
+             "\"leaf_base\":%lld,\"leaf_col\":%d,\"slices\":[",
+             d.mode, d.cls, d.conj, d.arena, (long long)d.inst_size, (long long)d.arena_off, (long long)d.leaf_base,
+             d.leaf_col);
+    s += buf;
+    for (int k = 0; k < d.n_slice; k++) {
+        snprintf(buf, sizeof buf, "%s[%d,%lld]", k ? "," : "", d.slice_qubit[k], (long long)d.slice_stride[k]);
+        s += buf;
+    }
+    s += "]}";
+}
+
+static void json_i64(std::string& s, const int64_t* v, int n) {
+    char buf[32];
+    s += "[";
+    for (int k = 0; k < n; k++) {
+        snprintf(buf, sizeof buf, "%s%lld", k ? "," : "", (long long)v[k]);
+        s += buf;
+    }
+    s += "]";
+}
+
+std::string describe_plan(const ptn_plan* p, int detail) {
+    std::string s = "{";
+    char buf[768];
+    snprintf(buf, sizeof buf,
+             "\"n_qubits\":%d,\"n_sites\":%d,\"n_leaves\":%zu,\"n_var_cols\":%d,\"plan_seconds\":%.6f,\"blocks\":[",
+             p->n_qubits, p->n_sites, p->leaves.size(), p->n_var_cols, p->plan_seconds);
+    s += buf;
+    for (size_t j = 0; j < p->blocks.size(); j++) {
+        const BlockPlan& b = p->blocks[j];
+        int cnt[3] = {0, 0, 0};
+        int64_t maxout = 0;
+        for (auto& st : b.steps) {
+            cnt[st.out_cls]++;
+            maxout = std::max<int64_t>(maxout, st.n_out);
+        }
+        snprintf(buf, sizeof buf,
+                 "%s{\"start\":%d,\"b\":%d,\"n_steps\":%zu,\"steps_const\":%d,\"steps_traj\":%d,\"steps_net\":%d,"
+                 "\"max_out_bits\":%lld,\"arena_const\":%lld,\"arena_traj\":%lld,\"arena_net\":%lld,"
+                 "\"macs_const\":%.6e,\"macs_traj\":%.6e,\"macs_net\":%.6e,\"bytes_traj\":%.6e,\"bytes_net\":%.6e,"
+                 "\"est_time\":%.6e,\"mult_traj\":%.1f,\"mult_net\":%.1f",
+                 j ? "," : "", b.start, b.b, b.steps.size(), cnt[0], cnt[1], cnt[2], (long long)maxout,
+                 (long long)b.arena_peak[0], (long long)b.arena_peak[1], (long long)b.arena_peak[2], b.est_macs[0],
+                 b.est_macs[1], b.est_macs[2], b.est_bytes[1], b.est_bytes[2], b.est_time, b.est_mult_traj,
+                 b.est_mult_net);
+        s += buf;
+        if (detail) {
+            s += ",\"steps\":[";
+            for (size_t i = 0; i < b.steps.size(); i++) {
+                const StepDesc& st = b.steps[i];
+                snprintf(buf, sizeof buf, "%s{\"out_cls\":%d,\"n_out\":%d,\"n_sum\":%d,\"out_arena\":%d,\"out_off\":%lld,\"ops\":[",
+                         i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.out_arena, (long long)st.out_off);
+                s += buf;
+                json_op(s, st.op[0]);
+                s += ",";
+                json_op(s, st.op[1]);
+                s += "],\"out_stride\":[";
+                json_i64(s, st.out_stride[0], st.n_out);
+                s += ",";
+                json_i64(s, st.out_stride[1], st.n_out);
+                s += "],\"sum_stride\":[";
+                json_i64(s, st.sum_stride[0], st.n_sum);
+                s += ",";
+                json_i64(s, st.sum_stride[1], st.n_sum);
+                s += "]}";
+            }
+            s += "],\"root\":{\"op\":";
+            json_op(s, b.root.op);
+            s += ",\"x_stride\":";
+            json_i64(s, b.root.x_stride, b.b);
+            s += "}";
+        }
+        s += "}";
+    }
+    s += "]";
+    if (detail) {
+        s += ",\"var_cols\":[";
+        for (int c = 0; c < p->n_var_cols; c++) {
+            s += c ? ",[" : "[";
+            for (int e = p->leaf_site_ptr[c]; e < p->leaf_site_ptr[c + 1]; e++) {
+                snprintf(buf, sizeof buf, "%s[%d,%d]", e > p->leaf_site_ptr[c] ? "," : "", p->leaf_site_idx[e],
+                         p->leaf_site_mul[e]);
+                s += buf;
+            }
+            s += "]";
+        }
+        s += "],\"var_table\":[";
+        for (size_t k = 0; k < p->var_table.size(); k++) {
+            snprintf(buf, sizeof buf, "%s%.9g", k ? "," : "", p->var_table[k]);
+            s += buf;
+        }
+        s += "],\"site_cdf\":[";
+        for (size_t k = 0; k < p->site_tables.size(); k++) {
+            const SiteTable& T = p->site_tables[k];
+            s += k ? ",[" : "[";
+            for (int a = 0; a < T.n_kraus; a++) {
+                snprintf(buf, sizeof buf, "%s%.17g", a ? "," : "", T.cdf[a]);
+                s += buf;
+            }
+            s += "]";
+        }
+        s += "]";
+    }
+    s += "}";
+    return s;
+}
+
+}  // namespace ptn

@@ -1,0 +1,132 @@
+// Internal data structures shared by the host planner (planner.cpp) and the
+// device runtime (runtime.cu, kernels_*.cu).  Not part of the public ABI.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ptn.h"
+
+namespace ptn {
+
+// Storage class of a tensor in a batch of block networks.
+//   CONST: one copy for the whole batch;
+//   TRAJ : one copy per distinct error set (trajectory) of the chunk;
+//   NET  : one copy per network (trajectory, prefix) of the chunk.
+enum Cls : int32_t { CLS_CONST = 0, CLS_TRAJ = 1, CLS_NET = 2 };
+enum OpMode : int32_t { OP_LEAF = 0, OP_BUF = 1 };
+
+constexpr int kMaxOut = 40;     // output bits of one contraction step
+constexpr int kMaxSum = 24;     // summed bits of one contraction step
+constexpr int kMaxSlice = 64;   // prefix (projected) bits read by one operand
+constexpr int kMaxBlocks = 64;
+constexpr int kMaxKraus = 16;
+
+// One operand of a batched pairwise contraction, as the kernels read it.
+struct OperandDesc {
+    int32_t mode;            // OP_LEAF: merged-gate variant table; OP_BUF: intermediate
+    int32_t cls;             // storage class (CLS_*)
+    int32_t conj;            // read the complex conjugate (bra layer)
+    int32_t arena;           // OP_BUF: arena of the buffer (= its storage class)
+    int64_t inst_size;       // elements per instance
+    int64_t arena_off;       // OP_BUF: offset of the buffer in its arena, in elements per instance
+    int64_t leaf_base;       // OP_LEAF: element offset of variant 0 in the variant table
+    int32_t leaf_col;        // OP_LEAF: column of the variant index table, -1 = single variant
+    int32_t n_slice;         // projected bits fixed from the network's prefix (NET steps)
+    int32_t slice_qubit[kMaxSlice];
+    int64_t slice_stride[kMaxSlice];
+};
+
+// One batched pairwise contraction:
+//   out[inst][o] = sum_k  A[inst'][addrA(o, k)] * B[inst''][addrB(o, k)]
+// with o = sum_p bit_p << p over the n_out output bits and k over the n_sum
+// summed bits; addr = sum_p bit_p(o) * out_stride[op][p] + sum_q bit_q(k) *
+// sum_stride[op][q] + the operand's slice offset.
+struct StepDesc {
+    int32_t out_cls;
+    int32_t n_out;
+    int32_t n_sum;
+    int32_t out_arena;
+    int64_t out_size;        // 2^n_out
+    int64_t out_off;         // offset of the output buffer in its arena (elements per instance)
+    OperandDesc op[2];
+    int64_t out_stride[2][kMaxOut];
+    int64_t sum_stride[2][kMaxSum];
+};
+
+struct LeafInfo {
+    int32_t gate;            // source gate, -1 for a |0> state
+    int32_t part;            // 0 whole gate / |0>, 1 factor on q0, 2 factor on q1
+    int32_t qubit0, qubit1;
+    std::vector<int32_t> sites;   // sites selecting the variant (mixed radix, first fastest)
+    std::vector<int32_t> radix;
+    int64_t n_var = 1;
+    int64_t size = 1;        // elements per variant
+    int64_t var_base = 0;    // element offset in the variant table
+    int32_t var_col = -1;    // column of var_ids, -1 if n_var == 1
+    // legs in storage order (position 0 = stride 1): role codes, see planner.cpp
+    std::vector<int32_t> legs;
+};
+
+struct RootRef {             // where the block's final tensor lives
+    OperandDesc op;          // read with NET addressing (slices applied)
+    int64_t x_stride[24];    // stride of block bit t in the root tensor
+};
+
+struct BlockPlan {
+    int32_t start = 0, b = 0;
+    std::vector<StepDesc> steps;
+    RootRef root;
+    int64_t arena_peak[3] = {0, 0, 0};   // elements per instance, per arena (CONST/TRAJ/NET)
+    double est_macs[3] = {0, 0, 0};      // complex MACs per instance by output class
+    double est_bytes[3] = {0, 0, 0};     // bytes moved per instance by output class
+    double est_time = 0;                 // modelled seconds at the planning multiplicities
+    double est_mult_traj = 0, est_mult_net = 0;
+    int32_t n_leaves_used = 0;
+    std::string path_summary;
+    // device copy
+    StepDesc* d_steps = nullptr;
+};
+
+struct SiteTable {           // per site: Kraus CDF and log q (FP64), padded to kMaxKraus
+    double cdf[kMaxKraus];
+    double logq[kMaxKraus];
+    int32_t n_kraus;
+    int32_t pad;
+};
+
+}  // namespace ptn
+
+struct ptn_plan {
+    int32_t n_qubits = 0;
+    int32_t n_sites = 0;
+    std::vector<ptn::LeafInfo> leaves;
+    int32_t n_var_cols = 0;
+    std::vector<float> var_table;        // complex64 interleaved (re, im)
+    std::vector<ptn::SiteTable> site_tables;
+    std::vector<ptn::BlockPlan> blocks;
+    std::vector<int32_t> leaf_site_ptr;  // CSR over leaves with var_col >= 0 (by column)
+    std::vector<int32_t> leaf_site_idx;
+    std::vector<int32_t> leaf_site_mul;
+    ptn_plan_opts opts{};
+    double plan_seconds = 0;
+    // device state (uploaded lazily)
+    int device = -1;
+    float* d_var_table = nullptr;
+    ptn::SiteTable* d_site_tables = nullptr;
+    int32_t* d_leaf_site_ptr = nullptr;
+    int32_t* d_leaf_site_idx = nullptr;
+    int32_t* d_leaf_site_mul = nullptr;
+    double mem_cap = 0;
+};
+
+namespace ptn {
+// planner.cpp
+ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* block_sizes,
+                      int32_t n_blocks, const ptn_plan_opts* o, ptn_plan* plan);
+std::string describe_plan(const ptn_plan* plan, int detail);
+// errors.cpp
+ptn_status set_error(ptn_status s, const char* fmt, ...);
+}  // namespace ptn

@@ -1,0 +1,725 @@
+// C-ABI entry points and the device runtime of the PTSBE hot path.
+//
+// Execution of a block (Sec. III-A/B): the networks of a level (one per
+// distinct (trajectory, prefix), grouped by trajectory) are split into chunks
+// that fit the memory cap; for every chunk the block's step list runs once,
+// each step a single launch over all instances of its storage class (every
+// distinct trajectory of the chunk for trajectory-only tensors, every network
+// for prefix-dependent ones), then the root tensor is finalised into the
+// networks' marginals.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace ptn {
+const char* last_error_text();
+void clear_error();
+}  // namespace ptn
+
+using namespace ptn;
+
+#define PTN_CUDA(call)                                                                                 \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return set_error(e_ == cudaErrorMemoryAllocation ? PTN_ERR_OOM : PTN_ERR_CUDA, "%s: %s (%s:%d)", \
+                             #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+    } while (0)
+
+static_assert(sizeof(StepDesc) % 16 == 0, "StepDesc must be a multiple of 16 bytes");
+static_assert(sizeof(RootRef) % 16 == 0, "RootRef must be a multiple of 16 bytes");
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    ptn_status grow(size_t bytes) {
+        if (bytes <= cap) return PTN_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, (size_t)256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return set_error(PTN_ERR_OOM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+        }
+        cap = want;
+        return PTN_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct HostBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    ptn_status grow(size_t bytes) {
+        if (bytes <= cap) return PTN_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMallocHost(&p, std::max(bytes, (size_t)256));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return set_error(PTN_ERR_OOM, "cudaMallocHost(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+        cap = std::max(bytes, (size_t)256);
+        return PTN_OK;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace
+
+// Per-plan device workspace (calls that use the same plan must not overlap).
+struct PlanWorkspace {
+    DevBuf arena[3];
+    DevBuf chunk_traj, net_tl, roots;
+    DevBuf marg, Z, w, cdf, m;
+    DevBuf lvl_traj[2], lvl_prefix[2], lvl_count[2];
+    DevBuf s_cap, s_tmp_off, s_rank0, s_excl, s_first, s_ndist, s_out_off, s_tmp_x, s_tmp_c, s_scan;
+    DevBuf zero_prefix;
+    HostBuf h_traj, h_chunk_traj, h_net_tl, h_small;
+    void release() {
+        DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &roots, &marg, &Z, &w, &cdf, &m,
+                         &lvl_traj[0], &lvl_traj[1], &lvl_prefix[0], &lvl_prefix[1], &lvl_count[0], &lvl_count[1],
+                         &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
+                         &s_tmp_c, &s_scan, &zero_prefix};
+        for (DevBuf* b : all) b->release();
+        h_traj.release();
+        h_chunk_traj.release();
+        h_net_tl.release();
+        h_small.release();
+    }
+};
+
+struct ptn_traj {
+    int64_t n_orig = 0, n_unique = 0;
+    int32_t n_sites = 0;
+    int32_t n_var_cols = 0;
+    uint8_t* kraus = nullptr;
+    double* logq = nullptr;
+    int64_t* mult = nullptr;
+    int64_t* first = nullptr;
+    int32_t* var_ids = nullptr;
+    const ptn_plan* plan = nullptr;
+};
+
+struct ptn_shots {
+    int64_t n = 0;
+    int32_t* traj = nullptr;
+    uint64_t* bits = nullptr;
+    int64_t* count = nullptr;
+    std::vector<int64_t> nets_per_block;
+};
+
+namespace {
+
+PlanWorkspace* workspace(const ptn_plan* plan);
+
+ptn_status ensure_device(const ptn_plan* cplan) {
+    ptn_plan* plan = const_cast<ptn_plan*>(cplan);
+    int dev = -1;
+    PTN_CUDA(cudaGetDevice(&dev));
+    if (plan->device == dev) return PTN_OK;
+    if (plan->device >= 0) return set_error(PTN_ERR_INVALID_ARG, "plan was uploaded to device %d, current is %d", plan->device, dev);
+    size_t vt_bytes = plan->var_table.size() * sizeof(float);
+    PTN_CUDA(cudaMalloc(&plan->d_var_table, std::max(vt_bytes, (size_t)16)));
+    PTN_CUDA(cudaMemcpy(plan->d_var_table, plan->var_table.data(), vt_bytes, cudaMemcpyHostToDevice));
+    size_t st_bytes = plan->site_tables.size() * sizeof(SiteTable);
+    PTN_CUDA(cudaMalloc(&plan->d_site_tables, std::max(st_bytes, (size_t)16)));
+    if (st_bytes) PTN_CUDA(cudaMemcpy(plan->d_site_tables, plan->site_tables.data(), st_bytes, cudaMemcpyHostToDevice));
+    auto up32 = [&](const std::vector<int32_t>& v, int32_t** d) -> ptn_status {
+        size_t by = std::max(v.size() * sizeof(int32_t), (size_t)16);
+        PTN_CUDA(cudaMalloc(d, by));
+        if (!v.empty()) PTN_CUDA(cudaMemcpy(*d, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        return PTN_OK;
+    };
+    ptn_status e;
+    if ((e = up32(plan->leaf_site_ptr, &plan->d_leaf_site_ptr))) return e;
+    if ((e = up32(plan->leaf_site_idx, &plan->d_leaf_site_idx))) return e;
+    if ((e = up32(plan->leaf_site_mul, &plan->d_leaf_site_mul))) return e;
+    for (auto& bp : plan->blocks) {
+        size_t by = bp.steps.size() * sizeof(StepDesc);
+        PTN_CUDA(cudaMalloc(&bp.d_steps, std::max(by, (size_t)16)));
+        if (by) PTN_CUDA(cudaMemcpy(bp.d_steps, bp.steps.data(), by, cudaMemcpyHostToDevice));
+    }
+    PlanWorkspace* ws = workspace(plan);
+    if ((e = ws->roots.grow(sizeof(RootRef) * plan->blocks.size()))) return e;
+    std::vector<RootRef> roots;
+    for (auto& bp : plan->blocks) roots.push_back(bp.root);
+    PTN_CUDA(cudaMemcpy(ws->roots.p, roots.data(), sizeof(RootRef) * roots.size(), cudaMemcpyHostToDevice));
+    if (plan->mem_cap <= 0) {
+        size_t fr = 0, tot = 0;
+        PTN_CUDA(cudaMemGetInfo(&fr, &tot));
+        plan->mem_cap = 0.4 * (double)fr;
+    }
+    plan->device = dev;
+    return PTN_OK;
+}
+
+// workspace storage keyed by plan (kept outside the public struct)
+struct WsEntry {
+    const ptn_plan* plan;
+    PlanWorkspace* ws;
+};
+std::vector<WsEntry>& ws_table() {
+    static std::vector<WsEntry> t;
+    return t;
+}
+PlanWorkspace* workspace(const ptn_plan* plan) {
+    for (auto& e : ws_table())
+        if (e.plan == plan) return e.ws;
+    PlanWorkspace* w = new PlanWorkspace();
+    ws_table().push_back({plan, w});
+    return w;
+}
+void drop_workspace(const ptn_plan* plan) {
+    auto& t = ws_table();
+    for (size_t i = 0; i < t.size(); i++)
+        if (t[i].plan == plan) {
+            t[i].ws->release();
+            delete t[i].ws;
+            t.erase(t.begin() + i);
+            return;
+        }
+}
+
+struct Chunk {
+    int64_t net0, n_net;     // networks [net0, net0 + n_net)
+    int64_t traj0, n_traj;   // entries [traj0, traj0 + n_traj) of the chunk_traj list
+};
+
+// Contract n_net networks of block j; marg/Z outputs are device arrays.
+ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const int32_t* d_net_traj,
+                          const uint64_t* d_net_prefix, int64_t n_net, float* marg, double* Z, int max_traj_chunk,
+                          cudaStream_t s) {
+    if (n_net <= 0) return PTN_OK;
+    PlanWorkspace* ws = workspace(plan);
+    const BlockPlan& bp = plan->blocks[j];
+    ptn_status e;
+    // host copy of the trajectory index of every network
+    if ((e = ws->h_traj.grow(sizeof(int32_t) * n_net))) return e;
+    PTN_CUDA(cudaMemcpyAsync(ws->h_traj.p, d_net_traj, sizeof(int32_t) * n_net, cudaMemcpyDeviceToHost, s));
+    PTN_CUDA(cudaStreamSynchronize(s));
+    const int32_t* ht = ws->h_traj.as<int32_t>();
+    for (int64_t i = 0; i < n_net; i++) {
+        if (ht[i] < 0 || ht[i] >= tr->n_unique)
+            return set_error(PTN_ERR_INVALID_ARG, "net_traj[%lld] = %d out of range", (long long)i, ht[i]);
+        if (i && ht[i] < ht[i - 1]) return set_error(PTN_ERR_INVALID_ARG, "net_traj must be non-decreasing");
+    }
+    // chunking against the memory cap
+    const double bT = 8.0 * (double)bp.arena_peak[CLS_TRAJ];
+    const double bN = 8.0 * (double)bp.arena_peak[CLS_NET] + 4.0 + 8.0;
+    const double bC = 8.0 * (double)bp.arena_peak[CLS_CONST];
+    const double cap = plan->mem_cap;
+    if (bC + bT + bN > cap)
+        return set_error(PTN_ERR_TOO_LARGE, "block %d needs %.3g bytes for one network (cap %.3g)", j, bC + bT + bN, cap);
+    std::vector<Chunk> chunks;
+    if ((e = ws->h_chunk_traj.grow(sizeof(int32_t) * n_net))) return e;
+    if ((e = ws->h_net_tl.grow(sizeof(int32_t) * n_net))) return e;
+    int32_t* hct = ws->h_chunk_traj.as<int32_t>();
+    int32_t* htl = ws->h_net_tl.as<int32_t>();
+    int64_t n_ct = 0;
+    {
+        Chunk c{0, 0, 0, 0};
+        int64_t i = 0;
+        while (i < n_net) {
+            int64_t k = i;
+            while (k < n_net && ht[k] == ht[i]) k++;
+            int64_t run = k - i;   // networks of trajectory ht[i]
+            int64_t done = 0;
+            while (done < run) {
+                bool traj_limit = max_traj_chunk > 0 && c.n_traj >= max_traj_chunk;
+                double room = cap - bC - bT * (double)(c.n_traj + 1) - bN * (double)c.n_net;
+                int64_t fit = room > 0 ? (int64_t)(room / bN) : 0;
+                if (traj_limit || fit <= 0) {
+                    if (c.n_net == 0) return set_error(PTN_ERR_TOO_LARGE, "block %d: no room for one network", j);
+                    chunks.push_back(c);
+                    c = Chunk{c.net0 + c.n_net, 0, n_ct, 0};
+                    continue;
+                }
+                int64_t take = std::min(fit, run - done);
+                hct[n_ct] = ht[i];
+                for (int64_t q = 0; q < take; q++) htl[c.net0 + c.n_net + q] = (int32_t)c.n_traj;
+                n_ct++;
+                c.n_traj++;
+                c.n_net += take;
+                done += take;
+            }
+            i = k;
+        }
+        if (c.n_net) chunks.push_back(c);
+    }
+    if ((e = ws->chunk_traj.grow(sizeof(int32_t) * n_ct))) return e;
+    if ((e = ws->net_tl.grow(sizeof(int32_t) * n_net))) return e;
+    PTN_CUDA(cudaMemcpyAsync(ws->chunk_traj.p, hct, sizeof(int32_t) * n_ct, cudaMemcpyHostToDevice, s));
+    PTN_CUDA(cudaMemcpyAsync(ws->net_tl.p, htl, sizeof(int32_t) * n_net, cudaMemcpyHostToDevice, s));
+    int64_t max_t = 0, max_n = 0;
+    for (auto& c : chunks) {
+        max_t = std::max(max_t, c.n_traj);
+        max_n = std::max(max_n, c.n_net);
+    }
+    if ((e = ws->arena[CLS_CONST].grow((size_t)(bC + 16)))) return e;
+    if ((e = ws->arena[CLS_TRAJ].grow((size_t)(bT * max_t + 16)))) return e;
+    if ((e = ws->arena[CLS_NET].grow((size_t)(8.0 * bp.arena_peak[CLS_NET] * max_n + 16)))) return e;
+    const RootRef* d_root = ws->roots.as<RootRef>() + j;
+    for (const Chunk& c : chunks) {
+        ChunkCtx ctx;
+        ctx.vtab = reinterpret_cast<const float2*>(plan->d_var_table);
+        ctx.var_ids = tr->var_ids;
+        ctx.n_var_cols = tr->n_var_cols;
+        ctx.pad = 0;
+        ctx.chunk_traj = ws->chunk_traj.as<int32_t>() + c.traj0;
+        ctx.net_tl = ws->net_tl.as<int32_t>() + c.net0;
+        ctx.net_prefix = d_net_prefix + c.net0;
+        for (int a = 0; a < 3; a++) ctx.arena[a] = ws->arena[a].as<float2>();
+        ctx.arena_inst[CLS_CONST] = 1;
+        ctx.arena_inst[CLS_TRAJ] = c.n_traj;
+        ctx.arena_inst[CLS_NET] = c.n_net;
+        for (size_t st = 0; st < bp.steps.size(); st++) {
+            const StepDesc& h = bp.steps[st];
+            int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
+            launch_contract_step(bp.d_steps + st, h, ctx, ni, s);
+        }
+        launch_finalize(d_root, ctx, bp.b, c.n_net, marg + c.net0 * ((int64_t)1 << bp.b), Z + c.net0, s);
+    }
+    PTN_CUDA(cudaGetLastError());
+    return PTN_OK;
+}
+
+}  // namespace
+
+// ====================================================================== API ==
+extern "C" {
+
+const char* ptn_version(void) { return "ptn 0.1 (sm_103a)"; }
+
+const char* ptn_status_string(ptn_status s) {
+    switch (s) {
+        case PTN_OK: return "PTN_OK";
+        case PTN_ERR_INVALID_ARG: return "PTN_ERR_INVALID_ARG";
+        case PTN_ERR_NOT_CPTP: return "PTN_ERR_NOT_CPTP";
+        case PTN_ERR_TOO_LARGE: return "PTN_ERR_TOO_LARGE";
+        case PTN_ERR_OOM: return "PTN_ERR_OOM";
+        case PTN_ERR_CUDA: return "PTN_ERR_CUDA";
+        case PTN_ERR_TIMEOUT: return "PTN_ERR_TIMEOUT";
+        case PTN_ERR_UNSUPPORTED: return "PTN_ERR_UNSUPPORTED";
+    }
+    return "PTN_UNKNOWN_STATUS";
+}
+
+const char* ptn_last_error(void) { return last_error_text(); }
+
+ptn_status ptn_plan_path(const ptn_circuit* circuit, const ptn_noise* noise, const int32_t* block_sizes,
+                         int32_t n_blocks, const ptn_plan_opts* opts, ptn_plan** plan_out) {
+    clear_error();
+    if (!plan_out) return set_error(PTN_ERR_INVALID_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    ptn_plan* p = new (std::nothrow) ptn_plan();
+    if (!p) return set_error(PTN_ERR_OOM, "host allocation failed");
+    ptn_status s;
+    try {
+        s = build_plan(circuit, noise, block_sizes, n_blocks, opts, p);
+    } catch (const std::bad_alloc&) {
+        s = set_error(PTN_ERR_OOM, "host allocation failed while planning");
+    }
+    if (s != PTN_OK) {
+        delete p;
+        return s;
+    }
+    *plan_out = p;
+    return PTN_OK;
+}
+
+ptn_status ptn_plan_describe(const ptn_plan* plan, int32_t detail, char* buf, size_t cap, size_t* len) {
+    if (!plan) return set_error(PTN_ERR_INVALID_ARG, "plan is NULL");
+    std::string d = describe_plan(plan, detail);
+    if (len) *len = d.size();
+    if (buf && cap) {
+        size_t n = std::min(cap - 1, d.size());
+        memcpy(buf, d.data(), n);
+        buf[n] = 0;
+    }
+    return PTN_OK;
+}
+
+void ptn_plan_destroy(ptn_plan* plan) {
+    if (!plan) return;
+    drop_workspace(plan);
+    if (plan->device >= 0) {
+        cudaFree(plan->d_var_table);
+        cudaFree(plan->d_site_tables);
+        cudaFree(plan->d_leaf_site_ptr);
+        cudaFree(plan->d_leaf_site_idx);
+        cudaFree(plan->d_leaf_site_mul);
+        for (auto& b : plan->blocks) cudaFree(b.d_steps);
+    }
+    delete plan;
+}
+
+ptn_status ptn_presample_trajectories(const ptn_plan* plan, uint64_t seed, int32_t circuit_id, int64_t n_traj,
+                                      int32_t dedup, ptn_traj** traj_out, ptn_stream stream) {
+    clear_error();
+    if (!plan || !traj_out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    *traj_out = nullptr;
+    if (n_traj < 1 || n_traj > (1 << 24)) return set_error(PTN_ERR_INVALID_ARG, "n_traj %lld out of 1..2^24", (long long)n_traj);
+    if (dedup && n_traj > (1 << 17)) return set_error(PTN_ERR_UNSUPPORTED, "dedup supports up to 2^17 trajectories");
+    ptn_status e = ensure_device(plan);
+    if (e) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t S = plan->n_sites;
+    ptn_traj* t = new ptn_traj();
+    t->plan = plan;
+    t->n_orig = n_traj;
+    t->n_sites = S;
+    t->n_var_cols = plan->n_var_cols;
+    uint8_t* kraus = nullptr;
+    double* logq = nullptr;
+    auto fail = [&](ptn_status st) {
+        cudaFree(kraus);
+        cudaFree(logq);
+        cudaFree(t->kraus);
+        cudaFree(t->logq);
+        cudaFree(t->mult);
+        cudaFree(t->first);
+        cudaFree(t->var_ids);
+        delete t;
+        return st;
+    };
+#define TRY_CUDA(call)                                                                                     \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail(set_error(e_ == cudaErrorMemoryAllocation ? PTN_ERR_OOM : PTN_ERR_CUDA, "%s: %s", \
+                                  #call, cudaGetErrorString(e_)));                                         \
+    } while (0)
+    TRY_CUDA(cudaMalloc(&kraus, std::max<size_t>((size_t)n_traj * S, 16)));
+    TRY_CUDA(cudaMalloc(&logq, sizeof(double) * n_traj));
+    launch_presample(plan->d_site_tables, S, n_traj, seed, circuit_id, kraus, logq, s);
+    TRY_CUDA(cudaGetLastError());
+    if (!dedup) {
+        t->n_unique = n_traj;
+        t->kraus = kraus;
+        t->logq = logq;
+        kraus = nullptr;
+        logq = nullptr;
+        TRY_CUDA(cudaMalloc(&t->mult, sizeof(int64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&t->first, sizeof(int64_t) * n_traj));
+        launch_fill_i64(t->mult, 1, n_traj, s);
+        // first = identity
+        std::vector<int64_t> id(n_traj);
+        for (int64_t i = 0; i < n_traj; i++) id[i] = i;
+        TRY_CUDA(cudaMemcpyAsync(t->first, id.data(), sizeof(int64_t) * n_traj, cudaMemcpyHostToDevice, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+    } else {
+        uint64_t* h = nullptr;
+        int64_t *first = nullptr, *flags = nullptr, *uid = nullptr, *tmp = nullptr;
+        int64_t n_u = 0;
+        TRY_CUDA(cudaMalloc(&h, sizeof(uint64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&first, sizeof(int64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&flags, sizeof(int64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&uid, sizeof(int64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&tmp, sizeof(int64_t) * scan_tmp_elems(n_traj)));
+        launch_row_hash(kraus, n_traj, S, h, s);
+        launch_first_occurrence(kraus, h, n_traj, S, first, s);
+        launch_flags_first(first, n_traj, flags, s);
+        launch_exclusive_scan(flags, uid, n_traj, tmp, s);
+        int64_t last[2];
+        TRY_CUDA(cudaMemcpyAsync(&last[0], uid + n_traj - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaMemcpyAsync(&last[1], flags + n_traj - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        n_u = last[0] + last[1];
+        t->n_unique = n_u;
+        TRY_CUDA(cudaMalloc(&t->kraus, std::max<size_t>((size_t)n_u * S, 16)));
+        TRY_CUDA(cudaMalloc(&t->logq, sizeof(double) * n_u));
+        TRY_CUDA(cudaMalloc(&t->mult, sizeof(int64_t) * n_u));
+        TRY_CUDA(cudaMalloc(&t->first, sizeof(int64_t) * n_u));
+        TRY_CUDA(cudaMemsetAsync(t->mult, 0, sizeof(int64_t) * n_u, s));
+        launch_dedup_compact(kraus, logq, first, uid, n_traj, S, t->kraus, t->logq, t->mult, t->first, s);
+        TRY_CUDA(cudaStreamSynchronize(s));
+        cudaFree(h);
+        cudaFree(first);
+        cudaFree(flags);
+        cudaFree(uid);
+        cudaFree(tmp);
+        cudaFree(kraus);
+        cudaFree(logq);
+        kraus = nullptr;
+        logq = nullptr;
+    }
+    TRY_CUDA(cudaMalloc(&t->var_ids, std::max<size_t>(sizeof(int32_t) * t->n_unique * std::max(1, plan->n_var_cols), 16)));
+    launch_var_ids(t->kraus, t->n_unique, S, plan->d_leaf_site_ptr, plan->d_leaf_site_idx, plan->d_leaf_site_mul,
+                   plan->n_var_cols, t->var_ids, s);
+    TRY_CUDA(cudaGetLastError());
+#undef TRY_CUDA
+    *traj_out = t;
+    return PTN_OK;
+}
+
+ptn_status ptn_traj_info(const ptn_traj* t, int64_t* n_unique, int32_t* n_sites, const uint8_t** kraus,
+                         const double** logq, const int64_t** mult, const int64_t** first) {
+    if (!t) return set_error(PTN_ERR_INVALID_ARG, "traj is NULL");
+    if (n_unique) *n_unique = t->n_unique;
+    if (n_sites) *n_sites = t->n_sites;
+    if (kraus) *kraus = t->kraus;
+    if (logq) *logq = t->logq;
+    if (mult) *mult = t->mult;
+    if (first) *first = t->first;
+    return PTN_OK;
+}
+
+ptn_status ptn_traj_copy(const ptn_traj* t, uint8_t* kraus_out, double* logq_out, int64_t* mult_out,
+                         int64_t* first_out, ptn_stream stream) {
+    if (!t) return set_error(PTN_ERR_INVALID_ARG, "traj is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = t->n_unique;
+    if (kraus_out && n * t->n_sites)
+        PTN_CUDA(cudaMemcpyAsync(kraus_out, t->kraus, (size_t)n * t->n_sites, cudaMemcpyDeviceToDevice, s));
+    if (logq_out) PTN_CUDA(cudaMemcpyAsync(logq_out, t->logq, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (mult_out) PTN_CUDA(cudaMemcpyAsync(mult_out, t->mult, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s));
+    if (first_out) PTN_CUDA(cudaMemcpyAsync(first_out, t->first, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s));
+    return PTN_OK;
+}
+
+void ptn_traj_destroy(ptn_traj* t) {
+    if (!t) return;
+    cudaFree(t->kraus);
+    cudaFree(t->logq);
+    cudaFree(t->mult);
+    cudaFree(t->first);
+    cudaFree(t->var_ids);
+    delete t;
+}
+
+ptn_status ptn_contract_batch(const ptn_plan* plan, const ptn_traj* traj, int32_t block, const int32_t* net_traj,
+                              const uint64_t* net_prefix, int64_t n_net, int32_t precision, float* marg_out,
+                              double* Z_out, ptn_stream stream) {
+    clear_error();
+    if (!plan || !traj || (n_net > 0 && (!net_traj || !net_prefix || !marg_out || !Z_out)))
+        return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    if (traj->plan != plan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
+    if (block < 0 || block >= (int32_t)plan->blocks.size()) return set_error(PTN_ERR_INVALID_ARG, "bad block %d", block);
+    if (precision != PTN_PREC_FP32) return set_error(PTN_ERR_UNSUPPORTED, "precision mode %d not built yet", precision);
+    if (n_net < 0) return set_error(PTN_ERR_INVALID_ARG, "n_net < 0");
+    ptn_status e = ensure_device(plan);
+    if (e) return e;
+    return contract_level(plan, traj, block, net_traj, net_prefix, n_net, marg_out, Z_out, 0, (cudaStream_t)stream);
+}
+
+ptn_status ptn_allocate_shots(const double* weights, int64_t n, int64_t total, uint64_t seed, int32_t circuit_id,
+                              int64_t* m_out, ptn_stream stream) {
+    clear_error();
+    if (!weights || !m_out || n < 1 || total < 0) return set_error(PTN_ERR_INVALID_ARG, "bad allocation arguments");
+    double* cdf = nullptr;
+    PTN_CUDA(cudaMallocAsync((void**)&cdf, sizeof(double) * n, (cudaStream_t)stream));
+    launch_alloc_shots(weights, n, total, seed, circuit_id, cdf, m_out, (cudaStream_t)stream);
+    PTN_CUDA(cudaFreeAsync(cdf, (cudaStream_t)stream));
+    PTN_CUDA(cudaGetLastError());
+    return PTN_OK;
+}
+
+static ptn_status alloc_sample_scratch(PlanWorkspace* ws, int64_t n_parent, int64_t n_traj, int64_t child_cap,
+                                       SampleScratch& sc) {
+    ptn_status e;
+    size_t np = sizeof(int64_t) * std::max<int64_t>(n_parent, 1);
+    if ((e = ws->s_cap.grow(np)) || (e = ws->s_tmp_off.grow(np)) || (e = ws->s_rank0.grow(np)) ||
+        (e = ws->s_excl.grow(np)) || (e = ws->s_ndist.grow(np)) || (e = ws->s_out_off.grow(np)) ||
+        (e = ws->s_first.grow(sizeof(int64_t) * std::max<int64_t>(n_traj, 1))) ||
+        (e = ws->s_tmp_x.grow(sizeof(int32_t) * std::max<int64_t>(child_cap, 1))) ||
+        (e = ws->s_tmp_c.grow(sizeof(int64_t) * std::max<int64_t>(child_cap, 1))) ||
+        (e = ws->s_scan.grow(sizeof(int64_t) * scan_tmp_elems(std::max<int64_t>(n_parent, 1)))))
+        return e;
+    sc.cap = ws->s_cap.as<int64_t>();
+    sc.tmp_off = ws->s_tmp_off.as<int64_t>();
+    sc.rank0 = ws->s_rank0.as<int64_t>();
+    sc.excl = ws->s_excl.as<int64_t>();
+    sc.first = ws->s_first.as<int64_t>();
+    sc.ndist = ws->s_ndist.as<int64_t>();
+    sc.out_off = ws->s_out_off.as<int64_t>();
+    sc.tmp_x = ws->s_tmp_x.as<int32_t>();
+    sc.tmp_c = ws->s_tmp_c.as<int64_t>();
+    sc.scan_tmp = ws->s_scan.as<int64_t>();
+    return PTN_OK;
+}
+
+// Scratch for the standalone sampling entry point (not tied to a plan).
+static PlanWorkspace* standalone_ws() {
+    static PlanWorkspace ws;
+    return &ws;
+}
+
+ptn_status ptn_sample_block(const float* marg, int32_t b, int32_t start, const int32_t* parent_traj,
+                            const uint64_t* parent_prefix, const int64_t* parent_count, int64_t n_parent,
+                            uint64_t seed, int32_t circuit_id, int32_t block, int32_t* child_traj,
+                            uint64_t* child_prefix, int64_t* child_count, int64_t child_cap, int64_t* n_child,
+                            ptn_stream stream) {
+    clear_error();
+    if (!n_child || b < 1 || b > 14 || start < 0 || start + b > 64 || n_parent < 0)
+        return set_error(PTN_ERR_INVALID_ARG, "bad sampling arguments (b must be 1..14)");
+    *n_child = 0;
+    if (n_parent == 0) return PTN_OK;
+    if (!marg || !parent_traj || !parent_prefix || !parent_count || !child_traj || !child_prefix || !child_count)
+        return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    // trajectory ids bound the "first parent" table
+    std::vector<int32_t> ht(n_parent);
+    PTN_CUDA(cudaMemcpyAsync(ht.data(), parent_traj, sizeof(int32_t) * n_parent, cudaMemcpyDeviceToHost, s));
+    PTN_CUDA(cudaStreamSynchronize(s));
+    int32_t tmax = 0;
+    for (int64_t i = 0; i < n_parent; i++) {
+        if (ht[i] < 0) return set_error(PTN_ERR_INVALID_ARG, "negative trajectory index");
+        if (i && ht[i] < ht[i - 1]) return set_error(PTN_ERR_INVALID_ARG, "parents must be grouped by trajectory");
+        tmax = std::max(tmax, ht[i]);
+    }
+    PlanWorkspace* ws = standalone_ws();
+    SampleScratch sc;
+    ptn_status e = alloc_sample_scratch(ws, n_parent, (int64_t)tmax + 1, child_cap, sc);
+    if (e) return e;
+    if ((e = ws->h_small.grow(64))) return e;
+    ptn_status st;
+    int64_t nc = run_sample_block(marg, b, start, parent_traj, parent_prefix, parent_count, n_parent,
+                                  (int64_t)tmax + 1, seed, circuit_id, block, child_traj, child_prefix, child_count,
+                                  child_cap, sc, ws->h_small.as<int64_t>(), s, &st);
+    if (st != PTN_OK) return st;
+    PTN_CUDA(cudaGetLastError());
+    *n_child = nc;
+    return PTN_OK;
+}
+
+ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const ptn_sample_opts* o,
+                            ptn_shots** shots_out, ptn_stream stream) {
+    clear_error();
+    if (!plan || !traj || !o || !shots_out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    *shots_out = nullptr;
+    if (traj->plan != plan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
+    if (o->precision != PTN_PREC_FP32) return set_error(PTN_ERR_UNSUPPORTED, "precision mode %d not built yet", o->precision);
+    if (o->mode != PTN_PROPORTIONAL_FIXED && o->mode != PTN_PROPORTIONAL_TOTAL)
+        return set_error(PTN_ERR_UNSUPPORTED, "sampling mode %d", o->mode);
+    int64_t total_cap;
+    if (o->mode == PTN_PROPORTIONAL_FIXED) {
+        if (o->shots_per_traj < 1) return set_error(PTN_ERR_INVALID_ARG, "shots_per_traj must be >= 1");
+        total_cap = o->shots_per_traj * traj->n_orig;
+    } else {
+        if (o->total_shots < 1) return set_error(PTN_ERR_INVALID_ARG, "total_shots must be >= 1");
+        total_cap = o->total_shots;
+    }
+    ptn_status e = ensure_device(plan);
+    if (e) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    PlanWorkspace* ws = workspace(plan);
+    const int64_t E = traj->n_unique;
+    const int64_t lvl_cap = std::max(E, total_cap);
+    for (int k = 0; k < 2; k++) {
+        if ((e = ws->lvl_traj[k].grow(sizeof(int32_t) * lvl_cap)) || (e = ws->lvl_prefix[k].grow(sizeof(uint64_t) * lvl_cap)) ||
+            (e = ws->lvl_count[k].grow(sizeof(int64_t) * lvl_cap)))
+            return e;
+    }
+    if ((e = ws->h_small.grow(64))) return e;
+    int cur = 0;
+    int64_t n = E;
+    launch_iota_i32(ws->lvl_traj[0].as<int32_t>(), E, s);
+    PTN_CUDA(cudaMemsetAsync(ws->lvl_prefix[0].p, 0, sizeof(uint64_t) * E, s));
+    if (o->mode == PTN_PROPORTIONAL_FIXED) launch_scale_i64(traj->mult, o->shots_per_traj, E, ws->lvl_count[0].as<int64_t>(), s);
+    std::vector<int64_t> nets;
+    for (size_t j = 0; j < plan->blocks.size() && n > 0; j++) {
+        const BlockPlan& bp = plan->blocks[j];
+        const int64_t nb = (int64_t)1 << bp.b;
+        if ((e = ws->marg.grow(sizeof(float) * n * nb)) || (e = ws->Z.grow(sizeof(double) * n))) return e;
+        e = contract_level(plan, traj, (int)j, ws->lvl_traj[cur].as<int32_t>(), ws->lvl_prefix[cur].as<uint64_t>(), n,
+                           ws->marg.as<float>(), ws->Z.as<double>(), o->max_traj_per_chunk, s);
+        if (e) return e;
+        if (j == 0 && o->mode == PTN_PROPORTIONAL_TOTAL) {
+            if ((e = ws->w.grow(sizeof(double) * E)) || (e = ws->cdf.grow(sizeof(double) * E))) return e;
+            launch_mult_times_z(traj->mult, ws->Z.as<double>(), E, ws->w.as<double>(), s);
+            launch_alloc_shots(ws->w.as<double>(), E, o->total_shots, o->seed, o->circuit_id, ws->cdf.as<double>(),
+                               ws->lvl_count[cur].as<int64_t>(), s);
+        }
+        SampleScratch sc;
+        if ((e = alloc_sample_scratch(ws, n, E, total_cap, sc))) return e;
+        ptn_status st;
+        int64_t nc = run_sample_block(ws->marg.as<float>(), bp.b, bp.start, ws->lvl_traj[cur].as<int32_t>(),
+                                      ws->lvl_prefix[cur].as<uint64_t>(), ws->lvl_count[cur].as<int64_t>(), n, E,
+                                      o->seed, o->circuit_id, (int)j, ws->lvl_traj[1 - cur].as<int32_t>(),
+                                      ws->lvl_prefix[1 - cur].as<uint64_t>(), ws->lvl_count[1 - cur].as<int64_t>(),
+                                      lvl_cap, sc, ws->h_small.as<int64_t>(), s, &st);
+        if (st != PTN_OK) return st;
+        nets.push_back(n);
+        cur = 1 - cur;
+        n = nc;
+    }
+    ptn_shots* r = new ptn_shots();
+    r->n = n;
+    r->nets_per_block = nets;
+    size_t m = std::max<int64_t>(n, 1);
+    cudaError_t ce;
+    if ((ce = cudaMalloc(&r->traj, sizeof(int32_t) * m)) != cudaSuccess || (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * m)) != cudaSuccess ||
+        (ce = cudaMalloc(&r->count, sizeof(int64_t) * m)) != cudaSuccess) {
+        cudaFree(r->traj);
+        cudaFree(r->bits);
+        cudaFree(r->count);
+        delete r;
+        return set_error(PTN_ERR_OOM, "result allocation: %s", cudaGetErrorString(ce));
+    }
+    if (n > 0) {
+        PTN_CUDA(cudaMemcpyAsync(r->traj, ws->lvl_traj[cur].p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        PTN_CUDA(cudaMemcpyAsync(r->bits, ws->lvl_prefix[cur].p, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+        PTN_CUDA(cudaMemcpyAsync(r->count, ws->lvl_count[cur].p, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    PTN_CUDA(cudaGetLastError());
+    *shots_out = r;
+    return PTN_OK;
+}
+
+ptn_status ptn_shots_info(const ptn_shots* r, int64_t* n_out, const int32_t** traj, const uint64_t** bits,
+                          const int64_t** count, int64_t* nets_per_block, int32_t cap_blocks) {
+    if (!r) return set_error(PTN_ERR_INVALID_ARG, "shots is NULL");
+    if (n_out) *n_out = r->n;
+    if (traj) *traj = r->traj;
+    if (bits) *bits = r->bits;
+    if (count) *count = r->count;
+    if (nets_per_block)
+        for (int32_t j = 0; j < cap_blocks; j++) nets_per_block[j] = j < (int32_t)r->nets_per_block.size() ? r->nets_per_block[j] : 0;
+    return PTN_OK;
+}
+
+ptn_status ptn_shots_copy(const ptn_shots* r, int32_t* traj_out, uint64_t* bits_out, int64_t* count_out,
+                          ptn_stream stream) {
+    if (!r) return set_error(PTN_ERR_INVALID_ARG, "shots is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r->n > 0) {
+        if (traj_out) PTN_CUDA(cudaMemcpyAsync(traj_out, r->traj, sizeof(int32_t) * r->n, cudaMemcpyDeviceToDevice, s));
+        if (bits_out) PTN_CUDA(cudaMemcpyAsync(bits_out, r->bits, sizeof(uint64_t) * r->n, cudaMemcpyDeviceToDevice, s));
+        if (count_out) PTN_CUDA(cudaMemcpyAsync(count_out, r->count, sizeof(int64_t) * r->n, cudaMemcpyDeviceToDevice, s));
+    }
+    return PTN_OK;
+}
+
+void ptn_shots_destroy(ptn_shots* r) {
+    if (!r) return;
+    cudaFree(r->traj);
+    cudaFree(r->bits);
+    cudaFree(r->count);
+    delete r;
+}
+
+}  // extern "C"

@@ -1,0 +1,30 @@
+// Kernel launch statistics (see ptn_stats_* in include/ptn.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ptn_internal.h"
+
+namespace ptn {
+
+enum KernelId {
+    K_CONTRACT_DIRECT = 0, K_CONTRACT_GEMM, K_FINALIZE, K_PRESAMPLE, K_LOGQ, K_DEDUP, K_VAR_IDS, K_SCAN,
+    K_ALLOC, K_SAMPLE_PARENTS, K_EMIT, K_MISC, K_COUNT
+};
+
+// Counts one launch of kernel `kid`; with timing on, brackets it with events.
+class StatScope {
+  public:
+    StatScope(int kid, cudaStream_t s, double bytes = 0, double flops = 0);
+    ~StatScope();
+
+  private:
+    int kid_;
+    cudaStream_t s_;
+    bool timing_ = false;
+    void* a_ = nullptr;
+    void* b_ = nullptr;
+    double bytes_ = 0, flops_ = 0;
+};
+
+}  // namespace ptn

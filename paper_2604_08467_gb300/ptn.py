@@ -1,0 +1,328 @@
+"""Thin ctypes binding of libptn (include/ptn.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+converts circuit descriptions into the C structs, passes torch tensors'
+device pointers and the current CUDA stream, and turns status codes into
+exceptions.  The library must be built (``build_lib.build()``); importing the
+binding without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+
+import numpy as np
+
+from . import build_lib
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+PTN_OK = 0
+STATUS_NAMES = {0: "PTN_OK", 1: "PTN_ERR_INVALID_ARG", 2: "PTN_ERR_NOT_CPTP", 3: "PTN_ERR_TOO_LARGE",
+                4: "PTN_ERR_OOM", 5: "PTN_ERR_CUDA", 6: "PTN_ERR_TIMEOUT", 7: "PTN_ERR_UNSUPPORTED"}
+PTN_PREC_FP32, PTN_PREC_BF16X3, PTN_PREC_FP16X3 = 0, 1, 2
+PTN_PROPORTIONAL_FIXED, PTN_PROPORTIONAL_TOTAL = 0, 1
+
+
+class PtnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ptn_gate(C.Structure):
+    _fields_ = [("arity", C.c_int32), ("q0", C.c_int32), ("q1", C.c_int32), ("param_kind", C.c_int32),
+                ("param_index", C.c_int32), ("reserved", C.c_int32), ("mat", C.c_double * 32)]
+
+
+class ptn_circuit(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_gates", C.c_int32), ("gates", C.POINTER(ptn_gate))]
+
+
+class ptn_channel(C.Structure):
+    _fields_ = [("n_kraus", C.c_int32), ("kraus", C.POINTER(C.c_double))]
+
+
+class ptn_site(C.Structure):
+    _fields_ = [("gate", C.c_int32), ("qubit", C.c_int32), ("channel", C.c_int32)]
+
+
+class ptn_noise(C.Structure):
+    _fields_ = [("n_channels", C.c_int32), ("channels", C.POINTER(ptn_channel)), ("n_sites", C.c_int32),
+                ("sites", C.POINTER(ptn_site))]
+
+
+class ptn_plan_opts(C.Structure):
+    _fields_ = [("hypersamples", C.c_int32), ("split_gates", C.c_int32), ("seed", C.c_uint64),
+                ("est_traj", C.c_double), ("est_shots", C.c_double), ("mem_cap_bytes", C.c_double)]
+
+
+class ptn_sample_opts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("circuit_id", C.c_int32), ("shots_per_traj", C.c_int64),
+                ("total_shots", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int32),
+                ("max_traj_per_chunk", C.c_int32), ("use_graphs", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ptn_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("timed_launches", C.c_int64),
+                ("ms", C.c_double), ("alg_bytes", C.c_double), ("alg_flops", C.c_double)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "ptn_plan_path": [C.POINTER(ptn_circuit), C.POINTER(ptn_noise), C.POINTER(C.c_int32), C.c_int32,
+                      C.POINTER(ptn_plan_opts), C.POINTER(_P)],
+    "ptn_plan_describe": [_P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
+    "ptn_plan_destroy": [_P],
+    "ptn_presample_trajectories": [_P, C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.POINTER(_P), _P],
+    "ptn_traj_info": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(_P), C.POINTER(_P),
+                      C.POINTER(_P), C.POINTER(_P)],
+    "ptn_traj_copy": [_P, _P, _P, _P, _P, _P],
+    "ptn_traj_destroy": [_P],
+    "ptn_contract_batch": [_P, _P, C.c_int32, _P, _P, C.c_int64, C.c_int32, _P, _P, _P],
+    "ptn_sample_block": [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_int64, C.c_uint64, C.c_int32, C.c_int32,
+                         _P, _P, _P, C.c_int64, C.POINTER(C.c_int64), _P],
+    "ptn_allocate_shots": [_P, C.c_int64, C.c_int64, C.c_uint64, C.c_int32, _P, _P],
+    "ptn_sample_shots": [_P, _P, C.POINTER(ptn_sample_opts), C.POINTER(_P), _P],
+    "ptn_shots_info": [_P, C.POINTER(C.c_int64), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                       C.POINTER(C.c_int64), C.c_int32],
+    "ptn_shots_copy": [_P, _P, _P, _P, _P],
+    "ptn_shots_destroy": [_P],
+    "ptn_stats_enable": [C.c_int32],
+    "ptn_stats_reset": [],
+    "ptn_stats_read": [C.POINTER(ptn_kernel_stat), C.c_int32, C.POINTER(C.c_int32)],
+    "ptn_status_string": [C.c_int],
+    "ptn_last_error": [],
+    "ptn_version": [],
+}
+_RESTYPE = {"ptn_plan_destroy": None, "ptn_traj_destroy": None, "ptn_shots_destroy": None,
+            "ptn_status_string": C.c_char_p, "ptn_last_error": C.c_char_p, "ptn_version": C.c_char_p}
+
+_lib_handle = None
+
+
+def library_path():
+    return build_lib.LIB
+
+
+def lib():
+    """Load libptn.so (building it first if sources are newer)."""
+    global _lib_handle
+    if _lib_handle is None:
+        path = build_lib.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libptn.so not found at {path}")
+        h = C.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(h, name)
+            f.argtypes = args
+            f.restype = _RESTYPE.get(name, C.c_int)
+        _lib_handle = h
+    return _lib_handle
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(status):
+    if status != PTN_OK:
+        raise PtnError(status, lib().ptn_last_error().decode())
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else int(t.data_ptr()))
+
+
+# ------------------------------------------------------------ marshalling --
+
+def circuit_structs(circ):
+    """workloads.Circuit -> (ptn_circuit, ptn_noise, keepalive)."""
+    n_g = len(circ.gates)
+    gates = (ptn_gate * max(n_g, 1))()
+    for l, g in enumerate(circ.gates):
+        gs = gates[l]
+        gs.arity = g.arity
+        gs.q0 = g.qubits[0]
+        gs.q1 = g.qubits[1] if g.arity == 2 else -1
+        gs.param_kind = int(getattr(g, "param_kind", 0))
+        gs.param_index = int(getattr(g, "param_index", -1))
+        m = np.asarray(g.matrix, dtype=np.complex128).reshape(-1)
+        flat = np.empty(2 * m.size)
+        flat[0::2], flat[1::2] = m.real, m.imag
+        for k, v in enumerate(flat):
+            gs.mat[k] = float(v)
+    c = ptn_circuit(circ.n_qubits, n_g, gates)
+    n_ch = len(circ.channels)
+    chans = (ptn_channel * max(n_ch, 1))()
+    kraus_arrays = []
+    for k, ch in enumerate(circ.channels):
+        arr = np.concatenate([np.stack([np.asarray(K, np.complex128).reshape(-1).real,
+                                        np.asarray(K, np.complex128).reshape(-1).imag], axis=1).reshape(-1)
+                              for K in ch.kraus]).astype(np.float64)
+        kraus_arrays.append(arr)
+        chans[k].n_kraus = len(ch.kraus)
+        chans[k].kraus = arr.ctypes.data_as(C.POINTER(C.c_double))
+    n_s = len(circ.sites)
+    sites = (ptn_site * max(n_s, 1))()
+    for s, st in enumerate(circ.sites):
+        sites[s].gate, sites[s].qubit, sites[s].channel = st.gate, st.qubit, st.channel
+    nz = ptn_noise(n_ch, chans, n_s, sites)
+    return c, nz, (gates, chans, kraus_arrays, sites)
+
+
+# -------------------------------------------------------------- handles ----
+
+class Plan:
+    def __init__(self, handle, n_qubits, block_sizes):
+        self.handle = handle
+        self.n_qubits = n_qubits
+        self.block_sizes = list(block_sizes)
+        s, self.blocks = 0, []
+        for b in self.block_sizes:
+            self.blocks.append((s, b))
+            s += b
+
+    def describe(self, detail=0):
+        n = C.c_size_t(0)
+        _check(lib().ptn_plan_describe(self.handle, detail, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value + 1)
+        _check(lib().ptn_plan_describe(self.handle, detail, buf, n.value + 1, C.byref(n)))
+        return json.loads(buf.value.decode())
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib_handle is not None:
+            _lib_handle.ptn_plan_destroy(self.handle)
+            self.handle = None
+
+
+class Traj:
+    def __init__(self, handle, plan):
+        self.handle = handle
+        self.plan = plan
+        n = C.c_int64(0)
+        S = C.c_int32(0)
+        _check(lib().ptn_traj_info(handle, C.byref(n), C.byref(S), None, None, None, None))
+        self.n_unique = n.value
+        self.n_sites = S.value
+
+    def to_torch(self, stream=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        kr = torch.empty((self.n_unique, self.n_sites), dtype=torch.uint8, device=dev)
+        lq = torch.empty(self.n_unique, dtype=torch.float64, device=dev)
+        mu = torch.empty(self.n_unique, dtype=torch.int64, device=dev)
+        fi = torch.empty(self.n_unique, dtype=torch.int64, device=dev)
+        _check(lib().ptn_traj_copy(self.handle, _ptr(kr), _ptr(lq), _ptr(mu), _ptr(fi), _stream(stream)))
+        return kr, lq, mu, fi
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib_handle is not None:
+            _lib_handle.ptn_traj_destroy(self.handle)
+            self.handle = None
+
+
+class Shots:
+    def __init__(self, handle, n_blocks):
+        self.handle = handle
+        n = C.c_int64(0)
+        nets = (C.c_int64 * max(n_blocks, 1))()
+        _check(lib().ptn_shots_info(handle, C.byref(n), None, None, None, nets, n_blocks))
+        self.n = n.value
+        self.nets_per_block = [nets[j] for j in range(n_blocks)]
+
+    def to_torch(self, stream=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t = torch.empty(self.n, dtype=torch.int32, device=dev)
+        b = torch.empty(self.n, dtype=torch.int64, device=dev)
+        c = torch.empty(self.n, dtype=torch.int64, device=dev)
+        _check(lib().ptn_shots_copy(self.handle, _ptr(t), _ptr(b), _ptr(c), _stream(stream)))
+        return t, b, c
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib_handle is not None:
+            _lib_handle.ptn_shots_destroy(self.handle)
+            self.handle = None
+
+
+# ------------------------------------------------------------------ calls ----
+
+def ptn_plan_path(circ, block_sizes=None, hypersamples=100, split_gates=1, seed=1234, est_traj=1024,
+                  est_shots=1e6, mem_cap_bytes=0.0):
+    c, nz, keep = circuit_structs(circ)
+    if block_sizes is None:
+        n = circ.n_qubits
+        f = -(-n // 10)
+        block_sizes = [10] * (f - 1) + [n - 10 * (f - 1)]
+    bs = (C.c_int32 * len(block_sizes))(*block_sizes)
+    opts = ptn_plan_opts(hypersamples, split_gates, seed, float(est_traj), float(est_shots), float(mem_cap_bytes))
+    h = C.c_void_p()
+    _check(lib().ptn_plan_path(C.byref(c), C.byref(nz), bs, len(block_sizes), C.byref(opts), C.byref(h)))
+    del keep
+    return Plan(h, circ.n_qubits, block_sizes)
+
+
+def ptn_presample_trajectories(plan, seed, n_traj, dedup=False, circuit_id=0, stream=None):
+    h = C.c_void_p()
+    _check(lib().ptn_presample_trajectories(plan.handle, seed, circuit_id, n_traj, int(bool(dedup)),
+                                            C.byref(h), _stream(stream)))
+    return Traj(h, plan)
+
+
+def ptn_contract_batch(plan, traj, block, net_traj, net_prefix, marg_out, Z_out, precision=PTN_PREC_FP32,
+                       stream=None):
+    n = int(net_traj.numel())
+    _check(lib().ptn_contract_batch(plan.handle, traj.handle, block, _ptr(net_traj), _ptr(net_prefix), n,
+                                    precision, _ptr(marg_out), _ptr(Z_out), _stream(stream)))
+
+
+def ptn_sample_block(marg, b, start, parent_traj, parent_prefix, parent_count, seed, circuit_id, block,
+                     child_traj, child_prefix, child_count, stream=None):
+    nc = C.c_int64(0)
+    _check(lib().ptn_sample_block(_ptr(marg), b, start, _ptr(parent_traj), _ptr(parent_prefix),
+                                  _ptr(parent_count), int(parent_traj.numel()), seed, circuit_id, block,
+                                  _ptr(child_traj), _ptr(child_prefix), _ptr(child_count),
+                                  int(child_traj.numel()), C.byref(nc), _stream(stream)))
+    return nc.value
+
+
+def ptn_allocate_shots(weights, total, seed, circuit_id, m_out, stream=None):
+    _check(lib().ptn_allocate_shots(_ptr(weights), int(weights.numel()), int(total), seed, circuit_id,
+                                    _ptr(m_out), _stream(stream)))
+
+
+def ptn_sample_shots(plan, traj, seed, shots_per_traj=None, total_shots=None, circuit_id=0,
+                     precision=PTN_PREC_FP32, max_traj_per_chunk=0, use_graphs=0, stream=None):
+    mode = PTN_PROPORTIONAL_FIXED if total_shots is None else PTN_PROPORTIONAL_TOTAL
+    o = ptn_sample_opts(mode, circuit_id, int(shots_per_traj or 0), int(total_shots or 0), seed, precision,
+                        max_traj_per_chunk, use_graphs, 0)
+    h = C.c_void_p()
+    _check(lib().ptn_sample_shots(plan.handle, traj.handle, C.byref(o), C.byref(h), _stream(stream)))
+    return Shots(h, len(plan.block_sizes))
+
+
+def ptn_stats_enable(on=True):
+    _check(lib().ptn_stats_enable(int(bool(on))))
+
+
+def ptn_stats_reset():
+    _check(lib().ptn_stats_reset())
+
+
+def ptn_stats_read():
+    """{kernel name: dict(launches, timed_launches, ms, alg_bytes, alg_flops)} (synchronises)."""
+    buf = (ptn_kernel_stat * 32)()
+    n = C.c_int32(0)
+    _check(lib().ptn_stats_read(buf, 32, C.byref(n)))
+    return {buf[i].name.decode(): dict(launches=buf[i].launches, timed_launches=buf[i].timed_launches,
+                                       ms=buf[i].ms, alg_bytes=buf[i].alg_bytes, alg_flops=buf[i].alg_flops)
+            for i in range(n.value)}

@@ -1,0 +1,83 @@
+"""Host-side replay of a lowered plan (from ptn_plan_describe(detail=1)) in
+NumPy, used by the CPU tests to check the planner and lowering logic against
+the oracle without a GPU.  It follows the addressing rules of the step
+descriptors literally (strides, slices, arenas, variant gather); it is test
+code, not a product path."""
+import numpy as np
+
+
+def var_ids(desc, kraus_rows):
+    cols = desc["var_cols"]
+    out = np.zeros((kraus_rows.shape[0], max(len(cols), 1)), dtype=np.int64)
+    for c, ent in enumerate(cols):
+        for site, mul in ent:
+            out[:, c] += kraus_rows[:, site].astype(np.int64) * mul
+    return out
+
+
+def _bits_offsets(strides, n):
+    idx = np.arange(1 << n, dtype=np.int64)
+    off = np.zeros(1 << n, dtype=np.int64)
+    for p, s in enumerate(strides):
+        off += ((idx >> p) & 1) * int(s)
+    return off
+
+
+def run_block(desc, j, kraus_rows, net_traj, net_prefix):
+    """Marginals [n_net, 2^b] (complex64 arithmetic) of block j for the given
+    networks (net_traj non-decreasing), one chunk holding all of them."""
+    blk = desc["blocks"][j]
+    vt = np.array(desc["var_table"], dtype=np.float32).view(np.complex64)
+    vids = var_ids(desc, kraus_rows)
+    net_traj = np.asarray(net_traj)
+    chunk_traj = []
+    net_tl = np.zeros(len(net_traj), dtype=np.int64)
+    for n, t in enumerate(net_traj):
+        if not chunk_traj or chunk_traj[-1] != t:
+            chunk_traj.append(int(t))
+        net_tl[n] = len(chunk_traj) - 1
+    n_traj, n_net = len(chunk_traj), len(net_traj)
+    inst_of = {0: 1, 1: n_traj, 2: n_net}
+    arenas = [np.zeros(max(blk["arena_const"], 1), np.complex64),
+              np.zeros(max(blk["arena_traj"] * n_traj, 1), np.complex64),
+              np.zeros(max(blk["arena_net"] * n_net, 1), np.complex64)]
+
+    def operand(d, out_cls, inst):
+        tl = net = 0
+        if out_cls == 2:
+            net, tl = inst, net_tl[inst]
+        elif out_cls == 1:
+            tl = inst
+        if d["mode"] == 0:
+            var = vids[chunk_traj[tl], d["leaf_col"]] if d["leaf_col"] >= 0 else 0
+            arr, base = vt, d["leaf_base"] + var * d["inst_size"]
+        else:
+            oi = 0 if d["cls"] == 0 else (tl if d["cls"] == 1 else net)
+            arr = arenas[d["arena"]]
+            base = d["arena_off"] * inst_of[d["arena"]] + oi * d["inst_size"]
+        for q, st in d["slices"]:
+            base += ((int(net_prefix[net]) >> q) & 1) * st
+        v = arr[base:base + d["inst_size"]]
+        return np.conj(v) if d["conj"] else v
+
+    for st in blk["steps"]:
+        n_inst = inst_of[st["out_cls"]]
+        oa = _bits_offsets(st["out_stride"][0], st["n_out"])
+        ob = _bits_offsets(st["out_stride"][1], st["n_out"])
+        ka = _bits_offsets(st["sum_stride"][0], st["n_sum"])
+        kb = _bits_offsets(st["sum_stride"][1], st["n_sum"])
+        size = 1 << st["n_out"]
+        out = arenas[st["out_arena"]]
+        obase = st["out_off"] * inst_of[st["out_arena"]]
+        for inst in range(n_inst):
+            A = operand(st["ops"][0], st["out_cls"], inst)
+            B = operand(st["ops"][1], st["out_cls"], inst)
+            val = (A[oa[:, None] + ka[None, :]] * B[ob[:, None] + kb[None, :]]).sum(axis=1)
+            out[obase + inst * size: obase + (inst + 1) * size] = val
+    root = blk["root"]
+    xo = _bits_offsets(root["x_stride"], blk["b"])
+    marg = np.zeros((n_net, 1 << blk["b"]), dtype=np.float64)
+    for n in range(n_net):
+        R = operand(root["op"], 2, n)
+        marg[n] = R[xo].real
+    return marg

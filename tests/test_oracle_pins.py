@@ -357,3 +357,10 @@ def test_allocation_sums_and_proportionality():
 
 def test_rank_offsets():
     assert sampling.rank_offsets([0, 0, 1, 1, 1], [3, 2, 1, 4, 2]).tolist() == [0, 3, 0, 1, 5]
+
+
+def test_zero_norm_parent_drops_its_shots():
+    rows = np.array([[0.0, 0.0, 0.0, 0.0], [1.0, 0.0, 0.0, 3.0]])
+    par, xs, cs = sampling.sample_block(rows, [0, 1], [5, 7], [0, 0], seed=1, block=0)
+    assert set(par.tolist()) == {1} and cs.sum() == 7
+    assert sampling.allocate_shots(np.zeros(3), 10, seed=1).tolist() == [0, 0, 0]

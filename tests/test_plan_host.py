@@ -1,0 +1,111 @@
+"""CPU tests of the host side of libptn: the library loads and exports every
+symbol of include/ptn.h, planning validates its inputs, and every lowered
+plan, replayed on the host by tests/plan_replay.py, reproduces the oracle's
+block marginals.  No GPU calls."""
+import os
+import re
+import zlib
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import pts, statevector as sv
+from paper_2604_08467_gb300 import ptn
+
+from plan_replay import run_block
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_header_symbol():
+    header = open(os.path.join(ROOT, "include", "ptn.h")).read()
+    declared = sorted(set(re.findall(r"^(?:ptn_status|void|const char\*)\s+(ptn_\w+)\s*\(", header, re.M)))
+    lib = ptn.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(ptn.exported_symbols())
+    assert lib.ptn_version().decode().startswith("ptn")
+    assert lib.ptn_status_string(3).decode() == "PTN_ERR_TOO_LARGE"
+
+
+def test_plan_rejects_non_cptp_channel():
+    rng = np.random.default_rng(0)
+    circ = W.brickwork_1d(4, 2, rng)
+    bad = W.depolarizing_kraus(0.1)
+    bad.kraus[0] = bad.kraus[0] * 1.01
+    W.attach_noise(circ, [bad])
+    with pytest.raises(ptn.PtnError) as e:
+        ptn.ptn_plan_path(circ, [4], hypersamples=2)
+    assert e.value.status == 2
+
+
+@pytest.mark.parametrize("blocks", [[3], [2, 2], [5, 1]])
+def test_plan_rejects_bad_blocks(blocks):
+    rng = np.random.default_rng(0)
+    circ = W.attach_noise(W.brickwork_1d(4, 2, rng), [W.depolarizing_kraus(0.1)])
+    if sum(blocks) == 4:
+        ptn.ptn_plan_path(circ, blocks, hypersamples=2)
+    else:
+        with pytest.raises(ptn.PtnError) as e:
+            ptn.ptn_plan_path(circ, blocks, hypersamples=2)
+        assert e.value.status == 1
+
+
+def _oracle_rows(circ, kraus, blocks, j, traj, prefix):
+    start, b = blocks[j]
+    out = []
+    cache = {}
+    for t, s in zip(traj, prefix):
+        if t not in cache:
+            cache[t] = np.abs(sv.trajectory_state(circ, kraus[t])) ** 2
+        out.append(sv.block_marginals(cache[t], circ.n_qubits, start, b)[int(s) & ((1 << start) - 1)])
+    return np.array(out)
+
+
+CASES = [
+    ("brick6", lambda r: W.attach_noise(W.brickwork_1d(6, 5, r), [W.depolarizing_kraus(0.2),
+                                                               W.amplitude_damping_kraus(0.3)]), [2, 3, 1]),
+    ("brick8", lambda r: W.attach_noise(W.brickwork_1d(8, 6, r), [W.depolarizing_kraus(0.1)]), [3, 3, 2]),
+    ("grid3x3", lambda r: W.attach_noise(W.grid_4colour(3, 3, 5, r), [W.depolarizing_kraus(0.1)]), [4, 5]),
+    ("hea5", lambda r: W.attach_noise(W.hea_ring(5, 2, r.standard_normal(20)), [W.depolarizing_kraus(0.1)]),
+     [2, 2, 1]),
+    ("idle_qubit", lambda r: W.attach_noise(W.Circuit(3, [W.Gate((0,), W.haar_u2(r)),
+                                                          W.Gate((0, 1), W.CZ.copy())]),
+                                            [W.amplitude_damping_kraus(0.4)]), [1, 2]),
+]
+
+
+@pytest.mark.parametrize("name,make,bs", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("split", [1, 0])
+def test_lowered_plan_reproduces_oracle_marginals(name, make, bs, split):
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    circ = make(rng)
+    n = circ.n_qubits
+    plan = ptn.ptn_plan_path(circ, bs, hypersamples=8, split_gates=split, est_traj=4, est_shots=64)
+    desc = plan.describe(detail=1)
+    kraus, _ = pts.presample(circ, 4, seed=17)
+    blocks = plan.blocks
+    prng = np.random.default_rng(5)
+    for j, (start, b) in enumerate(blocks):
+        traj = np.repeat(np.arange(4), 3)
+        prefix = prng.integers(0, 1 << start, size=len(traj)) if start else np.zeros(len(traj), int)
+        got = run_block(desc, j, kraus, traj, prefix)
+        want = _oracle_rows(circ, kraus, blocks, j, traj, prefix)
+        err = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
+        assert err < 2e-5, (name, j, err)
+
+
+def test_plan_c1_c2_sizes():
+    c1 = W.config_c1()
+    p1 = ptn.ptn_plan_path(c1["circuit"], c1["block_sizes"], hypersamples=4, est_traj=64, est_shots=64000)
+    d1 = p1.describe()
+    assert [b["b"] for b in d1["blocks"]] == [10, 2]
+    assert d1["n_sites"] == 184
+    c2 = W.config_c2()
+    p2 = ptn.ptn_plan_path(c2["circuit"], c2["block_sizes"], hypersamples=4, est_traj=4096, est_shots=1e6)
+    d2 = p2.describe()
+    assert [b["start"] for b in d2["blocks"]] == [0, 10, 20]
+    assert d2["n_sites"] == 1416
+    for b in d2["blocks"]:
+        assert b["max_out_bits"] <= 40

@@ -54,6 +54,10 @@ void launch_contract_step(const StepDesc* d_step, const StepDesc& h_step, const 
 void launch_finalize(const RootRef* d_root, const ChunkCtx& ctx, int b, int64_t n_net,
                      float* marg, double* Z, cudaStream_t s);
 
+// ---- tensor-core steps (kernels_gemm.cu); err: device word set on a timeout
+ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, float* pack_a,
+                            float* pack_b, int* err, cudaStream_t s);
+
 // ---- launchers (kernels_sample.cu)
 void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, uint64_t seed,
                       int32_t circuit, uint8_t* kraus, double* logq, cudaStream_t s);

@@ -1,0 +1,535 @@
+// Tensor-core execution of the large pairwise contractions of a path (the
+// batched complex GEMMs of Sec. III-A's contraction, real and imaginary parts
+// split into real GEMMs) on sm_103a: tcgen05.mma (kind::tf32) with the
+// accumulator in tensor memory, operands staged by TMA into 128-byte-swizzled
+// shared memory through an mbarrier pipeline.
+//
+// A step  C[inst][m, n] (h) = sum_k A[m, k] (h) * B[n, k] (h)  runs in two phases:
+//  1. pack: each operand is gathered (any bit layout, merged-gate variant,
+//     prefix slice) into row-major K-contiguous rows and split for FP32-accurate
+//     products on TF32 tensor cores, x = hi + lo with hi = x truncated to TF32
+//     and lo = x - hi (exact):
+//       A rows:  [ hi(re0) hi(im0) hi(re1) ... | lo(re0) lo(im0) ... ]
+//       B rows 2n, 2n+1 (the complex product as real dot products):
+//         row 2n   = (re, -im) per k,  row 2n+1 = (im, re) per k, each [hi | lo];
+//     so that  A_row . B_row(2n) = Re C[m, n]  and  A_row . B_row(2n+1) = Im C[m, n];
+//  2. GEMM: D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T accumulated in TMEM
+//     (the lo*lo term is below FP32 resolution), D[m][2n + c] -> C[m, n],
+//     written through the step's output strides (any layout).
+// Conjugated operands (bra layer) are conjugated while packing.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "kernels.cuh"
+#include "stats.h"
+
+namespace ptn {
+
+namespace {
+
+constexpr int kBM = 128;          // UMMA M (cta_group::1)
+constexpr int kBN = 128;          // UMMA N (realified B rows per tile)
+constexpr int kBK = 32;           // fp32 elements per 128-byte swizzle row
+constexpr int kStages = 3;        // pipeline depth (4 tiles of 16 KB per stage)
+constexpr int kTileA = kBM * kBK * 4;
+constexpr int kTileB = kBN * kBK * 4;
+constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;
+constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 1024;   // align slack + stages + barriers/offsets
+constexpr int kMaxPackBits = 40;
+
+struct PackArgs {
+    OperandDesc op;
+    int32_t pcls;            // instance class the packed operand is addressed by
+    int32_t role;            // 0: rows (A), 1: realified (B)
+    int32_t n_rb, n_hb, n_kb;
+    int32_t Kh;              // floats per half row (hi or lo), multiple of 32
+    int64_t n_pinst;
+    int64_t r_stride[kMaxPackBits];   // operand strides of the row bits
+    int64_t h_stride[kMaxPackBits];
+    int64_t k_stride[kMaxPackBits];
+    float* dst;
+};
+
+struct GemmArgs {
+    int32_t M, N2, Kh, nkb;
+    int32_t n_h;
+    int32_t a_pcls, b_pcls, out_cls;
+    int32_t n_mb, n_nb, n_hb, pad;
+    int64_t tiles_m, tiles_n, n_inst;
+    const int32_t* net_tl;
+    float2* out;
+    int64_t out_size;
+    int* err;
+    int64_t m_stride[kMaxOut];
+    int64_t n_stride[kMaxOut];
+    int64_t h_stride[kMaxOut];
+};
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, int pcls, int64_t inst,
+                                                          const ChunkCtx& c) {
+    int64_t tl = 0, net = 0;
+    if (pcls == CLS_NET) {
+        net = inst;
+        tl = c.net_tl[inst];
+    } else if (pcls == CLS_TRAJ) {
+        tl = inst;
+    }
+    const float2* p;
+    if (d.mode == OP_LEAF) {
+        int64_t var = 0;
+        if (d.leaf_col >= 0) var = c.var_ids[(int64_t)c.chunk_traj[tl] * c.n_var_cols + d.leaf_col];
+        p = c.vtab + d.leaf_base + var * d.inst_size;
+    } else {
+        const int64_t oi = d.cls == CLS_CONST ? 0 : (d.cls == CLS_TRAJ ? tl : net);
+        p = c.arena[d.arena] + d.arena_off * c.arena_inst[d.arena] + oi * d.inst_size;
+    }
+    if (pcls == CLS_NET && d.n_slice) {
+        const uint64_t pre = c.net_prefix[net];
+        int64_t off = 0;
+        for (int s = 0; s < d.n_slice; s++) off += (int64_t)((pre >> d.slice_qubit[s]) & 1ull) * d.slice_stride[s];
+        p += off;
+    }
+    return p;
+}
+
+// One thread per (packed instance, h, row, complex k) including the K padding.
+__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a, const ChunkCtx c) {
+    const int64_t kcp = a.Kh / 2;                       // complex slots per half row
+    const int64_t nrow = (int64_t)1 << a.n_rb, nh = (int64_t)1 << a.n_hb;
+    const int64_t kc_real = (int64_t)1 << a.n_kb;
+    const int64_t total = a.n_pinst * nh * nrow * kcp;
+    const int64_t rowlen = 2 * (int64_t)a.Kh;
+    int64_t cur = -1;
+    const float2* base = nullptr;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kc = g % kcp;
+        int64_t rest = g / kcp;
+        const int64_t row = rest % nrow;
+        rest /= nrow;
+        const int64_t h = rest % nh;
+        const int64_t pi = rest / nh;
+        float re = 0.f, im = 0.f;
+        if (kc < kc_real) {
+            if (pi != cur) {
+                base = pack_operand_ptr(a.op, a.pcls, pi, c);
+                cur = pi;
+            }
+            int64_t off = 0;
+            for (int i = 0; i < a.n_rb; i++)
+                if ((row >> i) & 1) off += a.r_stride[i];
+            for (int i = 0; i < a.n_hb; i++)
+                if ((h >> i) & 1) off += a.h_stride[i];
+            for (int i = 0; i < a.n_kb; i++)
+                if ((kc >> i) & 1) off += a.k_stride[i];
+            const float2 v = base[off];
+            re = v.x;
+            im = a.op.conj ? -v.y : v.y;
+        }
+        const int64_t z = pi * nh + h;
+        if (a.role == 0) {
+            float* d = a.dst + (z * nrow + row) * rowlen + 2 * kc;
+            const float hr = tf32_hi(re), hi_ = tf32_hi(im);
+            *reinterpret_cast<float2*>(d) = make_float2(hr, hi_);
+            *reinterpret_cast<float2*>(d + a.Kh) = make_float2(re - hr, im - hi_);
+        } else {
+            float* d0 = a.dst + (z * 2 * nrow + 2 * row) * rowlen + 2 * kc;
+            float* d1 = d0 + rowlen;
+            const float hr = tf32_hi(re), hm = tf32_hi(-im), hi_ = tf32_hi(im);
+            *reinterpret_cast<float2*>(d0) = make_float2(hr, hm);
+            *reinterpret_cast<float2*>(d0 + a.Kh) = make_float2(re - hr, -im - hm);
+            *reinterpret_cast<float2*>(d1) = make_float2(hi_, hr);
+            *reinterpret_cast<float2*>(d1 + a.Kh) = make_float2(im - hi_, re - hr);
+        }
+    }
+}
+
+// ------------------------------------------------------------- PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait (about 2 s of wall time); false when it gave up or another
+// thread of the block aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u) {
+            if (*abort) return false;
+            if (global_ns() - t0 > 2000000000ull) return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand tile in the 128-byte swizzle
+// layout TMA writes (rows of 128 B, 8-row atoms 1024 B apart).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
+    d |= (uint64_t)1u << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1u << 46;                   // descriptor version for tcgen05
+    d |= (uint64_t)2u << 61;                   // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = kBN.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t taddr, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One CTA = one 128 x kBN tile of one (instance, h) GEMM.  Warp 0 lane 0 issues
+// TMA loads, warp 1 lane 0 issues tcgen05.mma; all four warps drain TMEM.
+__global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB,
+                                                      const __grid_constant__ GemmArgs g) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* stage0 = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* accb = empty + kStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+    int64_t* noff = reinterpret_cast<int64_t*>(tslot + 4);   // kBN / 2 column offsets (in 256-byte tail)
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tiles = g.tiles_m * g.tiles_n;
+    const int64_t zt = blockIdx.x / tiles;
+    const int64_t t = blockIdx.x - zt * tiles;
+    const int64_t tm = t % g.tiles_m, tn = t / g.tiles_m;
+    const int64_t inst = zt / g.n_h;
+    const int64_t h = zt - inst * g.n_h;
+    const int m0 = (int)(tm * kBM), n0 = (int)(tn * kBN);
+
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (threadIdx.x < kBN / 2) {   // output offsets of this tile's complex columns
+        const int64_t n = (int64_t)(n0 / 2) + threadIdx.x;
+        int64_t off = 0;
+        for (int i = 0; i < g.n_nb; i++)
+            if ((n >> i) & 1) off += g.n_stride[i];
+        noff[threadIdx.x] = off;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)kBN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    auto pinst = [&](int pcls) -> int64_t {
+        if (pcls == g.out_cls) return inst;
+        if (pcls == CLS_TRAJ) return (int64_t)g.net_tl[inst];
+        return 0;
+    };
+    const int za = (int)(pinst(g.a_pcls) * g.n_h + h);
+    const int zb = (int)(pinst(g.b_pcls) * g.n_h + h);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < g.nkb; kb++) {
+                const int s = kb % kStages;
+                if (kb >= kStages && !mbar_wait(&empty[s], (uint32_t)((kb / kStages) - 1) & 1u, abort)) {
+                    atomicExch(g.err, 1);
+                    *abort = 1;
+                    break;
+                }
+                uint8_t* st = stage0 + s * kStageBytes;
+                mbar_expect_tx(&full[s], (uint32_t)kStageBytes);
+                tma_load_3d(st, &tmA, kb * kBK, m0, za, &full[s]);                       // A hi
+                tma_load_3d(st + kTileA, &tmA, g.Kh + kb * kBK, m0, za, &full[s]);       // A lo
+                tma_load_3d(st + 2 * kTileA, &tmB, kb * kBK, n0, zb, &full[s]);          // B hi
+                tma_load_3d(st + 2 * kTileA + kTileB, &tmB, g.Kh + kb * kBK, n0, zb, &full[s]);   // B lo
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < g.nkb; kb++) {
+                const int s = kb % kStages;
+                if (!mbar_wait(&full[s], (uint32_t)(kb / kStages) & 1u, abort)) {
+                    atomicExch(g.err, 2);
+                    *abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(stage0 + s * kStageBytes);
+                const uint32_t sal = sa + kTileA, sb = sa + 2 * kTileA, sbl = sb + kTileB;
+#pragma unroll
+                for (int kk = 0; kk < kBK / 8; kk++) {   // UMMA K = 8 tf32 = 32 bytes
+                    const uint32_t o = kk * 32;
+                    umma_tf32(tmem, sdesc_sw128(sa + o), sdesc_sw128(sb + o), issued++ ? 1u : 0u);
+                    umma_tf32(tmem, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
+                    umma_tf32(tmem, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
+                }
+                umma_commit(&empty[s]);   // stage free once these MMAs have read it
+            }
+            umma_commit(accb);
+        }
+        __syncwarp();
+    }
+    // epilogue: all four warps
+    const bool ok = mbar_wait(accb, 0u, abort);
+    __syncwarp();
+    tc_fence_after();
+    if (!ok) {
+        if (lane == 0) atomicExch(g.err, 3);
+    } else if (!*abort) {
+        const int64_t m = m0 + warp * 32 + lane;
+        int64_t moff = 0;
+        for (int i = 0; i < g.n_mb; i++)
+            if ((m >> i) & 1) moff += g.m_stride[i];
+        for (int i = 0; i < g.n_hb; i++)
+            if ((h >> i) & 1) moff += g.h_stride[i];
+        float2* out = g.out + inst * g.out_size + moff;
+        const bool row_ok = m < g.M;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kBN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row_ok) {
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int col = n0 + c0 + 2 * j;
+                    if (col < g.N2) out[noff[(c0 >> 1) + j]] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kBN) : "memory");
+    }
+}
+
+// ---------------------------------------------------------- host helpers --
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+ptn_status make_map(CUtensorMap* m, float* base, int64_t kp, int64_t rows, int64_t zs, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_error(PTN_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)zs};
+    cuuint64_t strides[2] = {(cuuint64_t)kp * 4, (cuuint64_t)kp * 4 * (cuuint64_t)rows};
+    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(PTN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PTN_OK;
+}
+
+int pack_class(const OperandDesc& d, int step_cls) {
+    if (step_cls == CLS_NET && d.n_slice) return CLS_NET;
+    if (d.mode == OP_LEAF) return d.leaf_col >= 0 ? CLS_TRAJ : CLS_CONST;
+    return d.cls;
+}
+
+}  // namespace
+
+int gemm_smem_bytes() { return kGemmSmem; }
+
+// Geometry of a GEMM step; used by the planner's memory accounting too.
+void gemm_geometry(const StepDesc& st, int64_t* rows_a, int64_t* rows_b2, int64_t* kh, int* n_h) {
+    const int a = st.gemm_a, b = 1 - a;
+    int nm = 0, nn = 0, nh = 0;
+    for (int p = 0; p < st.n_out; p++) {
+        const bool ia = st.out_stride[a][p] != 0, ib = st.out_stride[b][p] != 0;
+        if (ia && ib) nh++;
+        else if (ia) nm++;
+        else nn++;
+    }
+    const int64_t kc = (int64_t)1 << st.n_sum;
+    *rows_a = (int64_t)1 << nm;
+    *rows_b2 = (int64_t)2 << nn;
+    *kh = ((2 * kc + kBK - 1) / kBK) * kBK;
+    *n_h = 1 << nh;
+}
+
+ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, float* pack_a, float* pack_b,
+                            int* err, cudaStream_t s) {
+    const int a = st.gemm_a, b = 1 - a;
+    PackArgs pa, pb;
+    memset(&pa, 0, sizeof pa);
+    memset(&pb, 0, sizeof pb);
+    GemmArgs ga;
+    memset(&ga, 0, sizeof ga);
+    int nm = 0, nn = 0, nh = 0;
+    for (int p = 0; p < st.n_out; p++) {
+        const int64_t sa = st.out_stride[a][p], sb = st.out_stride[b][p], so = (int64_t)1 << p;
+        if (sa && sb) {
+            pa.h_stride[nh] = sa;
+            pb.h_stride[nh] = sb;
+            ga.h_stride[nh] = so;
+            nh++;
+        } else if (sa) {
+            pa.r_stride[nm] = sa;
+            ga.m_stride[nm] = so;
+            nm++;
+        } else {
+            pb.r_stride[nn] = sb;
+            ga.n_stride[nn] = so;
+            nn++;
+        }
+    }
+    for (int q = 0; q < st.n_sum; q++) {
+        pa.k_stride[q] = st.sum_stride[a][q];
+        pb.k_stride[q] = st.sum_stride[b][q];
+    }
+    const int64_t M = (int64_t)1 << nm, N = (int64_t)1 << nn, Kc = (int64_t)1 << st.n_sum;
+    const int64_t Kh = ((2 * Kc + kBK - 1) / kBK) * kBK;
+    const int64_t inst_of[3] = {1, ctx.arena_inst[CLS_TRAJ], ctx.arena_inst[CLS_NET]};
+    pa.op = st.op[a];
+    pb.op = st.op[b];
+    pa.pcls = pack_class(st.op[a], st.out_cls);
+    pb.pcls = pack_class(st.op[b], st.out_cls);
+    pa.role = 0;
+    pb.role = 1;
+    pa.n_rb = nm;
+    pb.n_rb = nn;
+    pa.n_hb = pb.n_hb = nh;
+    pa.n_kb = pb.n_kb = st.n_sum;
+    pa.Kh = pb.Kh = (int32_t)Kh;
+    pa.n_pinst = inst_of[pa.pcls];
+    pb.n_pinst = inst_of[pb.pcls];
+    pa.dst = pack_a;
+    pb.dst = pack_b;
+    ga.M = (int32_t)M;
+    ga.N2 = (int32_t)(2 * N);
+    ga.Kh = (int32_t)Kh;
+    ga.nkb = (int32_t)(Kh / kBK);
+    ga.n_h = 1 << nh;
+    ga.a_pcls = pa.pcls;
+    ga.b_pcls = pb.pcls;
+    ga.out_cls = st.out_cls;
+    ga.n_mb = nm;
+    ga.n_nb = nn;
+    ga.n_hb = nh;
+    ga.tiles_m = (M + kBM - 1) / kBM;
+    ga.tiles_n = (2 * N + kBN - 1) / kBN;
+    ga.n_inst = n_inst;
+    ga.net_tl = ctx.net_tl;
+    ga.out = ctx.arena[st.out_arena] + st.out_off * ctx.arena_inst[st.out_arena];
+    ga.out_size = st.out_size;
+    ga.err = err;
+    cudaError_t e;
+    auto grid = [](int64_t n) {
+        int64_t b = (n + 255) / 256;
+        return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+    };
+    const int64_t tot_a = pa.n_pinst * (1ll << nh) * M * (Kh / 2);
+    const int64_t tot_b = pb.n_pinst * (1ll << nh) * N * (Kh / 2);
+    {
+        StatScope sc(K_MISC, s, 8.0 * (double)(tot_a + tot_b) + 16.0 * (double)tot_a + 32.0 * (double)tot_b, 0.0);
+        k_pack<<<grid(tot_a), 256, 0, s>>>(pa, ctx);
+        k_pack<<<grid(tot_b), 256, 0, s>>>(pb, ctx);
+    }
+    CUtensorMap mA, mB;
+    ptn_status ps = make_map(&mA, pack_a, 2 * Kh, M, pa.n_pinst * (1ll << nh), kBM);
+    if (ps) return ps;
+    ps = make_map(&mB, pack_b, 2 * Kh, 2 * N, pb.n_pinst * (1ll << nh), kBN);
+    if (ps) return ps;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+        attr = true;
+    }
+    const int64_t blocks = ga.tiles_m * ga.tiles_n * n_inst * (1ll << nh);
+    const double flops = 8.0 * (double)n_inst * (double)(1ll << nh) * (double)M * (double)N * (double)Kc;
+    const double bytes = 8.0 * ((double)n_inst * (1ll << nh) * M * N) + 4.0 * 2 * Kh * ((double)pa.n_pinst * M + (double)pb.n_pinst * 2 * N) * (1ll << nh);
+    StatScope sc(K_CONTRACT_GEMM, s, bytes, flops);
+    k_gemm_tf32<<<(unsigned)blocks, 128, kGemmSmem, s>>>(mA, mB, ga);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "gemm launch: %s", cudaGetErrorString(e));
+    return PTN_OK;
+}
+
+}  // namespace ptn

@@ -448,7 +448,7 @@ int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptr
                                                             reinterpret_cast<const unsigned long long*>(sc.first),
                                                             n_parent, sc.rank0);
     const size_t smem = (size_t)(((int64_t)1 << b) * (sizeof(double) + sizeof(unsigned int)));
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_sample_parents, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 32 * 1024) cudaFuncSetAttribute(k_sample_parents, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     StatScope st_sp(K_SAMPLE_PARENTS, s, (double)n_parent * ((double)((int64_t)1 << b) * 4.0 + 40.0), 0.0);
     k_sample_parents<<<(unsigned)n_parent, 256, smem, s>>>(marg, b, ptraj, pcount, sc.rank0, sc.tmp_off, key,

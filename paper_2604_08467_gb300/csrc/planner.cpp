@@ -651,6 +651,10 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
             for (auto& x : rm.layout) x = idx[x].mirror;
             ref[mv.mc] = rm;
         }
+        int64_t pf[2][3];
+        classify_step(st, pf);
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
         bp.steps.push_back(st);
     }
     // root descriptor
@@ -667,6 +671,37 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         if (bp.root.x_stride[tb] < 0) return set_error(PTN_ERR_INVALID_ARG, "internal: root misses an open bit");
     for (int k = 0; k < 3; k++) bp.arena_peak[k] = arenas[k].peak;
     return PTN_OK;
+}
+
+// Choose the kernel of a step: a tensor-core GEMM when both free sides fill a
+// 128-row tile (realified B counts twice) and the contraction is deep enough,
+// else the direct kernel.  pack_floats[r][c]: floats per instance of class c
+// that packing operand r (0 = GEMM rows, 1 = realified) needs.
+void classify_step(StepDesc& st, int64_t pack_floats[2][3]) {
+    for (int r = 0; r < 2; r++)
+        for (int k = 0; k < 3; k++) pack_floats[r][k] = 0;
+    st.kind = STEP_DIRECT;
+    st.gemm_a = 0;
+    int free_[2] = {0, 0}, nh = 0;
+    for (int p = 0; p < st.n_out; p++) {
+        const bool i0 = st.out_stride[0][p] != 0, i1 = st.out_stride[1][p] != 0;
+        if (i0 && i1) nh++;
+        else if (i0) free_[0]++;
+        else free_[1]++;
+    }
+    const int a = free_[0] >= free_[1] ? 0 : 1, b = 1 - a;
+    if (st.n_sum < 3 || free_[a] < 7 || free_[b] < 6 || nh > 20) return;
+    st.kind = STEP_GEMM;
+    st.gemm_a = a;
+    const int64_t kc = (int64_t)1 << st.n_sum;
+    const int64_t kh = ((2 * kc + 31) / 32) * 32;
+    auto pcls = [&](const OperandDesc& d) {
+        if (st.out_cls == CLS_NET && d.n_slice) return (int)CLS_NET;
+        if (d.mode == OP_LEAF) return d.leaf_col >= 0 ? (int)CLS_TRAJ : (int)CLS_CONST;
+        return (int)d.cls;
+    };
+    pack_floats[0][pcls(st.op[a])] = ((int64_t)1 << nh) * ((int64_t)1 << free_[a]) * 2 * kh;
+    pack_floats[1][pcls(st.op[b])] = ((int64_t)1 << nh) * ((int64_t)2 << free_[b]) * 2 * kh;
 }
 
 // ------------------------------------------------------------ build plan --
@@ -1097,18 +1132,19 @@ std::string describe_plan(const ptn_plan* p, int detail) {
     s += buf;
     for (size_t j = 0; j < p->blocks.size(); j++) {
         const BlockPlan& b = p->blocks[j];
-        int cnt[3] = {0, 0, 0};
+        int cnt[3] = {0, 0, 0}, n_gemm = 0;
         int64_t maxout = 0;
         for (auto& st : b.steps) {
             cnt[st.out_cls]++;
+            n_gemm += st.kind == STEP_GEMM;
             maxout = std::max<int64_t>(maxout, st.n_out);
         }
         snprintf(buf, sizeof buf,
-                 "%s{\"start\":%d,\"b\":%d,\"n_steps\":%zu,\"steps_const\":%d,\"steps_traj\":%d,\"steps_net\":%d,"
+                 "%s{\"start\":%d,\"b\":%d,\"n_gemm\":%d,\"n_steps\":%zu,\"steps_const\":%d,\"steps_traj\":%d,\"steps_net\":%d,"
                  "\"max_out_bits\":%lld,\"arena_const\":%lld,\"arena_traj\":%lld,\"arena_net\":%lld,"
                  "\"macs_const\":%.6e,\"macs_traj\":%.6e,\"macs_net\":%.6e,\"bytes_traj\":%.6e,\"bytes_net\":%.6e,"
                  "\"est_time\":%.6e,\"mult_traj\":%.1f,\"mult_net\":%.1f",
-                 j ? "," : "", b.start, b.b, b.steps.size(), cnt[0], cnt[1], cnt[2], (long long)maxout,
+                 j ? "," : "", b.start, b.b, n_gemm, b.steps.size(), cnt[0], cnt[1], cnt[2], (long long)maxout,
                  (long long)b.arena_peak[0], (long long)b.arena_peak[1], (long long)b.arena_peak[2], b.est_macs[0],
                  b.est_macs[1], b.est_macs[2], b.est_bytes[1], b.est_bytes[2], b.est_time, b.est_mult_traj,
                  b.est_mult_net);
@@ -1117,8 +1153,8 @@ std::string describe_plan(const ptn_plan* p, int detail) {
             s += ",\"steps\":[";
             for (size_t i = 0; i < b.steps.size(); i++) {
                 const StepDesc& st = b.steps[i];
-                snprintf(buf, sizeof buf, "%s{\"out_cls\":%d,\"n_out\":%d,\"n_sum\":%d,\"out_arena\":%d,\"out_off\":%lld,\"ops\":[",
-                         i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.out_arena, (long long)st.out_off);
+                snprintf(buf, sizeof buf, "%s{\"out_cls\":%d,\"n_out\":%d,\"n_sum\":%d,\"kind\":%d,\"gemm_a\":%d,\"out_arena\":%d,\"out_off\":%lld,\"ops\":[",
+                         i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.kind, st.gemm_a, st.out_arena, (long long)st.out_off);
                 s += buf;
                 json_op(s, st.op[0]);
                 s += ",";

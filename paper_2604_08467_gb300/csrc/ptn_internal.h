@@ -44,11 +44,16 @@ struct OperandDesc {
 // with o = sum_p bit_p << p over the n_out output bits and k over the n_sum
 // summed bits; addr = sum_p bit_p(o) * out_stride[op][p] + sum_q bit_q(k) *
 // sum_stride[op][q] + the operand's slice offset.
+enum StepKind : int32_t { STEP_DIRECT = 0, STEP_GEMM = 1 };
+
 struct StepDesc {
     int32_t out_cls;
     int32_t n_out;
     int32_t n_sum;
     int32_t out_arena;
+    int32_t kind;            // STEP_DIRECT or STEP_GEMM
+    int32_t gemm_a;          // STEP_GEMM: which operand supplies the GEMM rows (the other is realified)
+    int32_t pad0, pad1;
     int64_t out_size;        // 2^n_out
     int64_t out_off;         // offset of the output buffer in its arena (elements per instance)
     OperandDesc op[2];
@@ -80,6 +85,7 @@ struct BlockPlan {
     std::vector<StepDesc> steps;
     RootRef root;
     int64_t arena_peak[3] = {0, 0, 0};   // elements per instance, per arena (CONST/TRAJ/NET)
+    int64_t pack_peak[2][3] = {{0, 0, 0}, {0, 0, 0}};   // GEMM packing floats per instance: [A/B][class]
     double est_macs[3] = {0, 0, 0};      // complex MACs per instance by output class
     double est_bytes[3] = {0, 0, 0};     // bytes moved per instance by output class
     double est_time = 0;                 // modelled seconds at the planning multiplicities
@@ -127,6 +133,7 @@ namespace ptn {
 ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* block_sizes,
                       int32_t n_blocks, const ptn_plan_opts* o, ptn_plan* plan);
 std::string describe_plan(const ptn_plan* plan, int detail);
+void classify_step(StepDesc& st, int64_t pack_floats[2][3]);   // planner.cpp
 // errors.cpp
 ptn_status set_error(ptn_status s, const char* fmt, ...);
 }  // namespace ptn

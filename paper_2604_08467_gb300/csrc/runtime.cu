@@ -98,12 +98,13 @@ struct PlanWorkspace {
     DevBuf lvl_traj[2], lvl_prefix[2], lvl_count[2];
     DevBuf s_cap, s_tmp_off, s_rank0, s_excl, s_first, s_ndist, s_out_off, s_tmp_x, s_tmp_c, s_scan;
     DevBuf zero_prefix;
+    DevBuf pack[2], err;
     HostBuf h_traj, h_chunk_traj, h_net_tl, h_small;
     void release() {
         DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &roots, &marg, &Z, &w, &cdf, &m,
                          &lvl_traj[0], &lvl_traj[1], &lvl_prefix[0], &lvl_prefix[1], &lvl_count[0], &lvl_count[1],
                          &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
-                         &s_tmp_c, &s_scan, &zero_prefix};
+                         &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err};
         for (DevBuf* b : all) b->release();
         h_traj.release();
         h_chunk_traj.release();
@@ -227,10 +228,11 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
             return set_error(PTN_ERR_INVALID_ARG, "net_traj[%lld] = %d out of range", (long long)i, ht[i]);
         if (i && ht[i] < ht[i - 1]) return set_error(PTN_ERR_INVALID_ARG, "net_traj must be non-decreasing");
     }
-    // chunking against the memory cap
-    const double bT = 8.0 * (double)bp.arena_peak[CLS_TRAJ];
-    const double bN = 8.0 * (double)bp.arena_peak[CLS_NET] + 4.0 + 8.0;
-    const double bC = 8.0 * (double)bp.arena_peak[CLS_CONST];
+    // chunking against the memory cap (arenas + GEMM operand packing, per instance)
+    auto pk = [&](int c) { return 4.0 * (double)(bp.pack_peak[0][c] + bp.pack_peak[1][c]); };
+    const double bT = 8.0 * (double)bp.arena_peak[CLS_TRAJ] + pk(CLS_TRAJ);
+    const double bN = 8.0 * (double)bp.arena_peak[CLS_NET] + 4.0 + 8.0 + pk(CLS_NET);
+    const double bC = 8.0 * (double)bp.arena_peak[CLS_CONST] + pk(CLS_CONST);
     const double cap = plan->mem_cap;
     if (bC + bT + bN > cap)
         return set_error(PTN_ERR_TOO_LARGE, "block %d needs %.3g bytes for one network (cap %.3g)", j, bC + bT + bN, cap);
@@ -279,9 +281,17 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         max_t = std::max(max_t, c.n_traj);
         max_n = std::max(max_n, c.n_net);
     }
-    if ((e = ws->arena[CLS_CONST].grow((size_t)(bC + 16)))) return e;
-    if ((e = ws->arena[CLS_TRAJ].grow((size_t)(bT * max_t + 16)))) return e;
+    if ((e = ws->arena[CLS_CONST].grow((size_t)(8.0 * bp.arena_peak[CLS_CONST] + 16)))) return e;
+    if ((e = ws->arena[CLS_TRAJ].grow((size_t)(8.0 * bp.arena_peak[CLS_TRAJ] * max_t + 16)))) return e;
     if ((e = ws->arena[CLS_NET].grow((size_t)(8.0 * bp.arena_peak[CLS_NET] * max_n + 16)))) return e;
+    for (int r = 0; r < 2; r++) {
+        const double need = 4.0 * ((double)bp.pack_peak[r][CLS_CONST] + (double)bp.pack_peak[r][CLS_TRAJ] * max_t +
+                                   (double)bp.pack_peak[r][CLS_NET] * max_n);
+        if (need > 0 && (e = ws->pack[r].grow((size_t)need + 256))) return e;
+    }
+    if ((e = ws->err.grow(sizeof(int)))) return e;
+    if ((e = ws->h_small.grow(64))) return e;
+    PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
     const RootRef* d_root = ws->roots.as<RootRef>() + j;
     for (const Chunk& c : chunks) {
         ChunkCtx ctx;
@@ -299,11 +309,21 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         for (size_t st = 0; st < bp.steps.size(); st++) {
             const StepDesc& h = bp.steps[st];
             int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
-            launch_contract_step(bp.d_steps + st, h, ctx, ni, s);
+            if (h.kind == STEP_GEMM) {
+                e = launch_gemm_step(h, ctx, ni, ws->pack[0].as<float>(), ws->pack[1].as<float>(), ws->err.as<int>(), s);
+                if (e) return e;
+            } else {
+                launch_contract_step(bp.d_steps + st, h, ctx, ni, s);
+            }
         }
         launch_finalize(d_root, ctx, bp.b, c.n_net, marg + c.net0 * ((int64_t)1 << bp.b), Z + c.net0, s);
     }
     PTN_CUDA(cudaGetLastError());
+    // a tensor-core step that gave up a bounded wait reports it through the error word
+    int* herr = reinterpret_cast<int*>(ws->h_small.as<int64_t>() + 4);
+    PTN_CUDA(cudaMemcpyAsync(herr, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PTN_CUDA(cudaStreamSynchronize(s));
+    if (*herr) return set_error(PTN_ERR_TIMEOUT, "block %d: a tensor-core step timed out (code %d)", j, *herr);
     return PTN_OK;
 }
 

@@ -313,3 +313,24 @@ def test_sample_shots_c2_proportional_total():
     assert res.nets_per_block[1] <= 1_000_000 and res.nets_per_block[2] >= res.nets_per_block[1]
     assert np.all(np.diff(t) >= 0)
     assert len(set(zip(t.tolist(), bits.tolist()))) == len(t)
+
+
+def test_contract_tensor_core_steps_vs_statevector():
+    """A 20-qubit brickwork whose block paths contain tensor-core (tcgen05)
+    GEMM steps, every block against c128 state vectors."""
+    rng = np.random.default_rng(2020)
+    circ = W.attach_noise(W.brickwork_1d(20, 10, rng), [W.depolarizing_kraus(0.01),
+                                                         W.amplitude_damping_kraus(0.01)])
+    plan = ptn.ptn_plan_path(circ, [10, 6, 4], hypersamples=16, est_traj=512, est_shots=1e5)
+    d = plan.describe()
+    assert sum(b["n_gemm"] for b in d["blocks"]) > 0
+    tr = ptn.ptn_presample_trajectories(plan, 31, 6)
+    kraus = tr.to_torch()[0].cpu().numpy()
+    probs = [np.abs(sv.trajectory_state(circ, kraus[t])) ** 2 for t in range(6)]
+    prng = np.random.default_rng(8)
+    for j, (start, b) in enumerate(plan.blocks):
+        traj = np.repeat(np.arange(6), 7)
+        prefix = prng.integers(0, 1 << start, size=len(traj)) if start else np.zeros(len(traj), int)
+        marg, Z = _contract(plan, tr, j, traj, prefix, b)
+        want = np.array([sv.block_marginals(probs[t], 20, start, b)[int(s)] for t, s in zip(traj, prefix)])
+        assert np.max(_rel(marg, want)) < 2e-5, j

@@ -7,8 +7,8 @@
 // A step  C[inst][m, n] (h) = sum_k A[m, k] (h) * B[n, k] (h)  runs in two phases:
 //  1. pack: each operand is gathered (any bit layout, merged-gate variant,
 //     prefix slice) into row-major K-contiguous rows and split for FP32-accurate
-//     products on TF32 tensor cores, x = hi + lo with hi = x truncated to TF32
-//     and lo = x - hi (exact):
+//     products on TF32 tensor cores, x = hi + lo with hi = x rounded to TF32
+//     and lo = (x - hi) rounded to TF32 (|x - hi - lo| <= 2^-24 |x|):
 //       A rows:  [ hi(re0) hi(im0) hi(re1) ... | lo(re0) lo(im0) ... ]
 //       B rows 2n, 2n+1 (the complex product as real dot products):
 //         row 2n   = (re, -im) per k,  row 2n+1 = (im, re) per k, each [hi | lo];
@@ -67,7 +67,20 @@ struct GemmArgs {
     int64_t h_stride[kMaxOut];
 };
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// Round to the nearest TF32 value (ties away from zero): add half of the 13
+// dropped mantissa bits, then clear them.  Splitting x = hi + lo with both
+// halves rounded this way makes the tensor core's TF32 read of either half
+// exact and leaves |x - hi - lo| <= 2^-24 |x|.
+__device__ __forceinline__ float tf32_rn(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+struct Split {
+    float hi, lo;
+};
+__device__ __forceinline__ Split tf32_split(float x) {
+    const float h = tf32_rn(x);
+    return {h, tf32_rn(x - h)};
+}
 
 __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, int pcls, int64_t inst,
                                                           const ChunkCtx& c) {
@@ -131,19 +144,18 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
             im = a.op.conj ? -v.y : v.y;
         }
         const int64_t z = pi * nh + h;
+        const Split sr = tf32_split(re), si = tf32_split(im);
         if (a.role == 0) {
             float* d = a.dst + (z * nrow + row) * rowlen + 2 * kc;
-            const float hr = tf32_hi(re), hi_ = tf32_hi(im);
-            *reinterpret_cast<float2*>(d) = make_float2(hr, hi_);
-            *reinterpret_cast<float2*>(d + a.Kh) = make_float2(re - hr, im - hi_);
+            *reinterpret_cast<float2*>(d) = make_float2(sr.hi, si.hi);
+            *reinterpret_cast<float2*>(d + a.Kh) = make_float2(sr.lo, si.lo);
         } else {
             float* d0 = a.dst + (z * 2 * nrow + 2 * row) * rowlen + 2 * kc;
             float* d1 = d0 + rowlen;
-            const float hr = tf32_hi(re), hm = tf32_hi(-im), hi_ = tf32_hi(im);
-            *reinterpret_cast<float2*>(d0) = make_float2(hr, hm);
-            *reinterpret_cast<float2*>(d0 + a.Kh) = make_float2(re - hr, -im - hm);
-            *reinterpret_cast<float2*>(d1) = make_float2(hi_, hr);
-            *reinterpret_cast<float2*>(d1 + a.Kh) = make_float2(im - hi_, re - hr);
+            *reinterpret_cast<float2*>(d0) = make_float2(sr.hi, -si.hi);
+            *reinterpret_cast<float2*>(d0 + a.Kh) = make_float2(sr.lo, -si.lo);
+            *reinterpret_cast<float2*>(d1) = make_float2(si.hi, sr.hi);
+            *reinterpret_cast<float2*>(d1 + a.Kh) = make_float2(si.lo, sr.lo);
         }
     }
 }

@@ -219,6 +219,33 @@ ptn_status ptn_sample_block(const float* marg, int32_t b, int32_t start,
                             int32_t* child_traj, uint64_t* child_prefix, int64_t* child_count,
                             int64_t child_cap, int64_t* n_child, ptn_stream stream);
 
+/* ptn_sample_block without any run-time allocation (the paper has no
+ * counterpart; this is a deployment variant).  Same arguments, results and
+ * bit-exact output as ptn_sample_block, but its scratch memory is a fixed
+ * 32 MiB array in the library's static device data instead of buffers the
+ * library allocates, for callers that cannot call cudaMalloc while they run
+ * (processes that reserve their whole GPU memory budget at start-up and
+ * forbid later allocations, which would also synchronise the device, or code
+ * that must stay inside a caching allocator).  Every GPU that loads the
+ * library holds the array until the process exits.
+ *  - Limits: the scratch holds 48 bytes per parent, 8 per trajectory index
+ *    (up to the largest index used), 12 per child slot (child_cap) plus scan
+ *    space; a call that needs more than 32 MiB returns PTN_ERR_TOO_LARGE with
+ *    the sizes in the error text, before launching any sampling work.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - All calls share the array, whatever their stream: calls that overlap on
+ *    the GPU race and corrupt each other's results; serialise them.  Each call
+ *    clears what must start at zero, so stale contents of an earlier call do
+ *    not leak into the next.
+ *  - Synchronises the stream (it validates the parents and reads sizes back). */
+ptn_status ptn_sample_block_noalloc(const float* marg, int32_t b, int32_t start,
+                                    const int32_t* parent_traj, const uint64_t* parent_prefix,
+                                    const int64_t* parent_count, int64_t n_parent,
+                                    uint64_t seed, int32_t circuit_id, int32_t block,
+                                    int32_t* child_traj, uint64_t* child_prefix, int64_t* child_count,
+                                    int64_t child_cap, int64_t* n_child, ptn_stream stream);
+
 /* Proportional shot allocation (Sec. II-C "shots m_i assigned by the rule"):
  * one multinomial draw of `total` shots over the device weights w[n] (FP64,
  * >= 0, not all zero), quantised like the marginals (b = ceil(log2 n)); shot t

@@ -83,6 +83,8 @@ _SIGS = {
     "ptn_contract_batch": [_P, _P, C.c_int32, _P, _P, C.c_int64, C.c_int32, _P, _P, _P],
     "ptn_sample_block": [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_int64, C.c_uint64, C.c_int32, C.c_int32,
                          _P, _P, _P, C.c_int64, C.POINTER(C.c_int64), _P],
+    "ptn_sample_block_noalloc": [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_int64, C.c_uint64, C.c_int32,
+                                 C.c_int32, _P, _P, _P, C.c_int64, C.POINTER(C.c_int64), _P],
     "ptn_allocate_shots": [_P, C.c_int64, C.c_int64, C.c_uint64, C.c_int32, _P, _P],
     "ptn_sample_shots": [_P, _P, C.POINTER(ptn_sample_opts), C.POINTER(_P), _P],
     "ptn_shots_info": [_P, C.POINTER(C.c_int64), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
@@ -292,6 +294,18 @@ def ptn_sample_block(marg, b, start, parent_traj, parent_prefix, parent_count, s
                                   _ptr(parent_count), int(parent_traj.numel()), seed, circuit_id, block,
                                   _ptr(child_traj), _ptr(child_prefix), _ptr(child_count),
                                   int(child_traj.numel()), C.byref(nc), _stream(stream)))
+    return nc.value
+
+
+def ptn_sample_block_noalloc(marg, b, start, parent_traj, parent_prefix, parent_count, seed, circuit_id, block,
+                             child_traj, child_prefix, child_count, stream=None):
+    """ptn_sample_block with its scratch in the library's fixed static device
+    array (no allocation during the call; see include/ptn.h)."""
+    nc = C.c_int64(0)
+    _check(lib().ptn_sample_block_noalloc(_ptr(marg), b, start, _ptr(parent_traj), _ptr(parent_prefix),
+                                          _ptr(parent_count), int(parent_traj.numel()), seed, circuit_id, block,
+                                          _ptr(child_traj), _ptr(child_prefix), _ptr(child_count),
+                                          int(child_traj.numel()), C.byref(nc), _stream(stream)))
     return nc.value
 
 

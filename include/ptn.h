@@ -120,6 +120,8 @@ typedef struct {
                                   distinct prefixes per block); 0 -> 1e6 */
     double   mem_cap_bytes;    /* device memory one execution chunk may use; 0 -> 40% of
                                   the device's free memory at first use */
+    int32_t  simt_only;        /* 1: run every step on the SIMT kernel (no tensor cores) */
+    int32_t  reserved;
 } ptn_plan_opts;
 
 /* ------------------------------------------------------------- planning -- */

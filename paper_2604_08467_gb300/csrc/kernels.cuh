@@ -55,8 +55,19 @@ void launch_finalize(const RootRef* d_root, const ChunkCtx& ctx, int b, int64_t 
                      float* marg, double* Z, cudaStream_t s);
 
 // ---- tensor-core steps (kernels_gemm.cu); err: device word set on a timeout
+// Networks of a chunk grouped by trajectory: group g holds networks
+// [net0[g], net0[g+1]) (host and device copies); the rest is device scratch
+// for the per-step tile table of stacked GEMMs.
+struct GroupTable {
+    int64_t n_groups = 0;
+    const int32_t* h_net0 = nullptr;
+    const int32_t* d_net0 = nullptr;
+    int64_t* d_cnt = nullptr;     // n_groups + 1
+    int64_t* d_tile0 = nullptr;   // n_groups + 1
+    int64_t* d_scan = nullptr;    // scan_tmp_elems(n_groups + 1)
+};
 ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, float* pack_a,
-                            float* pack_b, int* err, cudaStream_t s);
+                            float* pack_b, int* err, const GroupTable& grp, cudaStream_t s);
 
 // ---- launchers (kernels_sample.cu)
 void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, uint64_t seed,

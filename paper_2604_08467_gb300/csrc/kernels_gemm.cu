@@ -38,6 +38,11 @@ constexpr int kTileB = kBN * kBK * 4;
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;
 constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 1024;   // align slack + stages + barriers/offsets
 constexpr int kMaxPackBits = 40;
+// k-blocks are spread round-robin over kAcc TMEM accumulators that the
+// epilogue adds in FP32: the tensor core's FP32 accumulation truncates, so
+// shorter accumulation chains keep the contraction within FP32 accuracy.
+constexpr int kAcc = 4;
+constexpr uint32_t kTmemCols = kAcc * kBN;   // 512: the whole TMEM of the SM (one CTA per SM)
 
 struct PackArgs {
     OperandDesc op;
@@ -59,6 +64,12 @@ struct GemmArgs {
     int32_t n_mb, n_nb, n_hb, pad;
     int64_t tiles_m, tiles_n, n_inst;
     const int32_t* net_tl;
+    // stacked mode: the rows of all networks of one trajectory form one GEMM
+    // (rows = network-major (net, m)); tiles never cross trajectories
+    int32_t stacked, m_bits;
+    int64_t n_groups;
+    const int32_t* grp_net0;     // [n_groups + 1] first network of each trajectory group
+    const int64_t* grp_tile0;    // [n_groups + 1] first tile of each group
     float2* out;
     int64_t out_size;
     int* err;
@@ -265,13 +276,35 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
     int64_t* noff = reinterpret_cast<int64_t*>(tslot + 4);   // kBN / 2 column offsets (in 256-byte tail)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tiles = g.tiles_m * g.tiles_n;
-    const int64_t zt = blockIdx.x / tiles;
-    const int64_t t = blockIdx.x - zt * tiles;
-    const int64_t tm = t % g.tiles_m, tn = t / g.tiles_m;
-    const int64_t inst = zt / g.n_h;
-    const int64_t h = zt - inst * g.n_h;
-    const int m0 = (int)(tm * kBM), n0 = (int)(tn * kBN);
+    int64_t inst, h, row_end;
+    int m0, n0;
+    if (!g.stacked) {
+        const int64_t tiles = g.tiles_m * g.tiles_n;
+        const int64_t zt = blockIdx.x / tiles;
+        const int64_t t = blockIdx.x - zt * tiles;
+        const int64_t tm = t % g.tiles_m, tn = t / g.tiles_m;
+        inst = zt / g.n_h;
+        h = zt - inst * g.n_h;
+        m0 = (int)(tm * kBM);
+        n0 = (int)(tn * kBN);
+        row_end = g.M;
+    } else {
+        // group (trajectory) of this tile: largest grp with grp_tile0[grp] <= blockIdx.x
+        int64_t lo = 0, hi = g.n_groups - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (g.grp_tile0[mid] <= (int64_t)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t t = (int64_t)blockIdx.x - g.grp_tile0[lo];
+        const int64_t r0 = (int64_t)g.grp_net0[lo] << g.m_bits, r1 = (int64_t)g.grp_net0[lo + 1] << g.m_bits;
+        const int64_t tmg = (r1 - r0 + kBM - 1) / kBM;
+        m0 = (int)(r0 + (t % tmg) * kBM);
+        n0 = (int)((t / tmg) * kBN);
+        inst = lo;            // the trajectory (local index) supplies the B operand
+        h = 0;
+        row_end = r1;
+    }
 
     if (threadIdx.x == 32) {
         for (int s = 0; s < kStages; s++) {
@@ -292,7 +325,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"((uint32_t)kBN)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -306,8 +339,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
         if (pcls == CLS_TRAJ) return (int64_t)g.net_tl[inst];
         return 0;
     };
-    const int za = (int)(pinst(g.a_pcls) * g.n_h + h);
-    const int zb = (int)(pinst(g.b_pcls) * g.n_h + h);
+    int za, zb;
+    if (!g.stacked) {
+        za = (int)(pinst(g.a_pcls) * g.n_h + h);
+        zb = (int)(pinst(g.b_pcls) * g.n_h + h);
+    } else {
+        za = 0;
+        zb = g.b_pcls == CLS_TRAJ ? (int)inst : 0;
+    }
 
     if (warp == 0) {
         if (lane == 0) {
@@ -329,7 +368,6 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            int issued = 0;
             for (int kb = 0; kb < g.nkb; kb++) {
                 const int s = kb % kStages;
                 if (!mbar_wait(&full[s], (uint32_t)(kb / kStages) & 1u, abort)) {
@@ -340,12 +378,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
                 tc_fence_after();
                 const uint32_t sa = smem_u32(stage0 + s * kStageBytes);
                 const uint32_t sal = sa + kTileA, sb = sa + 2 * kTileA, sbl = sb + kTileB;
+                const uint32_t acc = tmem + (uint32_t)((kb % kAcc) * kBN);
+                const bool fresh = kb < kAcc;
 #pragma unroll
                 for (int kk = 0; kk < kBK / 8; kk++) {   // UMMA K = 8 tf32 = 32 bytes
                     const uint32_t o = kk * 32;
-                    umma_tf32(tmem, sdesc_sw128(sa + o), sdesc_sw128(sb + o), issued++ ? 1u : 0u);
-                    umma_tf32(tmem, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
-                    umma_tf32(tmem, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
+                    umma_tf32(acc, sdesc_sw128(sa + o), sdesc_sw128(sb + o), (fresh && kk == 0) ? 0u : 1u);
+                    umma_tf32(acc, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
+                    umma_tf32(acc, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
                 }
                 umma_commit(&empty[s]);   // stage free once these MMAs have read it
             }
@@ -360,23 +400,37 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
     if (!ok) {
         if (lane == 0) atomicExch(g.err, 3);
     } else if (!*abort) {
-        const int64_t m = m0 + warp * 32 + lane;
+        const int64_t row = (int64_t)m0 + warp * 32 + lane;
+        int64_t m = row, out_inst = inst;
+        if (g.stacked) {
+            out_inst = row >> g.m_bits;
+            m = row & (((int64_t)1 << g.m_bits) - 1);
+        }
         int64_t moff = 0;
         for (int i = 0; i < g.n_mb; i++)
             if ((m >> i) & 1) moff += g.m_stride[i];
         for (int i = 0; i < g.n_hb; i++)
             if ((h >> i) & 1) moff += g.h_stride[i];
-        float2* out = g.out + inst * g.out_size + moff;
-        const bool row_ok = m < g.M;
+        float2* out = g.out + out_inst * g.out_size + moff;
+        const bool row_ok = row < row_end;
+        const int n_acc = g.nkb < kAcc ? g.nkb : kAcc;
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
+            float v[32];
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
+            for (int a = 1; a < n_acc; a++) {
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * kBN + c0), r);
+#pragma unroll
+                for (int j = 0; j < 32; j++) v[j] += __uint_as_float(r[j]);
+            }
             if (row_ok) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int col = n0 + c0 + 2 * j;
-                    if (col < g.N2) out[noff[(c0 >> 1) + j]] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+                    if (col < g.N2) out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j], v[2 * j + 1]);
                 }
             }
         }
@@ -385,7 +439,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kBN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
 }
 
@@ -419,6 +473,20 @@ ptn_status make_map(CUtensorMap* m, float* base, int64_t kp, int64_t rows, int64
     return PTN_OK;
 }
 
+// Tiles of every trajectory group of a stacked GEMM (cnt[n_groups] = 0, so the
+// exclusive scan of cnt ends with the total).
+__global__ void k_group_tiles(const int32_t* __restrict__ net0, int64_t n_groups, int m_bits, int64_t tiles_n,
+                              int64_t* __restrict__ cnt) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > n_groups) return;
+    if (g == n_groups) {
+        cnt[g] = 0;
+        return;
+    }
+    const int64_t r = (int64_t)(net0[g + 1] - net0[g]) << m_bits;
+    cnt[g] = ((r + kBM - 1) / kBM) * tiles_n;
+}
+
 int pack_class(const OperandDesc& d, int step_cls) {
     if (step_cls == CLS_NET && d.n_slice) return CLS_NET;
     if (d.mode == OP_LEAF) return d.leaf_col >= 0 ? CLS_TRAJ : CLS_CONST;
@@ -427,27 +495,9 @@ int pack_class(const OperandDesc& d, int step_cls) {
 
 }  // namespace
 
-int gemm_smem_bytes() { return kGemmSmem; }
-
-// Geometry of a GEMM step; used by the planner's memory accounting too.
-void gemm_geometry(const StepDesc& st, int64_t* rows_a, int64_t* rows_b2, int64_t* kh, int* n_h) {
-    const int a = st.gemm_a, b = 1 - a;
-    int nm = 0, nn = 0, nh = 0;
-    for (int p = 0; p < st.n_out; p++) {
-        const bool ia = st.out_stride[a][p] != 0, ib = st.out_stride[b][p] != 0;
-        if (ia && ib) nh++;
-        else if (ia) nm++;
-        else nn++;
-    }
-    const int64_t kc = (int64_t)1 << st.n_sum;
-    *rows_a = (int64_t)1 << nm;
-    *rows_b2 = (int64_t)2 << nn;
-    *kh = ((2 * kc + kBK - 1) / kBK) * kBK;
-    *n_h = 1 << nh;
-}
-
 ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, float* pack_a, float* pack_b,
-                            int* err, cudaStream_t s) {
+                            int* err, const GroupTable& grp, cudaStream_t s) {
+    const bool stacked = st.kind == STEP_GEMM_STACKED;
     const int a = st.gemm_a, b = 1 - a;
     PackArgs pa, pb;
     memset(&pa, 0, sizeof pa);
@@ -525,7 +575,31 @@ ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_i
         k_pack<<<grid(tot_b), 256, 0, s>>>(pb, ctx);
     }
     CUtensorMap mA, mB;
-    ptn_status ps = make_map(&mA, pack_a, 2 * Kh, M, pa.n_pinst * (1ll << nh), kBM);
+    int64_t blocks = ga.tiles_m * ga.tiles_n * n_inst * (1ll << nh);
+    ptn_status ps;
+    if (!stacked) {
+        ps = make_map(&mA, pack_a, 2 * Kh, M, pa.n_pinst * (1ll << nh), kBM);
+    } else {
+        // rows of all networks, network-major; groups (trajectories) tile separately.
+        // The pack buffer holds at least one full tile of rows (planner), so a
+        // chunk with fewer rows still spans the TMA box.
+        const int64_t rows = pa.n_pinst * M;
+        ps = make_map(&mA, pack_a, 2 * Kh, rows < kBM ? kBM : rows, 1, kBM);
+        ga.stacked = 1;
+        ga.m_bits = nm;
+        ga.n_groups = grp.n_groups;
+        ga.grp_net0 = grp.d_net0;
+        ga.grp_tile0 = grp.d_tile0;
+        int64_t acc = 0;   // the same count the device tile table ends with
+        for (int64_t gi = 0; gi < grp.n_groups; gi++) {
+            const int64_t r = (int64_t)(grp.h_net0[gi + 1] - grp.h_net0[gi]) * M;
+            acc += ((r + kBM - 1) / kBM) * ga.tiles_n;
+        }
+        blocks = acc;
+        k_group_tiles<<<(unsigned)((grp.n_groups + 256) / 256), 256, 0, s>>>(grp.d_net0, grp.n_groups, nm,
+                                                                              ga.tiles_n, grp.d_cnt);
+        launch_exclusive_scan(grp.d_cnt, grp.d_tile0, grp.n_groups + 1, grp.d_scan, s);
+    }
     if (ps) return ps;
     ps = make_map(&mB, pack_b, 2 * Kh, 2 * N, pb.n_pinst * (1ll << nh), kBN);
     if (ps) return ps;
@@ -534,7 +608,7 @@ ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_i
         cudaFuncSetAttribute(k_gemm_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
         attr = true;
     }
-    const int64_t blocks = ga.tiles_m * ga.tiles_n * n_inst * (1ll << nh);
+    if (blocks <= 0) return PTN_OK;
     const double flops = 8.0 * (double)n_inst * (double)(1ll << nh) * (double)M * (double)N * (double)Kc;
     const double bytes = 8.0 * ((double)n_inst * (1ll << nh) * M * N) + 4.0 * 2 * Kh * ((double)pa.n_pinst * M + (double)pb.n_pinst * 2 * N) * (1ll << nh);
     StatScope sc(K_CONTRACT_GEMM, s, bytes, flops);

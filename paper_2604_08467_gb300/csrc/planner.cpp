@@ -652,7 +652,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
             ref[mv.mc] = rm;
         }
         int64_t pf[2][3];
-        classify_step(st, pf);
+        classify_step(st, pf, !plan->opts.simt_only);
         for (int r = 0; r < 2; r++)
             for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
         bp.steps.push_back(st);
@@ -673,15 +673,22 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
     return PTN_OK;
 }
 
-// Choose the kernel of a step: a tensor-core GEMM when both free sides fill a
-// 128-row tile (realified B counts twice) and the contraction is deep enough,
-// else the direct kernel.  pack_floats[r][c]: floats per instance of class c
-// that packing operand r (0 = GEMM rows, 1 = realified) needs.
-void classify_step(StepDesc& st, int64_t pack_floats[2][3]) {
+// Choose the kernel of a step.  Tensor cores (tcgen05) when the step is a
+// real matrix product worth a 128-row tile:
+//  - STEP_GEMM: both free sides fill tiles (realified B counts twice) and the
+//    contraction is deep enough; one GEMM per (instance, hyper index);
+//  - STEP_GEMM_STACKED: a network-level step whose network operand has few
+//    rows per network while the other operand is shared by all networks of a
+//    trajectory: the rows of all networks of a trajectory are stacked into one
+//    GEMM against the trajectory's operand;
+// else the direct SIMT kernel.  pack_floats[r][c]: floats per instance of
+// class c that packing operand r (0 = GEMM rows, 1 = realified) needs.
+void classify_step(StepDesc& st, int64_t pack_floats[2][3], bool allow_tc) {
     for (int r = 0; r < 2; r++)
         for (int k = 0; k < 3; k++) pack_floats[r][k] = 0;
     st.kind = STEP_DIRECT;
     st.gemm_a = 0;
+    if (!allow_tc) return;
     int free_[2] = {0, 0}, nh = 0;
     for (int p = 0; p < st.n_out; p++) {
         const bool i0 = st.out_stride[0][p] != 0, i1 = st.out_stride[1][p] != 0;
@@ -689,17 +696,32 @@ void classify_step(StepDesc& st, int64_t pack_floats[2][3]) {
         else if (i0) free_[0]++;
         else free_[1]++;
     }
-    const int a = free_[0] >= free_[1] ? 0 : 1, b = 1 - a;
-    if (st.n_sum < 3 || free_[a] < 7 || free_[b] < 6 || nh > 20) return;
-    st.kind = STEP_GEMM;
-    st.gemm_a = a;
-    const int64_t kc = (int64_t)1 << st.n_sum;
-    const int64_t kh = ((2 * kc + 31) / 32) * 32;
     auto pcls = [&](const OperandDesc& d) {
         if (st.out_cls == CLS_NET && d.n_slice) return (int)CLS_NET;
         if (d.mode == OP_LEAF) return d.leaf_col >= 0 ? (int)CLS_TRAJ : (int)CLS_CONST;
         return (int)d.cls;
     };
+    const int64_t kc = (int64_t)1 << st.n_sum;
+    const int64_t kh = ((2 * kc + 31) / 32) * 32;
+    if (st.n_sum < 3) return;
+    // stacked: network operand (rows) x trajectory-level operand (realified)
+    if (st.out_cls == CLS_NET && nh == 0) {
+        for (int a = 0; a < 2; a++) {
+            const int b = 1 - a;
+            if (pcls(st.op[a]) != CLS_NET || pcls(st.op[b]) == CLS_NET) continue;
+            if (free_[a] >= 7 || free_[b] < 6 || free_[a] > 16) continue;
+            st.kind = STEP_GEMM_STACKED;
+            st.gemm_a = a;
+            pack_floats[0][CLS_NET] = ((int64_t)1 << free_[a]) * 2 * kh;
+            pack_floats[0][CLS_CONST] = 128 * 2 * kh;   // one full tile of rows for small chunks
+            pack_floats[1][pcls(st.op[b])] = ((int64_t)2 << free_[b]) * 2 * kh;
+            return;
+        }
+    }
+    const int a = free_[0] >= free_[1] ? 0 : 1, b = 1 - a;
+    if (free_[a] < 7 || free_[b] < 6 || nh > 20) return;
+    st.kind = STEP_GEMM;
+    st.gemm_a = a;
     pack_floats[0][pcls(st.op[a])] = ((int64_t)1 << nh) * ((int64_t)1 << free_[a]) * 2 * kh;
     pack_floats[1][pcls(st.op[b])] = ((int64_t)1 << nh) * ((int64_t)2 << free_[b]) * 2 * kh;
 }
@@ -1136,7 +1158,7 @@ std::string describe_plan(const ptn_plan* p, int detail) {
         int64_t maxout = 0;
         for (auto& st : b.steps) {
             cnt[st.out_cls]++;
-            n_gemm += st.kind == STEP_GEMM;
+            n_gemm += st.kind != STEP_DIRECT;
             maxout = std::max<int64_t>(maxout, st.n_out);
         }
         snprintf(buf, sizeof buf,

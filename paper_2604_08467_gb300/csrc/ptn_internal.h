@@ -44,7 +44,7 @@ struct OperandDesc {
 // with o = sum_p bit_p << p over the n_out output bits and k over the n_sum
 // summed bits; addr = sum_p bit_p(o) * out_stride[op][p] + sum_q bit_q(k) *
 // sum_stride[op][q] + the operand's slice offset.
-enum StepKind : int32_t { STEP_DIRECT = 0, STEP_GEMM = 1 };
+enum StepKind : int32_t { STEP_DIRECT = 0, STEP_GEMM = 1, STEP_GEMM_STACKED = 2 };
 
 struct StepDesc {
     int32_t out_cls;
@@ -133,7 +133,7 @@ namespace ptn {
 ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* block_sizes,
                       int32_t n_blocks, const ptn_plan_opts* o, ptn_plan* plan);
 std::string describe_plan(const ptn_plan* plan, int detail);
-void classify_step(StepDesc& st, int64_t pack_floats[2][3]);   // planner.cpp
+void classify_step(StepDesc& st, int64_t pack_floats[2][3], bool allow_tc);   // planner.cpp
 // errors.cpp
 ptn_status set_error(ptn_status s, const char* fmt, ...);
 }  // namespace ptn

@@ -98,14 +98,16 @@ struct PlanWorkspace {
     DevBuf lvl_traj[2], lvl_prefix[2], lvl_count[2];
     DevBuf s_cap, s_tmp_off, s_rank0, s_excl, s_first, s_ndist, s_out_off, s_tmp_x, s_tmp_c, s_scan;
     DevBuf zero_prefix;
-    DevBuf pack[2], err;
-    HostBuf h_traj, h_chunk_traj, h_net_tl, h_small;
+    DevBuf pack[2], err, grp, grp_cnt, grp_tile0, grp_scan;
+    HostBuf h_traj, h_chunk_traj, h_net_tl, h_small, h_grp;
     void release() {
         DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &roots, &marg, &Z, &w, &cdf, &m,
                          &lvl_traj[0], &lvl_traj[1], &lvl_prefix[0], &lvl_prefix[1], &lvl_count[0], &lvl_count[1],
                          &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
-                         &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err};
+                         &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err, &grp, &grp_cnt,
+                         &grp_tile0, &grp_scan};
         for (DevBuf* b : all) b->release();
+        h_grp.release();
         h_traj.release();
         h_chunk_traj.release();
         h_net_tl.release();
@@ -281,6 +283,27 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         max_t = std::max(max_t, c.n_traj);
         max_n = std::max(max_n, c.n_net);
     }
+    // per chunk, the first network of every trajectory group (n_traj + 1 entries)
+    const int64_t n_grp_all = n_ct + (int64_t)chunks.size();
+    if ((e = ws->h_grp.grow(sizeof(int32_t) * n_grp_all)) || (e = ws->grp.grow(sizeof(int32_t) * n_grp_all)) ||
+        (e = ws->grp_cnt.grow(sizeof(int64_t) * (max_t + 1))) || (e = ws->grp_tile0.grow(sizeof(int64_t) * (max_t + 1))) ||
+        (e = ws->grp_scan.grow(sizeof(int64_t) * scan_tmp_elems(max_t + 1))))
+        return e;
+    int32_t* hg = ws->h_grp.as<int32_t>();
+    std::vector<int64_t> grp_off(chunks.size());
+    {
+        int64_t o = 0;
+        for (size_t ci = 0; ci < chunks.size(); ci++) {
+            const Chunk& c = chunks[ci];
+            grp_off[ci] = o;
+            int32_t t = -1;
+            for (int64_t q = 0; q < c.n_net; q++)
+                if (htl[c.net0 + q] != t) hg[o + (t = htl[c.net0 + q])] = (int32_t)q;
+            hg[o + c.n_traj] = (int32_t)c.n_net;
+            o += c.n_traj + 1;
+        }
+    }
+    PTN_CUDA(cudaMemcpyAsync(ws->grp.p, hg, sizeof(int32_t) * n_grp_all, cudaMemcpyHostToDevice, s));
     if ((e = ws->arena[CLS_CONST].grow((size_t)(8.0 * bp.arena_peak[CLS_CONST] + 16)))) return e;
     if ((e = ws->arena[CLS_TRAJ].grow((size_t)(8.0 * bp.arena_peak[CLS_TRAJ] * max_t + 16)))) return e;
     if ((e = ws->arena[CLS_NET].grow((size_t)(8.0 * bp.arena_peak[CLS_NET] * max_n + 16)))) return e;
@@ -293,7 +316,15 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     if ((e = ws->h_small.grow(64))) return e;
     PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
     const RootRef* d_root = ws->roots.as<RootRef>() + j;
-    for (const Chunk& c : chunks) {
+    for (size_t ci = 0; ci < chunks.size(); ci++) {
+        const Chunk& c = chunks[ci];
+        GroupTable gt;
+        gt.n_groups = c.n_traj;
+        gt.h_net0 = hg + grp_off[ci];
+        gt.d_net0 = ws->grp.as<int32_t>() + grp_off[ci];
+        gt.d_cnt = ws->grp_cnt.as<int64_t>();
+        gt.d_tile0 = ws->grp_tile0.as<int64_t>();
+        gt.d_scan = ws->grp_scan.as<int64_t>();
         ChunkCtx ctx;
         ctx.vtab = reinterpret_cast<const float2*>(plan->d_var_table);
         ctx.var_ids = tr->var_ids;
@@ -309,8 +340,9 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         for (size_t st = 0; st < bp.steps.size(); st++) {
             const StepDesc& h = bp.steps[st];
             int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
-            if (h.kind == STEP_GEMM) {
-                e = launch_gemm_step(h, ctx, ni, ws->pack[0].as<float>(), ws->pack[1].as<float>(), ws->err.as<int>(), s);
+            if (h.kind == STEP_GEMM || h.kind == STEP_GEMM_STACKED) {
+                e = launch_gemm_step(h, ctx, ni, ws->pack[0].as<float>(), ws->pack[1].as<float>(), ws->err.as<int>(),
+                                     gt, s);
                 if (e) return e;
             } else {
                 launch_contract_step(bp.d_steps + st, h, ctx, ni, s);

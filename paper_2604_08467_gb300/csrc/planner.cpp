@@ -182,10 +182,12 @@ struct Move {
 };
 
 struct CostModel {
-    double mult[3];             // CONST, TRAJ, NET copies
-    double flops_rate = 6.0e13; // complex-MAC work in real flops/s (8 flops per MAC)
-    double bw = 5.0e12;         // bytes/s
-    double launch = 3.0e-6;     // per step
+    double mult[3];              // CONST, TRAJ, NET copies
+    double tc_rate = 1.0e14;     // tensor-core steps, real flops/s (8 per complex MAC), FP32-accurate split
+    double simt_rate = 2.5e12;   // SIMT contraction kernel, real flops/s
+    double bw = 3.0e12;          // effective bytes/s of the memory-bound kernels
+    double launch = 3.0e-6;      // per launch
+    bool allow_tc = true;
 };
 
 struct Searcher {
@@ -261,19 +263,56 @@ struct Searcher {
     }
 
     // Cost of one step (count once for a lockstep mirror pair).
-    void account(int32_t cls, int64_t rank_out, int32_t nsum, const GT& A, const GT* B) {
-        double m = cm->mult[cls];
-        double mac = std::ldexp(1.0, (int)(rank_out + nsum));
+    // Modelled cost of one step on the kernel it will run on (the same
+    // eligibility rules as classify_step): tensor-core GEMMs pay their MACs at
+    // the tensor rate plus the operand packing traffic; other steps run on the
+    // SIMT kernel.  A trajectory-level operand of a network step is read once
+    // per trajectory.
+    void account(int32_t cls, const std::vector<int32_t>& out, int32_t nsum, const GT& A, const GT& B) {
+        const int64_t rank_out = (int64_t)out.size();
+        const double m = cm->mult[cls];
+        const double mac = std::ldexp(1.0, (int)(rank_out + nsum));
         double by = 8.0 * std::ldexp(1.0, (int)rank_out) * m;
-        auto rd = [&](const GT& g) {
-            if (cls == CLS_NET && g.cls != CLS_NET) return 8.0 * size_of(g, false) * cm->mult[g.cls];
-            return 8.0 * size_of(g, false) * cm->mult[g.cls];
-        };
-        by += rd(A);
-        if (B) by += rd(*B);
+        by += 8.0 * size_of(A, false) * cm->mult[A.cls];
+        by += 8.0 * size_of(B, false) * cm->mult[B.cls];
         macs[cls] += mac * m;
         bytes[cls] += by;
-        time += std::max(8.0 * mac * m / cm->flops_rate, by / cm->bw) + cm->launch;
+        int fr[2] = {0, 0}, nh = 0;
+        for (int32_t x : out) {
+            const bool ia = std::binary_search(A.idx.begin(), A.idx.end(), x);
+            const bool ib = std::binary_search(B.idx.begin(), B.idx.end(), x);
+            if (ia && ib) nh++;
+            else if (ia) fr[0]++;
+            else fr[1]++;
+        }
+        auto pcls = [&](const GT& g) { return (cls == CLS_NET && g.cls != CLS_NET && g.nslice > 0) ? (int)CLS_NET : (int)g.cls; };
+        const GT* op[2] = {&A, &B};
+        int kind = 0, ra = 0;
+        if (cm->allow_tc && nsum >= 3) {
+            if (cls == CLS_NET && nh == 0)
+                for (int a = 0; a < 2 && !kind; a++)
+                    if (pcls(*op[a]) == CLS_NET && pcls(*op[1 - a]) != CLS_NET && fr[a] < 7 && fr[1 - a] >= 6 && fr[a] <= 16) {
+                        kind = 2;
+                        ra = a;
+                    }
+            if (!kind) {
+                ra = fr[0] >= fr[1] ? 0 : 1;
+                if (fr[ra] >= 7 && fr[1 - ra] >= 6 && nh <= 20) kind = 1;
+            }
+        }
+        double t;
+        const double flops = 8.0 * mac * m;
+        if (kind) {
+            const double kh = std::ceil(2.0 * std::ldexp(1.0, nsum) / 32.0) * 32.0;
+            const double hh = std::ldexp(1.0, nh);
+            const double fa = hh * std::ldexp(1.0, fr[ra]) * 2 * kh * cm->mult[pcls(*op[ra])];
+            const double fb = hh * std::ldexp(2.0, fr[1 - ra]) * 2 * kh * cm->mult[pcls(*op[1 - ra])];
+            const double pack_bytes = 4.0 * 2.0 * (fa + fb) + 8.0 * (size_of(A, false) * cm->mult[A.cls] + size_of(B, false) * cm->mult[B.cls]);
+            t = flops / cm->tc_rate + (pack_bytes + 8.0 * std::ldexp(1.0, (int)rank_out) * m) / cm->bw + 3 * cm->launch;
+        } else {
+            t = std::max(flops / cm->simt_rate, by / cm->bw) + cm->launch;
+        }
+        time += t;
         max_rank = std::max<int64_t>(max_rank, rank_out);
     }
 
@@ -296,7 +335,7 @@ struct Searcher {
         std::vector<int32_t> out;
         int32_t nsum, cls, nslice;
         result(a, b, out, nsum, cls, nslice);
-        if (count) account(cls, (int64_t)out.size(), nsum, t[a], &t[b]);
+        if (count) account(cls, out, nsum, t[a], t[b]);
         GT g;
         g.idx = std::move(out);
         g.cls = cls;
@@ -561,6 +600,33 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
     for (auto it = s.moves.rbegin(); it != s.moves.rend(); ++it)
         if (it->c == root_src && it->type == MV_SLICE) root_src = it->a;
 
+    // The contraction that consumes every tensor (through slice views), and the
+    // bits it sums.  A producer writes those bits innermost, in increasing id
+    // order of the consumer's view, and every step lists its summed bits in
+    // increasing id order: the consumer then reads its operands' summed bits
+    // contiguously (coalesced packing for tensor-core steps).
+    std::vector<int32_t> cons(s.t.size(), -1);
+    for (size_t i = 0; i < s.moves.size(); i++) {
+        const Move& mv = s.moves[i];
+        if (mv.type != MV_CONTRACT) continue;
+        cons[mv.a] = cons[mv.b] = (int32_t)i;
+    }
+    for (auto it = s.moves.rbegin(); it != s.moves.rend(); ++it) {
+        if (it->type != MV_SLICE) continue;
+        cons[it->a] = cons[it->c];
+        if (it->ma >= 0) cons[it->ma] = cons[it->mc];
+    }
+    auto summed_by = [&](int32_t k) {
+        std::vector<int32_t> S;
+        const Move& m = s.moves[k];
+        const auto &ia = s.t[m.a].idx, &ib = s.t[m.b].idx, &ic = s.t[m.c].idx;
+        for (int32_t x : ia)
+            if (std::binary_search(ib.begin(), ib.end(), x) && !std::binary_search(ic.begin(), ic.end(), x) &&
+                idx[x].kind != IX_SLICE)
+                S.push_back(x);
+        return S;   // sorted (ia is sorted)
+    };
+
     std::string summary;
     for (const Move& mv : s.moves) {
         if (mv.type == MV_SLICE) {
@@ -590,6 +656,15 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
             out = open;
             out.insert(out.end(), rest.begin(), rest.end());
         } else {
+            std::vector<int32_t> lead;
+            if (cons[mv.c] >= 0) {
+                lead = summed_by(cons[mv.c]);
+            } else if (mv.mc >= 0 && cons[mv.mc] >= 0) {
+                for (int32_t x : summed_by(cons[mv.mc])) lead.push_back(idx[x].mirror);
+            }
+            for (int32_t x : lead)
+                if (std::binary_search(C.idx.begin(), C.idx.end(), x) && std::find(out.begin(), out.end(), x) == out.end())
+                    out.push_back(x);
             keep_from(A);
             keep_from(B);
         }
@@ -602,6 +677,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         std::vector<int32_t> sum;
         for (int32_t x : A.layout)
             if (pos_in(B.layout, x) >= 0 && pos_in(out, x) < 0 && idx[x].kind != IX_SLICE) sum.push_back(x);
+        std::sort(sum.begin(), sum.end());
         if ((int)sum.size() > kMaxSum)
             return set_error(PTN_ERR_TOO_LARGE, "a contraction step sums %d bits (max %d)",
                              (int)sum.size(), kMaxSum);
@@ -1080,6 +1156,7 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
         cm.mult[CLS_CONST] = 1.0;
         cm.mult[CLS_TRAJ] = E;
         cm.mult[CLS_NET] = j == 0 ? E : D;
+        cm.allow_tc = !opts.simt_only;
 
         Searcher best(net, cm), cur_s(net, cm);
         double best_time = INFINITY;

@@ -65,12 +65,30 @@ __global__ void __launch_bounds__(256) k_contract_direct(const StepDesc* __restr
         for (int i = threadIdx.x; i < (int)(sizeof(StepDesc) / sizeof(int4)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+    // Operand offsets of the low (up to 8) output bits, shared by the block: a
+    // block iteration covers 256 consecutive outputs, so each element adds one
+    // table entry to the offsets of its remaining high bits.
+    __shared__ int64_t tab[2][256];
+    const int lowb = s.n_out < 8 ? s.n_out : 8;
+    {
+        const int t = threadIdx.x;
+        int64_t a = 0, b = 0;
+        for (int p = 0; p < lowb; p++)
+            if ((t >> p) & 1) {
+                a += s.out_stride[0][p];
+                b += s.out_stride[1][p];
+            }
+        tab[0][t] = a;
+        tab[1][t] = b;
+    }
+    __syncthreads();
     const int64_t total = n_inst << s.n_out;
     const int64_t mask = s.out_size - 1;
+    const int64_t lowmask = (1ll << lowb) - 1;
     const int nk = s.n_sum;
     const bool ca = s.op[0].conj, cb = s.op[1].conj;
     float2* outbase = c.arena[s.out_arena] + s.out_off * c.arena_inst[s.out_arena];
-    int64_t cur_inst = -1;
+    int64_t cur_inst = -1, cur_hi = -1, hia = 0, hib = 0;
     const float2 *A = nullptr, *B = nullptr;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
@@ -81,12 +99,17 @@ __global__ void __launch_bounds__(256) k_contract_direct(const StepDesc* __restr
             B = operand_ptr(s.op[1], s.out_cls, inst, c);
             cur_inst = inst;
         }
-        int64_t oa = 0, ob = 0;
-        for (int p = 0; p < s.n_out; p++)
-            if ((o >> p) & 1) {
-                oa += s.out_stride[0][p];
-                ob += s.out_stride[1][p];
-            }
+        const int64_t hi = o >> lowb;
+        if (hi != cur_hi) {
+            hia = hib = 0;
+            for (int p = lowb; p < s.n_out; p++)
+                if ((o >> p) & 1) {
+                    hia += s.out_stride[0][p];
+                    hib += s.out_stride[1][p];
+                }
+            cur_hi = hi;
+        }
+        const int64_t oa = hia + tab[0][o & lowmask], ob = hib + tab[1][o & lowmask];
         float2 acc = make_float2(0.f, 0.f);
         int64_t ka = 0, kb = 0;
         const int64_t nterm = (int64_t)1 << nk;

@@ -66,8 +66,11 @@ struct GroupTable {
     int64_t* d_tile0 = nullptr;   // n_groups + 1
     int64_t* d_scan = nullptr;    // scan_tmp_elems(n_groups + 1)
 };
-ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, float* pack_a,
-                            float* pack_b, int* err, const GroupTable& grp, cudaStream_t s);
+// precision: PTN_PREC_*; amax_a/amax_b: device scratch of one uint32 per packed
+// instance (used by the FP16 mode's scaling).
+ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
+                            uint32_t* amax_a, uint32_t* amax_b, int* err, const GroupTable& grp, int precision,
+                            cudaStream_t s);
 
 // ---- launchers (kernels_sample.cu)
 void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, uint64_t seed,

@@ -1,23 +1,32 @@
 // Tensor-core execution of the large pairwise contractions of a path (the
 // batched complex GEMMs of Sec. III-A's contraction, real and imaginary parts
-// split into real GEMMs) on sm_103a: tcgen05.mma (kind::tf32) with the
-// accumulator in tensor memory, operands staged by TMA into 128-byte-swizzled
-// shared memory through an mbarrier pipeline.
+// split into real GEMMs) on sm_103a: tcgen05.mma with the accumulator in
+// tensor memory, operands staged by TMA into 128-byte-swizzled shared memory
+// through an mbarrier pipeline.
 //
 // A step  C[inst][m, n] (h) = sum_k A[m, k] (h) * B[n, k] (h)  runs in two phases:
 //  1. pack: each operand is gathered (any bit layout, merged-gate variant,
-//     prefix slice) into row-major K-contiguous rows and split for FP32-accurate
-//     products on TF32 tensor cores, x = hi + lo with hi = x rounded to TF32
-//     and lo = (x - hi) rounded to TF32 (|x - hi - lo| <= 2^-24 |x|):
+//     prefix slice) into row-major K-contiguous rows, each value split into a
+//     high and a low part in the tensor-core input format F:
 //       A rows:  [ hi(re0) hi(im0) hi(re1) ... | lo(re0) lo(im0) ... ]
 //       B rows 2n, 2n+1 (the complex product as real dot products):
 //         row 2n   = (re, -im) per k,  row 2n+1 = (im, re) per k, each [hi | lo];
 //     so that  A_row . B_row(2n) = Re C[m, n]  and  A_row . B_row(2n+1) = Im C[m, n];
-//  2. GEMM: D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T accumulated in TMEM
-//     (the lo*lo term is below FP32 resolution), D[m][2n + c] -> C[m, n],
-//     written through the step's output strides (any layout).
+//  2. GEMM: D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T with FP32 accumulation
+//     in TMEM (the lo*lo term is dropped), D[m][2n + c] -> C[m, n], written
+//     through the step's output strides (any layout).
+// Formats (the precision modes of the contraction):
+//  - TF32 (PTN_PREC_FP32): hi = x rounded to TF32, lo = (x - hi) rounded to
+//    TF32; |x - hi - lo| <= 2^-24 |x|, i.e. FP32-accurate products;
+//  - BF16 (PTN_PREC_BF16X3): hi, lo rounded to BF16 (16 significant bits in
+//    total, FP32 exponent range);
+//  - FP16 (PTN_PREC_FP16X3): hi, lo rounded to FP16 (22 significant bits) after
+//    scaling each packed instance by a power of two that brings its largest
+//    magnitude into [0.5, 1); the epilogue undoes both scales exactly.
 // Conjugated operands (bra layer) are conjugated while packing.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -31,10 +40,10 @@ namespace {
 
 constexpr int kBM = 128;          // UMMA M (cta_group::1)
 constexpr int kBN = 128;          // UMMA N (realified B rows per tile)
-constexpr int kBK = 32;           // fp32 elements per 128-byte swizzle row
+constexpr int kRowBytes = 128;    // one swizzle row of every tile
 constexpr int kStages = 3;        // pipeline depth (4 tiles of 16 KB per stage)
-constexpr int kTileA = kBM * kBK * 4;
-constexpr int kTileB = kBN * kBK * 4;
+constexpr int kTileA = kBM * kRowBytes;
+constexpr int kTileB = kBN * kRowBytes;
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;
 constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 1024;   // align slack + stages + barriers/offsets
 constexpr int kMaxPackBits = 40;
@@ -44,17 +53,41 @@ constexpr int kMaxPackBits = 40;
 constexpr int kAcc = 4;
 constexpr uint32_t kTmemCols = kAcc * kBN;   // 512: the whole TMEM of the SM (one CTA per SM)
 
+enum GemmFmt { FMT_TF32 = 0, FMT_BF16 = 1, FMT_FP16 = 2 };
+
+template <int F>
+struct Fmt;
+template <>
+struct Fmt<FMT_TF32> {
+    using T = float;
+    static constexpr int kBytes = 4;
+    static constexpr uint32_t kAB = 2;   // TF32 in the instruction descriptor
+};
+template <>
+struct Fmt<FMT_BF16> {
+    using T = __nv_bfloat16;
+    static constexpr int kBytes = 2;
+    static constexpr uint32_t kAB = 1;   // BF16
+};
+template <>
+struct Fmt<FMT_FP16> {
+    using T = __half;
+    static constexpr int kBytes = 2;
+    static constexpr uint32_t kAB = 0;   // F16
+};
+
 struct PackArgs {
     OperandDesc op;
     int32_t pcls;            // instance class the packed operand is addressed by
     int32_t role;            // 0: rows (A), 1: realified (B)
     int32_t n_rb, n_hb, n_kb;
-    int32_t Kh;              // floats per half row (hi or lo), multiple of 32
+    int32_t Kh;              // elements per half row (hi or lo), a multiple of one swizzle row
     int64_t n_pinst;
     int64_t r_stride[kMaxPackBits];   // operand strides of the row bits
     int64_t h_stride[kMaxPackBits];
     int64_t k_stride[kMaxPackBits];
-    float* dst;
+    void* dst;
+    const uint32_t* amax;    // FP16: largest |component| per packed instance (float bits), else null
 };
 
 struct GemmArgs {
@@ -73,24 +106,45 @@ struct GemmArgs {
     float2* out;
     int64_t out_size;
     int* err;
+    const uint32_t* amax_a;      // FP16 scales (see PackArgs), else null
+    const uint32_t* amax_b;
     int64_t m_stride[kMaxOut];
     int64_t n_stride[kMaxOut];
     int64_t h_stride[kMaxOut];
 };
 
+// Power-of-two exponent e with max magnitude in [2^(e-1), 2^e); 0 for max 0.
+__device__ __forceinline__ int scale_exp(const uint32_t* amax, int64_t pi) {
+    if (!amax) return 0;
+    const float m = __uint_as_float(amax[pi]);
+    if (!(m > 0.f)) return 0;
+    int e;
+    frexpf(m, &e);
+    return e;
+}
+
 // Round to the nearest TF32 value (ties away from zero): add half of the 13
-// dropped mantissa bits, then clear them.  Splitting x = hi + lo with both
-// halves rounded this way makes the tensor core's TF32 read of either half
-// exact and leaves |x - hi - lo| <= 2^-24 |x|.
+// dropped mantissa bits, then clear them.
 __device__ __forceinline__ float tf32_rn(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
-struct Split {
-    float hi, lo;
-};
-__device__ __forceinline__ Split tf32_split(float x) {
-    const float h = tf32_rn(x);
-    return {h, tf32_rn(x - h)};
+
+template <int F>
+__device__ __forceinline__ void split(float x, typename Fmt<F>::T& hi, typename Fmt<F>::T& lo);
+template <>
+__device__ __forceinline__ void split<FMT_TF32>(float x, float& hi, float& lo) {
+    hi = tf32_rn(x);
+    lo = tf32_rn(x - hi);
+}
+template <>
+__device__ __forceinline__ void split<FMT_BF16>(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+template <>
+__device__ __forceinline__ void split<FMT_FP16>(float x, __half& hi, __half& lo) {
+    hi = __float2half_rn(x);
+    lo = __float2half_rn(x - __half2float(hi));
 }
 
 __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, int pcls, int64_t inst,
@@ -120,8 +174,41 @@ __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, 
     return p;
 }
 
+__device__ __forceinline__ int64_t pack_offset(const PackArgs& a, int64_t row, int64_t h, int64_t kc) {
+    int64_t off = 0;
+    for (int i = 0; i < a.n_rb; i++)
+        if ((row >> i) & 1) off += a.r_stride[i];
+    for (int i = 0; i < a.n_hb; i++)
+        if ((h >> i) & 1) off += a.h_stride[i];
+    for (int i = 0; i < a.n_kb; i++)
+        if ((kc >> i) & 1) off += a.k_stride[i];
+    return off;
+}
+
+// Largest |component| of every packed instance (FP16 scaling).
+__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ PackArgs a, const ChunkCtx c,
+                                                uint32_t* __restrict__ amax) {
+    const int64_t nrow = (int64_t)1 << a.n_rb, nh = (int64_t)1 << a.n_hb, kc_real = (int64_t)1 << a.n_kb;
+    const int64_t total = a.n_pinst * nh * nrow * kc_real;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kc = g % kc_real;
+        int64_t rest = g / kc_real;
+        const int64_t row = rest % nrow;
+        rest /= nrow;
+        const int64_t h = rest % nh;
+        const int64_t pi = rest / nh;
+        const float2 v = pack_operand_ptr(a.op, a.pcls, pi, c)[pack_offset(a, row, h, kc)];
+        const float m = fmaxf(fabsf(v.x), fabsf(v.y));
+        if (m > 0.f) atomicMax(&amax[pi], __float_as_uint(m));
+    }
+}
+
 // One thread per (packed instance, h, row, complex k) including the K padding.
+template <int F>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a, const ChunkCtx c) {
+    using T = typename Fmt<F>::T;
+    T* dst = static_cast<T*>(a.dst);
     const int64_t kcp = a.Kh / 2;                       // complex slots per half row
     const int64_t nrow = (int64_t)1 << a.n_rb, nh = (int64_t)1 << a.n_hb;
     const int64_t kc_real = (int64_t)1 << a.n_kb;
@@ -129,6 +216,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
     const int64_t rowlen = 2 * (int64_t)a.Kh;
     int64_t cur = -1;
     const float2* base = nullptr;
+    float sc = 1.f;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t kc = g % kcp;
@@ -141,32 +229,36 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
         if (kc < kc_real) {
             if (pi != cur) {
                 base = pack_operand_ptr(a.op, a.pcls, pi, c);
+                sc = ldexpf(1.f, -scale_exp(a.amax, pi));
                 cur = pi;
             }
-            int64_t off = 0;
-            for (int i = 0; i < a.n_rb; i++)
-                if ((row >> i) & 1) off += a.r_stride[i];
-            for (int i = 0; i < a.n_hb; i++)
-                if ((h >> i) & 1) off += a.h_stride[i];
-            for (int i = 0; i < a.n_kb; i++)
-                if ((kc >> i) & 1) off += a.k_stride[i];
-            const float2 v = base[off];
-            re = v.x;
-            im = a.op.conj ? -v.y : v.y;
+            const float2 v = base[pack_offset(a, row, h, kc)];
+            re = v.x * sc;
+            im = (a.op.conj ? -v.y : v.y) * sc;
         }
         const int64_t z = pi * nh + h;
-        const Split sr = tf32_split(re), si = tf32_split(im);
+        T rh, rl, ih, il;
+        split<F>(re, rh, rl);
+        split<F>(im, ih, il);
         if (a.role == 0) {
-            float* d = a.dst + (z * nrow + row) * rowlen + 2 * kc;
-            *reinterpret_cast<float2*>(d) = make_float2(sr.hi, si.hi);
-            *reinterpret_cast<float2*>(d + a.Kh) = make_float2(sr.lo, si.lo);
+            T* d = dst + (z * nrow + row) * rowlen + 2 * kc;
+            d[0] = rh;
+            d[1] = ih;
+            d[a.Kh] = rl;
+            d[a.Kh + 1] = il;
         } else {
-            float* d0 = a.dst + (z * 2 * nrow + 2 * row) * rowlen + 2 * kc;
-            float* d1 = d0 + rowlen;
-            *reinterpret_cast<float2*>(d0) = make_float2(sr.hi, -si.hi);
-            *reinterpret_cast<float2*>(d0 + a.Kh) = make_float2(sr.lo, -si.lo);
-            *reinterpret_cast<float2*>(d1) = make_float2(si.hi, sr.hi);
-            *reinterpret_cast<float2*>(d1 + a.Kh) = make_float2(si.lo, sr.lo);
+            T* d0 = dst + (z * 2 * nrow + 2 * row) * rowlen + 2 * kc;
+            T* d1 = d0 + rowlen;
+            T nih, nil;
+            split<F>(-im, nih, nil);
+            d0[0] = rh;
+            d0[1] = nih;
+            d0[a.Kh] = rl;
+            d0[a.Kh + 1] = nil;
+            d1[0] = ih;
+            d1[1] = rh;
+            d1[a.Kh] = il;
+            d1[a.Kh + 1] = rl;
         }
     }
 }
@@ -231,16 +323,31 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = kBN.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+// Instruction descriptor: D = F32, A = B = format F, both K-major, M = 128, N = kBN.
+template <int F>
+__host__ __device__ constexpr uint32_t idesc() {
+    return (1u << 4) | (Fmt<F>::kAB << 7) | (Fmt<F>::kAB << 10) | ((uint32_t)(kBN >> 3) << 17) |
+           ((uint32_t)(kBM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_tf32(uint32_t taddr, uint64_t ad, uint64_t bd, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
-        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-        : "memory");
+// One MMA over 32 bytes of K (8 TF32 or 16 BF16/FP16 elements).
+template <int F>
+__device__ __forceinline__ void umma(uint32_t taddr, uint64_t ad, uint64_t bd, uint32_t acc) {
+    if constexpr (F == FMT_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(idesc<F>()), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(idesc<F>()), "r"(acc)
+            : "memory");
+    }
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -262,9 +369,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // One CTA = one 128 x kBN tile of one (instance, h) GEMM.  Warp 0 lane 0 issues
 // TMA loads, warp 1 lane 0 issues tcgen05.mma; all four warps drain TMEM.
-__global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CUtensorMap tmA,
-                                                      const __grid_constant__ CUtensorMap tmB,
-                                                      const __grid_constant__ GemmArgs g) {
+template <int F>
+__global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                 const __grid_constant__ CUtensorMap tmB,
+                                                 const __grid_constant__ GemmArgs g) {
+    constexpr int kBK = kRowBytes / Fmt<F>::kBytes;   // elements per swizzle row
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* stage0 = smem;
@@ -273,7 +382,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
     uint64_t* accb = empty + kStages;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-    int64_t* noff = reinterpret_cast<int64_t*>(tslot + 4);   // kBN / 2 column offsets (in 256-byte tail)
+    int64_t* noff = reinterpret_cast<int64_t*>(tslot + 4);   // kBN / 2 column offsets
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t inst, h, row_end;
@@ -340,12 +449,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
         return 0;
     };
     int za, zb;
+    int64_t pb;
     if (!g.stacked) {
         za = (int)(pinst(g.a_pcls) * g.n_h + h);
-        zb = (int)(pinst(g.b_pcls) * g.n_h + h);
+        pb = pinst(g.b_pcls);
+        zb = (int)(pb * g.n_h + h);
     } else {
         za = 0;
-        zb = g.b_pcls == CLS_TRAJ ? (int)inst : 0;
+        pb = g.b_pcls == CLS_TRAJ ? inst : 0;
+        zb = (int)pb;
     }
 
     if (warp == 0) {
@@ -381,11 +493,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
                 const uint32_t acc = tmem + (uint32_t)((kb % kAcc) * kBN);
                 const bool fresh = kb < kAcc;
 #pragma unroll
-                for (int kk = 0; kk < kBK / 8; kk++) {   // UMMA K = 8 tf32 = 32 bytes
+                for (int kk = 0; kk < kRowBytes / 32; kk++) {   // 32 bytes of K per MMA
                     const uint32_t o = kk * 32;
-                    umma_tf32(acc, sdesc_sw128(sa + o), sdesc_sw128(sb + o), (fresh && kk == 0) ? 0u : 1u);
-                    umma_tf32(acc, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
-                    umma_tf32(acc, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
+                    umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sb + o), (fresh && kk == 0) ? 0u : 1u);
+                    umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
+                    umma<F>(acc, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
                 }
                 umma_commit(&empty[s]);   // stage free once these MMAs have read it
             }
@@ -401,10 +513,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
         if (lane == 0) atomicExch(g.err, 3);
     } else if (!*abort) {
         const int64_t row = (int64_t)m0 + warp * 32 + lane;
-        int64_t m = row, out_inst = inst;
+        int64_t m = row, out_inst = inst, pa = 0;
         if (g.stacked) {
             out_inst = row >> g.m_bits;
             m = row & (((int64_t)1 << g.m_bits) - 1);
+            pa = out_inst;
+        } else {
+            pa = pinst(g.a_pcls);
         }
         int64_t moff = 0;
         for (int i = 0; i < g.n_mb; i++)
@@ -413,6 +528,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
             if ((h >> i) & 1) moff += g.h_stride[i];
         float2* out = g.out + out_inst * g.out_size + moff;
         const bool row_ok = row < row_end;
+        const float unscale = (F == FMT_FP16 && row_ok) ? ldexpf(1.f, scale_exp(g.amax_a, pa) + scale_exp(g.amax_b, pb)) : 1.f;
         const int n_acc = g.nkb < kAcc ? g.nkb : kAcc;
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
@@ -430,7 +546,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int col = n0 + c0 + 2 * j;
-                    if (col < g.N2) out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j], v[2 * j + 1]);
+                    if (col < g.N2) out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j] * unscale, v[2 * j + 1] * unscale);
                 }
             }
         }
@@ -441,6 +557,20 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tf32(const __grid_constant__ CU
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
+}
+
+// Tiles of every trajectory group of a stacked GEMM (cnt[n_groups] = 0, so the
+// exclusive scan of cnt ends with the total).
+__global__ void k_group_tiles(const int32_t* __restrict__ net0, int64_t n_groups, int m_bits, int64_t tiles_n,
+                              int64_t* __restrict__ cnt) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > n_groups) return;
+    if (g == n_groups) {
+        cnt[g] = 0;
+        return;
+    }
+    const int64_t r = (int64_t)(net0[g + 1] - net0[g]) << m_bits;
+    cnt[g] = ((r + kBM - 1) / kBM) * tiles_n;
 }
 
 // ---------------------------------------------------------- host helpers --
@@ -460,31 +590,20 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-ptn_status make_map(CUtensorMap* m, float* base, int64_t kp, int64_t rows, int64_t zs, int box_rows) {
+// 3D map over packed rows: (elements of a row, rows, instances), boxes of one
+// 128-byte swizzle row by box_rows rows.
+ptn_status make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int ebytes, int64_t row_elems, int64_t rows,
+                    int64_t zs, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(PTN_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)zs};
-    cuuint64_t strides[2] = {(cuuint64_t)kp * 4, (cuuint64_t)kp * 4 * (cuuint64_t)rows};
-    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+    cuuint64_t dims[3] = {(cuuint64_t)row_elems, (cuuint64_t)rows, (cuuint64_t)zs};
+    cuuint64_t strides[2] = {(cuuint64_t)row_elems * ebytes, (cuuint64_t)row_elems * ebytes * (cuuint64_t)rows};
+    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / ebytes), (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(PTN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return PTN_OK;
-}
-
-// Tiles of every trajectory group of a stacked GEMM (cnt[n_groups] = 0, so the
-// exclusive scan of cnt ends with the total).
-__global__ void k_group_tiles(const int32_t* __restrict__ net0, int64_t n_groups, int m_bits, int64_t tiles_n,
-                              int64_t* __restrict__ cnt) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g > n_groups) return;
-    if (g == n_groups) {
-        cnt[g] = 0;
-        return;
-    }
-    const int64_t r = (int64_t)(net0[g + 1] - net0[g]) << m_bits;
-    cnt[g] = ((r + kBM - 1) / kBM) * tiles_n;
 }
 
 int pack_class(const OperandDesc& d, int step_cls) {
@@ -493,10 +612,19 @@ int pack_class(const OperandDesc& d, int step_cls) {
     return d.cls;
 }
 
-}  // namespace
+unsigned grid_of(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
 
-ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, float* pack_a, float* pack_b,
-                            int* err, const GroupTable& grp, cudaStream_t s) {
+template <int F>
+ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
+                    uint32_t* amax_a, uint32_t* amax_b, int* err, const GroupTable& grp, cudaStream_t s) {
+    constexpr int kEB = Fmt<F>::kBytes;
+    constexpr int kBK = kRowBytes / kEB;
+    const CUtensorMapDataType dt = F == FMT_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : F == FMT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const bool stacked = st.kind == STEP_GEMM_STACKED;
     const int a = st.gemm_a, b = 1 - a;
     PackArgs pa, pb;
@@ -562,29 +690,35 @@ ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_i
     ga.out = ctx.arena[st.out_arena] + st.out_off * ctx.arena_inst[st.out_arena];
     ga.out_size = st.out_size;
     ga.err = err;
-    cudaError_t e;
-    auto grid = [](int64_t n) {
-        int64_t b = (n + 255) / 256;
-        return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
-    };
     const int64_t tot_a = pa.n_pinst * (1ll << nh) * M * (Kh / 2);
     const int64_t tot_b = pb.n_pinst * (1ll << nh) * N * (Kh / 2);
+    cudaError_t e;
+    if (F == FMT_FP16) {
+        e = cudaMemsetAsync(amax_a, 0, sizeof(uint32_t) * pa.n_pinst, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(amax_b, 0, sizeof(uint32_t) * pb.n_pinst, s);
+        if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "scale reset: %s", cudaGetErrorString(e));
+        StatScope sc(K_MISC, s, 8.0 * (double)(tot_a + tot_b), 0.0);
+        k_absmax<<<grid_of(tot_a), 256, 0, s>>>(pa, ctx, amax_a);
+        k_absmax<<<grid_of(tot_b), 256, 0, s>>>(pb, ctx, amax_b);
+        pa.amax = ga.amax_a = amax_a;
+        pb.amax = ga.amax_b = amax_b;
+    }
     {
-        StatScope sc(K_MISC, s, 8.0 * (double)(tot_a + tot_b) + 16.0 * (double)tot_a + 32.0 * (double)tot_b, 0.0);
-        k_pack<<<grid(tot_a), 256, 0, s>>>(pa, ctx);
-        k_pack<<<grid(tot_b), 256, 0, s>>>(pb, ctx);
+        StatScope sc(K_MISC, s, 8.0 * (double)(tot_a + tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b, 0.0);
+        k_pack<F><<<grid_of(tot_a), 256, 0, s>>>(pa, ctx);
+        k_pack<F><<<grid_of(tot_b), 256, 0, s>>>(pb, ctx);
     }
     CUtensorMap mA, mB;
     int64_t blocks = ga.tiles_m * ga.tiles_n * n_inst * (1ll << nh);
     ptn_status ps;
     if (!stacked) {
-        ps = make_map(&mA, pack_a, 2 * Kh, M, pa.n_pinst * (1ll << nh), kBM);
+        ps = make_map(&mA, pack_a, dt, kEB, 2 * Kh, M, pa.n_pinst * (1ll << nh), kBM);
     } else {
         // rows of all networks, network-major; groups (trajectories) tile separately.
         // The pack buffer holds at least one full tile of rows (planner), so a
         // chunk with fewer rows still spans the TMA box.
         const int64_t rows = pa.n_pinst * M;
-        ps = make_map(&mA, pack_a, 2 * Kh, rows < kBM ? kBM : rows, 1, kBM);
+        ps = make_map(&mA, pack_a, dt, kEB, 2 * Kh, rows < kBM ? kBM : rows, 1, kBM);
         ga.stacked = 1;
         ga.m_bits = nm;
         ga.n_groups = grp.n_groups;
@@ -601,21 +735,35 @@ ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_i
         launch_exclusive_scan(grp.d_cnt, grp.d_tile0, grp.n_groups + 1, grp.d_scan, s);
     }
     if (ps) return ps;
-    ps = make_map(&mB, pack_b, 2 * Kh, 2 * N, pb.n_pinst * (1ll << nh), kBN);
+    ps = make_map(&mB, pack_b, dt, kEB, 2 * Kh, 2 * N, pb.n_pinst * (1ll << nh), kBN);
     if (ps) return ps;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_gemm_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+        cudaFuncSetAttribute(k_gemm<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
         attr = true;
     }
     if (blocks <= 0) return PTN_OK;
     const double flops = 8.0 * (double)n_inst * (double)(1ll << nh) * (double)M * (double)N * (double)Kc;
-    const double bytes = 8.0 * ((double)n_inst * (1ll << nh) * M * N) + 4.0 * 2 * Kh * ((double)pa.n_pinst * M + (double)pb.n_pinst * 2 * N) * (1ll << nh);
+    const double bytes = 8.0 * ((double)n_inst * (1ll << nh) * M * N) +
+                         (double)kEB * 2 * Kh * ((double)pa.n_pinst * M + (double)pb.n_pinst * 2 * N) * (1ll << nh);
     StatScope sc(K_CONTRACT_GEMM, s, bytes, flops);
-    k_gemm_tf32<<<(unsigned)blocks, 128, kGemmSmem, s>>>(mA, mB, ga);
+    k_gemm<F><<<(unsigned)blocks, 128, kGemmSmem, s>>>(mA, mB, ga);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "gemm launch: %s", cudaGetErrorString(e));
     return PTN_OK;
+}
+
+}  // namespace
+
+ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
+                            uint32_t* amax_a, uint32_t* amax_b, int* err, const GroupTable& grp, int precision,
+                            cudaStream_t s) {
+    switch (precision) {
+        case PTN_PREC_FP32: return run_gemm<FMT_TF32>(st, ctx, n_inst, pack_a, pack_b, amax_a, amax_b, err, grp, s);
+        case PTN_PREC_BF16X3: return run_gemm<FMT_BF16>(st, ctx, n_inst, pack_a, pack_b, amax_a, amax_b, err, grp, s);
+        case PTN_PREC_FP16X3: return run_gemm<FMT_FP16>(st, ctx, n_inst, pack_a, pack_b, amax_a, amax_b, err, grp, s);
+    }
+    return set_error(PTN_ERR_UNSUPPORTED, "precision mode %d", precision);
 }
 
 }  // namespace ptn

@@ -98,14 +98,14 @@ struct PlanWorkspace {
     DevBuf lvl_traj[2], lvl_prefix[2], lvl_count[2];
     DevBuf s_cap, s_tmp_off, s_rank0, s_excl, s_first, s_ndist, s_out_off, s_tmp_x, s_tmp_c, s_scan;
     DevBuf zero_prefix;
-    DevBuf pack[2], err, grp, grp_cnt, grp_tile0, grp_scan;
+    DevBuf pack[2], err, grp, grp_cnt, grp_tile0, grp_scan, amax[2];
     HostBuf h_traj, h_chunk_traj, h_net_tl, h_small, h_grp;
     void release() {
         DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &roots, &marg, &Z, &w, &cdf, &m,
                          &lvl_traj[0], &lvl_traj[1], &lvl_prefix[0], &lvl_prefix[1], &lvl_count[0], &lvl_count[1],
                          &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
                          &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err, &grp, &grp_cnt,
-                         &grp_tile0, &grp_scan};
+                         &grp_tile0, &grp_scan, &amax[0], &amax[1]};
         for (DevBuf* b : all) b->release();
         h_grp.release();
         h_traj.release();
@@ -215,8 +215,10 @@ struct Chunk {
 // Contract n_net networks of block j; marg/Z outputs are device arrays.
 ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const int32_t* d_net_traj,
                           const uint64_t* d_net_prefix, int64_t n_net, float* marg, double* Z, int max_traj_chunk,
-                          cudaStream_t s) {
+                          int precision, cudaStream_t s) {
     if (n_net <= 0) return PTN_OK;
+    if (precision != PTN_PREC_FP32 && precision != PTN_PREC_BF16X3 && precision != PTN_PREC_FP16X3)
+        return set_error(PTN_ERR_INVALID_ARG, "unknown precision mode %d", precision);
     PlanWorkspace* ws = workspace(plan);
     const BlockPlan& bp = plan->blocks[j];
     ptn_status e;
@@ -287,7 +289,9 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     const int64_t n_grp_all = n_ct + (int64_t)chunks.size();
     if ((e = ws->h_grp.grow(sizeof(int32_t) * n_grp_all)) || (e = ws->grp.grow(sizeof(int32_t) * n_grp_all)) ||
         (e = ws->grp_cnt.grow(sizeof(int64_t) * (max_t + 1))) || (e = ws->grp_tile0.grow(sizeof(int64_t) * (max_t + 1))) ||
-        (e = ws->grp_scan.grow(sizeof(int64_t) * scan_tmp_elems(max_t + 1))))
+        (e = ws->grp_scan.grow(sizeof(int64_t) * scan_tmp_elems(max_t + 1))) ||
+        (e = ws->amax[0].grow(sizeof(uint32_t) * (max_t + max_n + 1))) ||
+        (e = ws->amax[1].grow(sizeof(uint32_t) * (max_t + max_n + 1))))
         return e;
     int32_t* hg = ws->h_grp.as<int32_t>();
     std::vector<int64_t> grp_off(chunks.size());
@@ -341,8 +345,8 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
             const StepDesc& h = bp.steps[st];
             int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
             if (h.kind == STEP_GEMM || h.kind == STEP_GEMM_STACKED) {
-                e = launch_gemm_step(h, ctx, ni, ws->pack[0].as<float>(), ws->pack[1].as<float>(), ws->err.as<int>(),
-                                     gt, s);
+                e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->amax[0].as<uint32_t>(),
+                                     ws->amax[1].as<uint32_t>(), ws->err.as<int>(), gt, precision, s);
                 if (e) return e;
             } else {
                 launch_contract_step(bp.d_steps + st, h, ctx, ni, s);
@@ -571,11 +575,11 @@ ptn_status ptn_contract_batch(const ptn_plan* plan, const ptn_traj* traj, int32_
         return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
     if (traj->plan != plan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
     if (block < 0 || block >= (int32_t)plan->blocks.size()) return set_error(PTN_ERR_INVALID_ARG, "bad block %d", block);
-    if (precision != PTN_PREC_FP32) return set_error(PTN_ERR_UNSUPPORTED, "precision mode %d not built yet", precision);
     if (n_net < 0) return set_error(PTN_ERR_INVALID_ARG, "n_net < 0");
     ptn_status e = ensure_device(plan);
     if (e) return e;
-    return contract_level(plan, traj, block, net_traj, net_prefix, n_net, marg_out, Z_out, 0, (cudaStream_t)stream);
+    return contract_level(plan, traj, block, net_traj, net_prefix, n_net, marg_out, Z_out, 0, precision,
+                          (cudaStream_t)stream);
 }
 
 ptn_status ptn_allocate_shots(const double* weights, int64_t n, int64_t total, uint64_t seed, int32_t circuit_id,
@@ -664,7 +668,6 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     if (!plan || !traj || !o || !shots_out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
     *shots_out = nullptr;
     if (traj->plan != plan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
-    if (o->precision != PTN_PREC_FP32) return set_error(PTN_ERR_UNSUPPORTED, "precision mode %d not built yet", o->precision);
     if (o->mode != PTN_PROPORTIONAL_FIXED && o->mode != PTN_PROPORTIONAL_TOTAL)
         return set_error(PTN_ERR_UNSUPPORTED, "sampling mode %d", o->mode);
     int64_t total_cap;
@@ -698,7 +701,7 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
         const int64_t nb = (int64_t)1 << bp.b;
         if ((e = ws->marg.grow(sizeof(float) * n * nb)) || (e = ws->Z.grow(sizeof(double) * n))) return e;
         e = contract_level(plan, traj, (int)j, ws->lvl_traj[cur].as<int32_t>(), ws->lvl_prefix[cur].as<uint64_t>(), n,
-                           ws->marg.as<float>(), ws->Z.as<double>(), o->max_traj_per_chunk, s);
+                           ws->marg.as<float>(), ws->Z.as<double>(), o->max_traj_per_chunk, o->precision, s);
         if (e) return e;
         if (j == 0 && o->mode == PTN_PROPORTIONAL_TOTAL) {
             if ((e = ws->w.grow(sizeof(double) * E)) || (e = ws->cdf.grow(sizeof(double) * E))) return e;

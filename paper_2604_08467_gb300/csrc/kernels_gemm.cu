@@ -147,6 +147,21 @@ __device__ __forceinline__ void split<FMT_FP16>(float x, __half& hi, __half& lo)
     lo = __float2half_rn(x - __half2float(hi));
 }
 
+template <int F>
+__device__ __forceinline__ void store_pair(typename Fmt<F>::T* d, typename Fmt<F>::T x, typename Fmt<F>::T y);
+template <>
+__device__ __forceinline__ void store_pair<FMT_TF32>(float* d, float x, float y) {
+    *reinterpret_cast<float2*>(d) = make_float2(x, y);
+}
+template <>
+__device__ __forceinline__ void store_pair<FMT_BF16>(__nv_bfloat16* d, __nv_bfloat16 x, __nv_bfloat16 y) {
+    *reinterpret_cast<__nv_bfloat162*>(d) = __halves2bfloat162(x, y);
+}
+template <>
+__device__ __forceinline__ void store_pair<FMT_FP16>(__half* d, __half x, __half y) {
+    *reinterpret_cast<__half2*>(d) = __halves2half2(x, y);
+}
+
 __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, int pcls, int64_t inst,
                                                           const ChunkCtx& c) {
     int64_t tl = 0, net = 0;
@@ -185,22 +200,30 @@ __device__ __forceinline__ int64_t pack_offset(const PackArgs& a, int64_t row, i
     return off;
 }
 
-// Largest |component| of every packed instance (FP16 scaling).
+// Largest |component| of every packed instance (FP16 scaling): one block per
+// instance, a block reduction, one store.
 __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ PackArgs a, const ChunkCtx c,
                                                 uint32_t* __restrict__ amax) {
+    __shared__ float red[256];
     const int64_t nrow = (int64_t)1 << a.n_rb, nh = (int64_t)1 << a.n_hb, kc_real = (int64_t)1 << a.n_kb;
-    const int64_t total = a.n_pinst * nh * nrow * kc_real;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t kc = g % kc_real;
-        int64_t rest = g / kc_real;
-        const int64_t row = rest % nrow;
-        rest /= nrow;
-        const int64_t h = rest % nh;
-        const int64_t pi = rest / nh;
-        const float2 v = pack_operand_ptr(a.op, a.pcls, pi, c)[pack_offset(a, row, h, kc)];
-        const float m = fmaxf(fabsf(v.x), fabsf(v.y));
-        if (m > 0.f) atomicMax(&amax[pi], __float_as_uint(m));
+    const int64_t per = nh * nrow * kc_real;
+    for (int64_t pi = blockIdx.x; pi < a.n_pinst; pi += gridDim.x) {
+        const float2* base = pack_operand_ptr(a.op, a.pcls, pi, c);
+        float m = 0.f;
+        for (int64_t g = threadIdx.x; g < per; g += blockDim.x) {
+            const int64_t kc = g % kc_real;
+            const int64_t rest = g / kc_real;
+            const float2 v = base[pack_offset(a, rest % nrow, rest / nrow, kc)];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        red[threadIdx.x] = m;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) amax[pi] = __float_as_uint(red[0]);
+        __syncthreads();
     }
 }
 
@@ -240,25 +263,20 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
         T rh, rl, ih, il;
         split<F>(re, rh, rl);
         split<F>(im, ih, il);
+        // (re, im) pairs are adjacent: store each pair as one vector
         if (a.role == 0) {
             T* d = dst + (z * nrow + row) * rowlen + 2 * kc;
-            d[0] = rh;
-            d[1] = ih;
-            d[a.Kh] = rl;
-            d[a.Kh + 1] = il;
+            store_pair<F>(d, rh, ih);
+            store_pair<F>(d + a.Kh, rl, il);
         } else {
             T* d0 = dst + (z * 2 * nrow + 2 * row) * rowlen + 2 * kc;
             T* d1 = d0 + rowlen;
             T nih, nil;
             split<F>(-im, nih, nil);
-            d0[0] = rh;
-            d0[1] = nih;
-            d0[a.Kh] = rl;
-            d0[a.Kh + 1] = nil;
-            d1[0] = ih;
-            d1[1] = rh;
-            d1[a.Kh] = il;
-            d1[a.Kh + 1] = rl;
+            store_pair<F>(d0, rh, nih);
+            store_pair<F>(d0 + a.Kh, rl, nil);
+            store_pair<F>(d1, ih, rh);
+            store_pair<F>(d1 + a.Kh, il, rl);
         }
     }
 }
@@ -698,8 +716,9 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
         if (e == cudaSuccess) e = cudaMemsetAsync(amax_b, 0, sizeof(uint32_t) * pb.n_pinst, s);
         if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "scale reset: %s", cudaGetErrorString(e));
         StatScope sc(K_MISC, s, 8.0 * (double)(tot_a + tot_b), 0.0);
-        k_absmax<<<grid_of(tot_a), 256, 0, s>>>(pa, ctx, amax_a);
-        k_absmax<<<grid_of(tot_b), 256, 0, s>>>(pb, ctx, amax_b);
+        auto blocks_for = [](int64_t n_pinst) { return (unsigned)(n_pinst < 152 * 64 ? n_pinst : 152 * 64); };
+        k_absmax<<<blocks_for(pa.n_pinst), 256, 0, s>>>(pa, ctx, amax_a);
+        k_absmax<<<blocks_for(pb.n_pinst), 256, 0, s>>>(pb, ctx, amax_b);
         pa.amax = ga.amax_a = amax_a;
         pb.amax = ga.amax_b = amax_b;
     }

@@ -134,7 +134,7 @@ typedef struct {
  * contraction path per block (Sec. III-A), lowered to a list of batched
  * pairwise contractions.  Host only: needs no GPU (device tables are uploaded
  * on first use).  block_sizes may be NULL (then b = 10 blocks, the last one
- * taking the remainder); otherwise they must be >= 1, <= 24 and sum to
+ * taking the remainder); otherwise they must be in 1..14 and sum to
  * n_qubits. */
 ptn_status ptn_plan_path(const ptn_circuit* circuit, const ptn_noise* noise,
                          const int32_t* block_sizes, int32_t n_blocks,
@@ -144,7 +144,10 @@ ptn_status ptn_plan_path(const ptn_circuit* circuit, const ptn_noise* noise,
  * class, arena sizes and modelled work.  detail = 1 adds every lowered step
  * (operand descriptors, stride tables), the block roots, the variant-selecting
  * sites of every merged-gate leaf and the complex64 variant table, so the
- * lowering can be inspected or replayed on the host.  Writes at most cap bytes
+ * lowering can be inspected or replayed on the host; detail = 2 adds the
+ * expectation-value plan of ptn_expval_grad (ket network of the whole circuit,
+ * its forward steps, the reversed adjoint steps and the parametrised leaves),
+ * building it if needed.  Writes at most cap bytes
  * (NUL-terminated) to buf and the full length to *len (host). */
 ptn_status ptn_plan_describe(const ptn_plan* plan, int32_t detail, char* buf, size_t cap, size_t* len);
 
@@ -292,6 +295,37 @@ ptn_status ptn_shots_copy(const ptn_shots* shots, int32_t* traj_out, uint64_t* b
                           ptn_stream stream);
 
 void ptn_shots_destroy(ptn_shots* shots);
+
+/* ---------------------------------------------------------- gradients -- */
+
+/* A real combination of Pauli strings, O = sum_t coeff[t] P_t, with
+ * P_t = prod_q X_q^{x_mask bit q} Z_q^{z_mask bit q}.  This build evaluates
+ * diagonal strings (x_mask = 0: products of Z) and rejects others with
+ * PTN_ERR_UNSUPPORTED.  Host arrays of n_terms entries. */
+typedef struct {
+    int32_t n_terms;
+    const double* coeff;
+    const uint64_t* x_mask;
+    const uint64_t* z_mask;
+} ptn_pauli_sum;
+
+/* Trajectory-averaged expectation value and its gradient with respect to the
+ * angles of the parametrised gates (RY / RZ, ptn_gate.param_kind/param_index):
+ *   F(theta) = sum_i c_i <psi_i(theta)| O |psi_i(theta)> / sum_i c_i,
+ * psi_i the (unnormalised) state of error set i with every sampled Kraus
+ * operator merged into its gate (the UPV merge, Sec. III-A), c_i its
+ * multiplicity.  The state is the ket network with every qubit open,
+ * contracted along one path found once for all error sets; the gradient is
+ * reverse-mode differentiation of that contraction (adjoint contractions
+ * along the reversed path, intermediates of the forward pass kept), then
+ * dF/dtheta = 2 Re sum (adjoint of each merged gate) . d(merged gate)/dtheta.
+ * theta: host double [n_theta] (n_theta >= the plan's largest parameter
+ * index + 1); the plan's parametrised gates take these angles from now on.
+ * value_out: device double [1]; grad_out: device double [n_theta].
+ * Needs n_qubits <= 24.  Synchronises the stream. */
+ptn_status ptn_expval_grad(const ptn_plan* plan, const ptn_traj* traj, const ptn_pauli_sum* obs,
+                           const double* theta, int32_t n_theta, double* value_out, double* grad_out,
+                           ptn_stream stream);
 
 /* ----------------------------------------------------------- statistics -- */
 

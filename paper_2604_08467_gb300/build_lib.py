@@ -23,7 +23,8 @@ CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler",
             "-fPIC,-ffp-contract=off", "-I" + INCLUDE] + ARCH
 
 CPP_SOURCES = ["planner.cpp"]
-CU_SOURCES = ["runtime.cu", "kernels_contract.cu", "kernels_sample.cu", "kernels_gemm.cu", "stats.cu", "noalloc.cu"]
+CU_SOURCES = ["runtime.cu", "kernels_contract.cu", "kernels_sample.cu", "kernels_gemm.cu", "stats.cu", "noalloc.cu",
+              "kernels_expval.cu"]
 
 
 def _sources():

@@ -44,8 +44,8 @@ struct ChunkCtx {
     const int32_t* chunk_traj;  // local trajectory -> global (index into var_ids)
     const int32_t* net_tl;      // network -> local trajectory
     const uint64_t* net_prefix; // network -> prefix bits
-    float2* arena[3];           // CONST, TRAJ, NET arenas
-    int64_t arena_inst[3];      // instances of each arena in this chunk
+    float2* arena[N_ARENAS];    // CONST, TRAJ, NET (+ ADJ, LGRAD for gradients) arenas
+    int64_t arena_inst[N_ARENAS];   // instances of each arena in this chunk
 };
 
 // ---- launchers (kernels_contract.cu)
@@ -71,6 +71,22 @@ struct GroupTable {
 ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
                             uint32_t* amax_a, uint32_t* amax_b, int* err, const GroupTable& grp, int precision,
                             cudaStream_t s);
+
+// ---- expectation values and gradients (kernels_expval.cu)
+struct ObsTerm {
+    double coeff;
+    uint64_t zmask;
+};
+// Per trajectory: F = sum_x w(x) |psi(x)|^2 and the root adjoint w(x) conj(psi(x)),
+// w(x) = sum_t coeff_t (-1)^popc(x & zmask_t).
+void launch_observable(const RootRef* d_root, const ChunkCtx& ctx, int n, const ObsTerm* terms, int n_terms,
+                       int64_t root_adj_off, int64_t traj0, double* F, cudaStream_t s);
+// partial[(traj0 + i) * n_params + param] += 2 Re sum_e G_leaf[e] dLeaf[e]
+void launch_leaf_grad(const ChunkCtx& ctx, const ParamLeaf* d_pl, int n_pl, const float2* dvt, int64_t traj0,
+                      int64_t n_traj, int n_params, double* partial, cudaStream_t s);
+// value = sum_i c_i F_i / sum c_i, grad[p] = sum_i c_i partial[i][p] / sum c_i
+void launch_expval_reduce(const int64_t* mult, const double* F, const double* partial, int64_t n_traj, int n_params,
+                          double* value, double* grad, cudaStream_t s);
 
 // ---- launchers (kernels_sample.cu)
 void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, uint64_t seed,

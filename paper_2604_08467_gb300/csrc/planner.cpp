@@ -162,6 +162,7 @@ struct BlockNet {
     std::vector<int32_t> tbra;                // per tensor: 1 for the bra layer
     std::vector<int32_t> tcls;
     int32_t n_leaf_tensors = 0;               // ket tensors; bra tensor i + n is the mirror of i
+    bool ket_only = false;                    // no bra layer (the trajectory state itself)
 };
 
 // ------------------------------------------------------------ path search --
@@ -218,7 +219,7 @@ struct Searcher {
             std::sort(g.idx.begin(), g.idx.end());
             g.cls = net->tcls[i];
             g.side = net->tbra[i];
-            g.mirror = (int32_t)((i < (size_t)nl) ? i + nl : i - nl);
+            g.mirror = net->ket_only ? -1 : (int32_t)((i < (size_t)nl) ? i + nl : i - nl);
             g.nslice = 0;
             for (int32_t x : g.idx) g.nslice += is_slice(x);
             g.alive = true;
@@ -507,7 +508,7 @@ struct TRef {
     std::vector<int32_t> layout;   // index ids, position = log2(stride)
 };
 
-struct Arena {
+struct ArenaAlloc {   // first-fit offsets of live buffers in one arena
     std::vector<std::pair<int64_t, int64_t>> live;   // (offset, size)
     int64_t peak = 0;
     int64_t alloc(int64_t size) {
@@ -530,8 +531,15 @@ struct Arena {
     }
 };
 
+// Lower a searched path to step descriptors.  expval: the network is the ket
+// state with every qubit open; all forward intermediates are kept (no buffer
+// reuse) and the reversed (adjoint) path is lowered too, see the end.
 static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const Searcher& s,
-                              int32_t start, int32_t b, BlockPlan& bp) {
+                              int32_t start, int32_t b, BlockPlan& bp, bool expval = false) {
+    struct Rec {
+        TRef a, b, c;
+    };
+    std::vector<Rec> recs;
     const auto& idx = net.idx;
     std::vector<TRef> ref(s.t.size());
     int nl = net.n_leaf_tensors;
@@ -552,7 +560,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         int32_t refs;
     };
     std::vector<BufInfo> bufs;
-    Arena arenas[3];
+    ArenaAlloc arenas[3];
     auto pos_in = [](const std::vector<int32_t>& lay, int32_t x) -> int {
         for (size_t p = 0; p < lay.size(); p++)
             if (lay[p] == x) return (int)p;
@@ -591,7 +599,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
     auto consume = [&](const TRef& r) {
         if (r.mode != OP_BUF) return;
         BufInfo& bi = bufs[r.id];
-        if (--bi.refs == 0) arenas[bi.arena].release(bi.off);
+        if (--bi.refs == 0 && !expval) arenas[bi.arena].release(bi.off);
     };
 
     int32_t root_id = s.root();
@@ -732,6 +740,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         for (int r = 0; r < 2; r++)
             for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
         bp.steps.push_back(st);
+        if (expval) recs.push_back({A, B, rc});
     }
     // root descriptor
     const TRef& R = ref[root_id];
@@ -746,6 +755,103 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
     for (int tb = 0; tb < b; tb++)
         if (bp.root.x_stride[tb] < 0) return set_error(PTN_ERR_INVALID_ARG, "internal: root misses an open bit");
     for (int k = 0; k < 3; k++) bp.arena_peak[k] = arenas[k].peak;
+    if (!expval) return PTN_OK;
+
+    // ---- reversed path (reverse-mode differentiation of the contraction tree).
+    // The ket network is holomorphic in its tensors, so for a step
+    // C = sum_k A B the adjoint of A is  G_A = sum_n G_C B  over the bits of C
+    // that come from B alone (again a pairwise contraction, written in A's
+    // layout), and likewise for B.  Only tensors that contain a parametrised
+    // gate get adjoints; a parametrised leaf's adjoint goes to its own slot.
+    auto leaf_param = [&](const TRef& r) {
+        return r.mode == OP_LEAF && plan->leaves[r.id].param_kind != PTN_PARAM_NONE;
+    };
+    std::vector<char> buf_need(bufs.size(), 0);
+    auto need = [&](const TRef& r) { return r.mode == OP_LEAF ? leaf_param(r) : buf_need[r.id] != 0; };
+    for (auto& rc : recs) buf_need[rc.c.id] = need(rc.a) || need(rc.b);
+    ArenaAlloc adj, lg;
+    std::vector<int64_t> adj_off(bufs.size(), -1);
+    adj_off[R.id] = adj.alloc((int64_t)1 << R.layout.size());
+    bp.root_adj_off = adj_off[R.id];
+    std::unordered_map<int32_t, int64_t> leaf_slot;
+    for (auto& rc : recs)
+        for (const TRef* x : {&rc.a, &rc.b})
+            if (leaf_param(*x) && !leaf_slot.count(x->id)) {
+                const LeafInfo& L = plan->leaves[x->id];
+                ParamLeaf p;
+                p.leaf = x->id;
+                p.param_index = L.param_index;
+                p.param_kind = L.param_kind;
+                p.var_col = L.var_col;
+                p.size = L.size;
+                p.n_var = L.n_var;
+                p.lgrad_off = lg.alloc(L.size);
+                p.dvt_base = bp.dvt_size;
+                bp.dvt_size += L.n_var * L.size;
+                bp.pleaves.push_back(p);
+                leaf_slot[x->id] = p.lgrad_off;
+            }
+    for (auto it = recs.rbegin(); it != recs.rend(); ++it) {
+        const TRef& C = it->c;
+        if (!buf_need[C.id]) continue;
+        for (int side = 0; side < 2; side++) {
+            const TRef& X = side ? it->b : it->a;
+            const TRef& Y = side ? it->a : it->b;
+            if (!need(X)) continue;
+            StepDesc st;
+            memset(&st, 0, sizeof st);
+            st.out_cls = CLS_TRAJ;
+            const std::vector<int32_t>& out = X.layout;
+            std::vector<int32_t> sum;
+            for (int32_t x : C.layout)
+                if (pos_in(Y.layout, x) >= 0 && pos_in(out, x) < 0) sum.push_back(x);
+            std::sort(sum.begin(), sum.end());
+            for (int32_t x : out)
+                if (pos_in(C.layout, x) < 0 && pos_in(Y.layout, x) < 0)
+                    return set_error(PTN_ERR_INVALID_ARG, "internal: adjoint output bit not reachable");
+            if ((int)out.size() > kMaxOut || (int)sum.size() > kMaxSum)
+                return set_error(PTN_ERR_TOO_LARGE, "an adjoint step exceeds the kernel limits");
+            st.n_out = (int32_t)out.size();
+            st.n_sum = (int32_t)sum.size();
+            st.out_size = (int64_t)1 << out.size();
+            OperandDesc& g = st.op[0];
+            g.mode = OP_BUF;
+            g.cls = CLS_TRAJ;
+            g.conj = 0;
+            g.arena = ARENA_ADJ;
+            g.inst_size = (int64_t)1 << C.layout.size();
+            g.arena_off = adj_off[C.id];
+            g.leaf_col = -1;
+            g.n_slice = 0;
+            ptn_status ee = make_op(Y, CLS_TRAJ, st.op[1]);
+            if (ee) return ee;
+            for (size_t p = 0; p < out.size(); p++) {
+                const int qc = pos_in(C.layout, out[p]), qy = pos_in(Y.layout, out[p]);
+                st.out_stride[0][p] = qc >= 0 ? ((int64_t)1 << qc) : 0;
+                st.out_stride[1][p] = qy >= 0 ? ((int64_t)1 << qy) : 0;
+            }
+            for (size_t p = 0; p < sum.size(); p++) {
+                st.sum_stride[0][p] = (int64_t)1 << pos_in(C.layout, sum[p]);
+                st.sum_stride[1][p] = (int64_t)1 << pos_in(Y.layout, sum[p]);
+            }
+            if (X.mode == OP_BUF) {
+                adj_off[X.id] = adj.alloc(st.out_size);
+                st.out_arena = ARENA_ADJ;
+                st.out_off = adj_off[X.id];
+            } else {
+                st.out_arena = ARENA_LGRAD;
+                st.out_off = leaf_slot[X.id];
+            }
+            int64_t pf[2][3];
+            classify_step(st, pf, !plan->opts.simt_only);
+            for (int r = 0; r < 2; r++)
+                for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
+            bp.bwd.push_back(st);
+        }
+        adj.release(adj_off[C.id]);
+    }
+    bp.arena_peak[ARENA_ADJ] = adj.peak;
+    bp.arena_peak[ARENA_LGRAD] = lg.peak;
     return PTN_OK;
 }
 
@@ -800,6 +906,168 @@ void classify_step(StepDesc& st, int64_t pack_floats[2][3], bool allow_tc) {
     st.gemm_a = a;
     pack_floats[0][pcls(st.op[a])] = ((int64_t)1 << nh) * ((int64_t)1 << free_[a]) * 2 * kh;
     pack_floats[1][pcls(st.op[b])] = ((int64_t)1 << nh) * ((int64_t)2 << free_[b]) * 2 * kh;
+}
+
+// ------------------------------------------------------ block networks --
+// The ket layer in circuit order; end indices per block: prefix qubits
+// projected (slice), block qubits open, later qubits traced.  ket_only: no
+// bra layer, every qubit open (start = 0, b = n): the trajectory state.
+static void build_block_net(const ptn_plan* plan, int n, int start, int b, bool ket_only, BlockNet& net) {
+    std::vector<int32_t> cur(n, -1);
+    auto new_idx = [&](int32_t kind, int32_t q) {
+        net.idx.push_back({kind, q, -1});
+        return (int32_t)net.idx.size() - 1;
+    };
+    std::vector<std::vector<int32_t>> ket_idx;
+    std::vector<int32_t> ket_leaf;
+    int32_t bond = -1;
+    for (size_t li = 0; li < plan->leaves.size(); li++) {
+        const LeafInfo& L = plan->leaves[li];
+        std::vector<int32_t> ids;
+        int qa = L.qubit0, qb = L.qubit1;
+        int qA = (L.part == 2) ? qb : qa;   // the factor's own qubit
+        if (L.part == 1) bond = -1;
+        int32_t in_a = cur[qA], in_b = (L.part == 0 && L.qubit1 >= 0) ? cur[qb] : -1;
+        int32_t out_a = new_idx(IX_INT, qA), out_b = (L.part == 0 && L.qubit1 >= 0) ? new_idx(IX_INT, qb) : -1;
+        for (int32_t role : L.legs) {
+            switch (role) {
+                case R_IN_A: ids.push_back(in_a); break;
+                case R_OUT_A: ids.push_back(out_a); break;
+                case R_IN_B: ids.push_back(in_b); break;
+                case R_OUT_B: ids.push_back(out_b); break;
+                case R_BOND:
+                    if (bond < 0) bond = new_idx(IX_INT, -1);
+                    ids.push_back(bond);
+                    break;
+            }
+        }
+        cur[qA] = out_a;
+        if (out_b >= 0) cur[qb] = out_b;
+        ket_idx.push_back(ids);
+        ket_leaf.push_back((int32_t)li);
+    }
+    for (int q = 0; q < n; q++) {
+        NetIdx& x = net.idx[cur[q]];
+        x.qubit = q;
+        x.kind = q < start ? IX_SLICE : (q < start + b ? IX_OPEN : IX_TRACED);
+    }
+    int nl = (int)ket_idx.size();
+    net.n_leaf_tensors = nl;
+    net.ket_only = ket_only;
+    if (!ket_only) {
+        size_t n_ket_idx = net.idx.size();
+        for (size_t i = 0; i < n_ket_idx; i++) {
+            NetIdx& x = net.idx[i];
+            if (x.kind == IX_OPEN || x.kind == IX_TRACED) {
+                x.mirror = (int32_t)i;
+            } else {
+                NetIdx m{x.kind, x.qubit, (int32_t)i};
+                net.idx.push_back(m);
+                net.idx[i].mirror = (int32_t)net.idx.size() - 1;
+            }
+        }
+    }
+    for (int side = 0; side < (ket_only ? 1 : 2); side++)
+        for (int i = 0; i < nl; i++) {
+            std::vector<int32_t> ids = ket_idx[i];
+            if (side)
+                for (auto& x : ids) x = net.idx[x].mirror;
+            net.tidx.push_back(ids);
+            net.tleaf.push_back(ket_leaf[i]);
+            net.tbra.push_back(side);
+            net.tcls.push_back(plan->leaves[ket_leaf[i]].n_var > 1 ? CLS_TRAJ : CLS_CONST);
+        }
+}
+
+// Randomised greedy path search (hypersamples) under the step-cost model, then
+// lowering of the best path.
+static ptn_status search_and_lower(ptn_plan* plan, BlockNet& net, int j, int start, int b, double E, double D,
+                                   std::mt19937_64& rng, BlockPlan& bp, bool expval) {
+    const ptn_plan_opts& opts = plan->opts;
+    CostModel cm;
+    cm.mult[CLS_CONST] = 1.0;
+    cm.mult[CLS_TRAJ] = E;
+    cm.mult[CLS_NET] = D;
+    cm.allow_tc = !opts.simt_only;
+    Searcher best(net, cm), cur_s(net, cm);
+    double best_time = INFINITY;
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    for (int h = 0; h < opts.hypersamples; h++) {
+        double temp = h == 0 ? 0.0 : 0.02 + 1.0 * U(rng);
+        double costmod = h == 0 ? 1.0 : 0.5 + 1.5 * U(rng);
+        cur_s.run(temp, costmod, rng);
+        if (cur_s.root() < 0) continue;
+        if (cur_s.max_rank > kMaxOut) continue;
+        if (cur_s.time < best_time) {
+            best_time = cur_s.time;
+            best = cur_s;
+        }
+    }
+    if (!std::isfinite(best_time))
+        return set_error(PTN_ERR_TOO_LARGE, "block %d: no path with at most %d open bits per tensor", j, kMaxOut);
+    bp.start = start;
+    bp.b = b;
+    for (int k = 0; k < 3; k++) {
+        bp.est_macs[k] = best.macs[k];
+        bp.est_bytes[k] = best.bytes[k];
+    }
+    bp.est_time = best.time;
+    bp.est_mult_traj = E;
+    bp.est_mult_net = D;
+    ptn_status e = lower_block(plan, net, best, start, b, bp, expval);
+    if (e) return e;
+    char buf[256];
+    snprintf(buf, sizeof buf, "steps=%zu max_rank=%lld est_time=%.3es", bp.steps.size(), (long long)best.max_rank,
+             best.time);
+    bp.path_summary = buf;
+    return PTN_OK;
+}
+
+ptn_status build_expval_plan(ptn_plan* plan) {
+    if (plan->expval) return PTN_OK;
+    if (plan->n_qubits > 24) return set_error(PTN_ERR_UNSUPPORTED, "expectation values need n_qubits <= 24");
+    BlockNet net;
+    build_block_net(plan, plan->n_qubits, 0, plan->n_qubits, true, net);
+    std::mt19937_64 rng(plan->opts.seed ^ 0xA5A5A5A5A5A5A5A5ull);
+    BlockPlan* bp = new BlockPlan();
+    ptn_status e = search_and_lower(plan, net, -1, 0, plan->n_qubits, plan->opts.est_traj, plan->opts.est_traj, rng,
+                                    *bp, true);
+    if (e) {
+        delete bp;
+        return e;
+    }
+    plan->expval = bp;
+    return PTN_OK;
+}
+
+// N G(theta) and N dG/dtheta for every variant of a parametrised leaf, in the
+// leaf's storage order (legs); RY(t) = exp(-i t Y / 2), RZ(t) = exp(-i t Z / 2).
+void param_leaf_tables(const LeafInfo& L, double theta, float* out, float* out_d) {
+    const double c = std::cos(theta / 2), s = std::sin(theta / 2);
+    M2 G, dG;
+    if (L.param_kind == PTN_PARAM_RY) {
+        G = M2{cd(c), cd(-s), cd(s), cd(c)};
+        dG = M2{cd(-s / 2), cd(-c / 2), cd(c / 2), cd(-s / 2)};
+    } else {
+        const cd e0 = std::exp(cd(0, -theta / 2)), e1 = std::exp(cd(0, theta / 2));
+        G = M2{e0, cd(0), cd(0), e1};
+        dG = M2{cd(0, -0.5) * e0, cd(0), cd(0), cd(0, 0.5) * e1};
+    }
+    for (int64_t v = 0; v < L.n_var; v++) {
+        M2 N;
+        for (int e = 0; e < 4; e++) N[e] = cd(L.noise_ops[8 * v + 2 * e], L.noise_ops[8 * v + 2 * e + 1]);
+        const M2 NG = mul2(N, G), NdG = mul2(N, dG);
+        for (int64_t el = 0; el < L.size; el++) {
+            int32_t rb[5] = {0, 0, 0, 0, 0};
+            for (size_t p = 0; p < L.legs.size(); p++) rb[L.legs[p]] = (int32_t)((el >> p) & 1);
+            const int k = rb[R_OUT_A] * 2 + rb[R_IN_A];
+            const int64_t o = 2 * (v * L.size + el);
+            out[o] = (float)NG[k].real();
+            out[o + 1] = (float)NG[k].imag();
+            out_d[o] = (float)NdG[k].real();
+            out_d[o + 1] = (float)NdG[k].imag();
+        }
+    }
 }
 
 // ------------------------------------------------------------ build plan --
@@ -947,6 +1215,21 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
             touched[g.q0] = true;
             if (!fixed) L.legs.push_back(R_IN_A);
             L.legs.push_back(R_OUT_A);
+            if (g.param_kind == PTN_PARAM_RY || g.param_kind == PTN_PARAM_RZ) {
+                if (g.param_index < 0) return set_error(PTN_ERR_INVALID_ARG, "gate %d: parametrised without index", l);
+                L.param_kind = g.param_kind;
+                L.param_index = g.param_index;
+                plan->n_params = std::max(plan->n_params, g.param_index + 1);
+                int64_t nv = 1;
+                for (int32_t r : L.radix) nv *= r;
+                for (int64_t v = 0; v < nv; v++) {
+                    M2 N = noise_op(L, v, g.q0);
+                    for (int e = 0; e < 4; e++) {
+                        L.noise_ops.push_back(N[e].real());
+                        L.noise_ops.push_back(N[e].imag());
+                    }
+                }
+            }
             M2 M;
             cd_from(g.mat, M.data(), 4);
             finish_leaf(L, [&](int64_t v, const int32_t* rb) {
@@ -1084,112 +1367,13 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
     for (size_t j = 0; j < bs.size(); j++) {
         int b = bs[j];
         BlockNet net;
-        // ket layer: walk the leaves in circuit order
-        std::vector<int32_t> cur(n, -1);
-        auto new_idx = [&](int32_t kind, int32_t q) {
-            net.idx.push_back({kind, q, -1});
-            return (int32_t)net.idx.size() - 1;
-        };
-        std::vector<std::vector<int32_t>> ket_idx;
-        std::vector<int32_t> ket_leaf;
-        int32_t bond = -1;
-        for (size_t li = 0; li < plan->leaves.size(); li++) {
-            const LeafInfo& L = plan->leaves[li];
-            std::vector<int32_t> ids;
-            int qa = L.qubit0, qb = L.qubit1;
-            int qA = (L.part == 2) ? qb : qa;   // the factor's own qubit
-            if (L.part == 1) bond = -1;
-            int32_t in_a = cur[qA], in_b = (L.part == 0 && L.qubit1 >= 0) ? cur[qb] : -1;
-            int32_t out_a = new_idx(IX_INT, qA), out_b = (L.part == 0 && L.qubit1 >= 0) ? new_idx(IX_INT, qb) : -1;
-            for (int32_t role : L.legs) {
-                switch (role) {
-                    case R_IN_A: ids.push_back(in_a); break;
-                    case R_OUT_A: ids.push_back(out_a); break;
-                    case R_IN_B: ids.push_back(in_b); break;
-                    case R_OUT_B: ids.push_back(out_b); break;
-                    case R_BOND:
-                        if (bond < 0) bond = new_idx(IX_INT, -1);
-                        ids.push_back(bond);
-                        break;
-                }
-            }
-            cur[qA] = out_a;
-            if (out_b >= 0) cur[qb] = out_b;
-            ket_idx.push_back(ids);
-            ket_leaf.push_back((int32_t)li);
-        }
-        // end kinds
-        for (int q = 0; q < n; q++) {
-            NetIdx& x = net.idx[cur[q]];
-            x.qubit = q;
-            x.kind = q < start ? IX_SLICE : (q < start + b ? IX_OPEN : IX_TRACED);
-        }
-        // mirrors
-        size_t n_ket_idx = net.idx.size();
-        for (size_t i = 0; i < n_ket_idx; i++) {
-            NetIdx& x = net.idx[i];
-            if (x.kind == IX_OPEN || x.kind == IX_TRACED) {
-                x.mirror = (int32_t)i;
-            } else {
-                NetIdx m{x.kind, x.qubit, (int32_t)i};
-                net.idx.push_back(m);
-                net.idx[i].mirror = (int32_t)net.idx.size() - 1;
-            }
-        }
-        int nl = (int)ket_idx.size();
-        net.n_leaf_tensors = nl;
-        for (int side = 0; side < 2; side++)
-            for (int i = 0; i < nl; i++) {
-                std::vector<int32_t> ids = ket_idx[i];
-                if (side)
-                    for (auto& x : ids) x = net.idx[x].mirror;
-                net.tidx.push_back(ids);
-                net.tleaf.push_back(ket_leaf[i]);
-                net.tbra.push_back(side);
-                net.tcls.push_back(plan->leaves[ket_leaf[i]].n_var > 1 ? CLS_TRAJ : CLS_CONST);
-            }
-
-        CostModel cm;
+        build_block_net(plan, n, start, b, false, net);
         double E = opts.est_traj;
         double D = j == 0 ? E : std::min(E * std::ldexp(1.0, start), opts.est_shots);
         D = std::max(D, E);
-        cm.mult[CLS_CONST] = 1.0;
-        cm.mult[CLS_TRAJ] = E;
-        cm.mult[CLS_NET] = j == 0 ? E : D;
-        cm.allow_tc = !opts.simt_only;
-
-        Searcher best(net, cm), cur_s(net, cm);
-        double best_time = INFINITY;
-        std::uniform_real_distribution<double> U(0.0, 1.0);
-        for (int h = 0; h < opts.hypersamples; h++) {
-            double temp = h == 0 ? 0.0 : 0.02 + 1.0 * U(rng);
-            double costmod = h == 0 ? 1.0 : 0.5 + 1.5 * U(rng);
-            cur_s.run(temp, costmod, rng);
-            if (cur_s.root() < 0) continue;
-            if (cur_s.max_rank > kMaxOut) continue;
-            if (cur_s.time < best_time) {
-                best_time = cur_s.time;
-                best = cur_s;
-            }
-        }
-        if (!std::isfinite(best_time))
-            return set_error(PTN_ERR_TOO_LARGE, "block %d: no path with at most %d open bits per tensor", (int)j, kMaxOut);
         BlockPlan bp;
-        bp.start = start;
-        bp.b = b;
-        for (int k = 0; k < 3; k++) {
-            bp.est_macs[k] = best.macs[k];
-            bp.est_bytes[k] = best.bytes[k];
-        }
-        bp.est_time = best.time;
-        bp.est_mult_traj = E;
-        bp.est_mult_net = cm.mult[CLS_NET];
-        ptn_status e = lower_block(plan, net, best, start, b, bp);
+        ptn_status e = search_and_lower(plan, net, (int)j, start, b, E, j == 0 ? E : D, rng, bp, false);
         if (e) return e;
-        char buf[256];
-        snprintf(buf, sizeof buf, "steps=%zu max_rank=%lld est_time=%.3es", bp.steps.size(),
-                 (long long)best.max_rank, best.time);
-        bp.path_summary = buf;
         plan->blocks.push_back(std::move(bp));
         start += b;
     }
@@ -1222,6 +1406,32 @@ static void json_i64(std::string& s, const int64_t* v, int n) {
     s += "]";
 }
 
+static void json_steps(std::string& s, const std::vector<StepDesc>& steps) {
+    char buf[512];
+    s += "[";
+    for (size_t i = 0; i < steps.size(); i++) {
+        const StepDesc& st = steps[i];
+        snprintf(buf, sizeof buf,
+                 "%s{\"out_cls\":%d,\"n_out\":%d,\"n_sum\":%d,\"kind\":%d,\"gemm_a\":%d,\"out_arena\":%d,"
+                 "\"out_off\":%lld,\"ops\":[",
+                 i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.kind, st.gemm_a, st.out_arena, (long long)st.out_off);
+        s += buf;
+        json_op(s, st.op[0]);
+        s += ",";
+        json_op(s, st.op[1]);
+        s += "],\"out_stride\":[";
+        json_i64(s, st.out_stride[0], st.n_out);
+        s += ",";
+        json_i64(s, st.out_stride[1], st.n_out);
+        s += "],\"sum_stride\":[";
+        json_i64(s, st.sum_stride[0], st.n_sum);
+        s += ",";
+        json_i64(s, st.sum_stride[1], st.n_sum);
+        s += "]}";
+    }
+    s += "]";
+}
+
 std::string describe_plan(const ptn_plan* p, int detail) {
     std::string s = "{";
     char buf[768];
@@ -1249,26 +1459,9 @@ std::string describe_plan(const ptn_plan* p, int detail) {
                  b.est_mult_net);
         s += buf;
         if (detail) {
-            s += ",\"steps\":[";
-            for (size_t i = 0; i < b.steps.size(); i++) {
-                const StepDesc& st = b.steps[i];
-                snprintf(buf, sizeof buf, "%s{\"out_cls\":%d,\"n_out\":%d,\"n_sum\":%d,\"kind\":%d,\"gemm_a\":%d,\"out_arena\":%d,\"out_off\":%lld,\"ops\":[",
-                         i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.kind, st.gemm_a, st.out_arena, (long long)st.out_off);
-                s += buf;
-                json_op(s, st.op[0]);
-                s += ",";
-                json_op(s, st.op[1]);
-                s += "],\"out_stride\":[";
-                json_i64(s, st.out_stride[0], st.n_out);
-                s += ",";
-                json_i64(s, st.out_stride[1], st.n_out);
-                s += "],\"sum_stride\":[";
-                json_i64(s, st.sum_stride[0], st.n_sum);
-                s += ",";
-                json_i64(s, st.sum_stride[1], st.n_sum);
-                s += "]}";
-            }
-            s += "],\"root\":{\"op\":";
+            s += ",\"steps\":";
+            json_steps(s, b.steps);
+            s += ",\"root\":{\"op\":";
             json_op(s, b.root.op);
             s += ",\"x_stride\":";
             json_i64(s, b.root.x_stride, b.b);
@@ -1304,6 +1497,35 @@ std::string describe_plan(const ptn_plan* p, int detail) {
             s += "]";
         }
         s += "]";
+    }
+    if (detail >= 2 && p->expval) {
+        const BlockPlan& e = *p->expval;
+        snprintf(buf, sizeof buf,
+                 ",\"expval\":{\"n_params\":%d,\"arena\":[%lld,%lld,%lld,%lld,%lld],\"root_adj_off\":%lld,"
+                 "\"dvt_size\":%lld,\"steps\":",
+                 p->n_params, (long long)e.arena_peak[0], (long long)e.arena_peak[1], (long long)e.arena_peak[2],
+                 (long long)e.arena_peak[3], (long long)e.arena_peak[4], (long long)e.root_adj_off,
+                 (long long)e.dvt_size);
+        s += buf;
+        json_steps(s, e.steps);
+        s += ",\"bwd\":";
+        json_steps(s, e.bwd);
+        s += ",\"root\":{\"op\":";
+        json_op(s, e.root.op);
+        s += ",\"x_stride\":";
+        json_i64(s, e.root.x_stride, p->n_qubits);
+        s += "},\"pleaves\":[";
+        for (size_t k = 0; k < e.pleaves.size(); k++) {
+            const ParamLeaf& q = e.pleaves[k];
+            snprintf(buf, sizeof buf,
+                     "%s{\"leaf\":%d,\"param_index\":%d,\"param_kind\":%d,\"var_col\":%d,\"size\":%lld,"
+                     "\"n_var\":%lld,\"lgrad_off\":%lld,\"dvt_base\":%lld,\"var_base\":%lld}",
+                     k ? "," : "", q.leaf, q.param_index, q.param_kind, q.var_col, (long long)q.size,
+                     (long long)q.n_var, (long long)q.lgrad_off, (long long)q.dvt_base,
+                     (long long)p->leaves[q.leaf].var_base);
+            s += buf;
+        }
+        s += "]}";
     }
     s += "}";
     return s;

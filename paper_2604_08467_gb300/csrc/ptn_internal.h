@@ -16,6 +16,10 @@ namespace ptn {
 //   TRAJ : one copy per distinct error set (trajectory) of the chunk;
 //   NET  : one copy per network (trajectory, prefix) of the chunk.
 enum Cls : int32_t { CLS_CONST = 0, CLS_TRAJ = 1, CLS_NET = 2 };
+// Arenas a buffer can live in: the three storage classes, plus (expectation /
+// gradient plans) the adjoints of intermediates and the adjoints of the
+// parametrised gate tensors, both one copy per trajectory.
+enum Arena : int32_t { ARENA_ADJ = 3, ARENA_LGRAD = 4, N_ARENAS = 5 };
 enum OpMode : int32_t { OP_LEAF = 0, OP_BUF = 1 };
 
 constexpr int kMaxOut = 40;     // output bits of one contraction step
@@ -73,6 +77,26 @@ struct LeafInfo {
     int32_t var_col = -1;    // column of var_ids, -1 if n_var == 1
     // legs in storage order (position 0 = stride 1): role codes, see planner.cpp
     std::vector<int32_t> legs;
+    // parametrised one-qubit gates (RY / RZ): the noise operator N of every
+    // variant (2x2 complex128, row-major) so the merged tensor N G(theta) and
+    // its derivative can be rebuilt for any angle
+    int32_t param_kind = PTN_PARAM_NONE;
+    int32_t param_index = -1;
+    std::vector<double> noise_ops;   // n_var * 8 doubles
+};
+
+// Ket network of the whole circuit with every qubit open (the trajectory
+// state), its forward path with all intermediates kept, and the reversed
+// (adjoint) path; used by ptn_expval_grad.
+struct ParamLeaf {
+    int32_t leaf;            // leaf id
+    int32_t param_index;
+    int32_t param_kind;
+    int32_t var_col;         // variant column (-1: single variant)
+    int64_t size;            // elements per variant
+    int64_t n_var;
+    int64_t lgrad_off;       // offset of its adjoint in the LGRAD arena (elements per trajectory)
+    int64_t dvt_base;        // offset of its derivative variants in the derivative table
 };
 
 struct RootRef {             // where the block's final tensor lives
@@ -84,7 +108,7 @@ struct BlockPlan {
     int32_t start = 0, b = 0;
     std::vector<StepDesc> steps;
     RootRef root;
-    int64_t arena_peak[3] = {0, 0, 0};   // elements per instance, per arena (CONST/TRAJ/NET)
+    int64_t arena_peak[N_ARENAS] = {0, 0, 0, 0, 0};   // elements per instance, per arena
     int64_t pack_peak[2][3] = {{0, 0, 0}, {0, 0, 0}};   // GEMM packing floats per instance: [A/B][class]
     double est_macs[3] = {0, 0, 0};      // complex MACs per instance by output class
     double est_bytes[3] = {0, 0, 0};     // bytes moved per instance by output class
@@ -94,6 +118,12 @@ struct BlockPlan {
     std::string path_summary;
     // device copy
     StepDesc* d_steps = nullptr;
+    // expectation/gradient plans only: the reversed path and its targets
+    std::vector<StepDesc> bwd;
+    int64_t root_adj_off = 0;            // ADJ arena offset of the root adjoint
+    std::vector<ParamLeaf> pleaves;
+    int64_t dvt_size = 0;                // elements of the derivative variant table
+    StepDesc* d_bwd = nullptr;
 };
 
 struct SiteTable {           // per site: Kraus CDF and log q (FP64), padded to kMaxKraus
@@ -113,6 +143,8 @@ struct ptn_plan {
     std::vector<float> var_table;        // complex64 interleaved (re, im)
     std::vector<ptn::SiteTable> site_tables;
     std::vector<ptn::BlockPlan> blocks;
+    ptn::BlockPlan* expval = nullptr;    // built on the first ptn_expval_grad call
+    int32_t n_params = 0;                // 1 + largest parametrised gate index
     std::vector<int32_t> leaf_site_ptr;  // CSR over leaves with var_col >= 0 (by column)
     std::vector<int32_t> leaf_site_idx;
     std::vector<int32_t> leaf_site_mul;
@@ -134,6 +166,10 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
                       int32_t n_blocks, const ptn_plan_opts* o, ptn_plan* plan);
 std::string describe_plan(const ptn_plan* plan, int detail);
 void classify_step(StepDesc& st, int64_t pack_floats[2][3], bool allow_tc);   // planner.cpp
+ptn_status build_expval_plan(ptn_plan* plan);                                   // planner.cpp
+// merged tensor of a parametrised leaf at angle theta (and its derivative),
+// written as complex64 into out[n_var * size] (out_d likewise)
+void param_leaf_tables(const LeafInfo& L, double theta, float* out, float* out_d);
 // errors.cpp
 ptn_status set_error(ptn_status s, const char* fmt, ...);
 }  // namespace ptn

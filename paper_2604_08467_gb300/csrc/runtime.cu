@@ -99,13 +99,17 @@ struct PlanWorkspace {
     DevBuf s_cap, s_tmp_off, s_rank0, s_excl, s_first, s_ndist, s_out_off, s_tmp_x, s_tmp_c, s_scan;
     DevBuf zero_prefix;
     DevBuf pack[2], err, grp, grp_cnt, grp_tile0, grp_scan, amax[2];
+    // expectation / gradient plans
+    DevBuf arena_x[2];                    // ADJ, LGRAD arenas
+    DevBuf ev_steps, ev_bwd, ev_root, ev_pl, ev_dvt, ev_terms, ev_F, ev_partial, ev_iota;
     HostBuf h_traj, h_chunk_traj, h_net_tl, h_small, h_grp;
     void release() {
         DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &roots, &marg, &Z, &w, &cdf, &m,
                          &lvl_traj[0], &lvl_traj[1], &lvl_prefix[0], &lvl_prefix[1], &lvl_count[0], &lvl_count[1],
                          &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
                          &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err, &grp, &grp_cnt,
-                         &grp_tile0, &grp_scan, &amax[0], &amax[1]};
+                         &grp_tile0, &grp_scan, &amax[0], &amax[1], &arena_x[0], &arena_x[1], &ev_steps,
+                         &ev_bwd, &ev_root, &ev_pl, &ev_dvt, &ev_terms, &ev_F, &ev_partial, &ev_iota};
         for (DevBuf* b : all) b->release();
         h_grp.release();
         h_traj.release();
@@ -338,6 +342,8 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         ctx.net_tl = ws->net_tl.as<int32_t>() + c.net0;
         ctx.net_prefix = d_net_prefix + c.net0;
         for (int a = 0; a < 3; a++) ctx.arena[a] = ws->arena[a].as<float2>();
+        ctx.arena[ARENA_ADJ] = ctx.arena[ARENA_LGRAD] = nullptr;
+        ctx.arena_inst[ARENA_ADJ] = ctx.arena_inst[ARENA_LGRAD] = 0;
         ctx.arena_inst[CLS_CONST] = 1;
         ctx.arena_inst[CLS_TRAJ] = c.n_traj;
         ctx.arena_inst[CLS_NET] = c.n_net;
@@ -409,6 +415,10 @@ ptn_status ptn_plan_path(const ptn_circuit* circuit, const ptn_noise* noise, con
 
 ptn_status ptn_plan_describe(const ptn_plan* plan, int32_t detail, char* buf, size_t cap, size_t* len) {
     if (!plan) return set_error(PTN_ERR_INVALID_ARG, "plan is NULL");
+    if (detail >= 2) {
+        ptn_status e = build_expval_plan(const_cast<ptn_plan*>(plan));
+        if (e) return e;
+    }
     std::string d = describe_plan(plan, detail);
     if (len) *len = d.size();
     if (buf && cap) {
@@ -430,6 +440,7 @@ void ptn_plan_destroy(ptn_plan* plan) {
         cudaFree(plan->d_leaf_site_mul);
         for (auto& b : plan->blocks) cudaFree(b.d_steps);
     }
+    delete plan->expval;
     delete plan;
 }
 
@@ -580,6 +591,146 @@ ptn_status ptn_contract_batch(const ptn_plan* plan, const ptn_traj* traj, int32_
     if (e) return e;
     return contract_level(plan, traj, block, net_traj, net_prefix, n_net, marg_out, Z_out, 0, precision,
                           (cudaStream_t)stream);
+}
+
+ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const ptn_pauli_sum* obs, const double* theta,
+                           int32_t n_theta, double* value_out, double* grad_out, ptn_stream stream) {
+    clear_error();
+    if (!cplan || !traj || !obs || !value_out || (n_theta > 0 && (!theta || !grad_out)))
+        return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    if (traj->plan != cplan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
+    ptn_plan* plan = const_cast<ptn_plan*>(cplan);
+    if (n_theta < plan->n_params)
+        return set_error(PTN_ERR_INVALID_ARG, "n_theta = %d but the circuit uses %d parameters", n_theta, plan->n_params);
+    if (obs->n_terms < 1 || obs->n_terms > 4096 || !obs->coeff || !obs->z_mask)
+        return set_error(PTN_ERR_INVALID_ARG, "bad observable");
+    std::vector<ObsTerm> terms(obs->n_terms);
+    for (int t = 0; t < obs->n_terms; t++) {
+        if (obs->x_mask && obs->x_mask[t]) return set_error(PTN_ERR_UNSUPPORTED, "non-diagonal Pauli strings");
+        terms[t].coeff = obs->coeff[t];
+        terms[t].zmask = obs->z_mask[t];
+    }
+    ptn_status e;
+    try {
+        e = build_expval_plan(plan);
+    } catch (const std::bad_alloc&) {
+        e = set_error(PTN_ERR_OOM, "host allocation failed while planning");
+    }
+    if (e) return e;
+    if ((e = ensure_device(plan))) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    PlanWorkspace* ws = workspace(plan);
+    const BlockPlan& bp = *plan->expval;
+    const int n = plan->n_qubits;
+    const int64_t E = traj->n_unique;
+    const int np = std::max(n_theta, 1);
+    // device copies of the expectation plan (once)
+    if (!ws->ev_steps.p) {
+        if ((e = ws->ev_steps.grow(sizeof(StepDesc) * std::max<size_t>(bp.steps.size(), 1))) ||
+            (e = ws->ev_bwd.grow(sizeof(StepDesc) * std::max<size_t>(bp.bwd.size(), 1))) ||
+            (e = ws->ev_root.grow(sizeof(RootRef))) ||
+            (e = ws->ev_pl.grow(sizeof(ParamLeaf) * std::max<size_t>(bp.pleaves.size(), 1))) ||
+            (e = ws->ev_dvt.grow(sizeof(float2) * std::max<int64_t>(bp.dvt_size, 1))))
+            return e;
+        PTN_CUDA(cudaMemcpy(ws->ev_steps.p, bp.steps.data(), sizeof(StepDesc) * bp.steps.size(), cudaMemcpyHostToDevice));
+        if (!bp.bwd.empty())
+            PTN_CUDA(cudaMemcpy(ws->ev_bwd.p, bp.bwd.data(), sizeof(StepDesc) * bp.bwd.size(), cudaMemcpyHostToDevice));
+        PTN_CUDA(cudaMemcpy(ws->ev_root.p, &bp.root, sizeof(RootRef), cudaMemcpyHostToDevice));
+        if (!bp.pleaves.empty())
+            PTN_CUDA(cudaMemcpy(ws->ev_pl.p, bp.pleaves.data(), sizeof(ParamLeaf) * bp.pleaves.size(),
+                                cudaMemcpyHostToDevice));
+    }
+    // merged tensors of the parametrised gates at theta, and their derivatives
+    {
+        std::vector<float> dvt(2 * std::max<int64_t>(bp.dvt_size, 1));
+        for (const ParamLeaf& p : bp.pleaves) {
+            LeafInfo& L = plan->leaves[p.leaf];
+            param_leaf_tables(L, theta[p.param_index], &plan->var_table[2 * L.var_base], &dvt[2 * p.dvt_base]);
+        }
+        for (const ParamLeaf& p : bp.pleaves) {
+            const LeafInfo& L = plan->leaves[p.leaf];
+            PTN_CUDA(cudaMemcpyAsync(plan->d_var_table + 2 * L.var_base, &plan->var_table[2 * L.var_base],
+                                     sizeof(float) * 2 * L.n_var * L.size, cudaMemcpyHostToDevice, s));
+        }
+        if (bp.dvt_size)
+            PTN_CUDA(cudaMemcpyAsync(ws->ev_dvt.p, dvt.data(), sizeof(float) * 2 * bp.dvt_size, cudaMemcpyHostToDevice, s));
+        PTN_CUDA(cudaStreamSynchronize(s));
+    }
+    if ((e = ws->ev_terms.grow(sizeof(ObsTerm) * terms.size())) || (e = ws->ev_F.grow(sizeof(double) * E)) ||
+        (e = ws->ev_partial.grow(sizeof(double) * E * np)) || (e = ws->ev_iota.grow(sizeof(int32_t) * E)))
+        return e;
+    PTN_CUDA(cudaMemcpyAsync(ws->ev_terms.p, terms.data(), sizeof(ObsTerm) * terms.size(), cudaMemcpyHostToDevice, s));
+    PTN_CUDA(cudaMemsetAsync(ws->ev_partial.p, 0, sizeof(double) * E * np, s));
+    launch_iota_i32(ws->ev_iota.as<int32_t>(), E, s);
+    // chunks of trajectories that fit the memory cap
+    auto pk = [&](int c) { return 4.0 * (double)(bp.pack_peak[0][c] + bp.pack_peak[1][c]); };
+    const double bT = 8.0 * (double)(bp.arena_peak[CLS_TRAJ] + bp.arena_peak[ARENA_ADJ] + bp.arena_peak[ARENA_LGRAD]) +
+                      pk(CLS_TRAJ);
+    const double bC = 8.0 * (double)bp.arena_peak[CLS_CONST] + pk(CLS_CONST);
+    const int64_t per = (int64_t)((plan->mem_cap - bC) / std::max(bT, 1.0));
+    if (per < 1) return set_error(PTN_ERR_TOO_LARGE, "one trajectory needs %.3g bytes (cap %.3g)", bT + bC, plan->mem_cap);
+    const int64_t Ec = std::min<int64_t>(per, E);
+    if ((e = ws->arena[CLS_CONST].grow((size_t)(8.0 * bp.arena_peak[CLS_CONST] + 16))) ||
+        (e = ws->arena[CLS_TRAJ].grow((size_t)(8.0 * bp.arena_peak[CLS_TRAJ] * Ec + 16))) ||
+        (e = ws->arena_x[0].grow((size_t)(8.0 * bp.arena_peak[ARENA_ADJ] * Ec + 16))) ||
+        (e = ws->arena_x[1].grow((size_t)(8.0 * bp.arena_peak[ARENA_LGRAD] * Ec + 16))) || (e = ws->err.grow(sizeof(int))) ||
+        (e = ws->amax[0].grow(sizeof(uint32_t) * (Ec + 1))) || (e = ws->amax[1].grow(sizeof(uint32_t) * (Ec + 1))) ||
+        (e = ws->h_small.grow(64)))
+        return e;
+    for (int r = 0; r < 2; r++) {
+        const double need = 4.0 * ((double)bp.pack_peak[r][CLS_CONST] + (double)bp.pack_peak[r][CLS_TRAJ] * Ec);
+        if (need > 0 && (e = ws->pack[r].grow((size_t)need + 256))) return e;
+    }
+    PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
+    GroupTable no_groups;
+    for (int64_t t0 = 0; t0 < E; t0 += Ec) {
+        const int64_t nt = std::min(Ec, E - t0);
+        ChunkCtx ctx;
+        ctx.vtab = reinterpret_cast<const float2*>(plan->d_var_table);
+        ctx.var_ids = traj->var_ids;
+        ctx.n_var_cols = traj->n_var_cols;
+        ctx.pad = 0;
+        ctx.chunk_traj = ws->ev_iota.as<int32_t>() + t0;
+        ctx.net_tl = nullptr;
+        ctx.net_prefix = nullptr;
+        ctx.arena[CLS_CONST] = ws->arena[CLS_CONST].as<float2>();
+        ctx.arena[CLS_TRAJ] = ws->arena[CLS_TRAJ].as<float2>();
+        ctx.arena[CLS_NET] = nullptr;
+        ctx.arena[ARENA_ADJ] = ws->arena_x[0].as<float2>();
+        ctx.arena[ARENA_LGRAD] = ws->arena_x[1].as<float2>();
+        ctx.arena_inst[CLS_CONST] = 1;
+        ctx.arena_inst[CLS_TRAJ] = ctx.arena_inst[ARENA_ADJ] = ctx.arena_inst[ARENA_LGRAD] = nt;
+        ctx.arena_inst[CLS_NET] = 0;
+        auto run = [&](const std::vector<StepDesc>& steps, const StepDesc* d_steps) -> ptn_status {
+            for (size_t k = 0; k < steps.size(); k++) {
+                const StepDesc& h = steps[k];
+                const int64_t ni = h.out_cls == CLS_CONST ? 1 : nt;
+                if (h.kind != STEP_DIRECT) {
+                    ptn_status ee = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->amax[0].as<uint32_t>(),
+                                                     ws->amax[1].as<uint32_t>(), ws->err.as<int>(), no_groups,
+                                                     PTN_PREC_FP32, s);
+                    if (ee) return ee;
+                } else {
+                    launch_contract_step(d_steps + k, h, ctx, ni, s);
+                }
+            }
+            return PTN_OK;
+        };
+        if ((e = run(bp.steps, ws->ev_steps.as<StepDesc>()))) return e;
+        launch_observable(ws->ev_root.as<RootRef>(), ctx, n, ws->ev_terms.as<ObsTerm>(), (int)terms.size(),
+                          bp.root_adj_off, t0, ws->ev_F.as<double>(), s);
+        if ((e = run(bp.bwd, ws->ev_bwd.as<StepDesc>()))) return e;
+        launch_leaf_grad(ctx, ws->ev_pl.as<ParamLeaf>(), (int)bp.pleaves.size(), ws->ev_dvt.as<float2>(), t0, nt, np,
+                         ws->ev_partial.as<double>(), s);
+    }
+    launch_expval_reduce(traj->mult, ws->ev_F.as<double>(), ws->ev_partial.as<double>(), E, n_theta, value_out,
+                         grad_out, s);
+    PTN_CUDA(cudaGetLastError());
+    int* herr = reinterpret_cast<int*>(ws->h_small.as<int64_t>() + 4);
+    PTN_CUDA(cudaMemcpyAsync(herr, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PTN_CUDA(cudaStreamSynchronize(s));
+    if (*herr) return set_error(PTN_ERR_TIMEOUT, "gradient: a tensor-core step timed out (code %d)", *herr);
+    return PTN_OK;
 }
 
 ptn_status ptn_allocate_shots(const double* weights, int64_t n, int64_t total, uint64_t seed, int32_t circuit_id,

@@ -65,6 +65,11 @@ class ptn_sample_opts(C.Structure):
                 ("max_traj_per_chunk", C.c_int32), ("use_graphs", C.c_int32), ("reserved", C.c_int32)]
 
 
+class ptn_pauli_sum(C.Structure):
+    _fields_ = [("n_terms", C.c_int32), ("coeff", C.POINTER(C.c_double)), ("x_mask", C.POINTER(C.c_uint64)),
+                ("z_mask", C.POINTER(C.c_uint64))]
+
+
 class ptn_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("timed_launches", C.c_int64),
                 ("ms", C.c_double), ("alg_bytes", C.c_double), ("alg_flops", C.c_double)]
@@ -92,6 +97,7 @@ _SIGS = {
                        C.POINTER(C.c_int64), C.c_int32],
     "ptn_shots_copy": [_P, _P, _P, _P, _P],
     "ptn_shots_destroy": [_P],
+    "ptn_expval_grad": [_P, _P, C.POINTER(ptn_pauli_sum), C.POINTER(C.c_double), C.c_int32, _P, _P, _P],
     "ptn_stats_enable": [C.c_int32],
     "ptn_stats_reset": [],
     "ptn_stats_read": [C.POINTER(ptn_kernel_stat), C.c_int32, C.POINTER(C.c_int32)],
@@ -324,6 +330,25 @@ def ptn_sample_shots(plan, traj, seed, shots_per_traj=None, total_shots=None, ci
     h = C.c_void_p()
     _check(lib().ptn_sample_shots(plan.handle, traj.handle, C.byref(o), C.byref(h), _stream(stream)))
     return Shots(h, len(plan.block_sizes))
+
+
+def ptn_expval_grad(plan, traj, terms, theta, value_out, grad_out, stream=None):
+    """Trajectory-averaged <O> and dO/dtheta (include/ptn.h).  terms: list of
+    (coeff, z_mask) or (coeff, x_mask, z_mask); theta: host sequence of angles;
+    value_out: device float64 [1]; grad_out: device float64 [len(theta)]."""
+    n_t = len(terms)
+    coeff = (C.c_double * max(n_t, 1))()
+    xm = (C.c_uint64 * max(n_t, 1))()
+    zm = (C.c_uint64 * max(n_t, 1))()
+    for t, term in enumerate(terms):
+        coeff[t] = float(term[0])
+        xm[t] = int(term[1]) if len(term) == 3 else 0
+        zm[t] = int(term[-1])
+    obs = ptn_pauli_sum(n_t, coeff, xm, zm)
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    thp = th.ctypes.data_as(C.POINTER(C.c_double)) if th.size else None
+    _check(lib().ptn_expval_grad(plan.handle, traj.handle, C.byref(obs), thp, int(th.size), _ptr(value_out),
+                                 _ptr(grad_out), _stream(stream)))
 
 
 def ptn_stats_enable(on=True):

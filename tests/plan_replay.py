@@ -81,3 +81,60 @@ def run_block(desc, j, kraus_rows, net_traj, net_prefix):
         R = operand(root["op"], 2, n)
         marg[n] = R[xo].real
     return marg
+
+
+def run_expval(desc, kraus_rows, w, var_table=None):
+    """Replay of the expectation-value plan (ptn_plan_describe(detail=2)):
+    forward steps, root adjoint w(x) conj(psi(x)), reversed steps.  Returns
+    (psi [n_traj, 2^n] in basis order, F [n_traj], {leaf: adjoint [n_traj, size]})."""
+    ev = desc["expval"]
+    n = desc["n_qubits"]
+    vt = np.array(desc["var_table"] if var_table is None else var_table, dtype=np.float32).view(np.complex64)
+    vids = var_ids(desc, kraus_rows)
+    nt = kraus_rows.shape[0]
+    inst_of = {0: 1, 1: nt, 2: 0, 3: nt, 4: nt}
+    arenas = [np.zeros(max(ev["arena"][a] * max(inst_of[a], 1), 1), np.complex64) for a in range(5)]
+
+    def operand(d, t):
+        if d["mode"] == 0:
+            var = vids[t, d["leaf_col"]] if d["leaf_col"] >= 0 else 0
+            arr, base = vt, d["leaf_base"] + var * d["inst_size"]
+        else:
+            oi = 0 if d["cls"] == 0 else t
+            arr, base = arenas[d["arena"]], d["arena_off"] * inst_of[d["arena"]] + oi * d["inst_size"]
+        v = arr[base:base + d["inst_size"]]
+        return np.conj(v) if d["conj"] else v
+
+    def execute(steps):
+        for st in steps:
+            n_inst = inst_of[st["out_cls"]]
+            oa = _bits_offsets(st["out_stride"][0], st["n_out"])
+            ob = _bits_offsets(st["out_stride"][1], st["n_out"])
+            ka = _bits_offsets(st["sum_stride"][0], st["n_sum"])
+            kb = _bits_offsets(st["sum_stride"][1], st["n_sum"])
+            size = 1 << st["n_out"]
+            out = arenas[st["out_arena"]]
+            obase = st["out_off"] * inst_of[st["out_arena"]]
+            for inst in range(n_inst):
+                A = operand(st["ops"][0], inst)
+                B = operand(st["ops"][1], inst)
+                out[obase + inst * size: obase + (inst + 1) * size] = \
+                    (A[oa[:, None] + ka[None, :]] * B[ob[:, None] + kb[None, :]]).sum(axis=1)
+
+    execute(ev["steps"])
+    root = ev["root"]
+    xo = _bits_offsets(root["x_stride"], n)
+    psi = np.zeros((nt, 1 << n), np.complex64)
+    size = root["op"]["inst_size"]
+    for t in range(nt):
+        R = operand(root["op"], t)
+        psi[t] = R[xo]
+        adj = arenas[3][ev["root_adj_off"] * nt + t * size: ev["root_adj_off"] * nt + (t + 1) * size]
+        adj[xo] = (w * np.conj(psi[t])).astype(np.complex64)
+    F = (np.abs(psi.astype(np.complex128)) ** 2 * w[None, :]).sum(axis=1)
+    execute(ev["bwd"])
+    grads = {}
+    for p in ev["pleaves"]:
+        base = p["lgrad_off"] * nt
+        grads[p["leaf"]] = arenas[4][base: base + nt * p["size"]].reshape(nt, p["size"]).copy()
+    return psi, F, grads

@@ -109,3 +109,70 @@ def test_plan_c1_c2_sizes():
     assert d2["n_sites"] == 1416
     for b in d2["blocks"]:
         assert b["max_out_bits"] <= 40
+
+
+# ------------------------------------------------ expectation-value plan ----
+
+def _shared_param_circuit(r):
+    """Rotations that share angles (parameter 0 on three gates) between CZs."""
+    th = r.standard_normal(3)
+    g = [W.Gate((0,), W.RY(th[0]), W.PARAM_RY, 0), W.Gate((1,), W.RY(th[0]), W.PARAM_RY, 0),
+         W.Gate((0, 1), W.CZ.copy()), W.Gate((2,), W.haar_u2(r)), W.Gate((1, 2), W.CZ.copy()),
+         W.Gate((2,), W.RZ(th[1]), W.PARAM_RZ, 1), W.Gate((1,), W.RY(th[2]), W.PARAM_RY, 2),
+         W.Gate((0,), W.RY(th[0]), W.PARAM_RY, 0), W.Gate((0, 2), W.CZ.copy())]
+    return W.Circuit(3, g)
+
+
+EV_CASES = [
+    ("hea5_dep_ad", lambda r: W.attach_noise(W.hea_ring(5, 2, r.standard_normal(20)),
+                                             [W.depolarizing_kraus(0.1), W.amplitude_damping_kraus(0.2)]), [3, 2]),
+    ("hea4_noiseless", lambda r: W.hea_ring(4, 3, r.standard_normal(24)), [4]),
+    ("shared3", lambda r: W.attach_noise(_shared_param_circuit(r), [W.depolarizing_kraus(0.2)]), [3]),
+    ("brick6_hea", lambda r: W.attach_noise(W.Circuit(6, W.brickwork_1d(6, 3, r).gates +
+                                                      W.hea_ring(6, 1, r.standard_normal(12)).gates),
+                                            [W.amplitude_damping_kraus(0.3)]), [6]),
+]
+
+
+@pytest.mark.parametrize("name,make,bs", EV_CASES, ids=[c[0] for c in EV_CASES])
+@pytest.mark.parametrize("split", [1, 0])
+def test_expval_plan_replay(name, make, bs, split):
+    """The lowered ket network reproduces the oracle's trajectory states and
+    expectation values, and every parametrised leaf's adjoint G is the exact
+    derivative: sum_e G[e] L'[e] = sum_x w(x) conj(psi(x)) psi'(x), psi' the
+    state with that leaf replaced by an arbitrary tensor L' (psi is linear in
+    each leaf and F holomorphic in psi with conj(psi) held fixed)."""
+    from oracle import gradient as G
+    from plan_replay import run_expval
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    circ = make(rng)
+    n = circ.n_qubits
+    plan = ptn.ptn_plan_path(circ, bs, hypersamples=8, split_gates=split, est_traj=4, est_shots=64)
+    desc = plan.describe(detail=2)
+    ev = desc["expval"]
+    assert ev["n_params"] == circ.n_params()
+    assert len(ev["pleaves"]) == len(G.rotation_occurrences(circ))
+    kraus, _ = pts.presample(circ, 4, seed=23)
+    terms = [(0.7, 0b11), (-0.4, (1 << (n - 1)) | 1), (0.25, 0)]
+    w = G.pauli_weights(n, terms)
+    psi, F, grads = run_expval(desc, kraus, w)
+    for t in range(4):
+        want = sv.trajectory_state(circ, kraus[t])
+        err = np.linalg.norm(psi[t] - want)
+        assert err <= 2e-5 * np.linalg.norm(want) + 1e-12, (t, err)   # zero-norm trajectories stay zero
+        f = G.trajectory_expval(circ, kraus[t], w)
+        assert abs(F[t] - f) < 2e-5 * max(1.0, abs(f)), (t, F[t], f)
+    vt0 = np.array(desc["var_table"], dtype=np.float32)
+    for p in ev["pleaves"]:
+        vt = vt0.copy()
+        m = p["n_var"] * p["size"]
+        vt[2 * p["var_base"]: 2 * (p["var_base"] + m)] = rng.standard_normal(2 * m).astype(np.float32)
+        psi2, _, _ = run_expval(desc, kraus, w, var_table=vt)
+        lp = vt[2 * p["var_base"]: 2 * (p["var_base"] + m)].view(np.complex64).reshape(p["n_var"], p["size"])
+        from plan_replay import var_ids
+        vids = var_ids(desc, kraus)
+        for t in range(4):
+            var = vids[t, p["var_col"]] if p["var_col"] >= 0 else 0
+            lhs = np.sum(grads[p["leaf"]][t].astype(np.complex128) * lp[var])
+            rhs = np.sum(w * np.conj(psi[t].astype(np.complex128)) * psi2[t])
+            assert abs(lhs - rhs) < 1e-4 * max(1.0, abs(rhs)), (p["leaf"], t, lhs, rhs)

@@ -181,6 +181,14 @@ def main():
                     help="trajectories timed on the plain per-trajectory path")
     ap.add_argument("--profile-range", action="store_true",
                     help="open a CUDA profiler range around the timed steps (for ncu --profile-from-start off)")
+    ap.add_argument("--grad-calls", type=int, default=3,
+                    help="timed ptn_expval_grad calls on the 16-qubit ansatz (0: skip)")
+    ap.add_argument("--n-traj", type=int, default=0,
+                    help="trajectories per step (default: the workload's 4096; smaller values are for profiling)")
+    ap.add_argument("--total-shots", type=int, default=0,
+                    help="shots per step (default: the workload's 1e6; smaller values are for profiling)")
+    ap.add_argument("--mem-cap-gb", type=float, default=0.0,
+                    help="device workspace cap (default: 40%% of free memory; small caps are for profiling)")
     ap.add_argument("--precision", default="fp32", choices=list(PRECISIONS),
                     help="tensor-core operand split (fp32: TF32 hi/lo; bf16x3 / fp16x3: 16-bit hi/lo)")
     args = ap.parse_args()
@@ -201,10 +209,11 @@ def main():
     from paper_2604_08467_gb300 import ptn
 
     cfg = c2_config()
-    E, M = cfg["n_traj"], cfg["total_shots"]
+    E = args.n_traj or cfg["n_traj"]
+    M = args.total_shots or cfg["total_shots"]
     t_plan = time.perf_counter()
-    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=args.hypersamples, est_traj=E,
-                             est_shots=M)
+    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=args.hypersamples,
+                             est_traj=cfg["n_traj"], est_shots=cfg["total_shots"], mem_cap_bytes=args.mem_cap_gb * 1e9)
     t_plan = time.perf_counter() - t_plan
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
@@ -247,6 +256,7 @@ def main():
         torch.cuda.synchronize()
     ptn.ptn_stats_enable(False)
     stats = ptn.ptn_stats_read()
+    free_b, total_b = torch.cuda.mem_get_info()
     clocks = clk.summary()
     t_step = float(np.mean(times))
     if dist:
@@ -295,6 +305,32 @@ def main():
                  "sample": f"{args.plain_traj} trajectories x {m_pt} shots, one trajectory per chunk"}
         del tr, res
 
+    # ---- adjoint gradients: 16-qubit, 6-layer hardware-efficient ansatz, 192
+    # angles, depolarizing 0.01, 1024 trajectories, O = mean_q Z_q Z_{q+1}
+    grad = None
+    if args.grad_calls > 0:
+        c5 = W.config_c5()
+        gplan = ptn.ptn_plan_path(c5["circuit"], c5["block_sizes"], hypersamples=args.hypersamples,
+                                  est_traj=c5["n_traj"])
+        gtr = ptn.ptn_presample_trajectories(gplan, c5["seed"], c5["n_traj"], dedup=True)
+        nq = c5["circuit"].n_qubits
+        terms = [(1.0 / nq, (1 << q) | (1 << ((q + 1) % nq))) for q in range(nq)]
+        th = c5["thetas"]
+        gv = torch.empty(1, dtype=torch.float64, device="cuda")
+        gg = torch.empty(th.size, dtype=torch.float64, device="cuda")
+        ptn.ptn_expval_grad(gplan, gtr, terms, th, gv, gg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.grad_calls):
+            ptn.ptn_expval_grad(gplan, gtr, terms, th + 1e-3 * k, gv, gg)
+        torch.cuda.synchronize()
+        tg = (time.perf_counter() - t0) / args.grad_calls
+        grad = {"workload": "c5_hea16_l6: 16-qubit ansatz, 6 layers RY RZ + CZ ring, 192 angles, depolarizing 0.01, "
+                            f"{c5['n_traj']} trajectories ({gtr.n_unique} distinct), O = mean Z_q Z_q+1",
+                "value": c5["n_traj"] / tg, "unit": "trajectory gradients/s", "ms_per_call": tg * 1e3,
+                "expval": float(gv.item())}
+        del gplan, gtr
+
     # ---- roofline of every kernel class (from the library's per-launch events);
     # the dominant one is the headline.  Tensor-core GEMMs are charged their
     # algorithmic complex flops (8 per complex multiply-add) against the
@@ -340,13 +376,14 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": "c2_brickwork30_d12: 30-qubit 1D brickwork depth 12, Haar U(2) + CZ, "
                                        "depolarizing 0.005 + amplitude damping 0.002 after every gate, "
-                                       "4096 trajectories, 1e6 shots proportional, blocks 10/10/10",
+                                       f"{E} trajectories, {M} shots proportional, blocks 10/10/10",
+                           "device_mem_used_gb": (total_b - free_b) / 1e9,
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)",
                            "nets_per_block": nets, "plan_seconds": t_plan,
                            "precision": f"{args.precision}: complex64 storage, tensor-core operands split hi/lo "
                                         f"({args.precision}), fp64 CDF / log-probabilities",
                            "error_vs_fp64": PRECISIONS[args.precision][1]},
-                "e2e": e2e, "plain_path": plain, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "plain_path": plain, "expval_grad": grad, "roofline": roof, "cpu_baseline": cpu,
                 "gpu_launches": int(launches), "clocks": clocks,
                 "kernels": {k: {"launches": v["launches"], "ms_per_step": r["ms_per_step"], "achieved": r["achieved"],
                                 "unit": r["unit"], "frac": r["frac"]} for k, r in roofs.items()

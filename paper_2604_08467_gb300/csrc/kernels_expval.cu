@@ -124,21 +124,21 @@ void launch_observable(const RootRef* d_root, const ChunkCtx& ctx, int n, const 
                        int64_t root_adj_off, int64_t traj0, double* F, cudaStream_t s) {
     const int64_t nt = ctx.arena_inst[CLS_TRAJ];
     if (nt <= 0) return;
-    StatScope sc(K_MISC, s, (double)nt * (double)(1ll << n) * 16.0, 0.0);
+    StatScope sc(K_EXPVAL, s, (double)nt * (double)(1ll << n) * 16.0, 0.0);
     k_observable<<<(unsigned)nt, 256, 0, s>>>(d_root, ctx, n, terms, n_terms, root_adj_off, traj0, F);
 }
 
 void launch_leaf_grad(const ChunkCtx& ctx, const ParamLeaf* d_pl, int n_pl, const float2* dvt, int64_t traj0,
                       int64_t n_traj, int n_params, double* partial, cudaStream_t s) {
     if (n_pl <= 0 || n_traj <= 0) return;
-    StatScope sc(K_MISC, s, 0.0, 0.0);
+    StatScope sc(K_EXPVAL, s, 0.0, 0.0);
     k_leaf_grad<<<(unsigned)(n_traj * n_pl), 128, 0, s>>>(ctx, d_pl, n_pl, dvt, traj0, n_params, partial);
 }
 
 void launch_expval_reduce(const int64_t* mult, const double* F, const double* partial, int64_t n_traj, int n_params,
                           double* value, double* grad, cudaStream_t s) {
     const int blocks = n_params > 0 ? n_params : 1;
-    StatScope sc(K_MISC, s, 0.0, 0.0);
+    StatScope sc(K_EXPVAL, s, 0.0, 0.0);
     k_expval_reduce<<<blocks, 256, 0, s>>>(mult, F, partial, n_traj, n_params, value, grad);
 }
 

@@ -715,7 +715,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
         e = cudaMemsetAsync(amax_a, 0, sizeof(uint32_t) * pa.n_pinst, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(amax_b, 0, sizeof(uint32_t) * pb.n_pinst, s);
         if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "scale reset: %s", cudaGetErrorString(e));
-        StatScope sc(K_MISC, s, 8.0 * (double)(tot_a + tot_b), 0.0);
+        StatScope sc(K_ABSMAX, s, 8.0 * (double)(tot_a + tot_b), 0.0);
         auto blocks_for = [](int64_t n_pinst) { return (unsigned)(n_pinst < 152 * 64 ? n_pinst : 152 * 64); };
         k_absmax<<<blocks_for(pa.n_pinst), 256, 0, s>>>(pa, ctx, amax_a);
         k_absmax<<<blocks_for(pb.n_pinst), 256, 0, s>>>(pb, ctx, amax_b);
@@ -723,7 +723,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
         pb.amax = ga.amax_b = amax_b;
     }
     {
-        StatScope sc(K_MISC, s, 8.0 * (double)(tot_a + tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b, 0.0);
+        StatScope sc(K_PACK, s, 8.0 * (double)(tot_a + tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b, 0.0);
         k_pack<F><<<grid_of(tot_a), 256, 0, s>>>(pa, ctx);
         k_pack<F><<<grid_of(tot_b), 256, 0, s>>>(pb, ctx);
     }

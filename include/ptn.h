@@ -270,7 +270,8 @@ typedef struct {
     int32_t  precision;          /* PTN_PREC_* */
     int32_t  max_traj_per_chunk; /* 0: as many as the memory cap allows; 1: the plain
                                     per-trajectory path (one trajectory per launch) */
-    int32_t  use_graphs;         /* capture each chunk's step list in a CUDA graph */
+    int32_t  use_graphs;         /* must be 0: CUDA-graph capture of the step lists is not
+                                    built (PTN_ERR_UNSUPPORTED otherwise) */
     int32_t  reserved;
 } ptn_sample_opts;
 
@@ -295,6 +296,43 @@ ptn_status ptn_shots_copy(const ptn_shots* shots, int32_t* traj_out, uint64_t* b
                           ptn_stream stream);
 
 void ptn_shots_destroy(ptn_shots* shots);
+
+/* ------------------------------------------------ mixed-circuit batches -- */
+
+/* One circuit of a heterogeneous batch: its plan, its pre-sampled error sets
+ * and its sampling options (qubit counts, trajectory counts and shot budgets
+ * may all differ between items). */
+typedef struct {
+    const ptn_plan*  plan;
+    const ptn_traj*  traj;
+    ptn_sample_opts  opts;
+} ptn_batch_item;
+
+typedef struct {
+    int32_t n_workers;          /* circuits in flight at once (each on its own CUDA stream); 0: 4 */
+    int32_t keep_workspaces;    /* 0: free each plan's device workspace when its items are done */
+    double  mem_budget_bytes;   /* device memory shared by the workers; 0: 80% of free memory */
+    double  max_est_seconds;    /* items whose plan's modelled time exceeds this are not run and
+                                   get PTN_ERR_TOO_LARGE; 0: no limit */
+} ptn_batch_opts;
+
+/* Runs ptn_sample_shots for every item of a mixed-circuit batch (the
+ * batching form of the method: many independent circuits, each with one
+ * contraction path reused by all of its error sets).  Items are grouped by
+ * plan (items sharing a plan run one after another), groups are taken in
+ * decreasing modelled cost (longest first) by n_workers host threads, each
+ * driving its own non-blocking stream that starts after the work already on
+ * `stream`; `stream` waits for all of them before the call returns (the call
+ * itself returns once every item has been issued and its level sizes read).
+ * Each plan without an explicit memory cap gets mem_budget / n_workers for
+ * the batch.  A failing item (e.g. PTN_ERR_TOO_LARGE: a circuit beyond the
+ * memory cap, the failures the paper counts in Sec. IV-D) does not stop the
+ * others: status_out[i] (host, n_items) holds each item's status and
+ * shots_out[i] (host, n_items) its result or NULL.  Returns PTN_OK unless
+ * the arguments are malformed.  Plans must have been made on the current
+ * device; a plan must not be used by another call while the batch runs. */
+ptn_status ptn_sample_shots_batch(const ptn_batch_item* items, int32_t n_items, const ptn_batch_opts* opts,
+                                  ptn_shots** shots_out, ptn_status* status_out, ptn_stream stream);
 
 /* ---------------------------------------------------------- gradients -- */
 

@@ -597,14 +597,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // thread-safe one-time lookup (function-local static initialisation)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+            return reinterpret_cast<EncodeTiledFn>(p);
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -756,11 +757,11 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     if (ps) return ps;
     ps = make_map(&mB, pack_b, dt, kEB, 2 * Kh, 2 * N, pb.n_pinst * (1ll << nh), kBN);
     if (ps) return ps;
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr_set = [] {
         cudaFuncSetAttribute(k_gemm<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr_set;
     if (blocks <= 0) return PTN_OK;
     const double flops = 8.0 * (double)n_inst * (double)(1ll << nh) * (double)M * (double)N * (double)Kc;
     const double bytes = 8.0 * ((double)n_inst * (1ll << nh) * M * N) +

@@ -157,6 +157,7 @@ struct ptn_plan {
     int32_t* d_leaf_site_ptr = nullptr;
     int32_t* d_leaf_site_idx = nullptr;
     int32_t* d_leaf_site_mul = nullptr;
+    ptn::RootRef* d_roots = nullptr;     // root descriptor of every block
     double mem_cap = 0;
 };
 

@@ -10,9 +10,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -37,25 +40,51 @@ static_assert(sizeof(RootRef) % 16 == 0, "RootRef must be a multiple of 16 bytes
 
 namespace {
 
+// Stream on which workspace buffers are (re)allocated and freed by the calling
+// thread: set by the batch executor's workers so that their allocations are
+// stream-ordered (cudaMallocAsync / cudaFreeAsync) and never synchronise the
+// device under other workers' work.  Unset: plain cudaMalloc / cudaFree.
+thread_local bool t_async_alloc = false;
+thread_local cudaStream_t t_alloc_stream = nullptr;
+struct AsyncAllocScope {
+    bool prev_on;
+    cudaStream_t prev_s;
+    explicit AsyncAllocScope(cudaStream_t s) : prev_on(t_async_alloc), prev_s(t_alloc_stream) {
+        t_async_alloc = true;
+        t_alloc_stream = s;
+    }
+    ~AsyncAllocScope() {
+        t_async_alloc = prev_on;
+        t_alloc_stream = prev_s;
+    }
+};
+
 struct DevBuf {
     void* p = nullptr;
     size_t cap = 0;
+    bool async = false;      // allocated by cudaMallocAsync
     ptn_status grow(size_t bytes) {
         if (bytes <= cap) return PTN_OK;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
+        release();
         size_t want = std::max(bytes, (size_t)256);
-        cudaError_t e = cudaMalloc(&p, want);
+        async = t_async_alloc;
+        cudaError_t e = async ? cudaMallocAsync(&p, want, t_alloc_stream) : cudaMalloc(&p, want);
         if (e != cudaSuccess) {
             p = nullptr;
-            return set_error(PTN_ERR_OOM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+            return set_error(PTN_ERR_OOM, "device allocation of %zu bytes: %s", want, cudaGetErrorString(e));
         }
         cap = want;
         return PTN_OK;
     }
+    // stream-ordered free only for stream-ordered memory inside an async scope;
+    // otherwise cudaFree (valid for both kinds, synchronising)
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (async && t_async_alloc)
+                cudaFreeAsync(p, t_alloc_stream);
+            else
+                cudaFree(p);
+        }
         p = nullptr;
         cap = 0;
     }
@@ -93,7 +122,7 @@ struct HostBuf {
 // Per-plan device workspace (calls that use the same plan must not overlap).
 struct PlanWorkspace {
     DevBuf arena[3];
-    DevBuf chunk_traj, net_tl, roots;
+    DevBuf chunk_traj, net_tl;
     DevBuf marg, Z, w, cdf, m;
     DevBuf lvl_traj[2], lvl_prefix[2], lvl_count[2];
     DevBuf s_cap, s_tmp_off, s_rank0, s_excl, s_first, s_ndist, s_out_off, s_tmp_x, s_tmp_c, s_scan;
@@ -104,7 +133,7 @@ struct PlanWorkspace {
     DevBuf ev_steps, ev_bwd, ev_root, ev_pl, ev_dvt, ev_terms, ev_F, ev_partial, ev_iota;
     HostBuf h_traj, h_chunk_traj, h_net_tl, h_small, h_grp;
     void release() {
-        DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &roots, &marg, &Z, &w, &cdf, &m,
+        DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &marg, &Z, &w, &cdf, &m,
                          &lvl_traj[0], &lvl_traj[1], &lvl_prefix[0], &lvl_prefix[1], &lvl_count[0], &lvl_count[1],
                          &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
                          &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err, &grp, &grp_cnt,
@@ -170,11 +199,10 @@ ptn_status ensure_device(const ptn_plan* cplan) {
         PTN_CUDA(cudaMalloc(&bp.d_steps, std::max(by, (size_t)16)));
         if (by) PTN_CUDA(cudaMemcpy(bp.d_steps, bp.steps.data(), by, cudaMemcpyHostToDevice));
     }
-    PlanWorkspace* ws = workspace(plan);
-    if ((e = ws->roots.grow(sizeof(RootRef) * plan->blocks.size()))) return e;
     std::vector<RootRef> roots;
     for (auto& bp : plan->blocks) roots.push_back(bp.root);
-    PTN_CUDA(cudaMemcpy(ws->roots.p, roots.data(), sizeof(RootRef) * roots.size(), cudaMemcpyHostToDevice));
+    PTN_CUDA(cudaMalloc(&plan->d_roots, sizeof(RootRef) * std::max<size_t>(roots.size(), 1)));
+    PTN_CUDA(cudaMemcpy(plan->d_roots, roots.data(), sizeof(RootRef) * roots.size(), cudaMemcpyHostToDevice));
     if (plan->mem_cap <= 0) {
         size_t fr = 0, tot = 0;
         PTN_CUDA(cudaMemGetInfo(&fr, &tot));
@@ -193,7 +221,12 @@ std::vector<WsEntry>& ws_table() {
     static std::vector<WsEntry> t;
     return t;
 }
+std::mutex& ws_mutex() {
+    static std::mutex m;
+    return m;
+}
 PlanWorkspace* workspace(const ptn_plan* plan) {
+    std::lock_guard<std::mutex> lk(ws_mutex());
     for (auto& e : ws_table())
         if (e.plan == plan) return e.ws;
     PlanWorkspace* w = new PlanWorkspace();
@@ -201,14 +234,21 @@ PlanWorkspace* workspace(const ptn_plan* plan) {
     return w;
 }
 void drop_workspace(const ptn_plan* plan) {
-    auto& t = ws_table();
-    for (size_t i = 0; i < t.size(); i++)
-        if (t[i].plan == plan) {
-            t[i].ws->release();
-            delete t[i].ws;
-            t.erase(t.begin() + i);
-            return;
-        }
+    PlanWorkspace* w = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ws_mutex());
+        auto& t = ws_table();
+        for (size_t i = 0; i < t.size(); i++)
+            if (t[i].plan == plan) {
+                w = t[i].ws;
+                t.erase(t.begin() + i);
+                break;
+            }
+    }
+    if (w) {
+        w->release();
+        delete w;
+    }
 }
 
 struct Chunk {
@@ -323,7 +363,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     if ((e = ws->err.grow(sizeof(int)))) return e;
     if ((e = ws->h_small.grow(64))) return e;
     PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
-    const RootRef* d_root = ws->roots.as<RootRef>() + j;
+    const RootRef* d_root = plan->d_roots + j;
     for (size_t ci = 0; ci < chunks.size(); ci++) {
         const Chunk& c = chunks[ci];
         GroupTable gt;
@@ -439,6 +479,7 @@ void ptn_plan_destroy(ptn_plan* plan) {
         cudaFree(plan->d_leaf_site_idx);
         cudaFree(plan->d_leaf_site_mul);
         for (auto& b : plan->blocks) cudaFree(b.d_steps);
+        cudaFree(plan->d_roots);
     }
     delete plan->expval;
     delete plan;
@@ -821,6 +862,7 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     if (traj->plan != plan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
     if (o->mode != PTN_PROPORTIONAL_FIXED && o->mode != PTN_PROPORTIONAL_TOTAL)
         return set_error(PTN_ERR_UNSUPPORTED, "sampling mode %d", o->mode);
+    if (o->use_graphs) return set_error(PTN_ERR_UNSUPPORTED, "CUDA-graph capture is not built");
     int64_t total_cap;
     if (o->mode == PTN_PROPORTIONAL_FIXED) {
         if (o->shots_per_traj < 1) return set_error(PTN_ERR_INVALID_ARG, "shots_per_traj must be >= 1");
@@ -893,6 +935,128 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     }
     PTN_CUDA(cudaGetLastError());
     *shots_out = r;
+    return PTN_OK;
+}
+
+ptn_status ptn_sample_shots_batch(const ptn_batch_item* items, int32_t n_items, const ptn_batch_opts* bo,
+                                  ptn_shots** shots_out, ptn_status* status_out, ptn_stream stream) {
+    clear_error();
+    if (n_items < 0 || (n_items > 0 && (!items || !shots_out || !status_out)))
+        return set_error(PTN_ERR_INVALID_ARG, "NULL argument or negative item count");
+    for (int32_t i = 0; i < n_items; i++) {
+        shots_out[i] = nullptr;
+        status_out[i] = PTN_OK;
+        if (!items[i].plan || !items[i].traj || items[i].traj->plan != items[i].plan)
+            return set_error(PTN_ERR_INVALID_ARG, "item %d: missing plan/trajectories or trajectories of another plan", i);
+    }
+    if (n_items == 0) return PTN_OK;
+    int dev = 0;
+    PTN_CUDA(cudaGetDevice(&dev));
+    const int n_workers = std::max(1, std::min(bo && bo->n_workers > 0 ? bo->n_workers : 4, 64));
+    const bool keep = bo && bo->keep_workspaces;
+    const double max_est = bo ? bo->max_est_seconds : 0.0;
+    // groups of items sharing a plan, in first-appearance order
+    struct Group {
+        const ptn_plan* plan;
+        std::vector<int32_t> items;
+        double cost;
+    };
+    std::vector<Group> groups;
+    for (int32_t i = 0; i < n_items; i++) {
+        size_t g = 0;
+        while (g < groups.size() && groups[g].plan != items[i].plan) g++;
+        if (g == groups.size()) groups.push_back({items[i].plan, {}, 0.0});
+        groups[g].items.push_back(i);
+    }
+    double budget = bo && bo->mem_budget_bytes > 0 ? bo->mem_budget_bytes : 0.0;
+    for (auto& g : groups) {
+        double est = 0;
+        for (const auto& b : g.plan->blocks) est += b.est_time;
+        g.cost = est * (double)g.items.size();
+        if (max_est > 0 && est > max_est)
+            for (int32_t i : g.items) status_out[i] = PTN_ERR_TOO_LARGE;
+    }
+    // longest first (ties by first appearance)
+    std::vector<size_t> order(groups.size());
+    for (size_t g = 0; g < order.size(); g++) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return groups[a].cost > groups[b].cost; });
+    // upload plans and set their caps on this thread; earlier workspaces are
+    // freed first so the workers allocate stream-ordered memory only
+    std::vector<double> saved_cap(groups.size());
+    for (auto& g : groups) {
+        drop_workspace(g.plan);
+        ptn_status e = ensure_device(g.plan);
+        if (e) {
+            for (int32_t i : g.items) status_out[i] = e;
+        }
+    }
+    if (budget <= 0) {
+        size_t fr = 0, tot = 0;
+        PTN_CUDA(cudaMemGetInfo(&fr, &tot));
+        budget = 0.8 * (double)fr;
+    }
+    for (size_t g = 0; g < groups.size(); g++) {
+        ptn_plan* pl = const_cast<ptn_plan*>(groups[g].plan);
+        saved_cap[g] = pl->mem_cap;
+        if (pl->opts.mem_cap_bytes <= 0) pl->mem_cap = budget / n_workers;
+    }
+    cudaStream_t s0 = (cudaStream_t)stream;
+    cudaEvent_t ev0;
+    PTN_CUDA(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+    PTN_CUDA(cudaEventRecord(ev0, s0));
+    std::vector<cudaStream_t> ws_streams(n_workers, nullptr);
+    std::vector<cudaEvent_t> ws_done(n_workers, nullptr);
+    for (int w = 0; w < n_workers; w++) {
+        PTN_CUDA(cudaStreamCreateWithFlags(&ws_streams[w], cudaStreamNonBlocking));
+        PTN_CUDA(cudaEventCreateWithFlags(&ws_done[w], cudaEventDisableTiming));
+        PTN_CUDA(cudaStreamWaitEvent(ws_streams[w], ev0, 0));
+    }
+    std::atomic<size_t> next{0};
+    std::mutex msg_mu;
+    std::string first_msg;
+    auto worker = [&](int w) {
+        cudaSetDevice(dev);
+        cudaStream_t s = ws_streams[w];
+        AsyncAllocScope scope(s);
+        for (;;) {
+            const size_t k = next.fetch_add(1);
+            if (k >= order.size()) break;
+            const Group& g = groups[order[k]];
+            for (int32_t i : g.items) {
+                if (status_out[i] != PTN_OK) continue;
+                ptn_status st;
+                try {
+                    st = ptn_sample_shots(items[i].plan, items[i].traj, &items[i].opts, &shots_out[i], s);
+                } catch (const std::bad_alloc&) {
+                    st = set_error(PTN_ERR_OOM, "host allocation failed");
+                }
+                status_out[i] = st;
+                if (st != PTN_OK) {
+                    std::lock_guard<std::mutex> lk(msg_mu);
+                    if (first_msg.empty()) {
+                        char buf[64];
+                        snprintf(buf, sizeof buf, "item %d: ", i);
+                        first_msg = std::string(buf) + last_error_text();
+                    }
+                }
+            }
+            if (!keep) drop_workspace(g.plan);
+        }
+        cudaEventRecord(ws_done[w], s);
+    };
+    std::vector<std::thread> threads;
+    for (int w = 0; w < n_workers; w++) threads.emplace_back(worker, w);
+    for (auto& t : threads) t.join();
+    for (int w = 0; w < n_workers; w++) {
+        cudaStreamWaitEvent(s0, ws_done[w], 0);
+        cudaEventDestroy(ws_done[w]);
+        cudaStreamDestroy(ws_streams[w]);
+    }
+    cudaEventDestroy(ev0);
+    for (size_t g = 0; g < groups.size(); g++) const_cast<ptn_plan*>(groups[g].plan)->mem_cap = saved_cap[g];
+    clear_error();
+    if (!first_msg.empty()) set_error(PTN_OK, "%s", first_msg.c_str());
+    PTN_CUDA(cudaGetLastError());
     return PTN_OK;
 }
 

@@ -65,6 +65,15 @@ class ptn_sample_opts(C.Structure):
                 ("max_traj_per_chunk", C.c_int32), ("use_graphs", C.c_int32), ("reserved", C.c_int32)]
 
 
+class ptn_batch_item(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("traj", C.c_void_p), ("opts", ptn_sample_opts)]
+
+
+class ptn_batch_opts(C.Structure):
+    _fields_ = [("n_workers", C.c_int32), ("keep_workspaces", C.c_int32), ("mem_budget_bytes", C.c_double),
+                ("max_est_seconds", C.c_double)]
+
+
 class ptn_pauli_sum(C.Structure):
     _fields_ = [("n_terms", C.c_int32), ("coeff", C.POINTER(C.c_double)), ("x_mask", C.POINTER(C.c_uint64)),
                 ("z_mask", C.POINTER(C.c_uint64))]
@@ -97,6 +106,8 @@ _SIGS = {
                        C.POINTER(C.c_int64), C.c_int32],
     "ptn_shots_copy": [_P, _P, _P, _P, _P],
     "ptn_shots_destroy": [_P],
+    "ptn_sample_shots_batch": [C.POINTER(ptn_batch_item), C.c_int32, C.POINTER(ptn_batch_opts), C.POINTER(_P),
+                               C.POINTER(C.c_int), _P],
     "ptn_expval_grad": [_P, _P, C.POINTER(ptn_pauli_sum), C.POINTER(C.c_double), C.c_int32, _P, _P, _P],
     "ptn_stats_enable": [C.c_int32],
     "ptn_stats_reset": [],
@@ -324,12 +335,43 @@ def ptn_allocate_shots(weights, total, seed, circuit_id, m_out, stream=None):
 
 def ptn_sample_shots(plan, traj, seed, shots_per_traj=None, total_shots=None, circuit_id=0,
                      precision=PTN_PREC_FP32, max_traj_per_chunk=0, use_graphs=0, stream=None):
-    mode = PTN_PROPORTIONAL_FIXED if total_shots is None else PTN_PROPORTIONAL_TOTAL
-    o = ptn_sample_opts(mode, circuit_id, int(shots_per_traj or 0), int(total_shots or 0), seed, precision,
-                        max_traj_per_chunk, use_graphs, 0)
+    o = _sample_opts(seed, shots_per_traj, total_shots, circuit_id, precision, max_traj_per_chunk)
+    o.use_graphs = use_graphs
     h = C.c_void_p()
     _check(lib().ptn_sample_shots(plan.handle, traj.handle, C.byref(o), C.byref(h), _stream(stream)))
     return Shots(h, len(plan.block_sizes))
+
+
+def _sample_opts(seed, shots_per_traj=None, total_shots=None, circuit_id=0, precision=PTN_PREC_FP32,
+                 max_traj_per_chunk=0):
+    mode = PTN_PROPORTIONAL_FIXED if total_shots is None else PTN_PROPORTIONAL_TOTAL
+    return ptn_sample_opts(mode, circuit_id, int(shots_per_traj or 0), int(total_shots or 0), seed, precision,
+                           max_traj_per_chunk, 0, 0)
+
+
+def ptn_sample_shots_batch(items, n_workers=4, keep_workspaces=False, mem_budget_bytes=0.0, max_est_seconds=0.0,
+                           stream=None):
+    """Mixed-circuit batch (include/ptn.h).  items: list of dicts with keys
+    plan, traj, seed and shots_per_traj or total_shots (optional circuit_id,
+    precision).  Returns a list of (status, Shots or None) in item order."""
+    n = len(items)
+    arr = (ptn_batch_item * max(n, 1))()
+    for i, it in enumerate(items):
+        arr[i].plan = it["plan"].handle
+        arr[i].traj = it["traj"].handle
+        arr[i].opts = _sample_opts(it["seed"], it.get("shots_per_traj"), it.get("total_shots"),
+                                   it.get("circuit_id", 0), it.get("precision", PTN_PREC_FP32))
+    bo = ptn_batch_opts(n_workers, int(bool(keep_workspaces)), float(mem_budget_bytes), float(max_est_seconds))
+    outs = (C.c_void_p * max(n, 1))()
+    sts = (C.c_int * max(n, 1))()
+    _check(lib().ptn_sample_shots_batch(arr, n, C.byref(bo), outs, sts, _stream(stream)))
+    res = []
+    for i, it in enumerate(items):
+        if sts[i] == PTN_OK:
+            res.append((PTN_OK, Shots(C.c_void_p(outs[i]), len(it["plan"].block_sizes))))
+        else:
+            res.append((sts[i], None))
+    return res
 
 
 def ptn_expval_grad(plan, traj, terms, theta, value_out, grad_out, stream=None):

@@ -169,42 +169,56 @@ def run_reference(args, rank):
 
 # ------------------------------------------------------------- our arm ----
 
-def run_mixed_batch(ptn, torch, hypersamples, workers):
+def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers):
     """Plans (untimed), pre-samples (untimed) and runs the mixed batch through
     ptn_sample_shots_batch, once with one circuit in flight and once with
     `workers`; circuits beyond the planner's limits or the memory cap count as
-    failed (TOO_LARGE), as do those whose modelled time exceeds 120 s."""
+    failed (TOO_LARGE), as do those whose modelled time exceeds 120 s.  With
+    several ranks, the circuits are shared out by modelled cost (longest
+    first, no collective on the data path)."""
     cfgs = W.config_c3()
-    items, plan_fail = [], 0
+    plans, status = {}, {}
     t0 = time.perf_counter()
     for c in cfgs:
         try:
-            p = ptn.ptn_plan_path(c["circuit"], c["block_sizes"], hypersamples=hypersamples, est_traj=c["n_traj"],
-                                  est_shots=c["total_shots"])
-        except ptn.PtnError:
-            plan_fail += 1
-            continue
+            plans[c["name"]] = ptn.ptn_plan_path(c["circuit"], c["block_sizes"], hypersamples=hypersamples,
+                                                 est_traj=c["n_traj"], est_shots=c["total_shots"])
+        except ptn.PtnError as e:
+            status[c["name"]] = f"plan: {ptn.STATUS_NAMES.get(e.status, e.status)}"
+    planned = [c for c in cfgs if c["name"] in plans]
+    costs = [sum(b["est_time"] for b in plans[c["name"]].describe()["blocks"]) for c in planned]
+    mine = [planned[i] for i in shard.shard_items(costs, world)[rank]]
+    items, names = [], []
+    for c in mine:
+        p = plans[c["name"]]
         tr = ptn.ptn_presample_trajectories(p, c["seed"], c["n_traj"], dedup=True, circuit_id=c["circuit_id"])
         items.append(dict(plan=p, traj=tr, seed=c["seed"], total_shots=c["total_shots"], circuit_id=c["circuit_id"]))
+        names.append(c["name"])
     t_plan = time.perf_counter() - t0
     runs = {}
     for nw in sorted({1, workers}):
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out = ptn.ptn_sample_shots_batch(items, n_workers=nw, max_est_seconds=120.0)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        dt = shard.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
         ok = [it for it, (st, _) in zip(items, out) if st == 0]
-        shots = sum(it["total_shots"] for it in ok)
-        runs[nw] = {"seconds": dt, "completed": len(ok), "shots": shots, "value": shots / dt}
+        shots = shard.sum_over_ranks(sum(it["total_shots"] for it in ok), dist, device="cuda")
+        done = shard.sum_over_ranks(len(ok), dist, device="cuda")
+        runs[nw] = {"seconds": dt, "completed": int(done), "shots": int(shots), "value": shots / dt}
+        if nw == workers:
+            for nm, (st, _) in zip(names, out):
+                status[nm] = "ok" if st == 0 else f"run: {ptn.STATUS_NAMES.get(st, st)}"
         del out
     best = runs[workers]
     return {"workload": "64 circuits: 20-40-qubit 1D brickwork or 6x5 grid, depth 8-16, depolarizing 0.001-0.02, "
                         "16-8192 trajectories, 1e3-1e6 shots each",
             "value": best["value"], "unit": "shots/s", "workers": workers, "completed": best["completed"],
-            "completed_fraction": best["completed"] / len(cfgs), "failed_at_plan": plan_fail,
-            "failed_at_run": len(items) - best["completed"], "seconds": best["seconds"],
-            "serial_seconds": runs[1]["seconds"], "plan_and_presample_seconds": t_plan}
+            "completed_fraction": best["completed"] / len(cfgs), "shots": best["shots"], "seconds": best["seconds"],
+            "serial_seconds": runs[1]["seconds"], "plan_and_presample_seconds": t_plan,
+            "status_rank0": {nm: status.get(nm, "other rank") for nm in (c["name"] for c in cfgs)}}
 
 
 def main():
@@ -246,7 +260,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_2604_08467_gb300 import ptn
+    from paper_2604_08467_gb300 import ptn, shard
 
     cfg = c2_config()
     E = args.n_traj or cfg["n_traj"]
@@ -260,7 +274,7 @@ def main():
     prec = PRECISIONS[args.precision][0]
 
     def step(k):
-        tr = ptn.ptn_presample_trajectories(plan, cfg["seed"] + 7919 * (rank * 1000 + k), E)
+        tr = ptn.ptn_presample_trajectories(plan, shard.rank_seed(cfg["seed"], rank, k), E)
         res = ptn.ptn_sample_shots(plan, tr, cfg["seed"] + k, total_shots=M, precision=prec)
         return tr, res
 
@@ -298,11 +312,7 @@ def main():
     stats = ptn.ptn_stats_read()
     free_b, total_b = torch.cuda.mem_get_info()
     clocks = clk.summary()
-    t_step = float(np.mean(times))
-    if dist:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = shard.max_over_ranks(float(np.mean(times)), dist, device="cuda")
     value = M * world / t_step
 
     # ---- end to end through the public API, result copied to pinned host memory
@@ -333,7 +343,7 @@ def main():
     # ---- plain per-trajectory path on a subset (same kernels, one trajectory per launch)
     plain = None
     if args.plain_traj > 0:
-        tr = ptn.ptn_presample_trajectories(plan, cfg["seed"] + 5, args.plain_traj)
+        tr = ptn.ptn_presample_trajectories(plan, shard.rank_seed(cfg["seed"], rank, 999_999), args.plain_traj)
         m_pt = M // E
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -375,7 +385,8 @@ def main():
     # depth 8-16, 16-8192 trajectories, 1e3-1e6 shots (the batching workload)
     mixed = None
     if args.mixed_batch > 0:
-        mixed = run_mixed_batch(ptn, torch, args.hypersamples, args.mixed_batch)
+        del plan          # frees the brickwork workspace so the batch gets the device memory
+        mixed = run_mixed_batch(ptn, shard, torch, dist, rank, world, args.hypersamples, args.mixed_batch)
 
     # ---- roofline of every kernel class (from the library's per-launch events);
     # the dominant one is the headline.  Tensor-core GEMMs are charged their

@@ -227,56 +227,80 @@ __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ PackArgs
     }
 }
 
-// One thread per (packed instance, h, row, complex k) including the K padding.
+// Packing: one warp per packed row (instance, h, row) when a half row holds
+// >= 32 complex slots, else 32 / slots rows per warp.  Every size is a power of
+// two, so the row index is decoded with shifts.  The row's base offset is
+// formed once per row; the K offsets come from a per-block shared table in two
+// levels (bits 0-9 and 10-19; bit 20 and up, rarely used, by a loop), so a
+// contiguous K axis turns into coalesced float2 loads.  Stores are float2 /
+// 32-bit pairs, consecutive lanes on consecutive slots.
+constexpr int kKTab = 1024;
 template <int F>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a, const ChunkCtx c) {
     using T = typename Fmt<F>::T;
+    __shared__ int64_t ktab[2 * kKTab];
+    const int n_lo = a.n_kb < 10 ? a.n_kb : 10;
+    const int n_mid = a.n_kb < 20 ? a.n_kb - n_lo : 10;
+    for (int i = threadIdx.x; i < 2 * kKTab; i += blockDim.x) {
+        const int lvl = i >= kKTab, v = i & (kKTab - 1);
+        int64_t off = 0;
+        const int nb = lvl ? n_mid : n_lo, b0 = lvl ? 10 : 0;
+        for (int t = 0; t < nb; t++)
+            if ((v >> t) & 1) off += a.k_stride[b0 + t];
+        ktab[i] = off;
+    }
+    __syncthreads();
     T* dst = static_cast<T*>(a.dst);
-    const int64_t kcp = a.Kh / 2;                       // complex slots per half row
-    const int64_t nrow = (int64_t)1 << a.n_rb, nh = (int64_t)1 << a.n_hb;
+    const int lk = 31 - __clz(a.Kh / 2);                // log2 complex slots per half row
+    const int64_t kcp = (int64_t)1 << lk;
     const int64_t kc_real = (int64_t)1 << a.n_kb;
-    const int64_t total = a.n_pinst * nh * nrow * kcp;
     const int64_t rowlen = 2 * (int64_t)a.Kh;
-    int64_t cur = -1;
-    const float2* base = nullptr;
-    float sc = 1.f;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t kc = g % kcp;
-        int64_t rest = g / kcp;
-        const int64_t row = rest % nrow;
-        rest /= nrow;
-        const int64_t h = rest % nh;
-        const int64_t pi = rest / nh;
-        float re = 0.f, im = 0.f;
-        if (kc < kc_real) {
-            if (pi != cur) {
-                base = pack_operand_ptr(a.op, a.pcls, pi, c);
-                sc = ldexpf(1.f, -scale_exp(a.amax, pi));
-                cur = pi;
+    const int rpw = lk >= 5 ? 1 : (32 >> lk);           // rows per warp
+    const int lane = threadIdx.x & 31;
+    const int sub = lk >= 5 ? 0 : (lane >> lk);         // row of this lane within the warp
+    const int lstep = lk >= 5 ? 32 : (int)kcp;          // slots a lane advances by
+    const int l0 = lk >= 5 ? lane : (lane & ((int)kcp - 1));
+    const int64_t n_rows = a.n_pinst << (a.n_hb + a.n_rb);
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w * rpw < n_rows; w += warps) {
+        const int64_t jr = w * rpw + sub;                // (pi, h, row), row fastest
+        if (jr >= n_rows) continue;
+        const int64_t row = jr & (((int64_t)1 << a.n_rb) - 1);
+        const int64_t z = jr >> a.n_rb;                  // pi * nh + h
+        const int64_t h = z & (((int64_t)1 << a.n_hb) - 1);
+        const int64_t pi = z >> a.n_hb;
+        const float2* base = pack_operand_ptr(a.op, a.pcls, pi, c);
+        for (int i = 0; i < a.n_rb; i++)
+            if ((row >> i) & 1) base += a.r_stride[i];
+        for (int i = 0; i < a.n_hb; i++)
+            if ((h >> i) & 1) base += a.h_stride[i];
+        const float sc = ldexpf(1.f, -scale_exp(a.amax, pi));
+        const float csign = a.op.conj ? -1.f : 1.f;
+        T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
+        for (int64_t kc = l0; kc < kcp; kc += lstep) {
+            float re = 0.f, im = 0.f;
+            if (kc < kc_real) {
+                int64_t off = ktab[kc & (kKTab - 1)] + ktab[kKTab + ((kc >> 10) & (kKTab - 1))];
+                for (int t = 20; t < a.n_kb; t++)
+                    if ((kc >> t) & 1) off += a.k_stride[t];
+                const float2 v = base[off];
+                re = v.x * sc;
+                im = csign * v.y * sc;
             }
-            const float2 v = base[pack_offset(a, row, h, kc)];
-            re = v.x * sc;
-            im = (a.op.conj ? -v.y : v.y) * sc;
-        }
-        const int64_t z = pi * nh + h;
-        T rh, rl, ih, il;
-        split<F>(re, rh, rl);
-        split<F>(im, ih, il);
-        // (re, im) pairs are adjacent: store each pair as one vector
-        if (a.role == 0) {
-            T* d = dst + (z * nrow + row) * rowlen + 2 * kc;
-            store_pair<F>(d, rh, ih);
-            store_pair<F>(d + a.Kh, rl, il);
-        } else {
-            T* d0 = dst + (z * 2 * nrow + 2 * row) * rowlen + 2 * kc;
-            T* d1 = d0 + rowlen;
-            T nih, nil;
-            split<F>(-im, nih, nil);
-            store_pair<F>(d0, rh, nih);
-            store_pair<F>(d0 + a.Kh, rl, nil);
-            store_pair<F>(d1, ih, rh);
-            store_pair<F>(d1 + a.Kh, il, rl);
+            T rh, rl, ih, il;
+            split<F>(re, rh, rl);
+            split<F>(im, ih, il);
+            if (a.role == 0) {
+                store_pair<F>(d0 + 2 * kc, rh, ih);
+                store_pair<F>(d0 + a.Kh + 2 * kc, rl, il);
+            } else {
+                T nih, nil;
+                split<F>(-im, nih, nil);
+                store_pair<F>(d0 + 2 * kc, rh, nih);
+                store_pair<F>(d0 + a.Kh + 2 * kc, rl, nil);
+                store_pair<F>(d0 + rowlen + 2 * kc, ih, rh);
+                store_pair<F>(d0 + rowlen + a.Kh + 2 * kc, il, rl);
+            }
         }
     }
 }
@@ -727,6 +751,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
         StatScope sc(K_PACK, s, 8.0 * (double)(tot_a + tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b, 0.0);
         k_pack<F><<<grid_of(tot_a), 256, 0, s>>>(pa, ctx);
         k_pack<F><<<grid_of(tot_b), 256, 0, s>>>(pb, ctx);
+        // (grid_of sizes by complex slots; the kernel strides over rows by warps)
     }
     CUtensorMap mA, mB;
     int64_t blocks = ga.tiles_m * ga.tiles_n * n_inst * (1ll << nh);

@@ -386,6 +386,22 @@ ptn_status ptn_stats_enable(int32_t timing_on);
 ptn_status ptn_stats_reset(void);
 ptn_status ptn_stats_read(ptn_kernel_stat* out, int32_t cap, int32_t* n_out);
 
+/* The same timings per path step: block (-1 for launches outside a block's
+ * step list, -2 / -3 for the forward / adjoint steps of ptn_expval_grad), step
+ * index within the block's lowered list, kernel.  Timing must have been
+ * enabled.  Fills up to cap records (host array) ordered by block, step. */
+typedef struct {
+    int32_t block;
+    int32_t step;
+    char    kernel[32];
+    int64_t launches;
+    double  ms;
+    double  alg_bytes;
+    double  alg_flops;
+} ptn_step_stat;
+
+ptn_status ptn_stats_read_steps(ptn_step_stat* out, int32_t cap, int32_t* n_out);
+
 /* ------------------------------------------------------------- utilities -- */
 
 const char* ptn_status_string(ptn_status status);

@@ -2,11 +2,10 @@
 // step of P^j for every network of a chunk, Sec. III-A) and the marginal
 // finalisation of the block's root tensor (Sec. II-B).
 //
-// k_contract_direct: one thread per output element of one instance; the
-// element's operand addresses come from the step's per-bit stride tables, so
-// any bit layout of either operand is read without a separate permutation
-// pass.  The summed bits are walked in Gray-code order so each term updates
-// one stride.  The first operand read of a merged-gate leaf goes through the
+// k_contract_direct: each output element of one instance is one thread's
+// accumulation; the element's operand addresses come from the step's per-bit
+// stride tables, so any bit layout of either operand is read without a
+// separate permutation pass.  The first operand read of a merged-gate leaf goes through the
 // trajectory's variant index: the UPV merge happens as a gather fused into its
 // first consumer.
 #include <cuda_runtime.h>
@@ -48,16 +47,17 @@ __device__ __forceinline__ const float2* operand_ptr(const OperandDesc& d, int o
     return p;
 }
 
-__device__ __forceinline__ float2 cmul_acc(float2 acc, float2 a, float2 b) {
-    acc.x = fmaf(a.x, b.x, acc.x);
-    acc.x = fmaf(-a.y, b.y, acc.x);
-    acc.y = fmaf(a.x, b.y, acc.y);
-    acc.y = fmaf(a.y, b.x, acc.y);
-    return acc;
-}
-
-__global__ void __launch_bounds__(256) k_contract_direct(const StepDesc* __restrict__ gstep, ChunkCtx c,
-                                                         int64_t n_inst) {
+// A warp takes tiles of 128 consecutive outputs (instance-major), four per
+// lane (lane, lane + 32, ...): four independent accumulation chains, and each
+// store instruction of the warp covers 32 consecutive outputs.  Offsets of the
+// low 8 output bits and of the low 8 summed bits come from per-block tables;
+// higher summed bits are walked in Gray-code order.  OffT is int32_t when
+// every in-instance offset fits (the usual case), halving the address math.
+constexpr int kDirThreads = 256;
+constexpr int kDirU = 4;
+template <typename OffT>
+__global__ void __launch_bounds__(kDirThreads, 3) k_contract_direct(const StepDesc* __restrict__ gstep, ChunkCtx c,
+                                                                 int64_t n_inst) {
     __shared__ __align__(16) StepDesc s;
     {
         const int4* src = reinterpret_cast<const int4*>(gstep);
@@ -65,72 +65,103 @@ __global__ void __launch_bounds__(256) k_contract_direct(const StepDesc* __restr
         for (int i = threadIdx.x; i < (int)(sizeof(StepDesc) / sizeof(int4)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    // Operand offsets of the low (up to 8) output bits, shared by the block: a
-    // block iteration covers 256 consecutive outputs, so each element adds one
-    // table entry to the offsets of its remaining high bits.
-    __shared__ int64_t tab[2][256];
+    __shared__ OffT otab[2][256];
+    __shared__ OffT ktab[2][256];
     const int lowb = s.n_out < 8 ? s.n_out : 8;
-    {
-        const int t = threadIdx.x;
-        int64_t a = 0, b = 0;
+    const int nk = s.n_sum;
+    const int klo = nk < 8 ? nk : 8;
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        OffT a = 0, b = 0, ka = 0, kb = 0;
         for (int p = 0; p < lowb; p++)
             if ((t >> p) & 1) {
-                a += s.out_stride[0][p];
-                b += s.out_stride[1][p];
+                a += (OffT)s.out_stride[0][p];
+                b += (OffT)s.out_stride[1][p];
             }
-        tab[0][t] = a;
-        tab[1][t] = b;
+        for (int p = 0; p < klo; p++)
+            if ((t >> p) & 1) {
+                ka += (OffT)s.sum_stride[0][p];
+                kb += (OffT)s.sum_stride[1][p];
+            }
+        otab[0][t] = a;
+        otab[1][t] = b;
+        ktab[0][t] = ka;
+        ktab[1][t] = kb;
     }
     __syncthreads();
     const int64_t total = n_inst << s.n_out;
     const int64_t mask = s.out_size - 1;
-    const int64_t lowmask = (1ll << lowb) - 1;
-    const int nk = s.n_sum;
-    const bool ca = s.op[0].conj, cb = s.op[1].conj;
+    const int lowmask = (1 << lowb) - 1;
+    const int n_lo = 1 << klo;
+    const int64_t n_hi = (int64_t)1 << (nk - klo);
+    const float sa = s.op[0].conj ? -1.f : 1.f, sb = s.op[1].conj ? -1.f : 1.f;
     float2* outbase = c.arena[s.out_arena] + s.out_off * c.arena_inst[s.out_arena];
-    int64_t cur_inst = -1, cur_hi = -1, hia = 0, hib = 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_tiles = (total + 32 * kDirU - 1) / (32 * kDirU);
+    const int64_t warps = (int64_t)gridDim.x * (kDirThreads / 32);
+    int64_t cur_inst = -1, cur_hi = -1;
+    OffT hia = 0, hib = 0;
     const float2 *A = nullptr, *B = nullptr;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t inst = g >> s.n_out;
-        const int64_t o = g & mask;
-        if (inst != cur_inst) {
-            A = operand_ptr(s.op[0], s.out_cls, inst, c);
-            B = operand_ptr(s.op[1], s.out_cls, inst, c);
-            cur_inst = inst;
+    for (int64_t tile = (int64_t)blockIdx.x * (kDirThreads / 32) + (threadIdx.x >> 5); tile < n_tiles; tile += warps) {
+        const float2* pa[kDirU];
+        const float2* pb[kDirU];
+        float2 acc[kDirU];
+#pragma unroll
+        for (int u = 0; u < kDirU; u++) {
+            acc[u] = make_float2(0.f, 0.f);
+            const int64_t g = tile * (32 * kDirU) + u * 32 + lane;
+            const int64_t gg = g < total ? g : total - 1;     // tail lanes compute a valid dummy
+            const int64_t inst = gg >> s.n_out;
+            const int64_t o = gg & mask;
+            if (inst != cur_inst) {
+                A = operand_ptr(s.op[0], s.out_cls, inst, c);
+                B = operand_ptr(s.op[1], s.out_cls, inst, c);
+                cur_inst = inst;
+            }
+            const int64_t hi = o >> lowb;
+            if (hi != cur_hi) {
+                hia = hib = 0;
+                for (int p = lowb; p < s.n_out; p++)
+                    if ((o >> p) & 1) {
+                        hia += (OffT)s.out_stride[0][p];
+                        hib += (OffT)s.out_stride[1][p];
+                    }
+                cur_hi = hi;
+            }
+            pa[u] = A + (hia + otab[0][o & lowmask]);
+            pb[u] = B + (hib + otab[1][o & lowmask]);
         }
-        const int64_t hi = o >> lowb;
-        if (hi != cur_hi) {
-            hia = hib = 0;
-            for (int p = lowb; p < s.n_out; p++)
-                if ((o >> p) & 1) {
-                    hia += s.out_stride[0][p];
-                    hib += s.out_stride[1][p];
-                }
-            cur_hi = hi;
-        }
-        const int64_t oa = hia + tab[0][o & lowmask], ob = hib + tab[1][o & lowmask];
-        float2 acc = make_float2(0.f, 0.f);
-        int64_t ka = 0, kb = 0;
-        const int64_t nterm = (int64_t)1 << nk;
-        for (int64_t t = 0; t < nterm; t++) {
-            if (t) {
-                const int bit = __ffsll(t) - 1;
-                const int64_t gray = t ^ (t >> 1);
+        OffT ha = 0, hb = 0;
+        for (int64_t th = 0; th < n_hi; th++) {
+            if (th) {
+                const int bit = __ffsll(th) - 1;
+                const int64_t gray = th ^ (th >> 1);
+                const OffT da = (OffT)s.sum_stride[0][klo + bit], db = (OffT)s.sum_stride[1][klo + bit];
                 if ((gray >> bit) & 1) {
-                    ka += s.sum_stride[0][bit];
-                    kb += s.sum_stride[1][bit];
+                    ha += da;
+                    hb += db;
                 } else {
-                    ka -= s.sum_stride[0][bit];
-                    kb -= s.sum_stride[1][bit];
+                    ha -= da;
+                    hb -= db;
                 }
             }
-            float2 a = A[oa + ka], b = B[ob + kb];
-            if (ca) a.y = -a.y;
-            if (cb) b.y = -b.y;
-            acc = cmul_acc(acc, a, b);
+            for (int tl = 0; tl < n_lo; tl++) {
+                const OffT ka = ha + ktab[0][tl], kb = hb + ktab[1][tl];
+#pragma unroll
+                for (int u = 0; u < kDirU; u++) {
+                    const float2 x = pa[u][ka], y = pb[u][kb];
+                    const float xi = sa * x.y, yi = sb * y.y;
+                    acc[u].x = fmaf(x.x, y.x, acc[u].x);
+                    acc[u].x = fmaf(-xi, yi, acc[u].x);
+                    acc[u].y = fmaf(x.x, yi, acc[u].y);
+                    acc[u].y = fmaf(xi, y.x, acc[u].y);
+                }
+            }
         }
-        outbase[inst * s.out_size + o] = acc;
+#pragma unroll
+        for (int u = 0; u < kDirU; u++) {
+            const int64_t g = tile * (32 * kDirU) + u * 32 + lane;
+            if (g < total) outbase[g] = acc[u];
+        }
     }
 }
 
@@ -172,9 +203,13 @@ void launch_contract_step(const StepDesc* d_step, const StepDesc& h, const Chunk
                           cudaStream_t s) {
     const int64_t total = n_inst << h.n_out;
     if (total <= 0) return;
-    int64_t blocks = (total + 255) / 256;
+    const int64_t tiles = (total + 32 * kDirU - 1) / (32 * kDirU);
+    int64_t blocks = (tiles + kDirThreads / 32 - 1) / (kDirThreads / 32);
     const int64_t cap = 152 * 16;
     if (blocks > cap) blocks = cap;
+    // 32-bit in-instance offsets when both operands and the output fit
+    const bool off32 = h.op[0].inst_size < (1ll << 31) && h.op[1].inst_size < (1ll << 31) &&
+                       h.out_size < (1ll << 31);
     // algorithmic traffic: every distinct operand element once, the output once
     double bytes = 8.0 * (double)total;
     for (int o = 0; o < 2; o++) {
@@ -185,7 +220,10 @@ void launch_contract_step(const StepDesc* d_step, const StepDesc& h, const Chunk
     }
     const double flops = 8.0 * (double)total * (double)(1ll << h.n_sum);
     StatScope sc(K_CONTRACT_DIRECT, s, bytes, flops);
-    k_contract_direct<<<(unsigned)blocks, 256, 0, s>>>(d_step, ctx, n_inst);
+    if (off32)
+        k_contract_direct<int32_t><<<(unsigned)blocks, kDirThreads, 0, s>>>(d_step, ctx, n_inst);
+    else
+        k_contract_direct<int64_t><<<(unsigned)blocks, kDirThreads, 0, s>>>(d_step, ctx, n_inst);
 }
 
 void launch_finalize(const RootRef* d_root, const ChunkCtx& ctx, int b, int64_t n_net, float* marg, double* Z,

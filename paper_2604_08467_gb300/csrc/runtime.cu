@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "stats.h"
 
 namespace ptn {
 const char* last_error_text();
@@ -389,6 +390,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         ctx.arena_inst[CLS_NET] = c.n_net;
         for (size_t st = 0; st < bp.steps.size(); st++) {
             const StepDesc& h = bp.steps[st];
+            StepTag tag(j, (int)st);
             int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
             if (h.kind == STEP_GEMM || h.kind == STEP_GEMM_STACKED) {
                 e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->amax[0].as<uint32_t>(),
@@ -398,6 +400,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
                 launch_contract_step(bp.d_steps + st, h, ctx, ni, s);
             }
         }
+        StepTag tag(j, (int)bp.steps.size());
         launch_finalize(d_root, ctx, bp.b, c.n_net, marg + c.net0 * ((int64_t)1 << bp.b), Z + c.net0, s);
     }
     PTN_CUDA(cudaGetLastError());
@@ -742,9 +745,10 @@ ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const pt
         ctx.arena_inst[CLS_CONST] = 1;
         ctx.arena_inst[CLS_TRAJ] = ctx.arena_inst[ARENA_ADJ] = ctx.arena_inst[ARENA_LGRAD] = nt;
         ctx.arena_inst[CLS_NET] = 0;
-        auto run = [&](const std::vector<StepDesc>& steps, const StepDesc* d_steps) -> ptn_status {
+        auto run = [&](const std::vector<StepDesc>& steps, const StepDesc* d_steps, int tag_block) -> ptn_status {
             for (size_t k = 0; k < steps.size(); k++) {
                 const StepDesc& h = steps[k];
+                StepTag tag(tag_block, (int)k);
                 const int64_t ni = h.out_cls == CLS_CONST ? 1 : nt;
                 if (h.kind != STEP_DIRECT) {
                     ptn_status ee = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->amax[0].as<uint32_t>(),
@@ -757,10 +761,10 @@ ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const pt
             }
             return PTN_OK;
         };
-        if ((e = run(bp.steps, ws->ev_steps.as<StepDesc>()))) return e;
+        if ((e = run(bp.steps, ws->ev_steps.as<StepDesc>(), -2))) return e;
         launch_observable(ws->ev_root.as<RootRef>(), ctx, n, ws->ev_terms.as<ObsTerm>(), (int)terms.size(),
                           bp.root_adj_off, t0, ws->ev_F.as<double>(), s);
-        if ((e = run(bp.bwd, ws->ev_bwd.as<StepDesc>()))) return e;
+        if ((e = run(bp.bwd, ws->ev_bwd.as<StepDesc>(), -3))) return e;
         launch_leaf_grad(ctx, ws->ev_pl.as<ParamLeaf>(), (int)bp.pleaves.size(), ws->ev_dvt.as<float2>(), t0, nt, np,
                          ws->ev_partial.as<double>(), s);
     }

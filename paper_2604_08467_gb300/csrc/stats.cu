@@ -2,8 +2,11 @@
 // CUDA-event durations with the algorithmic bytes and flops of every launch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "stats.h"
@@ -14,7 +17,9 @@ struct Rec {
     int kid;
     cudaEvent_t a, b;
     double bytes, flops;
+    int block, step;
 };
+thread_local int t_block = -1, t_step = -1;
 struct State {
     std::mutex mu;
     bool timing = false;
@@ -42,7 +47,14 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+void set_step_tag(int block, int step) {
+    t_block = block;
+    t_step = step;
+}
+
 StatScope::StatScope(int kid, cudaStream_t s, double bytes, double flops) : kid_(kid), s_(s) {
+    block_ = t_block;
+    step_ = t_step;
     State& g = st();
     std::lock_guard<std::mutex> lk(g.mu);
     g.launches[kid]++;
@@ -61,7 +73,7 @@ StatScope::~StatScope() {
     State& g = st();
     std::lock_guard<std::mutex> lk(g.mu);
     cudaEventRecord((cudaEvent_t)b_, s_);
-    g.recs.push_back({kid_, (cudaEvent_t)a_, (cudaEvent_t)b_, bytes_, flops_});
+    g.recs.push_back({kid_, (cudaEvent_t)a_, (cudaEvent_t)b_, bytes_, flops_, block_, step_});
 }
 
 }  // namespace ptn
@@ -109,6 +121,36 @@ extern "C" ptn_status ptn_stats_read(ptn_kernel_stat* out, int32_t cap, int32_t*
     int n = 0;
     for (int k = 0; k < K_COUNT && n < cap; k++)
         if (acc[k].launches) out[n++] = acc[k];
+    if (n_out) *n_out = n;
+    return PTN_OK;
+}
+
+extern "C" ptn_status ptn_stats_read_steps(ptn_step_stat* out, int32_t cap, int32_t* n_out) {
+    State& g = st();
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "stats: %s", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lk(g.mu);
+    std::map<std::tuple<int, int, int>, ptn_step_stat> acc;
+    for (auto& r : g.recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        ptn_step_stat& x = acc[std::make_tuple(r.block, r.step, r.kid)];
+        if (!x.launches) {
+            x.block = r.block;
+            x.step = r.step;
+            strncpy(x.kernel, kNames[r.kid], sizeof x.kernel - 1);
+        }
+        x.launches++;
+        x.ms += ms;
+        x.alg_bytes += r.bytes;
+        x.alg_flops += r.flops;
+    }
+    int n = 0;
+    for (auto& kv : acc) {
+        if (n >= cap) break;
+        if (out) out[n] = kv.second;
+        n++;
+    }
     if (n_out) *n_out = n;
     return PTN_OK;
 }

@@ -12,6 +12,13 @@ enum KernelId {
     K_ALLOC, K_SAMPLE_PARENTS, K_EMIT, K_PACK, K_ABSMAX, K_EXPVAL, K_MISC, K_COUNT
 };
 
+// Path step the calling thread is launching (recorded with each timed launch).
+void set_step_tag(int block, int step);
+struct StepTag {
+    StepTag(int block, int step) { set_step_tag(block, step); }
+    ~StepTag() { set_step_tag(-1, -1); }
+};
+
 // Counts one launch of kernel `kid`; with timing on, brackets it with events.
 class StatScope {
   public:
@@ -25,6 +32,7 @@ class StatScope {
     void* a_ = nullptr;
     void* b_ = nullptr;
     double bytes_ = 0, flops_ = 0;
+    int block_ = -1, step_ = -1;
 };
 
 }  // namespace ptn

@@ -65,6 +65,11 @@ class ptn_sample_opts(C.Structure):
                 ("max_traj_per_chunk", C.c_int32), ("use_graphs", C.c_int32), ("reserved", C.c_int32)]
 
 
+class ptn_step_stat(C.Structure):
+    _fields_ = [("block", C.c_int32), ("step", C.c_int32), ("kernel", C.c_char * 32), ("launches", C.c_int64),
+                ("ms", C.c_double), ("alg_bytes", C.c_double), ("alg_flops", C.c_double)]
+
+
 class ptn_batch_item(C.Structure):
     _fields_ = [("plan", C.c_void_p), ("traj", C.c_void_p), ("opts", ptn_sample_opts)]
 
@@ -112,6 +117,7 @@ _SIGS = {
     "ptn_stats_enable": [C.c_int32],
     "ptn_stats_reset": [],
     "ptn_stats_read": [C.POINTER(ptn_kernel_stat), C.c_int32, C.POINTER(C.c_int32)],
+    "ptn_stats_read_steps": [C.POINTER(ptn_step_stat), C.c_int32, C.POINTER(C.c_int32)],
     "ptn_status_string": [C.c_int],
     "ptn_last_error": [],
     "ptn_version": [],
@@ -409,3 +415,13 @@ def ptn_stats_read():
     return {buf[i].name.decode(): dict(launches=buf[i].launches, timed_launches=buf[i].timed_launches,
                                        ms=buf[i].ms, alg_bytes=buf[i].alg_bytes, alg_flops=buf[i].alg_flops)
             for i in range(n.value)}
+
+
+def ptn_stats_read_steps():
+    """[(block, step, kernel, launches, ms, alg_bytes, alg_flops)] (synchronises)."""
+    n = C.c_int32(0)
+    _check(lib().ptn_stats_read_steps(None, 1 << 30, C.byref(n)))
+    buf = (ptn_step_stat * max(n.value, 1))()
+    _check(lib().ptn_stats_read_steps(buf, n.value, C.byref(n)))
+    return [(r.block, r.step, r.kernel.decode(), r.launches, r.ms, r.alg_bytes, r.alg_flops)
+            for r in buf[:n.value]]

@@ -333,6 +333,8 @@ def main():
         hc.copy_(cnt, non_blocking=True)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
+        if int(hc.sum()) != M:
+            raise RuntimeError(f"step produced {int(hc.sum())} shots, expected {M}")
         d2h = t.numel() * 4 + bits.numel() * 8 + cnt.numel() * 8
         # host->device per step: the chunk index tables the runtime uploads per block
         h2d = 8 * E + sum(4 * n for n in res.nets_per_block) + 4 * E

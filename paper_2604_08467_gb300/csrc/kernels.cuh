@@ -66,11 +66,10 @@ struct GroupTable {
     int64_t* d_tile0 = nullptr;   // n_groups + 1
     int64_t* d_scan = nullptr;    // scan_tmp_elems(n_groups + 1)
 };
-// precision: PTN_PREC_*; amax_a/amax_b: device scratch of one uint32 per packed
-// instance (used by the FP16 mode's scaling).
+// precision: PTN_PREC_*.  pack_a / pack_b: packing scratch sized for 4-byte
+// elements plus 1/64 slack (the FP16 mode keeps its per-row exponents there).
 ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
-                            uint32_t* amax_a, uint32_t* amax_b, int* err, const GroupTable& grp, int precision,
-                            cudaStream_t s);
+                            int* err, const GroupTable& grp, int precision, cudaStream_t s);
 
 // ---- expectation values and gradients (kernels_expval.cu)
 struct ObsTerm {

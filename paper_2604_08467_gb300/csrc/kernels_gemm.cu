@@ -87,7 +87,8 @@ struct PackArgs {
     int64_t h_stride[kMaxPackBits];
     int64_t k_stride[kMaxPackBits];
     void* dst;
-    const uint32_t* amax;    // FP16: largest |component| per packed instance (float bits), else null
+    int8_t* row_exp;         // FP16: per packed row, the power-of-two exponent e of its largest
+                             // |component| (the row is stored scaled by 2^-e), else null
 };
 
 struct GemmArgs {
@@ -106,22 +107,12 @@ struct GemmArgs {
     float2* out;
     int64_t out_size;
     int* err;
-    const uint32_t* amax_a;      // FP16 scales (see PackArgs), else null
-    const uint32_t* amax_b;
+    const int8_t* exp_a;         // FP16 row exponents of A and B (see PackArgs), else null
+    const int8_t* exp_b;
     int64_t m_stride[kMaxOut];
     int64_t n_stride[kMaxOut];
     int64_t h_stride[kMaxOut];
 };
-
-// Power-of-two exponent e with max magnitude in [2^(e-1), 2^e); 0 for max 0.
-__device__ __forceinline__ int scale_exp(const uint32_t* amax, int64_t pi) {
-    if (!amax) return 0;
-    const float m = __uint_as_float(amax[pi]);
-    if (!(m > 0.f)) return 0;
-    int e;
-    frexpf(m, &e);
-    return e;
-}
 
 // Round to the nearest TF32 value (ties away from zero): add half of the 13
 // dropped mantissa bits, then clear them.
@@ -189,44 +180,6 @@ __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, 
     return p;
 }
 
-__device__ __forceinline__ int64_t pack_offset(const PackArgs& a, int64_t row, int64_t h, int64_t kc) {
-    int64_t off = 0;
-    for (int i = 0; i < a.n_rb; i++)
-        if ((row >> i) & 1) off += a.r_stride[i];
-    for (int i = 0; i < a.n_hb; i++)
-        if ((h >> i) & 1) off += a.h_stride[i];
-    for (int i = 0; i < a.n_kb; i++)
-        if ((kc >> i) & 1) off += a.k_stride[i];
-    return off;
-}
-
-// Largest |component| of every packed instance (FP16 scaling): one block per
-// instance, a block reduction, one store.
-__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ PackArgs a, const ChunkCtx c,
-                                                uint32_t* __restrict__ amax) {
-    __shared__ float red[256];
-    const int64_t nrow = (int64_t)1 << a.n_rb, nh = (int64_t)1 << a.n_hb, kc_real = (int64_t)1 << a.n_kb;
-    const int64_t per = nh * nrow * kc_real;
-    for (int64_t pi = blockIdx.x; pi < a.n_pinst; pi += gridDim.x) {
-        const float2* base = pack_operand_ptr(a.op, a.pcls, pi, c);
-        float m = 0.f;
-        for (int64_t g = threadIdx.x; g < per; g += blockDim.x) {
-            const int64_t kc = g % kc_real;
-            const int64_t rest = g / kc_real;
-            const float2 v = base[pack_offset(a, rest % nrow, rest / nrow, kc)];
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-        }
-        red[threadIdx.x] = m;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) amax[pi] = __float_as_uint(red[0]);
-        __syncthreads();
-    }
-}
-
 // Packing: one warp per packed row (instance, h, row) when a half row holds
 // >= 32 complex slots, else 32 / slots rows per warp.  Every size is a power of
 // two, so the row index is decoded with shifts.  The row's base offset is
@@ -262,6 +215,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
     const int l0 = lk >= 5 ? lane : (lane & ((int)kcp - 1));
     const int64_t n_rows = a.n_pinst << (a.n_hb + a.n_rb);
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // (FP16 rows span >= 32 slots, so rpw == 1 there and the warp reduction sees one row)
     for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w * rpw < n_rows; w += warps) {
         const int64_t jr = w * rpw + sub;                // (pi, h, row), row fastest
         if (jr >= n_rows) continue;
@@ -274,7 +228,26 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
             if ((row >> i) & 1) base += a.r_stride[i];
         for (int i = 0; i < a.n_hb; i++)
             if ((h >> i) & 1) base += a.h_stride[i];
-        const float sc = ldexpf(1.f, -scale_exp(a.amax, pi));
+        float sc = 1.f;
+        if constexpr (F == FMT_FP16) {
+            // per-row scaling: largest |component| of the row -> exponent e, row * 2^-e
+            float mx = 0.f;
+            for (int64_t kc = l0; kc < kc_real; kc += lstep) {
+                int64_t off = ktab[kc & (kKTab - 1)] + ktab[kKTab + ((kc >> 10) & (kKTab - 1))];
+                for (int t = 20; t < a.n_kb; t++)
+                    if ((kc >> t) & 1) off += a.k_stride[t];
+                const float2 v = base[off];
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            int e = 0;
+            if (mx > 0.f) {
+                frexpf(mx, &e);
+                e = e < -100 ? -100 : (e > 100 ? 100 : e);
+            }
+            sc = ldexpf(1.f, -e);
+            if (lane == 0) a.row_exp[jr] = (int8_t)e;
+        }
         const float csign = a.op.conj ? -1.f : 1.f;
         T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
         for (int64_t kc = l0; kc < kcp; kc += lstep) {
@@ -555,13 +528,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
         if (lane == 0) atomicExch(g.err, 3);
     } else if (!*abort) {
         const int64_t row = (int64_t)m0 + warp * 32 + lane;
-        int64_t m = row, out_inst = inst, pa = 0;
+        int64_t m = row, out_inst = inst;
         if (g.stacked) {
             out_inst = row >> g.m_bits;
             m = row & (((int64_t)1 << g.m_bits) - 1);
-            pa = out_inst;
-        } else {
-            pa = pinst(g.a_pcls);
         }
         int64_t moff = 0;
         for (int i = 0; i < g.n_mb; i++)
@@ -570,7 +540,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
             if ((h >> i) & 1) moff += g.h_stride[i];
         float2* out = g.out + out_inst * g.out_size + moff;
         const bool row_ok = row < row_end;
-        const float unscale = (F == FMT_FP16 && row_ok) ? ldexpf(1.f, scale_exp(g.amax_a, pa) + scale_exp(g.amax_b, pb)) : 1.f;
+        // FP16: A row and B column exponents (packed row indices za * M + row, zb * N + n)
+        const int ea = (F == FMT_FP16 && row_ok) ? (int)g.exp_a[(int64_t)za * g.M + row] : 0;
+        const int8_t* eb = F == FMT_FP16 ? g.exp_b + (int64_t)zb * (g.N2 >> 1) : nullptr;
         const int n_acc = g.nkb < kAcc ? g.nkb : kAcc;
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
@@ -588,7 +560,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int col = n0 + c0 + 2 * j;
-                    if (col < g.N2) out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j] * unscale, v[2 * j + 1] * unscale);
+                    if (col < g.N2) {
+                        const float u = F == FMT_FP16 ? ldexpf(1.f, ea + (int)eb[col >> 1]) : 1.f;
+                        out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j] * u, v[2 * j + 1] * u);
+                    }
                 }
             }
         }
@@ -662,7 +637,7 @@ unsigned grid_of(int64_t n) {
 
 template <int F>
 ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
-                    uint32_t* amax_a, uint32_t* amax_b, int* err, const GroupTable& grp, cudaStream_t s) {
+                    int* err, const GroupTable& grp, cudaStream_t s) {
     constexpr int kEB = Fmt<F>::kBytes;
     constexpr int kBK = kRowBytes / kEB;
     const CUtensorMapDataType dt = F == FMT_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -737,15 +712,17 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     const int64_t tot_b = pb.n_pinst * (1ll << nh) * N * (Kh / 2);
     cudaError_t e;
     if (F == FMT_FP16) {
-        e = cudaMemsetAsync(amax_a, 0, sizeof(uint32_t) * pa.n_pinst, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(amax_b, 0, sizeof(uint32_t) * pb.n_pinst, s);
-        if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "scale reset: %s", cudaGetErrorString(e));
-        StatScope sc(K_ABSMAX, s, 8.0 * (double)(tot_a + tot_b), 0.0);
-        auto blocks_for = [](int64_t n_pinst) { return (unsigned)(n_pinst < 152 * 64 ? n_pinst : 152 * 64); };
-        k_absmax<<<blocks_for(pa.n_pinst), 256, 0, s>>>(pa, ctx, amax_a);
-        k_absmax<<<blocks_for(pb.n_pinst), 256, 0, s>>>(pb, ctx, amax_b);
-        pa.amax = ga.amax_a = amax_a;
-        pb.amax = ga.amax_b = amax_b;
+        // row exponents live after the packed rows (the pack buffers are sized for
+        // 4-byte elements plus slack, FP16 rows use half of that)
+        auto after = [&](void* base, int64_t rows) {
+            const int64_t bytes = rows * 2 * Kh * kEB;
+            return reinterpret_cast<int8_t*>(static_cast<uint8_t*>(base) + ((bytes + 255) & ~(int64_t)255));
+        };
+        pa.row_exp = after(pack_a, pa.n_pinst * (1ll << nh) * M);
+        pb.row_exp = after(pack_b, pb.n_pinst * (1ll << nh) * 2 * N);   // B rows are realified pairs
+        ga.exp_a = pa.row_exp;
+        ga.exp_b = pb.row_exp;
+        if (Kh / 2 < 32) return set_error(PTN_ERR_INVALID_ARG, "internal: FP16 rows shorter than a warp");
     }
     {
         StatScope sc(K_PACK, s, 8.0 * (double)(tot_a + tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b, 0.0);
@@ -801,12 +778,12 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
 }  // namespace
 
 ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
-                            uint32_t* amax_a, uint32_t* amax_b, int* err, const GroupTable& grp, int precision,
+                            int* err, const GroupTable& grp, int precision,
                             cudaStream_t s) {
     switch (precision) {
-        case PTN_PREC_FP32: return run_gemm<FMT_TF32>(st, ctx, n_inst, pack_a, pack_b, amax_a, amax_b, err, grp, s);
-        case PTN_PREC_BF16X3: return run_gemm<FMT_BF16>(st, ctx, n_inst, pack_a, pack_b, amax_a, amax_b, err, grp, s);
-        case PTN_PREC_FP16X3: return run_gemm<FMT_FP16>(st, ctx, n_inst, pack_a, pack_b, amax_a, amax_b, err, grp, s);
+        case PTN_PREC_FP32: return run_gemm<FMT_TF32>(st, ctx, n_inst, pack_a, pack_b, err, grp, s);
+        case PTN_PREC_BF16X3: return run_gemm<FMT_BF16>(st, ctx, n_inst, pack_a, pack_b, err, grp, s);
+        case PTN_PREC_FP16X3: return run_gemm<FMT_FP16>(st, ctx, n_inst, pack_a, pack_b, err, grp, s);
     }
     return set_error(PTN_ERR_UNSUPPORTED, "precision mode %d", precision);
 }

@@ -128,7 +128,7 @@ struct PlanWorkspace {
     DevBuf lvl_traj[2], lvl_prefix[2], lvl_count[2];
     DevBuf s_cap, s_tmp_off, s_rank0, s_excl, s_first, s_ndist, s_out_off, s_tmp_x, s_tmp_c, s_scan;
     DevBuf zero_prefix;
-    DevBuf pack[2], err, grp, grp_cnt, grp_tile0, grp_scan, amax[2];
+    DevBuf pack[2], err, grp, grp_cnt, grp_tile0, grp_scan;
     // expectation / gradient plans
     DevBuf arena_x[2];                    // ADJ, LGRAD arenas
     DevBuf ev_steps, ev_bwd, ev_root, ev_pl, ev_dvt, ev_terms, ev_F, ev_partial, ev_iota;
@@ -138,7 +138,7 @@ struct PlanWorkspace {
                          &lvl_traj[0], &lvl_traj[1], &lvl_prefix[0], &lvl_prefix[1], &lvl_count[0], &lvl_count[1],
                          &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
                          &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err, &grp, &grp_cnt,
-                         &grp_tile0, &grp_scan, &amax[0], &amax[1], &arena_x[0], &arena_x[1], &ev_steps,
+                         &grp_tile0, &grp_scan, &arena_x[0], &arena_x[1], &ev_steps,
                          &ev_bwd, &ev_root, &ev_pl, &ev_dvt, &ev_terms, &ev_F, &ev_partial, &ev_iota};
         for (DevBuf* b : all) b->release();
         h_grp.release();
@@ -334,9 +334,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     const int64_t n_grp_all = n_ct + (int64_t)chunks.size();
     if ((e = ws->h_grp.grow(sizeof(int32_t) * n_grp_all)) || (e = ws->grp.grow(sizeof(int32_t) * n_grp_all)) ||
         (e = ws->grp_cnt.grow(sizeof(int64_t) * (max_t + 1))) || (e = ws->grp_tile0.grow(sizeof(int64_t) * (max_t + 1))) ||
-        (e = ws->grp_scan.grow(sizeof(int64_t) * scan_tmp_elems(max_t + 1))) ||
-        (e = ws->amax[0].grow(sizeof(uint32_t) * (max_t + max_n + 1))) ||
-        (e = ws->amax[1].grow(sizeof(uint32_t) * (max_t + max_n + 1))))
+        (e = ws->grp_scan.grow(sizeof(int64_t) * scan_tmp_elems(max_t + 1))))
         return e;
     int32_t* hg = ws->h_grp.as<int32_t>();
     std::vector<int64_t> grp_off(chunks.size());
@@ -359,7 +357,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     for (int r = 0; r < 2; r++) {
         const double need = 4.0 * ((double)bp.pack_peak[r][CLS_CONST] + (double)bp.pack_peak[r][CLS_TRAJ] * max_t +
                                    (double)bp.pack_peak[r][CLS_NET] * max_n);
-        if (need > 0 && (e = ws->pack[r].grow((size_t)need + 256))) return e;
+        if (need > 0 && (e = ws->pack[r].grow((size_t)(need + need / 64) + 4096))) return e;
     }
     if ((e = ws->err.grow(sizeof(int)))) return e;
     if ((e = ws->h_small.grow(64))) return e;
@@ -393,8 +391,8 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
             StepTag tag(j, (int)st);
             int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
             if (h.kind == STEP_GEMM || h.kind == STEP_GEMM_STACKED) {
-                e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->amax[0].as<uint32_t>(),
-                                     ws->amax[1].as<uint32_t>(), ws->err.as<int>(), gt, precision, s);
+                e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(), gt,
+                                     precision, s);
                 if (e) return e;
             } else {
                 launch_contract_step(bp.d_steps + st, h, ctx, ni, s);
@@ -718,12 +716,11 @@ ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const pt
         (e = ws->arena[CLS_TRAJ].grow((size_t)(8.0 * bp.arena_peak[CLS_TRAJ] * Ec + 16))) ||
         (e = ws->arena_x[0].grow((size_t)(8.0 * bp.arena_peak[ARENA_ADJ] * Ec + 16))) ||
         (e = ws->arena_x[1].grow((size_t)(8.0 * bp.arena_peak[ARENA_LGRAD] * Ec + 16))) || (e = ws->err.grow(sizeof(int))) ||
-        (e = ws->amax[0].grow(sizeof(uint32_t) * (Ec + 1))) || (e = ws->amax[1].grow(sizeof(uint32_t) * (Ec + 1))) ||
         (e = ws->h_small.grow(64)))
         return e;
     for (int r = 0; r < 2; r++) {
         const double need = 4.0 * ((double)bp.pack_peak[r][CLS_CONST] + (double)bp.pack_peak[r][CLS_TRAJ] * Ec);
-        if (need > 0 && (e = ws->pack[r].grow((size_t)need + 256))) return e;
+        if (need > 0 && (e = ws->pack[r].grow((size_t)(need + need / 64) + 4096))) return e;
     }
     PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
     GroupTable no_groups;
@@ -751,9 +748,8 @@ ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const pt
                 StepTag tag(tag_block, (int)k);
                 const int64_t ni = h.out_cls == CLS_CONST ? 1 : nt;
                 if (h.kind != STEP_DIRECT) {
-                    ptn_status ee = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->amax[0].as<uint32_t>(),
-                                                     ws->amax[1].as<uint32_t>(), ws->err.as<int>(), no_groups,
-                                                     PTN_PREC_FP32, s);
+                    ptn_status ee = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(),
+                                                     no_groups, PTN_PREC_FP32, s);
                     if (ee) return ee;
                 } else {
                     launch_contract_step(d_steps + k, h, ctx, ni, s);

@@ -49,6 +49,7 @@ def test_marginal_error_by_precision(slice16, prec):
         ptn.ptn_contract_batch(plan, tr, j, nt, npf, marg, Z, precision=prec)
         got = marg.cpu().numpy().astype(np.float64)
         want = np.array([sv.block_marginals(probs[t], 16, start, b)[int(s)] for t, s in zip(traj, prefix)])
+        assert np.all(np.isfinite(got))
         err = np.linalg.norm(got - want, axis=1) / np.maximum(np.linalg.norm(want, axis=1), 1e-12)
         worst = max(worst, float(err.max()))
     print(f"\n[precision] {NAME[prec]}: max norm-wise marginal error {worst:.3e}")
@@ -75,3 +76,39 @@ def test_sampled_tvd_by_precision(slice16, prec):
         tvd = 0.5 * np.abs(pe - pq).sum()
         print(f"\n[precision] {NAME[prec]}: TVD on qubits {qs} = {tvd:.4f} (bound {3 / np.sqrt(N):.4f})")
         assert tvd < 3 / np.sqrt(N)
+
+
+@pytest.mark.parametrize("prec", [ptn.PTN_PREC_FP32, ptn.PTN_PREC_FP16X3, ptn.PTN_PREC_BF16X3])
+def test_c2_marginal_error_by_precision(prec):
+    """The 30-qubit brickwork workload (4096 trajectories, launched as in the
+    benchmark) in each precision mode: sampled networks of every block against
+    the exact-MPS oracle, within the mode's bound."""
+    from oracle import mps
+    cfg = W.config_c2()
+    circ = cfg["circuit"]
+    plan = ptn.ptn_plan_path(circ, cfg["block_sizes"], hypersamples=16, est_traj=cfg["n_traj"],
+                             est_shots=cfg["total_shots"])
+    tr = ptn.ptn_presample_trajectories(plan, cfg["seed"], cfg["n_traj"])
+    kraus = tr.to_torch()[0].cpu().numpy()
+    pick = [0, 2049, 4095]
+    states = {t: mps.trajectory_mps(circ, kraus[t]) for t in pick}
+    prng = np.random.default_rng(6)
+    worst = 0.0
+    for j in range(3):
+        start = 10 * j
+        traj = np.arange(4096) if j == 0 else np.repeat(pick, 3)
+        prefix = np.zeros(len(traj), int) if j == 0 else prng.integers(0, 1 << start, size=len(traj))
+        nt = torch.tensor(traj, dtype=torch.int32, device="cuda")
+        npf = torch.tensor(prefix, dtype=torch.int64, device="cuda")
+        marg = torch.empty((len(traj), 1024), dtype=torch.float32, device="cuda")
+        Z = torch.empty(len(traj), dtype=torch.float64, device="cuda")
+        ptn.ptn_contract_batch(plan, tr, j, nt, npf, marg, Z, precision=prec)
+        got = marg.cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(got))
+        rows = range(len(traj)) if j else pick
+        for n in rows:
+            t, s = int(traj[n]), int(prefix[n])
+            want = states[t].block_marginal(start, 10, s)
+            worst = max(worst, float(np.linalg.norm(got[n] - want) / max(np.linalg.norm(want), 1e-12)))
+    print(f"\n[precision c2] {NAME[prec]}: max norm-wise marginal error {worst:.3e}")
+    assert worst < BOUND[prec]

@@ -10,6 +10,9 @@
 // first consumer.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "kernels.cuh"
 #include "stats.h"
 
@@ -165,6 +168,169 @@ __global__ void __launch_bounds__(kDirThreads, 3) k_contract_direct(const StepDe
     }
 }
 
+// Register-tiled variant: a thread computes a 2^RA x 2^RB micro-tile of
+// outputs spanned by RA output bits along which only A varies and RB bits
+// along which only B varies, so every term loads 2^RA + 2^RB operand values
+// for 2^(RA+RB) complex multiply-adds.  The remaining output bits (the tile
+// origin) run over the lanes, lowest first.
+struct MicroBits {
+    int32_t ta[2], tb[2];      // output bits of the micro-tile (A-only, B-only)
+    int32_t ins[4];            // the same bits in ascending order (zero insertion)
+    int32_t n_ins;
+};
+template <int RA, int RB>
+__global__ void __launch_bounds__(kDirThreads, 2) k_contract_micro(const StepDesc* __restrict__ gstep, ChunkCtx c,
+                                                                   int64_t n_inst, const MicroBits mb) {
+    __shared__ __align__(16) StepDesc s;
+    {
+        const int4* src = reinterpret_cast<const int4*>(gstep);
+        int4* dst = reinterpret_cast<int4*>(&s);
+        for (int i = threadIdx.x; i < (int)(sizeof(StepDesc) / sizeof(int4)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    __shared__ int32_t otab[2][256];
+    __shared__ int32_t ktab[2][256];
+    const int lowb = s.n_out < 8 ? s.n_out : 8;
+    const int nk = s.n_sum;
+    const int klo = nk < 8 ? nk : 8;
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        int32_t a = 0, b = 0, ka = 0, kb = 0;
+        for (int p = 0; p < lowb; p++)
+            if ((t >> p) & 1) {
+                a += (int32_t)s.out_stride[0][p];
+                b += (int32_t)s.out_stride[1][p];
+            }
+        for (int p = 0; p < klo; p++)
+            if ((t >> p) & 1) {
+                ka += (int32_t)s.sum_stride[0][p];
+                kb += (int32_t)s.sum_stride[1][p];
+            }
+        otab[0][t] = a;
+        otab[1][t] = b;
+        ktab[0][t] = ka;
+        ktab[1][t] = kb;
+    }
+    __syncthreads();
+    constexpr int NA = 1 << RA, NB = 1 << RB;
+    int32_t da[NA], db[NB];
+    int64_t doa[NA], dob[NB];
+#pragma unroll
+    for (int i = 0; i < NA; i++) {
+        da[i] = 0;
+        doa[i] = 0;
+#pragma unroll
+        for (int j = 0; j < RA; j++)
+            if ((i >> j) & 1) {
+                da[i] += (int32_t)s.out_stride[0][mb.ta[j]];
+                doa[i] += (int64_t)1 << mb.ta[j];
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        db[i] = 0;
+        dob[i] = 0;
+#pragma unroll
+        for (int j = 0; j < RB; j++)
+            if ((i >> j) & 1) {
+                db[i] += (int32_t)s.out_stride[1][mb.tb[j]];
+                dob[i] += (int64_t)1 << mb.tb[j];
+            }
+    }
+    const int nq = s.n_out - RA - RB;
+    const int64_t total = n_inst << nq;
+    const int64_t qmask = ((int64_t)1 << nq) - 1;
+    const int lowmask = (1 << lowb) - 1;
+    const int n_lo = 1 << klo;
+    const int64_t n_hi = (int64_t)1 << (nk - klo);
+    const float sa = s.op[0].conj ? -1.f : 1.f, sb = s.op[1].conj ? -1.f : 1.f;
+    float2* outbase = c.arena[s.out_arena] + s.out_off * c.arena_inst[s.out_arena];
+    int64_t cur_inst = -1, cur_hi = -1;
+    int32_t hia = 0, hib = 0;
+    const float2 *A = nullptr, *B = nullptr;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t inst = g >> nq;
+        int64_t o = g & qmask;
+        for (int z = 0; z < mb.n_ins; z++) {
+            const int cbit = mb.ins[z];
+            o = ((o >> cbit) << (cbit + 1)) | (o & (((int64_t)1 << cbit) - 1));
+        }
+        if (inst != cur_inst) {
+            A = operand_ptr(s.op[0], s.out_cls, inst, c);
+            B = operand_ptr(s.op[1], s.out_cls, inst, c);
+            cur_inst = inst;
+        }
+        const int64_t hi = o >> lowb;
+        if (hi != cur_hi) {
+            hia = hib = 0;
+            for (int p = lowb; p < s.n_out; p++)
+                if ((o >> p) & 1) {
+                    hia += (int32_t)s.out_stride[0][p];
+                    hib += (int32_t)s.out_stride[1][p];
+                }
+            cur_hi = hi;
+        }
+        const float2* pa = A + (hia + otab[0][o & lowmask]);
+        const float2* pb = B + (hib + otab[1][o & lowmask]);
+        float2 acc[NA][NB];
+#pragma unroll
+        for (int i = 0; i < NA; i++)
+#pragma unroll
+            for (int j = 0; j < NB; j++) acc[i][j] = make_float2(0.f, 0.f);
+        int32_t ha = 0, hb = 0;
+        for (int64_t th = 0; th < n_hi; th++) {
+            if (th) {
+                const int bit = __ffsll(th) - 1;
+                const int64_t gray = th ^ (th >> 1);
+                const int32_t dka = (int32_t)s.sum_stride[0][klo + bit], dkb = (int32_t)s.sum_stride[1][klo + bit];
+                if ((gray >> bit) & 1) {
+                    ha += dka;
+                    hb += dkb;
+                } else {
+                    ha -= dka;
+                    hb -= dkb;
+                }
+            }
+            for (int tl = 0; tl < n_lo; tl++) {
+                const int32_t ka = ha + ktab[0][tl], kb = hb + ktab[1][tl];
+                float2 av[NA], bv[NB];
+#pragma unroll
+                for (int i = 0; i < NA; i++) {
+                    av[i] = pa[da[i] + ka];
+                    av[i].y *= sa;
+                }
+#pragma unroll
+                for (int j = 0; j < NB; j++) {
+                    bv[j] = pb[db[j] + kb];
+                    bv[j].y *= sb;
+                }
+#pragma unroll
+                for (int i = 0; i < NA; i++)
+#pragma unroll
+                    for (int j = 0; j < NB; j++) {
+                        acc[i][j].x = fmaf(av[i].x, bv[j].x, acc[i][j].x);
+                        acc[i][j].x = fmaf(-av[i].y, bv[j].y, acc[i][j].x);
+                        acc[i][j].y = fmaf(av[i].x, bv[j].y, acc[i][j].y);
+                        acc[i][j].y = fmaf(av[i].y, bv[j].x, acc[i][j].y);
+                    }
+            }
+        }
+        float2* out = outbase + inst * s.out_size + o;
+#pragma unroll
+        for (int i = 0; i < NA; i++)
+#pragma unroll
+            for (int j = 0; j < NB; j++) out[doa[i] + dob[j]] = acc[i][j];
+    }
+}
+
+template <int RA, int RB>
+static void launch_micro(const StepDesc* d_step, const ChunkCtx& ctx, int64_t n_inst, const MicroBits& mb,
+                         int64_t total_q, cudaStream_t s) {
+    int64_t blocks = (total_q + kDirThreads - 1) / kDirThreads;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_contract_micro<RA, RB><<<(unsigned)blocks, kDirThreads, 0, s>>>(d_step, ctx, n_inst, mb);
+}
+
 // marg[n][x] = Re(root_n[x]) (the double-layer diagonal), Z[n] = sum_x in FP64.
 __global__ void __launch_bounds__(256) k_finalize(const RootRef* __restrict__ groot, ChunkCtx c, int b,
                                                   float* __restrict__ marg, double* __restrict__ Z) {
@@ -220,6 +386,32 @@ void launch_contract_step(const StepDesc* d_step, const StepDesc& h, const Chunk
     }
     const double flops = 8.0 * (double)total * (double)(1ll << h.n_sum);
     StatScope sc(K_CONTRACT_DIRECT, s, bytes, flops);
+    // micro-tile bits: the highest output bits along which only one operand varies
+    MicroBits mb;
+    memset(&mb, 0, sizeof mb);
+    int ra = 0, rb = 0;
+    for (int p = h.n_out - 1; p >= 0; p--) {
+        const bool va = h.out_stride[0][p] != 0, vb = h.out_stride[1][p] != 0;
+        if (va && !vb && ra < 2) mb.ta[ra++] = p;
+        else if (vb && !va && rb < 2) mb.tb[rb++] = p;
+    }
+    if (off32 && ra + rb > 0) {
+        for (int j = 0; j < ra; j++) mb.ins[mb.n_ins++] = mb.ta[j];
+        for (int j = 0; j < rb; j++) mb.ins[mb.n_ins++] = mb.tb[j];
+        std::sort(mb.ins, mb.ins + mb.n_ins);
+        const int64_t tq = n_inst << (h.n_out - ra - rb);
+        switch (ra * 3 + rb) {
+            case 1: launch_micro<0, 1>(d_step, ctx, n_inst, mb, tq, s); break;
+            case 2: launch_micro<0, 2>(d_step, ctx, n_inst, mb, tq, s); break;
+            case 3: launch_micro<1, 0>(d_step, ctx, n_inst, mb, tq, s); break;
+            case 4: launch_micro<1, 1>(d_step, ctx, n_inst, mb, tq, s); break;
+            case 5: launch_micro<1, 2>(d_step, ctx, n_inst, mb, tq, s); break;
+            case 6: launch_micro<2, 0>(d_step, ctx, n_inst, mb, tq, s); break;
+            case 7: launch_micro<2, 1>(d_step, ctx, n_inst, mb, tq, s); break;
+            default: launch_micro<2, 2>(d_step, ctx, n_inst, mb, tq, s); break;
+        }
+        return;
+    }
     if (off32)
         k_contract_direct<int32_t><<<(unsigned)blocks, kDirThreads, 0, s>>>(d_step, ctx, n_inst);
     else

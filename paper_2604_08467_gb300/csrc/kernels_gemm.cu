@@ -45,7 +45,7 @@ constexpr int kStages = 3;        // pipeline depth (4 tiles of 16 KB per stage)
 constexpr int kTileA = kBM * kRowBytes;
 constexpr int kTileB = kBN * kRowBytes;
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;
-constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 1024;   // align slack + stages + barriers/offsets
+constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 3072;   // align slack + stages + barriers/offsets
 constexpr int kMaxPackBits = 40;
 // k-blocks are spread round-robin over kAcc TMEM accumulators that the
 // epilogue adds in FP32: the tensor core's FP32 accumulation truncates, so
@@ -96,7 +96,7 @@ struct GemmArgs {
     int32_t n_h;
     int32_t a_pcls, b_pcls, out_cls;
     int32_t n_mb, n_nb, n_hb, pad;
-    int64_t tiles_m, tiles_n, n_inst;
+    int64_t tiles_m, tiles_n, n_inst, n_tiles;
     const int32_t* net_tl;
     // stacked mode: the rows of all networks of one trajectory form one GEMM
     // (rows = network-major (net, m)); tiles never cross trajectories
@@ -288,6 +288,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -315,6 +318,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
             if (*abort) return false;
             if (global_ns() - t0 > 2000000000ull) return false;
         }
+    }
+}
+// Bounded wait that ignores the abort flag (used to drain own async work).
+__device__ __forceinline__ bool mbar_wait_plain(uint64_t* bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && global_ns() - t0 > 2000000000ull) return false;
     }
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
@@ -382,70 +393,86 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// One CTA = one 128 x kBN tile of one (instance, h) GEMM.  Warp 0 lane 0 issues
-// TMA loads, warp 1 lane 0 issues tcgen05.mma; all four warps drain TMEM.
+// Persistent warp-specialised GEMM: each CTA (one per SM) walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 lane 0 streams the K-blocks
+// of all its tiles through the kStages shared-memory ring by TMA; warp 1
+// lane 0 issues tcgen05.mma into the TMEM accumulators; warps 2-5 (one per
+// TMEM lane quadrant) drain a finished tile while the producer already loads
+// the next one.  The MMA warp starts a tile only after the epilogue has
+// released the accumulators (acc_empty), and the epilogue starts after the
+// tile's last MMA completes (acc_full).  Every wait is bounded.
+constexpr int kGemmThreads = 192;
+struct TileInfo {
+    int64_t inst, h, row_end;
+    int m0, n0, za, zb;
+};
+__device__ __forceinline__ TileInfo decode_tile(const GemmArgs& g, int64_t tile) {
+    TileInfo t;
+    if (!g.stacked) {
+        const int64_t tiles = g.tiles_m * g.tiles_n;
+        const int64_t zt = tile / tiles;
+        const int64_t r = tile - zt * tiles;
+        const int64_t tm = r % g.tiles_m, tn = r / g.tiles_m;
+        t.inst = zt / g.n_h;
+        t.h = zt - t.inst * g.n_h;
+        t.m0 = (int)(tm * kBM);
+        t.n0 = (int)(tn * kBN);
+        t.row_end = g.M;
+        const int64_t pa = g.a_pcls == g.out_cls ? t.inst : (g.a_pcls == CLS_TRAJ ? (int64_t)g.net_tl[t.inst] : 0);
+        const int64_t pb = g.b_pcls == g.out_cls ? t.inst : (g.b_pcls == CLS_TRAJ ? (int64_t)g.net_tl[t.inst] : 0);
+        t.za = (int)(pa * g.n_h + t.h);
+        t.zb = (int)(pb * g.n_h + t.h);
+    } else {
+        // group (trajectory) of this tile: largest grp with grp_tile0[grp] <= tile
+        int64_t lo = 0, hi = g.n_groups - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (g.grp_tile0[mid] <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t r = tile - g.grp_tile0[lo];
+        const int64_t r0 = (int64_t)g.grp_net0[lo] << g.m_bits, r1 = (int64_t)g.grp_net0[lo + 1] << g.m_bits;
+        const int64_t tmg = (r1 - r0 + kBM - 1) / kBM;
+        t.m0 = (int)(r0 + (r % tmg) * kBM);
+        t.n0 = (int)((r / tmg) * kBN);
+        t.inst = lo;          // the trajectory (local index) supplies the B operand
+        t.h = 0;
+        t.row_end = r1;
+        t.za = 0;
+        t.zb = g.b_pcls == CLS_TRAJ ? (int)lo : 0;
+    }
+    return t;
+}
+
 template <int F>
-__global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                 const __grid_constant__ CUtensorMap tmB,
-                                                 const __grid_constant__ GemmArgs g) {
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB,
+                                                          const __grid_constant__ GemmArgs g) {
     constexpr int kBK = kRowBytes / Fmt<F>::kBytes;   // elements per swizzle row
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* stage0 = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
     uint64_t* empty = full + kStages;
-    uint64_t* accb = empty + kStages;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+    uint64_t* acc_full = empty + kStages;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* drain = acc_empty + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-    int64_t* noff = reinterpret_cast<int64_t*>(tslot + 4);   // kBN / 2 column offsets
+    int64_t* noff_all = reinterpret_cast<int64_t*>(tslot + 4);   // 4 epilogue warps x kBN / 2 column offsets
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t inst, h, row_end;
-    int m0, n0;
-    if (!g.stacked) {
-        const int64_t tiles = g.tiles_m * g.tiles_n;
-        const int64_t zt = blockIdx.x / tiles;
-        const int64_t t = blockIdx.x - zt * tiles;
-        const int64_t tm = t % g.tiles_m, tn = t / g.tiles_m;
-        inst = zt / g.n_h;
-        h = zt - inst * g.n_h;
-        m0 = (int)(tm * kBM);
-        n0 = (int)(tn * kBN);
-        row_end = g.M;
-    } else {
-        // group (trajectory) of this tile: largest grp with grp_tile0[grp] <= blockIdx.x
-        int64_t lo = 0, hi = g.n_groups - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (g.grp_tile0[mid] <= (int64_t)blockIdx.x) lo = mid;
-            else hi = mid - 1;
-        }
-        const int64_t t = (int64_t)blockIdx.x - g.grp_tile0[lo];
-        const int64_t r0 = (int64_t)g.grp_net0[lo] << g.m_bits, r1 = (int64_t)g.grp_net0[lo + 1] << g.m_bits;
-        const int64_t tmg = (r1 - r0 + kBM - 1) / kBM;
-        m0 = (int)(r0 + (t % tmg) * kBM);
-        n0 = (int)((t / tmg) * kBN);
-        inst = lo;            // the trajectory (local index) supplies the B operand
-        h = 0;
-        row_end = r1;
-    }
-
     if (threadIdx.x == 32) {
         for (int s = 0; s < kStages; s++) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 4);   // one arrival per epilogue warp
+        mbar_init(drain, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (threadIdx.x < kBN / 2) {   // output offsets of this tile's complex columns
-        const int64_t n = (int64_t)(n0 / 2) + threadIdx.x;
-        int64_t off = 0;
-        for (int i = 0; i < g.n_nb; i++)
-            if ((n >> i) & 1) off += g.n_stride[i];
-        noff[threadIdx.x] = off;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -457,115 +484,143 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
-    auto pinst = [&](int pcls) -> int64_t {
-        if (pcls == g.out_cls) return inst;
-        if (pcls == CLS_TRAJ) return (int64_t)g.net_tl[inst];
-        return 0;
-    };
-    int za, zb;
-    int64_t pb;
-    if (!g.stacked) {
-        za = (int)(pinst(g.a_pcls) * g.n_h + h);
-        pb = pinst(g.b_pcls);
-        zb = (int)(pb * g.n_h + h);
-    } else {
-        za = 0;
-        pb = g.b_pcls == CLS_TRAJ ? inst : 0;
-        zb = (int)pb;
-    }
+    const int64_t n_tiles = g.n_tiles;
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int kb = 0; kb < g.nkb; kb++) {
-                const int s = kb % kStages;
-                if (kb >= kStages && !mbar_wait(&empty[s], (uint32_t)((kb / kStages) - 1) & 1u, abort)) {
-                    atomicExch(g.err, 1);
-                    *abort = 1;
-                    break;
+            int64_t it = 0;
+            for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
+                const TileInfo t = decode_tile(g, tile);
+                for (int kb = 0; kb < g.nkb; kb++, it++) {
+                    const int s = (int)(it % kStages);
+                    if (it >= kStages && !mbar_wait(&empty[s], (uint32_t)((it / kStages) - 1) & 1u, abort)) {
+                        atomicExch(g.err, 1);
+                        *abort = 1;
+                        break;
+                    }
+                    uint8_t* st = stage0 + s * kStageBytes;
+                    mbar_expect_tx(&full[s], (uint32_t)kStageBytes);
+                    tma_load_3d(st, &tmA, kb * kBK, t.m0, t.za, &full[s]);                          // A hi
+                    tma_load_3d(st + kTileA, &tmA, g.Kh + kb * kBK, t.m0, t.za, &full[s]);          // A lo
+                    tma_load_3d(st + 2 * kTileA, &tmB, kb * kBK, t.n0, t.zb, &full[s]);             // B hi
+                    tma_load_3d(st + 2 * kTileA + kTileB, &tmB, g.Kh + kb * kBK, t.n0, t.zb, &full[s]);   // B lo
                 }
-                uint8_t* st = stage0 + s * kStageBytes;
-                mbar_expect_tx(&full[s], (uint32_t)kStageBytes);
-                tma_load_3d(st, &tmA, kb * kBK, m0, za, &full[s]);                       // A hi
-                tma_load_3d(st + kTileA, &tmA, g.Kh + kb * kBK, m0, za, &full[s]);       // A lo
-                tma_load_3d(st + 2 * kTileA, &tmB, kb * kBK, n0, zb, &full[s]);          // B hi
-                tma_load_3d(st + 2 * kTileA + kTileB, &tmB, g.Kh + kb * kBK, n0, zb, &full[s]);   // B lo
+            }
+            if (*abort) {
+                // let this CTA's own copies land before it exits: the last load of
+                // every stage is that stage's newest phase
+                const int64_t first = it > kStages ? it - kStages : 0;
+                for (int64_t j = first; j < it; j++) mbar_wait_plain(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            for (int kb = 0; kb < g.nkb; kb++) {
-                const int s = kb % kStages;
-                if (!mbar_wait(&full[s], (uint32_t)(kb / kStages) & 1u, abort)) {
-                    atomicExch(g.err, 2);
+            int64_t it = 0, lt = 0;
+            for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x, lt++) {
+                if (lt > 0 && !mbar_wait(acc_empty, (uint32_t)((lt - 1) & 1), abort)) {
+                    atomicExch(g.err, 4);
                     *abort = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(stage0 + s * kStageBytes);
-                const uint32_t sal = sa + kTileA, sb = sa + 2 * kTileA, sbl = sb + kTileB;
-                const uint32_t acc = tmem + (uint32_t)((kb % kAcc) * kBN);
-                const bool fresh = kb < kAcc;
+                bool ok = true;
+                for (int kb = 0; kb < g.nkb; kb++, it++) {
+                    const int s = (int)(it % kStages);
+                    if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, abort)) {
+                        atomicExch(g.err, 2);
+                        *abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(stage0 + s * kStageBytes);
+                    const uint32_t sal = sa + kTileA, sb = sa + 2 * kTileA, sbl = sb + kTileB;
+                    const uint32_t acc = tmem + (uint32_t)((kb % kAcc) * kBN);
+                    const bool fresh = kb < kAcc;
 #pragma unroll
-                for (int kk = 0; kk < kRowBytes / 32; kk++) {   // 32 bytes of K per MMA
-                    const uint32_t o = kk * 32;
-                    umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sb + o), (fresh && kk == 0) ? 0u : 1u);
-                    umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
-                    umma<F>(acc, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
+                    for (int kk = 0; kk < kRowBytes / 32; kk++) {   // 32 bytes of K per MMA
+                        const uint32_t o = kk * 32;
+                        umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sb + o), (fresh && kk == 0) ? 0u : 1u);
+                        umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
+                        umma<F>(acc, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
+                    }
+                    umma_commit(&empty[s]);   // stage free once these MMAs have read it
                 }
-                umma_commit(&empty[s]);   // stage free once these MMAs have read it
+                if (!ok) break;
+                umma_commit(acc_full);        // accumulators complete for this tile
             }
-            umma_commit(accb);
+            if (*abort) {   // MMAs still in flight finish before TMEM is freed
+                umma_commit(drain);
+                mbar_wait_plain(drain, 0u);
+            }
         }
         __syncwarp();
-    }
-    // epilogue: all four warps
-    const bool ok = mbar_wait(accb, 0u, abort);
-    __syncwarp();
-    tc_fence_after();
-    if (!ok) {
-        if (lane == 0) atomicExch(g.err, 3);
-    } else if (!*abort) {
-        const int64_t row = (int64_t)m0 + warp * 32 + lane;
-        int64_t m = row, out_inst = inst;
-        if (g.stacked) {
-            out_inst = row >> g.m_bits;
-            m = row & (((int64_t)1 << g.m_bits) - 1);
-        }
-        int64_t moff = 0;
-        for (int i = 0; i < g.n_mb; i++)
-            if ((m >> i) & 1) moff += g.m_stride[i];
-        for (int i = 0; i < g.n_hb; i++)
-            if ((h >> i) & 1) moff += g.h_stride[i];
-        float2* out = g.out + out_inst * g.out_size + moff;
-        const bool row_ok = row < row_end;
-        // FP16: A row and B column exponents (packed row indices za * M + row, zb * N + n)
-        const int ea = (F == FMT_FP16 && row_ok) ? (int)g.exp_a[(int64_t)za * g.M + row] : 0;
-        const int8_t* eb = F == FMT_FP16 ? g.exp_b + (int64_t)zb * (g.N2 >> 1) : nullptr;
+    } else {
+        // epilogue warps 2..5: TMEM lane quadrant q = warp % 4 holds tile rows 32q..32q+31
+        const int q = warp & 3;
+        int64_t* noff = noff_all + (warp - 2) * (kBN / 2);
         const int n_acc = g.nkb < kAcc ? g.nkb : kAcc;
-#pragma unroll 1
-        for (int c0 = 0; c0 < kBN; c0 += 32) {
-            float v[32];
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-#pragma unroll
-            for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
-            for (int a = 1; a < n_acc; a++) {
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * kBN + c0), r);
-#pragma unroll
-                for (int j = 0; j < 32; j++) v[j] += __uint_as_float(r[j]);
+        int64_t lt = 0;
+        for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x, lt++) {
+            const TileInfo t = decode_tile(g, tile);
+            for (int c = lane; c < kBN / 2; c += 32) {   // output offsets of this tile's complex columns
+                const int64_t n = (int64_t)(t.n0 / 2) + c;
+                int64_t off = 0;
+                for (int i = 0; i < g.n_nb; i++)
+                    if ((n >> i) & 1) off += g.n_stride[i];
+                noff[c] = off;
             }
-            if (row_ok) {
+            __syncwarp();
+            if (!mbar_wait(acc_full, (uint32_t)(lt & 1), abort)) {
+                if (lane == 0) atomicExch(g.err, 3);
+                *abort = 1;
+                break;
+            }
+            __syncwarp();
+            tc_fence_after();
+            const int64_t row = (int64_t)t.m0 + q * 32 + lane;
+            int64_t m = row, out_inst = t.inst;
+            if (g.stacked) {
+                out_inst = row >> g.m_bits;
+                m = row & (((int64_t)1 << g.m_bits) - 1);
+            }
+            int64_t moff = 0;
+            for (int i = 0; i < g.n_mb; i++)
+                if ((m >> i) & 1) moff += g.m_stride[i];
+            for (int i = 0; i < g.n_hb; i++)
+                if ((t.h >> i) & 1) moff += g.h_stride[i];
+            const bool row_ok = row < t.row_end;
+            float2* out = g.out + (row_ok ? out_inst : 0) * g.out_size + moff;
+            // FP16: A row and B column exponents (packed row indices za * M + row, zb * N + n)
+            const int ea = (F == FMT_FP16 && row_ok) ? (int)g.exp_a[(int64_t)t.za * g.M + row] : 0;
+            const int8_t* eb = F == FMT_FP16 ? g.exp_b + (int64_t)t.zb * (g.N2 >> 1) : nullptr;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kBN; c0 += 32) {
+                float v[32];
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const int col = n0 + c0 + 2 * j;
-                    if (col < g.N2) {
-                        const float u = F == FMT_FP16 ? ldexpf(1.f, ea + (int)eb[col >> 1]) : 1.f;
-                        out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j] * u, v[2 * j + 1] * u);
+                for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
+                for (int a = 1; a < n_acc; a++) {
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * kBN + c0), r);
+#pragma unroll
+                    for (int j = 0; j < 32; j++) v[j] += __uint_as_float(r[j]);
+                }
+                if (row_ok) {
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int col = t.n0 + c0 + 2 * j;
+                        if (col < g.N2) {
+                            const float u = F == FMT_FP16 ? ldexpf(1.f, ea + (int)eb[col >> 1]) : 1.f;
+                            out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j] * u, v[2 * j + 1] * u);
+                        }
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);   // accumulators read: the next tile may start
         }
     }
     tc_fence_before();
@@ -769,7 +824,15 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     const double bytes = 8.0 * ((double)n_inst * (1ll << nh) * M * N) +
                          (double)kEB * 2 * Kh * ((double)pa.n_pinst * M + (double)pb.n_pinst * 2 * N) * (1ll << nh);
     StatScope sc(K_CONTRACT_GEMM, s, bytes, flops);
-    k_gemm<F><<<(unsigned)blocks, 128, kGemmSmem, s>>>(mA, mB, ga);
+    ga.n_tiles = blocks;
+    static const int n_sm = [] {
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 148;
+    }();
+    const int64_t grid = blocks < n_sm ? blocks : n_sm;
+    k_gemm<F><<<(unsigned)grid, kGemmThreads, kGemmSmem, s>>>(mA, mB, ga);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "gemm launch: %s", cudaGetErrorString(e));
     return PTN_OK;

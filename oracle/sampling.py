@@ -8,7 +8,7 @@ one contraction per trajectory, and for j > 1 each *distinct* prefix
 drawn from its conditional marginal.  Shots are carried as (prefix, count)
 pairs, so no contraction is repeated for a repeated prefix.
 
-Conventions (readings of points the paper leaves open, listed in the design doc):
+Conventions (readings of points the paper leaves open):
 
 * a marginal row p[0 .. 2^b) (unnormalised, FP32 or FP64, negatives clamped to
   zero) is quantised to integers P_x = rint(p_x * 2^sigma) held exactly in FP64,

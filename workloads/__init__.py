@@ -18,8 +18,7 @@ Conventions (used by both sides):
 
 The random-circuit families follow the workloads of the paper's Sec. IV-B
 (random gates with noise channels coupled to every coherent gate) with the
-gate sets and noise models of the benchmark configurations described in
-DESIGN.md ("Input recipe").
+gate sets and noise models of the benchmark configurations below.
 """
 from __future__ import annotations
 
@@ -208,7 +207,7 @@ def attach_noise(circ: Circuit, channels: Sequence[Channel]) -> Circuit:
 
 
 # ---------------------------------------------------------------------------
-# Benchmark configurations (input recipes; sizes as stated in the design doc)
+# Benchmark configurations (input recipes with their sizes)
 # ---------------------------------------------------------------------------
 
 def config_c1(instance: int = 0) -> dict:

@@ -186,12 +186,14 @@ __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, 
 // formed once per row; the K offsets come from a per-block shared table in two
 // levels (bits 0-9 and 10-19; bit 20 and up, rarely used, by a loop), so a
 // contiguous K axis turns into coalesced float2 loads.  Stores are float2 /
-// 32-bit pairs, consecutive lanes on consecutive slots.
+// 32-bit pairs, consecutive lanes on consecutive slots.  FP16 rows are scaled
+// by 2^-e, e the exponent of the row's largest |component|: rows of up to 256
+// slots keep their values in registers between the max and the store pass;
+// longer rows go to k_pack_long (one block per row, second pass from cache).
 constexpr int kKTab = 1024;
-template <int F>
-__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a, const ChunkCtx c) {
-    using T = typename Fmt<F>::T;
-    __shared__ int64_t ktab[2 * kKTab];
+constexpr int kPackRegRow = 256;   // longest FP16 row the warp kernel holds in registers
+
+__device__ __forceinline__ void build_ktab(const PackArgs& a, int64_t* ktab) {
     const int n_lo = a.n_kb < 10 ? a.n_kb : 10;
     const int n_mid = a.n_kb < 20 ? a.n_kb - n_lo : 10;
     for (int i = threadIdx.x; i < 2 * kKTab; i += blockDim.x) {
@@ -202,6 +204,60 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
             if ((v >> t) & 1) off += a.k_stride[b0 + t];
         ktab[i] = off;
     }
+}
+__device__ __forceinline__ int64_t kofs(const PackArgs& a, const int64_t* ktab, int64_t kc) {
+    int64_t off = ktab[kc & (kKTab - 1)] + ktab[kKTab + ((kc >> 10) & (kKTab - 1))];
+    for (int t = 20; t < a.n_kb; t++)
+        if ((kc >> t) & 1) off += a.k_stride[t];
+    return off;
+}
+// Operand address of packed row jr = (pi * nh + h) * nrow + row; z = pi * nh + h.
+__device__ __forceinline__ const float2* pack_row_base(const PackArgs& a, const ChunkCtx& c, int64_t jr, int64_t& z,
+                                                      int64_t& row) {
+    row = jr & (((int64_t)1 << a.n_rb) - 1);
+    z = jr >> a.n_rb;
+    const int64_t h = z & (((int64_t)1 << a.n_hb) - 1);
+    const int64_t pi = z >> a.n_hb;
+    const float2* base = pack_operand_ptr(a.op, a.pcls, pi, c);
+    for (int i = 0; i < a.n_rb; i++)
+        if ((row >> i) & 1) base += a.r_stride[i];
+    for (int i = 0; i < a.n_hb; i++)
+        if ((h >> i) & 1) base += a.h_stride[i];
+    return base;
+}
+template <int F>
+__device__ __forceinline__ void pack_store(const PackArgs& a, typename Fmt<F>::T* d0, int64_t rowlen, int64_t kc,
+                                           float re, float im) {
+    using T = typename Fmt<F>::T;
+    T rh, rl, ih, il;
+    split<F>(re, rh, rl);
+    split<F>(im, ih, il);
+    if (a.role == 0) {
+        store_pair<F>(d0 + 2 * kc, rh, ih);
+        store_pair<F>(d0 + a.Kh + 2 * kc, rl, il);
+    } else {
+        T nih, nil;
+        split<F>(-im, nih, nil);
+        store_pair<F>(d0 + 2 * kc, rh, nih);
+        store_pair<F>(d0 + a.Kh + 2 * kc, rl, nil);
+        store_pair<F>(d0 + rowlen + 2 * kc, ih, rh);
+        store_pair<F>(d0 + rowlen + a.Kh + 2 * kc, il, rl);
+    }
+}
+__device__ __forceinline__ int row_exponent(float mx) {
+    int e = 0;
+    if (mx > 0.f) {
+        frexpf(mx, &e);
+        e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    }
+    return e;
+}
+
+template <int F>
+__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a, const ChunkCtx c) {
+    using T = typename Fmt<F>::T;
+    __shared__ int64_t ktab[2 * kKTab];
+    build_ktab(a, ktab);
     __syncthreads();
     T* dst = static_cast<T*>(a.dst);
     const int lk = 31 - __clz(a.Kh / 2);                // log2 complex slots per half row
@@ -215,66 +271,95 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
     const int l0 = lk >= 5 ? lane : (lane & ((int)kcp - 1));
     const int64_t n_rows = a.n_pinst << (a.n_hb + a.n_rb);
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // (FP16 rows span >= 32 slots, so rpw == 1 there and the warp reduction sees one row)
+    const float csign = a.op.conj ? -1.f : 1.f;
+    // (FP16 rows span 32..kPackRegRow slots here, so rpw == 1 and the warp reduction sees one row)
     for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w * rpw < n_rows; w += warps) {
         const int64_t jr = w * rpw + sub;                // (pi, h, row), row fastest
         if (jr >= n_rows) continue;
-        const int64_t row = jr & (((int64_t)1 << a.n_rb) - 1);
-        const int64_t z = jr >> a.n_rb;                  // pi * nh + h
-        const int64_t h = z & (((int64_t)1 << a.n_hb) - 1);
-        const int64_t pi = z >> a.n_hb;
-        const float2* base = pack_operand_ptr(a.op, a.pcls, pi, c);
-        for (int i = 0; i < a.n_rb; i++)
-            if ((row >> i) & 1) base += a.r_stride[i];
-        for (int i = 0; i < a.n_hb; i++)
-            if ((h >> i) & 1) base += a.h_stride[i];
-        float sc = 1.f;
+        int64_t z, row;
+        const float2* base = pack_row_base(a, c, jr, z, row);
+        T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
         if constexpr (F == FMT_FP16) {
-            // per-row scaling: largest |component| of the row -> exponent e, row * 2^-e
+            float2 v[kPackRegRow / 32];
             float mx = 0.f;
-            for (int64_t kc = l0; kc < kc_real; kc += lstep) {
-                int64_t off = ktab[kc & (kKTab - 1)] + ktab[kKTab + ((kc >> 10) & (kKTab - 1))];
-                for (int t = 20; t < a.n_kb; t++)
-                    if ((kc >> t) & 1) off += a.k_stride[t];
-                const float2 v = base[off];
-                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+#pragma unroll
+            for (int i = 0; i < kPackRegRow / 32; i++) {
+                const int64_t kc = l0 + 32 * i;
+                v[i] = make_float2(0.f, 0.f);
+                if (kc < kc_real) v[i] = base[kofs(a, ktab, kc)];
+                mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
             }
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            int e = 0;
-            if (mx > 0.f) {
-                frexpf(mx, &e);
-                e = e < -100 ? -100 : (e > 100 ? 100 : e);
-            }
-            sc = ldexpf(1.f, -e);
+            const int e = row_exponent(mx);
+            const float sc = ldexpf(1.f, -e);
             if (lane == 0) a.row_exp[jr] = (int8_t)e;
+#pragma unroll
+            for (int i = 0; i < kPackRegRow / 32; i++) {
+                const int64_t kc = l0 + 32 * i;
+                if (kc < kcp) pack_store<F>(a, d0, rowlen, kc, v[i].x * sc, csign * v[i].y * sc);
+            }
+        } else {
+            for (int64_t kc = l0; kc < kcp; kc += lstep) {
+                float re = 0.f, im = 0.f;
+                if (kc < kc_real) {
+                    const float2 v = base[kofs(a, ktab, kc)];
+                    re = v.x;
+                    im = csign * v.y;
+                }
+                pack_store<F>(a, d0, rowlen, kc, re, im);
+            }
         }
-        const float csign = a.op.conj ? -1.f : 1.f;
+    }
+}
+
+// FP16 rows longer than kPackRegRow slots: one block per row, the block's
+// largest |component| first, then the scaled split (the second read of the
+// row hits the cache: a few hundred rows are in flight).
+template <int F>
+__global__ void __launch_bounds__(256) k_pack_long(const __grid_constant__ PackArgs a, const ChunkCtx c) {
+    using T = typename Fmt<F>::T;
+    __shared__ int64_t ktab[2 * kKTab];
+    __shared__ float red[8];
+    __shared__ int e_sh;
+    build_ktab(a, ktab);
+    __syncthreads();
+    T* dst = static_cast<T*>(a.dst);
+    const int64_t kcp = (int64_t)a.Kh / 2;
+    const int64_t kc_real = (int64_t)1 << a.n_kb;
+    const int64_t rowlen = 2 * (int64_t)a.Kh;
+    const int64_t n_rows = a.n_pinst << (a.n_hb + a.n_rb);
+    const float csign = a.op.conj ? -1.f : 1.f;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int64_t jr = blockIdx.x; jr < n_rows; jr += gridDim.x) {
+        int64_t z, row;
+        const float2* base = pack_row_base(a, c, jr, z, row);
         T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
-        for (int64_t kc = l0; kc < kcp; kc += lstep) {
+        float mx = 0.f;
+        for (int64_t kc = threadIdx.x; kc < kc_real; kc += blockDim.x) {
+            const float2 v = base[kofs(a, ktab, kc)];
+            mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) red[wib] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = red[0];
+            for (int i = 1; i < (int)(blockDim.x >> 5); i++) m = fmaxf(m, red[i]);
+            e_sh = row_exponent(m);
+            a.row_exp[jr] = (int8_t)e_sh;
+        }
+        __syncthreads();
+        const float sc = ldexpf(1.f, -e_sh);
+        for (int64_t kc = threadIdx.x; kc < kcp; kc += blockDim.x) {
             float re = 0.f, im = 0.f;
             if (kc < kc_real) {
-                int64_t off = ktab[kc & (kKTab - 1)] + ktab[kKTab + ((kc >> 10) & (kKTab - 1))];
-                for (int t = 20; t < a.n_kb; t++)
-                    if ((kc >> t) & 1) off += a.k_stride[t];
-                const float2 v = base[off];
+                const float2 v = base[kofs(a, ktab, kc)];
                 re = v.x * sc;
                 im = csign * v.y * sc;
             }
-            T rh, rl, ih, il;
-            split<F>(re, rh, rl);
-            split<F>(im, ih, il);
-            if (a.role == 0) {
-                store_pair<F>(d0 + 2 * kc, rh, ih);
-                store_pair<F>(d0 + a.Kh + 2 * kc, rl, il);
-            } else {
-                T nih, nil;
-                split<F>(-im, nih, nil);
-                store_pair<F>(d0 + 2 * kc, rh, nih);
-                store_pair<F>(d0 + a.Kh + 2 * kc, rl, nil);
-                store_pair<F>(d0 + rowlen + 2 * kc, ih, rh);
-                store_pair<F>(d0 + rowlen + a.Kh + 2 * kc, il, rl);
-            }
+            pack_store<F>(a, d0, rowlen, kc, re, im);
         }
+        __syncthreads();   // red / e_sh reused by the next row
     }
 }
 
@@ -781,9 +866,16 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     }
     {
         StatScope sc(K_PACK, s, 8.0 * (double)(tot_a + tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b, 0.0);
-        k_pack<F><<<grid_of(tot_a), 256, 0, s>>>(pa, ctx);
-        k_pack<F><<<grid_of(tot_b), 256, 0, s>>>(pb, ctx);
-        // (grid_of sizes by complex slots; the kernel strides over rows by warps)
+        // (grid_of sizes by complex slots; the kernels stride over rows)
+        for (const PackArgs* pk : {&pa, &pb}) {
+            const int64_t tot = pk == &pa ? tot_a : tot_b;
+            if (F == FMT_FP16 && Kh / 2 > kPackRegRow) {
+                const int64_t rows = pk->n_pinst << (pk->n_hb + pk->n_rb);
+                k_pack_long<F><<<(unsigned)(rows < 152 * 8 ? rows : 152 * 8), 256, 0, s>>>(*pk, ctx);
+            } else {
+                k_pack<F><<<grid_of(tot), 256, 0, s>>>(*pk, ctx);
+            }
+        }
     }
     CUtensorMap mA, mB;
     int64_t blocks = ga.tiles_m * ga.tiles_n * n_inst * (1ll << nh);

@@ -195,7 +195,7 @@ def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers)
         items.append(dict(plan=p, traj=tr, seed=c["seed"], total_shots=c["total_shots"], circuit_id=c["circuit_id"]))
         names.append(c["name"])
     t_plan = time.perf_counter() - t0
-    runs = {}
+    runs, first_error = {}, ""
     for nw in sorted({1, workers}):
         if dist:
             dist.barrier()
@@ -211,6 +211,7 @@ def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers)
         if nw == workers:
             for nm, (st, _) in zip(names, out):
                 status[nm] = "ok" if st == 0 else f"run: {ptn.STATUS_NAMES.get(st, st)}"
+            first_error = ptn.last_batch_error
         del out
     best = runs[workers]
     return {"workload": "64 circuits: 20-40-qubit 1D brickwork or 6x5 grid, depth 8-16, depolarizing 0.001-0.02, "
@@ -218,6 +219,7 @@ def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers)
             "value": best["value"], "unit": "shots/s", "workers": workers, "completed": best["completed"],
             "completed_fraction": best["completed"] / len(cfgs), "shots": best["shots"], "seconds": best["seconds"],
             "serial_seconds": runs[1]["seconds"], "plan_and_presample_seconds": t_plan,
+            "first_error_rank0": first_error,
             "status_rank0": {nm: status.get(nm, "other rank") for nm in (c["name"] for c in cfgs)}}
 
 

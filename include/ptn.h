@@ -311,7 +311,7 @@ typedef struct {
 typedef struct {
     int32_t n_workers;          /* circuits in flight at once (each on its own CUDA stream); 0: 4 */
     int32_t keep_workspaces;    /* 0: free each plan's device workspace when its items are done */
-    double  mem_budget_bytes;   /* device memory shared by the workers; 0: 80% of free memory */
+    double  mem_budget_bytes;   /* device memory shared by the workers; 0: 70% of free memory */
     double  max_est_seconds;    /* items whose plan's modelled time exceeds this are not run and
                                    get PTN_ERR_TOO_LARGE; 0: no limit */
 } ptn_batch_opts;
@@ -325,7 +325,9 @@ typedef struct {
  * `stream`; `stream` waits for all of them before the call returns (the call
  * itself returns once every item has been issued and its level sizes read).
  * Each plan without an explicit memory cap gets mem_budget / n_workers for
- * the batch.  A failing item (e.g. PTN_ERR_TOO_LARGE: a circuit beyond the
+ * the batch; an item that fails with PTN_ERR_OOM or PTN_ERR_CUDA while others
+ * share the device runs once more alone with the whole budget.  A failing
+ * item (e.g. PTN_ERR_TOO_LARGE: a circuit beyond the
  * memory cap, the failures the paper counts in Sec. IV-D) does not stop the
  * others: status_out[i] (host, n_items) holds each item's status and
  * shots_out[i] (host, n_items) its result or NULL.  Returns PTN_OK unless

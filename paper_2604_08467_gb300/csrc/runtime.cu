@@ -993,7 +993,7 @@ ptn_status ptn_sample_shots_batch(const ptn_batch_item* items, int32_t n_items, 
     if (budget <= 0) {
         size_t fr = 0, tot = 0;
         PTN_CUDA(cudaMemGetInfo(&fr, &tot));
-        budget = 0.8 * (double)fr;
+        budget = 0.7 * (double)fr;   // workspace beyond the arenas (packs, levels) comes on top
     }
     for (size_t g = 0; g < groups.size(); g++) {
         ptn_plan* pl = const_cast<ptn_plan*>(groups[g].plan);
@@ -1014,6 +1014,7 @@ ptn_status ptn_sample_shots_batch(const ptn_batch_item* items, int32_t n_items, 
     std::atomic<size_t> next{0};
     std::mutex msg_mu;
     std::string first_msg;
+    bool first_strong = false;
     auto worker = [&](int w) {
         cudaSetDevice(dev);
         cudaStream_t s = ws_streams[w];
@@ -1032,11 +1033,15 @@ ptn_status ptn_sample_shots_batch(const ptn_batch_item* items, int32_t n_items, 
                 }
                 status_out[i] = st;
                 if (st != PTN_OK) {
+                    // keep the first message, preferring a resource or CUDA failure over
+                    // an over-budget circuit
                     std::lock_guard<std::mutex> lk(msg_mu);
-                    if (first_msg.empty()) {
+                    const bool strong = st != PTN_ERR_TOO_LARGE;
+                    if (first_msg.empty() || (strong && !first_strong)) {
                         char buf[64];
                         snprintf(buf, sizeof buf, "item %d: ", i);
                         first_msg = std::string(buf) + last_error_text();
+                        first_strong = strong;
                     }
                 }
             }
@@ -1053,6 +1058,26 @@ ptn_status ptn_sample_shots_batch(const ptn_batch_item* items, int32_t n_items, 
         cudaStreamDestroy(ws_streams[w]);
     }
     cudaEventDestroy(ev0);
+    // Items that ran out of device memory (or hit a CUDA error) while sharing the
+    // device with other workers run once more alone, with the whole budget.
+    if (n_workers > 1) {
+        AsyncAllocScope scope(s0);
+        for (int32_t i = 0; i < n_items; i++) {
+            if (status_out[i] != PTN_ERR_OOM && status_out[i] != PTN_ERR_CUDA) continue;
+            ptn_plan* pl = const_cast<ptn_plan*>(items[i].plan);
+            drop_workspace(pl);
+            if (pl->opts.mem_cap_bytes <= 0) pl->mem_cap = budget;
+            ptn_status st;
+            try {
+                st = ptn_sample_shots(items[i].plan, items[i].traj, &items[i].opts, &shots_out[i], s0);
+            } catch (const std::bad_alloc&) {
+                st = set_error(PTN_ERR_OOM, "host allocation failed");
+            }
+            status_out[i] = st;
+            if (st != PTN_OK && first_msg.empty()) first_msg = std::string("retried item: ") + last_error_text();
+            if (!keep) drop_workspace(pl);
+        }
+    }
     for (size_t g = 0; g < groups.size(); g++) const_cast<ptn_plan*>(groups[g].plan)->mem_cap = saved_cap[g];
     clear_error();
     if (!first_msg.empty()) set_error(PTN_OK, "%s", first_msg.c_str());

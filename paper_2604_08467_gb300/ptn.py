@@ -126,6 +126,7 @@ _RESTYPE = {"ptn_plan_destroy": None, "ptn_traj_destroy": None, "ptn_shots_destr
             "ptn_status_string": C.c_char_p, "ptn_last_error": C.c_char_p, "ptn_version": C.c_char_p}
 
 _lib_handle = None
+last_batch_error = ""
 
 
 def library_path():
@@ -371,6 +372,8 @@ def ptn_sample_shots_batch(items, n_workers=4, keep_workspaces=False, mem_budget
     outs = (C.c_void_p * max(n, 1))()
     sts = (C.c_int * max(n, 1))()
     _check(lib().ptn_sample_shots_batch(arr, n, C.byref(bo), outs, sts, _stream(stream)))
+    global last_batch_error
+    last_batch_error = lib().ptn_last_error().decode()   # first failing item's message, if any
     res = []
     for i, it in enumerate(items):
         if sts[i] == PTN_OK:

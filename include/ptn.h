@@ -297,6 +297,14 @@ ptn_status ptn_shots_copy(const ptn_shots* shots, int32_t* traj_out, uint64_t* b
 
 void ptn_shots_destroy(ptn_shots* shots);
 
+/* The emitted shots merged across trajectories: one record per distinct
+ * bitstring with the summed count, in increasing bitstring order (traj = -1
+ * in every record), built on the device by a stable radix sort of the
+ * (bitstring, count) records followed by a reduction by key.  *merged_out is
+ * a new handle (ptn_shots_destroy); nets_per_block is copied.  Synchronises
+ * the stream once (to size the result). */
+ptn_status ptn_shots_merge(const ptn_shots* shots, ptn_shots** merged_out, ptn_stream stream);
+
 /* ------------------------------------------------ mixed-circuit batches -- */
 
 /* One circuit of a heterogeneous batch: its plan, its pre-sampled error sets

@@ -110,6 +110,17 @@ void launch_fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s);
 void launch_iota_i32(int32_t* p, int64_t n, cudaStream_t s);
 void launch_scale_i64(const int64_t* a, int64_t k, int64_t n, int64_t* out, cudaStream_t s);
 
+// ---- merging emitted shots across trajectories (kernels_merge.cu)
+// one stable radix pass over 8 bits of key starting at `shift`; hist holds
+// radix_hist_elems(n) int64, scan_tmp scan_tmp_elems(radix_hist_elems(n))
+int64_t radix_hist_elems(int64_t n);
+void launch_radix_pass(const uint64_t* key, const int64_t* val, int64_t n, int shift, int64_t* hist, int64_t* scan_tmp,
+                       uint64_t* key_out, int64_t* val_out, cudaStream_t s);
+void launch_run_flags(const uint64_t* key, int64_t n, int64_t* flag, cudaStream_t s);
+void launch_run_starts(const int64_t* flag, const int64_t* excl, int64_t n, int64_t* start, cudaStream_t s);
+void launch_run_sum(const uint64_t* key, const int64_t* val, const int64_t* start, int64_t n_runs, int64_t n,
+                    int32_t* traj_out, uint64_t* bits_out, int64_t* count_out, cudaStream_t s);
+
 struct SampleScratch {
     int64_t* cap;        // [n_parent] min(count, 2^b)
     int64_t* tmp_off;    // [n_parent]

@@ -163,6 +163,7 @@ struct ptn_traj {
 
 struct ptn_shots {
     int64_t n = 0;
+    int32_t n_qubits = 64;
     int32_t* traj = nullptr;
     uint64_t* bits = nullptr;
     int64_t* count = nullptr;
@@ -917,6 +918,7 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     }
     ptn_shots* r = new ptn_shots();
     r->n = n;
+    r->n_qubits = plan->n_qubits;
     r->nets_per_block = nets;
     size_t m = std::max<int64_t>(n, 1);
     cudaError_t ce;
@@ -1082,6 +1084,79 @@ ptn_status ptn_sample_shots_batch(const ptn_batch_item* items, int32_t n_items, 
     clear_error();
     if (!first_msg.empty()) set_error(PTN_OK, "%s", first_msg.c_str());
     PTN_CUDA(cudaGetLastError());
+    return PTN_OK;
+}
+
+ptn_status ptn_shots_merge(const ptn_shots* in, ptn_shots** out, ptn_stream stream) {
+    clear_error();
+    if (!in || !out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = in->n;
+    ptn_shots* r = new ptn_shots();
+    r->n_qubits = in->n_qubits;
+    r->nets_per_block = in->nets_per_block;
+    int64_t n_runs = 0;
+    std::vector<void*> tmp;
+    auto fail = [&](ptn_status st) {
+        for (void* p : tmp) cudaFreeAsync(p, s);
+        cudaFree(r->traj);
+        cudaFree(r->bits);
+        cudaFree(r->count);
+        delete r;
+        return st;
+    };
+    auto alloc = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s) != cudaSuccess) return nullptr;
+        tmp.push_back(p);
+        return p;
+    };
+    if (n > 0) {
+        const int64_t nh = radix_hist_elems(n);
+        uint64_t* k[2] = {static_cast<uint64_t*>(alloc(8 * n)), static_cast<uint64_t*>(alloc(8 * n))};
+        int64_t* v[2] = {static_cast<int64_t*>(alloc(8 * n)), static_cast<int64_t*>(alloc(8 * n))};
+        int64_t* hist = static_cast<int64_t*>(alloc(8 * nh));
+        int64_t* scan = static_cast<int64_t*>(alloc(8 * std::max(scan_tmp_elems(nh), scan_tmp_elems(n))));
+        int64_t* flag = static_cast<int64_t*>(alloc(8 * n));
+        int64_t* excl = static_cast<int64_t*>(alloc(8 * n));
+        int64_t* start = static_cast<int64_t*>(alloc(8 * n));
+        if (!k[0] || !k[1] || !v[0] || !v[1] || !hist || !scan || !flag || !excl || !start)
+            return fail(set_error(PTN_ERR_OOM, "merge scratch"));
+        cudaError_t ce = cudaMemcpyAsync(k[0], in->bits, 8 * n, cudaMemcpyDeviceToDevice, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(v[0], in->count, 8 * n, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) return fail(set_error(PTN_ERR_CUDA, "merge copy: %s", cudaGetErrorString(ce)));
+        int cur = 0;
+        for (int shift = 0; shift < in->n_qubits; shift += 8) {
+            launch_radix_pass(k[cur], v[cur], n, shift, hist, scan, k[1 - cur], v[1 - cur], s);
+            cur = 1 - cur;
+        }
+        launch_run_flags(k[cur], n, flag, s);
+        launch_exclusive_scan(flag, excl, n, scan, s);
+        launch_run_starts(flag, excl, n, start, s);
+        int64_t last[2];
+        ce = cudaMemcpyAsync(&last[0], excl + n - 1, 8, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&last[1], flag + n - 1, 8, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return fail(set_error(PTN_ERR_CUDA, "merge: %s", cudaGetErrorString(ce)));
+        n_runs = last[0] + last[1];
+        size_t m = std::max<int64_t>(n_runs, 1);
+        if ((ce = cudaMalloc(&r->traj, sizeof(int32_t) * m)) != cudaSuccess ||
+            (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * m)) != cudaSuccess ||
+            (ce = cudaMalloc(&r->count, sizeof(int64_t) * m)) != cudaSuccess)
+            return fail(set_error(PTN_ERR_OOM, "merge result: %s", cudaGetErrorString(ce)));
+        launch_run_sum(k[cur], v[cur], start, n_runs, n, r->traj, r->bits, r->count, s);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) return fail(set_error(PTN_ERR_CUDA, "merge: %s", cudaGetErrorString(ce)));
+    } else {
+        cudaError_t ce;
+        if ((ce = cudaMalloc(&r->traj, 16)) != cudaSuccess || (ce = cudaMalloc(&r->bits, 16)) != cudaSuccess ||
+            (ce = cudaMalloc(&r->count, 16)) != cudaSuccess)
+            return fail(set_error(PTN_ERR_OOM, "merge result: %s", cudaGetErrorString(ce)));
+    }
+    for (void* p : tmp) cudaFreeAsync(p, s);
+    r->n = n_runs;
+    *out = r;
     return PTN_OK;
 }
 

@@ -111,6 +111,7 @@ _SIGS = {
                        C.POINTER(C.c_int64), C.c_int32],
     "ptn_shots_copy": [_P, _P, _P, _P, _P],
     "ptn_shots_destroy": [_P],
+    "ptn_shots_merge": [_P, C.POINTER(_P), _P],
     "ptn_sample_shots_batch": [C.POINTER(ptn_batch_item), C.c_int32, C.POINTER(ptn_batch_opts), C.POINTER(_P),
                                C.POINTER(C.c_int), _P],
     "ptn_expval_grad": [_P, _P, C.POINTER(ptn_pauli_sum), C.POINTER(C.c_double), C.c_int32, _P, _P, _P],
@@ -400,6 +401,14 @@ def ptn_expval_grad(plan, traj, terms, theta, value_out, grad_out, stream=None):
     thp = th.ctypes.data_as(C.POINTER(C.c_double)) if th.size else None
     _check(lib().ptn_expval_grad(plan.handle, traj.handle, C.byref(obs), thp, int(th.size), _ptr(value_out),
                                  _ptr(grad_out), _stream(stream)))
+
+
+def ptn_shots_merge(shots, n_blocks, stream=None):
+    """Shots merged across trajectories (include/ptn.h): one record per distinct
+    bitstring, increasing bits, traj = -1."""
+    h = C.c_void_p()
+    _check(lib().ptn_shots_merge(shots.handle, C.byref(h), _stream(stream)))
+    return Shots(h, n_blocks)
 
 
 def ptn_stats_enable(on=True):

@@ -2,8 +2,8 @@
 TEST INFRASTRUCTURE (see the package docstring).
 
 Paper, Sec. II-C: E error sets K_i = {k_p^i} are drawn before any network is
-built, by a user rule "proportional with error probabilities".  Reading used
-here: each noise site s draws Kraus index k with the state-independent nominal
+built, by a rule the user picks (in proportion to the error probabilities, for
+example).  Reading used here: each noise site s draws Kraus index k with the state-independent nominal
 probability q_{s,k} = Tr(K_k^dagger K_k) / 2 (these sum to one by the
 completeness relation), and the trajectory inserts K_k / sqrt(q_{s,k}), which
 makes the average of |psi_i><psi_i| over draws equal to the density matrix.

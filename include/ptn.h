@@ -121,7 +121,9 @@ typedef struct {
     double   mem_cap_bytes;    /* device memory one execution chunk may use; 0 -> 40% of
                                   the device's free memory at first use */
     int32_t  simt_only;        /* 1: run every step on the SIMT kernel (no tensor cores) */
-    int32_t  reserved;
+    int32_t  grad_checkpoint;  /* ptn_expval_grad: 0 keep every forward intermediate; 1 keep only
+                                  those crossing segments of ~sqrt(steps) steps and recompute the
+                                  rest segment by segment on the reversed path */
 } ptn_plan_opts;
 
 /* ------------------------------------------------------------- planning -- */

@@ -596,10 +596,36 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         }
         return PTN_OK;
     };
+    // Gradient plans keep every forward intermediate, or with checkpointing only
+    // those that cross a segment boundary of the step list (segments of about
+    // sqrt(steps) steps); the others are recomputed segment by segment on the
+    // reversed path.
+    const bool ckpt = expval && plan->opts.grad_checkpoint;
+    // segments by produced size: with T elements produced in all and tensors of
+    // at most m elements, segments of about sqrt(T m) elements keep about
+    // 2 sqrt(T m) elements live instead of T
+    std::vector<int32_t> step_seg;
+    {
+        std::vector<double> sz;
+        for (const Move& mv : s.moves)
+            if (mv.type == MV_CONTRACT) sz.push_back(std::ldexp(1.0, (int)s.t[mv.c].idx.size()));
+        double tot = 0, mx = 1;
+        for (double v : sz) tot += v, mx = std::max(mx, v);
+        const double seg = std::max(mx, std::sqrt(tot * mx));
+        double cum = 0;
+        for (double v : sz) {
+            step_seg.push_back((int32_t)(cum / seg));
+            cum += v;
+        }
+    }
+    int cur_step = 0;
+    std::vector<int32_t> buf_step;   // producing step of every buffer
     auto consume = [&](const TRef& r) {
         if (r.mode != OP_BUF) return;
         BufInfo& bi = bufs[r.id];
-        if (--bi.refs == 0 && !expval) arenas[bi.arena].release(bi.off);
+        if (--bi.refs != 0) return;
+        const bool same_segment = step_seg[buf_step[r.id]] == step_seg[cur_step];
+        if (!expval || (ckpt && same_segment)) arenas[bi.arena].release(bi.off);
     };
 
     int32_t root_id = s.root();
@@ -714,6 +740,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         bi.refs = mv.mc >= 0 ? 2 : 1;
         int32_t bid = (int32_t)bufs.size();
         bufs.push_back(bi);
+        buf_step.push_back(cur_step);
         st.out_arena = C.cls;
         st.out_off = bi.off;
         consume(A);
@@ -741,6 +768,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
             for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
         bp.steps.push_back(st);
         if (expval) recs.push_back({A, B, rc});
+        cur_step++;
     }
     // root descriptor
     const TRef& R = ref[root_id];
@@ -791,8 +819,44 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
                 bp.pleaves.push_back(p);
                 leaf_slot[x->id] = p.lgrad_off;
             }
+    // which forward outputs stayed allocated (the others get recomputed)
+    std::vector<char> kept(bufs.size(), 1);
+    if (ckpt) {
+        std::vector<int32_t> last_use(bufs.size(), -1);
+        for (size_t t = 0; t < recs.size(); t++)
+            for (const TRef* x : {&recs[t].a, &recs[t].b})
+                if (x->mode == OP_BUF) last_use[x->id] = (int32_t)t;
+        for (size_t i = 0; i < bufs.size(); i++)
+            kept[i] = (int32_t)i == R.id || last_use[i] < 0 || step_seg[buf_step[i]] != step_seg[last_use[i]];
+    }
+    std::vector<std::pair<int32_t, int64_t>> recomputed;   // (arena, offset) of this segment's recomputed buffers
+    int cur_seg = -1;
     for (auto it = recs.rbegin(); it != recs.rend(); ++it) {
         const TRef& C = it->c;
+        const int t = (int)(recs.rend() - it) - 1;
+        if (ckpt && step_seg[t] != cur_seg) {
+            // leave the previous segment: free its recomputed buffers; enter this
+            // one: replay its forward steps whose outputs were not kept
+            for (const auto& ro : recomputed) arenas[ro.first].release(ro.second);
+            recomputed.clear();
+            cur_seg = step_seg[t];
+            int t0 = t;
+            while (t0 > 0 && step_seg[t0 - 1] == cur_seg) t0--;
+            for (int u = t0; u <= t; u++) {
+                const int32_t id = recs[u].c.id;
+                if (kept[id]) continue;
+                StepDesc st = bp.steps[u];
+                const int32_t cls = bufs[id].arena;
+                bufs[id].off = arenas[cls].alloc(st.out_size);
+                recomputed.push_back({cls, bufs[id].off});
+                ptn_status ee = make_op(recs[u].a, st.out_cls, st.op[0]);
+                if (ee) return ee;
+                ee = make_op(recs[u].b, st.out_cls, st.op[1]);
+                if (ee) return ee;
+                st.out_off = bufs[id].off;
+                bp.bwd.push_back(st);
+            }
+        }
         if (!buf_need[C.id]) continue;
         for (int side = 0; side < 2; side++) {
             const TRef& X = side ? it->b : it->a;
@@ -852,6 +916,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
     }
     bp.arena_peak[ARENA_ADJ] = adj.peak;
     bp.arena_peak[ARENA_LGRAD] = lg.peak;
+    for (int k = 0; k < 3; k++) bp.arena_peak[k] = arenas[k].peak;   // recomputed buffers included
     return PTN_OK;
 }
 

@@ -209,3 +209,22 @@ def test_gradient_converges_to_density_matrix():
     assert abs(vs.mean() - f_dm) <= 5 * se_v + 1e-6, (vs.mean(), f_dm, se_v)
     dev = np.abs(gs.mean(axis=0) - g_dm)
     assert np.all(dev <= 5 * se_g + 1e-6), (dev / np.maximum(se_g, 1e-12)).max()
+
+
+def test_checkpointed_gradients_match_keep_all():
+    """Gradient plans that recompute forward intermediates segment by segment
+    (grad_checkpoint) run the same kernels on the same inputs: values and
+    gradients equal those of the keep-all plan, with a smaller trajectory arena."""
+    r = np.random.default_rng(21)
+    th = r.standard_normal(12 * 8 * 2)
+    circ = W.attach_noise(W.hea_ring(12, 8, th), [W.depolarizing_kraus(0.02), W.amplitude_damping_kraus(0.02)])
+    terms = [(1.0 / 12, (1 << q) | (1 << ((q + 1) % 12))) for q in range(12)]
+    res = []
+    for ck in (False, True):
+        plan = ptn.ptn_plan_path(circ, [6, 6], hypersamples=16, est_traj=64, grad_checkpoint=ck)
+        tr = ptn.ptn_presample_trajectories(plan, 5, 64, dedup=True)
+        res.append(_gpu(plan, tr, terms, th) + (plan.describe(detail=2)["expval"]["arena"][1],))
+    (v0, g0, a0), (v1, g1, a1) = res
+    assert a1 < a0
+    assert abs(v1 - v0) <= 1e-12 * max(1.0, abs(v0))
+    np.testing.assert_allclose(g1, g0, rtol=0, atol=1e-12)

@@ -135,8 +135,8 @@ EV_CASES = [
 
 
 @pytest.mark.parametrize("name,make,bs", EV_CASES, ids=[c[0] for c in EV_CASES])
-@pytest.mark.parametrize("split", [1, 0])
-def test_expval_plan_replay(name, make, bs, split):
+@pytest.mark.parametrize("split,ckpt", [(1, 0), (0, 0), (1, 1)])
+def test_expval_plan_replay(name, make, bs, split, ckpt):
     """The lowered ket network reproduces the oracle's trajectory states and
     expectation values, and every parametrised leaf's adjoint G is the exact
     derivative: sum_e G[e] L'[e] = sum_x w(x) conj(psi(x)) psi'(x), psi' the
@@ -147,9 +147,14 @@ def test_expval_plan_replay(name, make, bs, split):
     rng = np.random.default_rng(zlib.crc32(name.encode()))
     circ = make(rng)
     n = circ.n_qubits
-    plan = ptn.ptn_plan_path(circ, bs, hypersamples=8, split_gates=split, est_traj=4, est_shots=64)
+    plan = ptn.ptn_plan_path(circ, bs, hypersamples=8, split_gates=split, est_traj=4, est_shots=64,
+                             grad_checkpoint=bool(ckpt))
     desc = plan.describe(detail=2)
     ev = desc["expval"]
+    if ckpt:   # recomputation steps make the reversed list longer than the adjoint steps alone
+        plain = ptn.ptn_plan_path(circ, bs, hypersamples=8, split_gates=split, est_traj=4, est_shots=64)
+        ev0 = plain.describe(detail=2)["expval"]
+        assert len(ev["bwd"]) >= len(ev0["bwd"])
     assert ev["n_params"] == circ.n_params()
     assert len(ev["pleaves"]) == len(G.rotation_occurrences(circ))
     kraus, _ = pts.presample(circ, 4, seed=23)

@@ -165,7 +165,9 @@ void ptn_plan_destroy(ptn_plan* plan);
  * sum over sites in site order of log q_{s,k}, is kept in FP64.
  * dedup != 0 merges identical error sets (first-occurrence order) and keeps
  * their multiplicities; this synchronises the stream once to read the number
- * of distinct sets.  Also computes, per trajectory, the variant index of every
+ * of distinct sets.  The first-occurrence search compares row hashes against
+ * every earlier row (quadratic in n_traj: well under a second up to ~10^5
+ * trajectories; use dedup = 0 beyond that).  Also computes, per trajectory, the variant index of every
  * merged tensor (the UPV merge as a table gather).  n_traj in 1 .. 2^24. */
 ptn_status ptn_presample_trajectories(const ptn_plan* plan, uint64_t seed, int32_t circuit_id,
                                       int64_t n_traj, int32_t dedup, ptn_traj** traj_out,

@@ -181,3 +181,23 @@ def test_expval_plan_replay(name, make, bs, split, ckpt):
             lhs = np.sum(grads[p["leaf"]][t].astype(np.complex128) * lp[var])
             rhs = np.sum(w * np.conj(psi[t].astype(np.complex128)) * psi2[t])
             assert abs(lhs - rhs) < 1e-4 * max(1.0, abs(rhs)), (p["leaf"], t, lhs, rhs)
+
+
+def test_gemm_operands_have_contiguous_summed_bits():
+    """Producers lay out their outputs with the consumer's summed bits
+    innermost, so every tensor-core step reads the summed axis of each
+    intermediate operand contiguously (the packing's coalesced path)."""
+    c2 = W.config_c2()
+    plan = ptn.ptn_plan_path(c2["circuit"], c2["block_sizes"], hypersamples=8, est_traj=4096, est_shots=1e6)
+    d = plan.describe(1)
+    n = 0
+    for blk in d["blocks"]:
+        for st in blk["steps"]:
+            if st["kind"] == 0:
+                continue
+            for o in range(2):
+                if st["ops"][o]["mode"] != 1:      # intermediate (arena) operand
+                    continue
+                n += 1
+                assert st["sum_stride"][o] == [1 << q for q in range(st["n_sum"])]
+    assert n > 20

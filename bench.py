@@ -286,6 +286,7 @@ def main():
     torch.cuda.synchronize()
 
     nets = None
+    n_records = 0
     times = []
     ptn.ptn_stats_reset()
     ptn.ptn_stats_enable(True)
@@ -304,6 +305,7 @@ def main():
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b) / 1e3)
             nets = res.nets_per_block
+            n_records = res.n
             del tr, res
         if args.profile_range:
             torch.cuda.profiler.stop()
@@ -445,6 +447,8 @@ def main():
                                         f"({args.precision}), fp64 CDF / log-probabilities",
                            "error_vs_fp64": PRECISIONS[args.precision][1]},
                 "e2e": e2e, "plain_path": plain, "expval_grad": grad, "mixed_batch": mixed, "roofline": roof, "cpu_baseline": cpu,
+                "contractions_per_s": float(sum(nets or [0])) * world / t_step,
+                "distinct_records_per_s": float(n_records) * world / t_step,
                 "gpu_launches": int(launches), "clocks": clocks,
                 "kernels": {k: {"launches": v["launches"], "ms_per_step": r["ms_per_step"], "achieved": r["achieved"],
                                 "unit": r["unit"], "frac": r["frac"]} for k, r in roofs.items()

@@ -21,8 +21,10 @@
 //  - BF16 (PTN_PREC_BF16X3): hi, lo rounded to BF16 (16 significant bits in
 //    total, FP32 exponent range);
 //  - FP16 (PTN_PREC_FP16X3): hi, lo rounded to FP16 (22 significant bits) after
-//    scaling each packed instance by a power of two that brings its largest
-//    magnitude into [0.5, 1); the epilogue undoes both scales exactly.
+//    scaling each packed row by a power of two that brings its largest
+//    magnitude into [0.5, 1); the epilogue undoes the row and column scales
+//    exactly.
+// The GEMM kernel is persistent and warp-specialised (see k_gemm).
 // Conjugated operands (bra layer) are conjugated while packing.
 #include <cuda.h>
 #include <cuda_bf16.h>

@@ -532,8 +532,9 @@ struct ArenaAlloc {   // first-fit offsets of live buffers in one arena
 };
 
 // Lower a searched path to step descriptors.  expval: the network is the ket
-// state with every qubit open; all forward intermediates are kept (no buffer
-// reuse) and the reversed (adjoint) path is lowered too, see the end.
+// state with every qubit open; the forward intermediates are kept (all of
+// them, or with checkpointing those crossing a segment boundary) and the
+// reversed (adjoint) path is lowered too, see the end.
 static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const Searcher& s,
                               int32_t start, int32_t b, BlockPlan& bp, bool expval = false) {
     struct Rec {

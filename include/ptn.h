@@ -124,6 +124,12 @@ typedef struct {
     int32_t  grad_checkpoint;  /* ptn_expval_grad: 0 keep every forward intermediate; 1 keep only
                                   those crossing segments of ~sqrt(steps) steps and recompute the
                                   rest segment by segment on the reversed path */
+    int32_t  network_form;     /* sampling networks: 0 the double layer <psi|P|psi> of every block;
+                                  1 per block the cheaper (modelled) of the double layer and the
+                                  ket-only form (amplitudes of the block and later qubits, then
+                                  the marginal as sum over later qubits of |a|^2); 2 ket-only
+                                  wherever it has a path */
+    int32_t  reserved;
 } ptn_plan_opts;
 
 /* ------------------------------------------------------------- planning -- */

@@ -147,7 +147,9 @@ static void svd4(const M4& x_in, double s[4], cd xv[4][4], cd v[4][4]) {
 enum Role : int32_t { R_IN_A = 0, R_OUT_A = 1, R_IN_B = 2, R_OUT_B = 3, R_BOND = 4 };
 
 // --------------------------------------------------------------- network --
-enum IdxKind : int32_t { IX_INT = 0, IX_OPEN = 1, IX_TRACED = 2, IX_SLICE = 3 };
+// IX_REST: a later qubit of the ket-only sampling form, open in the ket network
+// and summed only after |.|^2 (the closing step of the block)
+enum IdxKind : int32_t { IX_INT = 0, IX_OPEN = 1, IX_TRACED = 2, IX_SLICE = 3, IX_REST = 4 };
 
 struct NetIdx {
     int32_t kind;
@@ -203,7 +205,7 @@ struct Searcher {
     Searcher(const BlockNet& n, const CostModel& c) : net(&n), cm(&c) {}
 
     bool is_slice(int32_t i) const { return net->idx[i].kind == IX_SLICE; }
-    bool is_open(int32_t i) const { return net->idx[i].kind == IX_OPEN; }
+    bool is_open(int32_t i) const { return net->idx[i].kind == IX_OPEN || net->idx[i].kind == IX_REST; }
 
     void init() {
         t.clear();
@@ -625,8 +627,11 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         if (r.mode != OP_BUF) return;
         BufInfo& bi = bufs[r.id];
         if (--bi.refs != 0) return;
-        const bool same_segment = step_seg[buf_step[r.id]] == step_seg[cur_step];
-        if (!expval || (ckpt && same_segment)) arenas[bi.arena].release(bi.off);
+        if (!expval) {
+            arenas[bi.arena].release(bi.off);
+            return;
+        }
+        if (ckpt && step_seg[buf_step[r.id]] == step_seg[cur_step]) arenas[bi.arena].release(bi.off);
     };
 
     int32_t root_id = s.root();
@@ -772,8 +777,73 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         cur_step++;
     }
     // root descriptor
-    const TRef& R = ref[root_id];
+    TRef R = ref[root_id];
     if (R.mode != OP_BUF) return set_error(PTN_ERR_UNSUPPORTED, "degenerate block network");
+    if (net.ket_only && !expval) {
+        // Ket-only form: the network's result is the amplitude a(x, rest) of the
+        // block bits and the later qubits; the closing step forms the marginal
+        // sum_rest a(x, rest) conj(a(x, rest)) (real; the finalisation reads its
+        // real part), one pairwise contraction of the tensor with its conjugate.
+        std::vector<int32_t> xs, rs;
+        bool sliced = false;
+        for (int32_t x : R.layout) {
+            const int32_t k = idx[x].kind;
+            if (k == IX_OPEN) xs.push_back(x);
+            else if (k == IX_REST) rs.push_back(x);
+            else if (k == IX_SLICE) sliced = true;
+            else return set_error(PTN_ERR_INVALID_ARG, "internal: unexpected bit in a ket-only root");
+        }
+        std::sort(xs.begin(), xs.end(), [&](int32_t u, int32_t v) { return idx[u].qubit < idx[v].qubit; });
+        if ((int)rs.size() > kMaxSum)
+            return set_error(PTN_ERR_TOO_LARGE, "ket-only block sums %d later qubits (max %d)", (int)rs.size(), kMaxSum);
+        const int32_t cls = (R.cls == CLS_NET || sliced) ? (int32_t)CLS_NET : R.cls;
+        StepDesc st;
+        memset(&st, 0, sizeof st);
+        st.out_cls = cls;
+        st.n_out = (int32_t)xs.size();
+        st.n_sum = (int32_t)rs.size();
+        st.out_size = (int64_t)1 << xs.size();
+        TRef Rc = R;
+        Rc.conj = 1;
+        ptn_status e0 = make_op(R, cls, st.op[0]);
+        if (e0) return e0;
+        e0 = make_op(Rc, cls, st.op[1]);
+        if (e0) return e0;
+        for (size_t p = 0; p < xs.size(); p++)
+            st.out_stride[0][p] = st.out_stride[1][p] = (int64_t)1 << pos_in(R.layout, xs[p]);
+        for (size_t q = 0; q < rs.size(); q++)
+            st.sum_stride[0][q] = st.sum_stride[1][q] = (int64_t)1 << pos_in(R.layout, rs[q]);
+        BufInfo bi;
+        bi.arena = cls;
+        bi.off = arenas[cls].alloc(st.out_size);
+        bi.refs = 1;
+        const int32_t bid = (int32_t)bufs.size();
+        bufs.push_back(bi);
+        buf_step.push_back(cur_step);
+        st.out_arena = cls;
+        st.out_off = bi.off;
+        consume(R);
+        int64_t pf[2][3];
+        classify_step(st, pf, !plan->opts.simt_only);
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
+        bp.steps.push_back(st);
+        cur_step++;
+        {   // modelled cost of the closing step (the search did not see it)
+            const double inst = cls == CLS_NET ? bp.est_mult_net : bp.est_mult_traj;
+            const double macs = std::ldexp(1.0, st.n_out + st.n_sum) * inst;
+            bp.est_macs[cls] += macs;
+            bp.est_time += std::max(8.0 * macs / 2.5e12, 8.0 * (2.0 * std::ldexp(1.0, st.n_out + st.n_sum) +
+                                                              std::ldexp(1.0, st.n_out)) * inst / 3.0e12);
+        }
+        TRef rn;
+        rn.mode = OP_BUF;
+        rn.id = bid;
+        rn.conj = 0;
+        rn.cls = cls;
+        rn.layout = xs;
+        R = rn;
+    }
     ptn_status e = make_op(R, CLS_NET, bp.root.op);
     if (e) return e;
     for (int tb = 0; tb < b; tb++) bp.root.x_stride[tb] = -1;
@@ -1015,7 +1085,7 @@ static void build_block_net(const ptn_plan* plan, int n, int start, int b, bool 
     for (int q = 0; q < n; q++) {
         NetIdx& x = net.idx[cur[q]];
         x.qubit = q;
-        x.kind = q < start ? IX_SLICE : (q < start + b ? IX_OPEN : IX_TRACED);
+        x.kind = q < start ? IX_SLICE : (q < start + b ? IX_OPEN : (ket_only ? IX_REST : IX_TRACED));
     }
     int nl = (int)ket_idx.size();
     net.n_leaf_tensors = nl;
@@ -1438,7 +1508,28 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
         double D = j == 0 ? E : std::min(E * std::ldexp(1.0, start), opts.est_shots);
         D = std::max(D, E);
         BlockPlan bp;
-        ptn_status e = search_and_lower(plan, net, (int)j, start, b, E, j == 0 ? E : D, rng, bp, false);
+        ptn_status e = PTN_OK;
+        if (opts.network_form == 0) {
+            e = search_and_lower(plan, net, (int)j, start, b, E, j == 0 ? E : D, rng, bp, false);
+        } else {
+            // ket-only form (amplitudes of the block and later qubits, closing |.|^2
+            // step), alone (form 2) or against the double layer (form 1) by
+            // modelled time; either falls back to the double layer without a path
+            // (the ket-only search draws from its own stream, so the double-layer
+            // path is the one form 0 finds)
+            BlockNet knet;
+            build_block_net(plan, n, start, b, true, knet);
+            BlockPlan bk, bd;
+            std::mt19937_64 krng(rng);   // a copy: rng itself is not advanced
+            const ptn_status ek = search_and_lower(plan, knet, (int)j, start, b, E, j == 0 ? E : D, krng, bk, false);
+            ptn_status ed = PTN_ERR_TOO_LARGE;
+            if (opts.network_form == 1 || ek != PTN_OK)
+                ed = search_and_lower(plan, net, (int)j, start, b, E, j == 0 ? E : D, rng, bd, false);
+            if (ek == PTN_OK && (ed != PTN_OK || bk.est_time <= bd.est_time)) bp = std::move(bk);
+            else if (ed == PTN_OK) bp = std::move(bd);
+            else e = ed;
+            if (!e) clear_error();
+        }
         if (e) return e;
         plan->blocks.push_back(std::move(bp));
         start += b;

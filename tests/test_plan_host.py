@@ -77,12 +77,16 @@ CASES = [
 
 
 @pytest.mark.parametrize("name,make,bs", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("split", [1, 0])
-def test_lowered_plan_reproduces_oracle_marginals(name, make, bs, split):
+@pytest.mark.parametrize("split,form", [(1, 0), (0, 0), (1, 2), (0, 1)])
+def test_lowered_plan_reproduces_oracle_marginals(name, make, bs, split, form):
+    """form 0: double-layer networks; 2: ket-only networks (amplitudes of the
+    block and later qubits, then the closing |.|^2 step); 1: the cheaper of the
+    two per block."""
     rng = np.random.default_rng(zlib.crc32(name.encode()))
     circ = make(rng)
     n = circ.n_qubits
-    plan = ptn.ptn_plan_path(circ, bs, hypersamples=8, split_gates=split, est_traj=4, est_shots=64)
+    plan = ptn.ptn_plan_path(circ, bs, hypersamples=8, split_gates=split, est_traj=4, est_shots=64,
+                             network_form=form)
     desc = plan.describe(detail=1)
     kraus, _ = pts.presample(circ, 4, seed=17)
     blocks = plan.blocks

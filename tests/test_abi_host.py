@@ -60,3 +60,18 @@ def test_plan_options_and_status_strings():
     plan = ptn.ptn_plan_path(circ, [4], hypersamples=2)
     d = plan.describe(detail=2)           # builds the gradient plan on the host
     assert d["expval"]["n_params"] == 0 and d["expval"]["pleaves"] == []
+
+
+def test_header_is_plain_c():
+    """include/ptn.h compiles as C99 (and C++17): the boundary uses no C++ types."""
+    import os
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    header = os.path.join(root, "include", "ptn.h")
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    r = subprocess.run([cc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Werror", header],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

@@ -1223,6 +1223,8 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
     if (opts.hypersamples <= 0) opts.hypersamples = 100;
     if (opts.est_traj <= 0) opts.est_traj = 1024;
     if (opts.est_shots <= 0) opts.est_shots = 1e6;
+    if (opts.network_form < 0 || opts.network_form > 2)
+        return set_error(PTN_ERR_INVALID_ARG, "network_form must be 0, 1 or 2");
     plan->opts = opts;
     plan->mem_cap = opts.mem_cap_bytes;
 

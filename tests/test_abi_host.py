@@ -75,3 +75,10 @@ def test_header_is_plain_c():
     r = subprocess.run([cc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Werror", header],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_plan_rejects_unknown_network_form():
+    circ = W.attach_noise(W.brickwork_1d(4, 2, np.random.default_rng(0)), [W.depolarizing_kraus(0.1)])
+    with pytest.raises(ptn.PtnError) as e:
+        ptn.ptn_plan_path(circ, [4], hypersamples=2, network_form=3)
+    assert e.value.status == INVALID

@@ -224,7 +224,8 @@ ptn_status ptn_contract_batch(const ptn_plan* plan, const ptn_traj* traj, int32_
  * and picks the smallest x with floor(a T / 2^64) < C[x].  The distinct
  * outcomes are written, in canonical order (parents in order, x ascending), as
  * children (traj, prefix | x << start, count) to the device arrays child_*
- * (capacity child_cap >= sum_n min(count_n, 2^b)).  Parents must be grouped by
+ * (capacity child_cap >= sum_n min(count_n, 2^b); a smaller capacity returns
+ * PTN_ERR_INVALID_ARG and writes no child).  Parents must be grouped by
  * trajectory.  Writes the number of children to *n_child (host); synchronises
  * the stream. */
 ptn_status ptn_sample_block(const float* marg, int32_t b, int32_t start,
@@ -247,6 +248,8 @@ ptn_status ptn_sample_block(const float* marg, int32_t b, int32_t start,
  *    (up to the largest index used), 12 per child slot (child_cap) plus scan
  *    space; a call that needs more than 32 MiB returns PTN_ERR_TOO_LARGE with
  *    the sizes in the error text, before launching any sampling work.
+ *  - The array used is the current device's; the stream must belong to that
+ *    device (PTN_ERR_INVALID_ARG otherwise).
  *  - The first call on a device looks up the array's device address (with
  *    that device current); make that first call before any stream capture.
  *  - All calls share the array, whatever their stream: calls that overlap on

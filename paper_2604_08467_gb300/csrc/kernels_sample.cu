@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(256) k_sample_parents(const float* __restrict_
                                                         const int32_t* __restrict__ traj,
                                                         const int64_t* __restrict__ count,
                                                         const int64_t* __restrict__ rank0,
-                                                        const int64_t* __restrict__ tmp_off, uint2 key,
-                                                        uint32_t tagw, int32_t* __restrict__ tmp_x,
+                                                        const int64_t* __restrict__ tmp_off, int64_t tmp_cap,
+                                                        uint2 key, uint32_t tagw, int32_t* __restrict__ tmp_x,
                                                         int64_t* __restrict__ tmp_c, int64_t* __restrict__ ndist) {
     extern __shared__ unsigned char smem[];
     const int64_t nb = (int64_t)1 << b;
@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(256) k_sample_parents(const float* __restrict_
         const unsigned int h = x < nb ? hist[x] : 0u;
         int64_t tot;
         const int64_t ex = block_exclusive_scan(h ? 1 : 0, sh, &tot);
-        if (h) {
+        // slots past tmp_cap are never written; the host reports the shortfall
+        if (h && dst + wpos + ex < tmp_cap) {
             tmp_x[dst + wpos + ex] = (int32_t)x;
             tmp_c[dst + wpos + ex] = (int64_t)h;
         }
@@ -451,21 +452,27 @@ int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptr
     if (smem > 32 * 1024) cudaFuncSetAttribute(k_sample_parents, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     StatScope st_sp(K_SAMPLE_PARENTS, s, (double)n_parent * ((double)((int64_t)1 << b) * 4.0 + 40.0), 0.0);
-    k_sample_parents<<<(unsigned)n_parent, 256, smem, s>>>(marg, b, ptraj, pcount, sc.rank0, sc.tmp_off, key,
-                                                           philox_tag(STREAM_SAMPLE, circuit, block), sc.tmp_x,
+    k_sample_parents<<<(unsigned)n_parent, 256, smem, s>>>(marg, b, ptraj, pcount, sc.rank0, sc.tmp_off, child_cap,
+                                                           key, philox_tag(STREAM_SAMPLE, circuit, block), sc.tmp_x,
                                                            sc.tmp_c, sc.ndist);
     launch_exclusive_scan(sc.ndist, sc.out_off, n_parent, sc.scan_tmp, s);
     cudaMemcpyAsync(host_tmp, sc.out_off + n_parent - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(host_tmp + 1, sc.ndist + n_parent - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(host_tmp + 2, sc.tmp_off + n_parent - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(host_tmp + 3, sc.cap + n_parent - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         *st = set_error(PTN_ERR_CUDA, "sampling: %s", cudaGetErrorString(cudaGetLastError()));
         return -1;
     }
-    const int64_t n_child = host_tmp[0] + host_tmp[1];
-    if (n_child > child_cap) {
-        *st = set_error(PTN_ERR_INVALID_ARG, "child capacity %lld < %lld", (long long)child_cap, (long long)n_child);
+    // the temporary child slots (sum of min(count, 2^b)) share the caller's
+    // capacity; the kernel skipped slots beyond it, so the result is incomplete
+    const int64_t slots = host_tmp[2] + host_tmp[3];
+    if (slots > child_cap) {
+        *st = set_error(PTN_ERR_INVALID_ARG, "child capacity %lld < sum of min(count, 2^b) = %lld",
+                        (long long)child_cap, (long long)slots);
         return -1;
     }
+    const int64_t n_child = host_tmp[0] + host_tmp[1];
     StatScope st_em(K_EMIT, s, (double)n_child * 32.0, 0.0);
     k_emit_children<<<grid_for(n_parent * 32, 256, 1 << 30), 256, 0, s>>>(ptraj, pprefix, sc.tmp_off, sc.ndist,
                                                                           sc.out_off, sc.tmp_x, sc.tmp_c, start,

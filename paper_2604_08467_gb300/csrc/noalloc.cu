@@ -11,9 +11,13 @@
 // until the process exits.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace ptn {
+void clear_error();
 namespace {
 
 // Scratch shared by every call (any stream) on a device.
@@ -21,9 +25,27 @@ constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of the array, looked up once per device with that device
-// current (in host code the symbol name only stands in for it).
+// current (in host code the symbol name only stands in for it).  The lookup
+// runs under a mutex; later calls read the published pointer atomically.
 constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {};
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
+std::mutex g_scratch_mutex;
+
+cudaError_t scratch_address(int dev, void** out) {
+    void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lk(g_scratch_mutex);
+        p = g_scratch_ptr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return e;
+            if (!p) return cudaErrorInvalidSymbol;
+            g_scratch_ptr[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
+    return cudaSuccess;
+}
 
 // Checks that parents are grouped by (non-decreasing) trajectory and finds the
 // largest trajectory index; out[0] = max index, out[1] = 1 if unsorted or negative.
@@ -48,6 +70,7 @@ extern "C" ptn_status ptn_sample_block_noalloc(const float* marg, int32_t b, int
                                                int32_t circuit_id, int32_t block, int32_t* child_traj,
                                                uint64_t* child_prefix, int64_t* child_count, int64_t child_cap,
                                                int64_t* n_child, ptn_stream stream) {
+    clear_error();
     if (!n_child || b < 1 || b > 14 || start < 0 || start + b > 64 || n_parent < 0 || child_cap < 0)
         return set_error(PTN_ERR_INVALID_ARG, "bad sampling arguments (b must be 1..14)");
     *n_child = 0;
@@ -55,18 +78,22 @@ extern "C" ptn_status ptn_sample_block_noalloc(const float* marg, int32_t b, int
     if (!marg || !parent_traj || !parent_prefix || !parent_count || !child_traj || !child_prefix || !child_count)
         return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    int dev = 0;
+    // The array used is the one of the current device, which must also be the
+    // device the stream belongs to.
+    int dev = 0, sdev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return set_error(PTN_ERR_UNSUPPORTED, "device index %d", dev);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return set_error(PTN_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
+    if (s) {
+        e = cudaStreamGetDevice(s, &sdev);
+        if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "cudaStreamGetDevice: %s", cudaGetErrorString(e));
+        if (sdev != dev)
+            return set_error(PTN_ERR_INVALID_ARG, "stream belongs to device %d but device %d is current", sdev, dev);
     }
-    unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    void* scratch = nullptr;
+    e = scratch_address(dev, &scratch);
+    if (e != cudaSuccess) return set_error(PTN_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    unsigned char* base = static_cast<unsigned char*>(scratch);
 
     // Layout of the scratch for this call; everything must fit the fixed array.
     const size_t np = sizeof(int64_t) * (size_t)n_parent;
@@ -121,7 +148,7 @@ extern "C" ptn_status ptn_sample_block_noalloc(const float* marg, int32_t b, int
     sc.tmp_x = reinterpret_cast<int32_t*>(base + o_tmp_x);
     sc.tmp_c = reinterpret_cast<int64_t*>(base + o_tmp_c);
     sc.scan_tmp = reinterpret_cast<int64_t*>(base + o_scan);
-    int64_t host_tmp[2] = {0, 0};   // sizes read back by the sampling step
+    int64_t host_tmp[4] = {0, 0, 0, 0};   // sizes read back by the sampling step
     ptn_status st;
     const int64_t nc = run_sample_block(marg, b, start, parent_traj, parent_prefix, parent_count, n_parent, n_traj,
                                         seed, circuit_id, block, child_traj, child_prefix, child_count, child_cap, sc,

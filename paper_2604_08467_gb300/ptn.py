@@ -315,13 +315,27 @@ def ptn_contract_batch(plan, traj, block, net_traj, net_prefix, marg_out, Z_out,
                                     precision, _ptr(marg_out), _ptr(Z_out), _stream(stream)))
 
 
+def _sample_block_sizes(marg, b, parent_traj, parent_prefix, parent_count, child_traj, child_prefix, child_count):
+    """(n_parent, child_cap) of a sampling call, checked against every buffer
+    the library reads or writes (device buffers are not bounds-checked)."""
+    n = int(parent_traj.numel())
+    if int(parent_prefix.numel()) < n or int(parent_count.numel()) < n:
+        raise ValueError("parent_prefix / parent_count shorter than parent_traj")
+    if int(marg.numel()) != n << b:
+        raise ValueError(f"marg has {int(marg.numel())} entries, expected n_parent * 2^b = {n << b}")
+    cap = min(int(child_traj.numel()), int(child_prefix.numel()), int(child_count.numel()))
+    return n, cap
+
+
 def ptn_sample_block(marg, b, start, parent_traj, parent_prefix, parent_count, seed, circuit_id, block,
                      child_traj, child_prefix, child_count, stream=None):
+    n, cap = _sample_block_sizes(marg, b, parent_traj, parent_prefix, parent_count, child_traj, child_prefix,
+                                 child_count)
     nc = C.c_int64(0)
     _check(lib().ptn_sample_block(_ptr(marg), b, start, _ptr(parent_traj), _ptr(parent_prefix),
-                                  _ptr(parent_count), int(parent_traj.numel()), seed, circuit_id, block,
+                                  _ptr(parent_count), n, seed, circuit_id, block,
                                   _ptr(child_traj), _ptr(child_prefix), _ptr(child_count),
-                                  int(child_traj.numel()), C.byref(nc), _stream(stream)))
+                                  cap, C.byref(nc), _stream(stream)))
     return nc.value
 
 
@@ -329,11 +343,13 @@ def ptn_sample_block_noalloc(marg, b, start, parent_traj, parent_prefix, parent_
                              child_traj, child_prefix, child_count, stream=None):
     """ptn_sample_block with its scratch in the library's fixed static device
     array (no allocation during the call; see include/ptn.h)."""
+    n, cap = _sample_block_sizes(marg, b, parent_traj, parent_prefix, parent_count, child_traj, child_prefix,
+                                 child_count)
     nc = C.c_int64(0)
     _check(lib().ptn_sample_block_noalloc(_ptr(marg), b, start, _ptr(parent_traj), _ptr(parent_prefix),
-                                          _ptr(parent_count), int(parent_traj.numel()), seed, circuit_id, block,
+                                          _ptr(parent_count), n, seed, circuit_id, block,
                                           _ptr(child_traj), _ptr(child_prefix), _ptr(child_count),
-                                          int(child_traj.numel()), C.byref(nc), _stream(stream)))
+                                          cap, C.byref(nc), _stream(stream)))
     return nc.value
 
 

@@ -220,6 +220,34 @@ def test_sample_block_degenerate_rows():
     assert cp[ct == 2].tolist() == [15]
 
 
+def test_sample_block_rejects_short_child_capacity():
+    """A child capacity below sum_n min(count_n, 2^b) is an error (nothing is
+    written past the caller's buffers); a capacity equal to it succeeds."""
+    b, n = 6, 40
+    rows = W.synthetic_marginals(n, b, seed=5)
+    counts = np.full(n, 100)
+    need = int(np.minimum(counts, 1 << b).sum())
+    dev = DEV
+    args = (torch.tensor(rows, dtype=torch.float32, device=dev), b, 0,
+            torch.arange(n, dtype=torch.int32, device=dev), torch.zeros(n, dtype=torch.int64, device=dev),
+            torch.tensor(counts, dtype=torch.int64, device=dev), 3, 0, 0)
+    for fn in (ptn.ptn_sample_block, ptn.ptn_sample_block_noalloc):
+        guard = 4096
+        ct = torch.full((need - 1 + guard,), -7, dtype=torch.int32, device=dev)
+        cp = torch.full((need - 1 + guard,), -7, dtype=torch.int64, device=dev)
+        cc = torch.full((need - 1 + guard,), -7, dtype=torch.int64, device=dev)
+        with pytest.raises(ptn.PtnError) as e:
+            fn(*args, ct[:need - 1], cp[:need - 1], cc[:need - 1])
+        assert e.value.status == 1 and "capacity" in str(e.value)
+        torch.cuda.synchronize()
+        assert bool((ct[need - 1:] == -7).all()) and bool((cc[need - 1:] == -7).all())
+        ct2 = torch.empty(need, dtype=torch.int32, device=dev)
+        cp2 = torch.empty(need, dtype=torch.int64, device=dev)
+        cc2 = torch.empty(need, dtype=torch.int64, device=dev)
+        nc = fn(*args, ct2, cp2, cc2)
+        assert int(cc2[:nc].sum()) == counts.sum()
+
+
 def test_allocate_shots_bit_exact():
     rng = np.random.default_rng(12)
     for n, total in [(4096, 1_000_000), (1, 10), (37, 12345)]:

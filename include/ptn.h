@@ -388,6 +388,18 @@ ptn_status ptn_expval_grad(const ptn_plan* plan, const ptn_traj* traj, const ptn
                            const double* theta, int32_t n_theta, double* value_out, double* grad_out,
                            ptn_stream stream);
 
+/* Amplitudes of the trajectory states psi_i (the ket network of the whole
+ * circuit with every sampled Kraus operator merged into its gate, Sec. III-A,
+ * contracted along the path ptn_expval_grad uses): for the distinct error sets
+ * i = traj0 .. traj0 + n_traj - 1 of `traj`,
+ *   amp_out[(i - traj0) * 2^n + x] = <x|psi_i>,  bit q of x = qubit q,
+ * unnormalised (|psi_i|^2 = w_i, the trajectory weight).  amp_out: device
+ * complex64 (re, im float pairs), n_traj * 2^n entries.  precision selects the
+ * tensor-core operand split (PTN_PREC_*), as for the sampling contractions.
+ * Needs n_qubits <= 24.  Synchronises the stream. */
+ptn_status ptn_trajectory_amplitudes(const ptn_plan* plan, const ptn_traj* traj, int64_t traj0, int64_t n_traj,
+                                     int32_t precision, float* amp_out, ptn_stream stream);
+
 /* ----------------------------------------------------------- statistics -- */
 
 /* Per-kernel launch statistics (instrumentation for roofline reporting).

@@ -12,12 +12,12 @@ from .statevector import apply_gate
 
 
 def _apply_left(rho, n, qubits, m):
-    # columns of rho are vectors: apply to each column
+    """M acting on the row index of rho, i.e. on every column of rho.  The
+    flattened matrix rho[r, c] -> r * 2^n + c is a 2n-qubit vector whose
+    qubit q + n is the row's qubit q, so this is one gate application on it
+    (the same sums as applying M to each column in turn)."""
     d = 1 << n
-    out = np.empty_like(rho)
-    for c in range(d):
-        out[:, c] = apply_gate(rho[:, c], n, qubits, m)
-    return out
+    return apply_gate(rho.reshape(-1), 2 * n, [q + n for q in qubits], m).reshape(d, d)
 
 
 def apply_unitary(rho, n, qubits, m):

@@ -17,13 +17,18 @@ shifted, because F is a trigonometric polynomial of degree one in its angle
 (the state is linear in R_P(t) = cos(t/2) I - i sin(t/2) P and F quadratic in
 the state).  This holds for unnormalised trajectory states and for the density
 matrix alike.  Central finite differences are provided as an independent
-second method.
+second method, and reverse-mode (adjoint) forms on the state vector and on
+the density matrix as a third: with the gate sequence E_L ... E_1, the
+derivative of <O> with respect to the angle of gate l is the overlap of the
+backward-propagated observable (adjoint state, or Heisenberg-evolved O for
+the density matrix) after gate l with the derivative of gate l applied to the
+forward state before it; d R_P(t) / dt = R_P(t) (-i P / 2).
 """
 import copy
 
 import numpy as np
 
-from .densmat import apply_channel, apply_unitary
+from .densmat import _apply_left, apply_channel, apply_unitary
 from .pts import gate_sites, merged_gate
 from .statevector import apply_gate
 
@@ -149,3 +154,124 @@ def density_grad_shift(circ, terms, theta):
         grad[p] += 0.5 * (density_expval(circ, terms, theta, (l, np.pi / 2)) -
                           density_expval(circ, terms, theta, (l, -np.pi / 2)))
     return grad
+
+
+# ------------------------------------------------------- reverse mode -----
+
+def trajectory_grad_adjoint(circ, choices, w, n_params):
+    """(<psi|O|psi>, d<psi|O|psi>/dtheta) for one unnormalised trajectory state
+    by the adjoint method: forward states before every rotation are kept, the
+    adjoint lambda = O psi is carried back through U_l^dagger, and rotation l
+    (merged tensor U_l = N_l R_P(t), N_l its noise operators) contributes
+    2 Re <lambda_l| U_l (-i P / 2) |phi_{l-1}>."""
+    n = circ.n_qubits
+    sg = gate_sites(circ)
+    mats = [merged_gate(circ, l, choices, sg) for l in range(len(circ.gates))]
+    phi = np.zeros(1 << n, dtype=np.complex128)
+    phi[0] = 1.0
+    before = {}
+    for l, g in enumerate(circ.gates):
+        if g.param_kind in (PARAM_RY, PARAM_RZ):
+            before[l] = phi
+        phi = apply_gate(phi, n, g.qubits, mats[l])
+    lam = w * phi
+    value = float(np.real(np.vdot(phi, lam)))
+    grad = np.zeros(n_params)
+    for l in range(len(circ.gates) - 1, -1, -1):
+        g = circ.gates[l]
+        if l in before:
+            dU = mats[l] @ (-0.5j * _PAULI[g.param_kind])
+            grad[g.param_index] += 2.0 * np.real(np.vdot(lam, apply_gate(before[l], n, g.qubits, dU)))
+        lam = apply_gate(lam, n, g.qubits, mats[l].conj().T)
+    return value, grad
+
+
+def expval_grad_adjoint(circ, kraus_rows, mult, terms, theta):
+    """(F, dF/dtheta) over the error sets kraus_rows with multiplicities mult,
+    every entry of the gradient, by the adjoint method."""
+    c = at_angles(circ, theta)
+    w = pauli_weights(c.n_qubits, terms)
+    mult = np.asarray(mult, dtype=np.float64)
+    vals, grads = [], []
+    for row in kraus_rows:
+        v, g = trajectory_grad_adjoint(c, row, w, len(theta))
+        vals.append(v)
+        grads.append(g)
+    return (float(np.sum(mult * np.array(vals)) / np.sum(mult)),
+            (mult[:, None] * np.array(grads)).sum(axis=0) / np.sum(mult))
+
+
+def _row_col(rho, n, q_row, q_col, m):
+    """Apply the 4x4 matrix m (index order (o_row, o_col, i_row, i_col)) to
+    the row qubit q_row and column qubit q_col of rho, seen as the 2n-qubit
+    vector rho[r, c] -> r * 2^n + c (row qubit q is vector qubit q + n)."""
+    d = 1 << n
+    return apply_gate(rho.reshape(-1), 2 * n, [q_row + n, q_col], m).reshape(d, d)
+
+
+def _unitary_super(U):
+    """U rho U^dagger as a 4x4 (o_row, o_col, i_row, i_col) matrix on one qubit."""
+    U = np.asarray(U)
+    return np.kron(U, U.conj())
+
+
+def _channel_super(kraus, adjoint=False):
+    """sum_k K rho K^dagger (or, adjoint=True, the Heisenberg map
+    sum_k K^dagger Lambda K) as a 4x4 matrix on one qubit."""
+    S = np.zeros((4, 4), dtype=np.complex128)
+    for K in kraus:
+        K = np.asarray(K, dtype=np.complex128)
+        S += np.kron(K.conj().T, K.T) if adjoint else np.kron(K, K.conj())
+    return S
+
+
+def _apply_unitary_rho(rho, n, qubits, U):
+    """U rho U^dagger for a gate on one or two qubits."""
+    U = np.asarray(U)
+    if len(qubits) == 1:
+        return _row_col(rho, n, qubits[0], qubits[0], _unitary_super(U))
+    x = _apply_left(rho, n, qubits, U)
+    d = 1 << n
+    return apply_gate(x.reshape(-1), 2 * n, list(qubits), U.conj()).reshape(d, d)
+
+
+def density_grad_adjoint(circ, terms, theta):
+    """(Tr(O rho), dTr(O rho)/dtheta) for the exact noisy evolution by reverse
+    mode on the density matrix: rho before every rotation is kept, Lambda = O
+    is evolved back through the adjoint channels and unitaries, and rotation
+    l contributes 2 Re Tr(Lambda_l dU rho_{l-1} U^dagger), dU = U (-i P / 2).
+    One-qubit gates and channels act as 4x4 superoperators on the (row,
+    column) qubit pair, which is the same sum as their Kraus form."""
+    c = at_angles(circ, theta)
+    n = c.n_qubits
+    d = 1 << n
+    rho = np.zeros((d, d), dtype=np.complex128)
+    rho[0, 0] = 1.0
+    sites_of = gate_sites(c)
+    chan = [_channel_super(ch.kraus) for ch in c.channels]
+    chan_adj = [_channel_super(ch.kraus, adjoint=True) for ch in c.channels]
+    before = {}
+    for l, g in enumerate(c.gates):
+        if g.param_kind in (PARAM_RY, PARAM_RZ):
+            before[l] = rho
+        rho = _apply_unitary_rho(rho, n, g.qubits, g.matrix)
+        for s in sites_of[l]:
+            site = c.sites[s]
+            rho = _row_col(rho, n, site.qubit, site.qubit, chan[site.channel])
+    wdiag = pauli_weights(n, terms)
+    value = float(np.real(np.sum(np.diag(rho) * wdiag)))
+    lam = np.diag(wdiag).astype(np.complex128)
+    grad = np.zeros(len(theta))
+    for l in range(len(c.gates) - 1, -1, -1):
+        g = c.gates[l]
+        for s in reversed(sites_of[l]):
+            site = c.sites[s]
+            lam = _row_col(lam, n, site.qubit, site.qubit, chan_adj[site.channel])
+        if l in before:
+            U = np.asarray(g.matrix)
+            dU = U @ (-0.5j * _PAULI[g.param_kind])
+            # dU rho U^dagger on the gate's (row, column) qubit
+            x = _row_col(before[l], n, g.qubits[0], g.qubits[0], np.kron(dU, U.conj()))
+            grad[g.param_index] += 2.0 * np.real(np.sum(lam.T * x))
+        lam = _apply_unitary_rho(lam, n, g.qubits, np.asarray(g.matrix).conj().T)
+    return value, grad

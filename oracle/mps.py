@@ -51,7 +51,7 @@ class MPS:
         r = np.ones((1, 1), dtype=np.complex128)
         for q in range(self.n - 1, start - 1, -1):
             a = self.t[q]
-            r = np.einsum("lir,rs,mis->lm", a, r, a.conj())
+            r = sum(a[:, i, :] @ r @ a[:, i, :].conj().T for i in range(2))
         return r
 
     def block_marginal(self, start, b, prefix, renv=None):
@@ -64,6 +64,30 @@ class MPS:
             v = np.concatenate([v @ a[:, 0, :], v @ a[:, 1, :]], axis=0)
         r = self.right_env(start + b) if renv is None else renv
         return np.real(np.einsum("xa,ab,xb->x", v, r, v.conj()))
+
+
+    def left_env(self, stop):
+        """Trace of qubits 0..stop-1: L[a, a'] (chi x chi, ket index first)."""
+        v = np.ones((1, 1), dtype=np.complex128)
+        for q in range(stop):
+            a = self.t[q]
+            v = sum(a[:, i, :].T @ v @ a[:, i, :].conj() for i in range(2))
+        return v
+
+    def window_marginal(self, start, b):
+        """p(x) for the b qubits start..start+b-1 with every other qubit
+        traced (bit q of x = qubit start+q): sum over a, a', c, c' of
+        L[a, a'] P_x[a, c] R[c, c'] conj(P_x[a', c']), P_x the product of the
+        window's site matrices for outcome x."""
+        L = self.left_env(start)
+        R = self.right_env(start + b)
+        out = np.empty(1 << b)
+        for x in range(1 << b):
+            P = np.eye(self.t[start].shape[0], dtype=np.complex128)
+            for k in range(b):
+                P = P @ self.t[start + k][:, (x >> k) & 1, :]
+            out[x] = np.real(np.einsum("ac,ab,bd,cd->", L, P, R, P.conj()))
+        return out
 
 
 def trajectory_mps(circ, choices):

@@ -80,6 +80,8 @@ struct ObsTerm {
 // w(x) = sum_t coeff_t (-1)^popc(x & zmask_t).
 void launch_observable(const RootRef* d_root, const ChunkCtx& ctx, int n, const ObsTerm* terms, int n_terms,
                        int64_t root_adj_off, int64_t traj0, double* F, cudaStream_t s);
+// amp[t][x] = psi_t(x), bit q of x = qubit q, for the n_traj trajectories of the chunk
+void launch_amplitudes(const RootRef* d_root, const ChunkCtx& ctx, int n, int64_t n_traj, float2* amp, cudaStream_t s);
 // partial[(traj0 + i) * n_params + param] += 2 Re sum_e G_leaf[e] dLeaf[e]
 void launch_leaf_grad(const ChunkCtx& ctx, const ParamLeaf* d_pl, int n_pl, const float2* dvt, int64_t traj0,
                       int64_t n_traj, int n_params, double* partial, cudaStream_t s);

@@ -118,6 +118,29 @@ __global__ void __launch_bounds__(256) k_expval_reduce(const int64_t* __restrict
     }
 }
 
+// amp[t][x] = psi_t(x) in qubit order (bit q of x = qubit q); one block per trajectory
+__global__ void __launch_bounds__(256) k_amplitudes(const RootRef* __restrict__ groot, ChunkCtx c, int n,
+                                                    float2* __restrict__ amp) {
+    __shared__ __align__(16) RootRef r;
+    {
+        const int4* src = reinterpret_cast<const int4*>(groot);
+        int4* dst = reinterpret_cast<int4*>(&r);
+        for (int i = threadIdx.x; i < (int)(sizeof(RootRef) / sizeof(int4)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int64_t t = blockIdx.x;
+    const int64_t size = r.op.inst_size;
+    const int64_t inst = r.op.cls == CLS_CONST ? 0 : t;
+    const float2* psi = c.arena[r.op.arena] + r.op.arena_off * c.arena_inst[r.op.arena] + inst * size;
+    const int64_t nx = (int64_t)1 << n;
+    for (int64_t x = threadIdx.x; x < nx; x += blockDim.x) {
+        int64_t off = 0;
+        for (int q = 0; q < n; q++)
+            if ((x >> q) & 1) off += r.x_stride[q];
+        amp[t * nx + x] = psi[off];
+    }
+}
+
 }  // namespace
 
 void launch_observable(const RootRef* d_root, const ChunkCtx& ctx, int n, const ObsTerm* terms, int n_terms,
@@ -126,6 +149,12 @@ void launch_observable(const RootRef* d_root, const ChunkCtx& ctx, int n, const 
     if (nt <= 0) return;
     StatScope sc(K_EXPVAL, s, (double)nt * (double)(1ll << n) * 16.0, 0.0);
     k_observable<<<(unsigned)nt, 256, 0, s>>>(d_root, ctx, n, terms, n_terms, root_adj_off, traj0, F);
+}
+
+void launch_amplitudes(const RootRef* d_root, const ChunkCtx& ctx, int n, int64_t n_traj, float2* amp, cudaStream_t s) {
+    if (n_traj <= 0) return;
+    StatScope sc(K_EXPVAL, s, (double)n_traj * (double)(1ll << n) * 16.0, 0.0);
+    k_amplitudes<<<(unsigned)n_traj, 256, 0, s>>>(d_root, ctx, n, amp);
 }
 
 void launch_leaf_grad(const ChunkCtx& ctx, const ParamLeaf* d_pl, int n_pl, const float2* dvt, int64_t traj0,

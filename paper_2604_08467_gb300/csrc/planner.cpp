@@ -1527,8 +1527,12 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
             ptn_status ed = PTN_ERR_TOO_LARGE;
             if (opts.network_form == 1 || ek != PTN_OK)
                 ed = search_and_lower(plan, net, (int)j, start, b, E, j == 0 ? E : D, rng, bd, false);
-            if (ek == PTN_OK && (ed != PTN_OK || bk.est_time <= bd.est_time)) bp = std::move(bk);
-            else if (ed == PTN_OK) bp = std::move(bd);
+            if (ek == PTN_OK && (ed != PTN_OK || bk.est_time <= bd.est_time)) {
+                bp = std::move(bk);
+                bp.ket_only = 1;
+            } else if (ed == PTN_OK) {
+                bp = std::move(bd);
+            }
             else e = ed;
             if (!e) clear_error();
         }
@@ -1608,11 +1612,11 @@ std::string describe_plan(const ptn_plan* p, int detail) {
             maxout = std::max<int64_t>(maxout, st.n_out);
         }
         snprintf(buf, sizeof buf,
-                 "%s{\"start\":%d,\"b\":%d,\"n_gemm\":%d,\"n_steps\":%zu,\"steps_const\":%d,\"steps_traj\":%d,\"steps_net\":%d,"
+                 "%s{\"start\":%d,\"b\":%d,\"ket_only\":%d,\"n_gemm\":%d,\"n_steps\":%zu,\"steps_const\":%d,\"steps_traj\":%d,\"steps_net\":%d,"
                  "\"max_out_bits\":%lld,\"arena_const\":%lld,\"arena_traj\":%lld,\"arena_net\":%lld,"
                  "\"macs_const\":%.6e,\"macs_traj\":%.6e,\"macs_net\":%.6e,\"bytes_traj\":%.6e,\"bytes_net\":%.6e,"
                  "\"est_time\":%.6e,\"mult_traj\":%.1f,\"mult_net\":%.1f",
-                 j ? "," : "", b.start, b.b, n_gemm, b.steps.size(), cnt[0], cnt[1], cnt[2], (long long)maxout,
+                 j ? "," : "", b.start, b.b, b.ket_only, n_gemm, b.steps.size(), cnt[0], cnt[1], cnt[2], (long long)maxout,
                  (long long)b.arena_peak[0], (long long)b.arena_peak[1], (long long)b.arena_peak[2], b.est_macs[0],
                  b.est_macs[1], b.est_macs[2], b.est_bytes[1], b.est_bytes[2], b.est_time, b.est_mult_traj,
                  b.est_mult_net);

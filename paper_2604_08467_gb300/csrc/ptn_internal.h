@@ -106,6 +106,7 @@ struct RootRef {             // where the block's final tensor lives
 
 struct BlockPlan {
     int32_t start = 0, b = 0;
+    int32_t ket_only = 0;                // sampling block lowered in the ket-only network form
     std::vector<StepDesc> steps;
     RootRef root;
     int64_t arena_peak[N_ARENAS] = {0, 0, 0, 0, 0};   // elements per instance, per arena

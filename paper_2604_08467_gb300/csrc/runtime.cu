@@ -636,6 +636,116 @@ ptn_status ptn_contract_batch(const ptn_plan* plan, const ptn_traj* traj, int32_
                           (cudaStream_t)stream);
 }
 
+}  // extern "C"
+
+namespace {
+// Device copies of the whole-circuit ket plan (forward steps, reversed steps,
+// root, parametrised leaves), made once per plan.
+ptn_status upload_expval_plan(const BlockPlan& bp, PlanWorkspace* ws) {
+    if (ws->ev_steps.p) return PTN_OK;
+    ptn_status e;
+    if ((e = ws->ev_steps.grow(sizeof(StepDesc) * std::max<size_t>(bp.steps.size(), 1))) ||
+        (e = ws->ev_bwd.grow(sizeof(StepDesc) * std::max<size_t>(bp.bwd.size(), 1))) ||
+        (e = ws->ev_root.grow(sizeof(RootRef))) ||
+        (e = ws->ev_pl.grow(sizeof(ParamLeaf) * std::max<size_t>(bp.pleaves.size(), 1))) ||
+        (e = ws->ev_dvt.grow(sizeof(float2) * std::max<int64_t>(bp.dvt_size, 1))))
+        return e;
+    PTN_CUDA(cudaMemcpy(ws->ev_steps.p, bp.steps.data(), sizeof(StepDesc) * bp.steps.size(), cudaMemcpyHostToDevice));
+    if (!bp.bwd.empty())
+        PTN_CUDA(cudaMemcpy(ws->ev_bwd.p, bp.bwd.data(), sizeof(StepDesc) * bp.bwd.size(), cudaMemcpyHostToDevice));
+    PTN_CUDA(cudaMemcpy(ws->ev_root.p, &bp.root, sizeof(RootRef), cudaMemcpyHostToDevice));
+    if (!bp.pleaves.empty())
+        PTN_CUDA(cudaMemcpy(ws->ev_pl.p, bp.pleaves.data(), sizeof(ParamLeaf) * bp.pleaves.size(),
+                            cudaMemcpyHostToDevice));
+    return PTN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ptn_status ptn_trajectory_amplitudes(const ptn_plan* cplan, const ptn_traj* traj, int64_t traj0, int64_t n_traj,
+                                     int32_t precision, float* amp_out, ptn_stream stream) {
+    clear_error();
+    if (!cplan || !traj || (n_traj > 0 && !amp_out)) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    if (traj->plan != cplan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
+    if (traj0 < 0 || n_traj < 0 || traj0 + n_traj > traj->n_unique)
+        return set_error(PTN_ERR_INVALID_ARG, "trajectory range [%lld, %lld) outside 0..%lld", (long long)traj0,
+                         (long long)(traj0 + n_traj), (long long)traj->n_unique);
+    if (precision != PTN_PREC_FP32 && precision != PTN_PREC_BF16X3 && precision != PTN_PREC_FP16X3)
+        return set_error(PTN_ERR_INVALID_ARG, "unknown precision mode %d", precision);
+    ptn_plan* plan = const_cast<ptn_plan*>(cplan);
+    ptn_status e;
+    try {
+        e = build_expval_plan(plan);
+    } catch (const std::bad_alloc&) {
+        e = set_error(PTN_ERR_OOM, "host allocation failed while planning");
+    }
+    if (e) return e;
+    if ((e = ensure_device(plan))) return e;
+    if (n_traj == 0) return PTN_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    PlanWorkspace* ws = workspace(plan);
+    const BlockPlan& bp = *plan->expval;
+    if ((e = upload_expval_plan(bp, ws))) return e;
+    const int64_t E = traj->n_unique;
+    if ((e = ws->ev_iota.grow(sizeof(int32_t) * E))) return e;
+    launch_iota_i32(ws->ev_iota.as<int32_t>(), E, s);
+    // forward steps only: the arenas of the kept intermediates, no adjoints
+    auto pk = [&](int c) { return 4.0 * (double)(bp.pack_peak[0][c] + bp.pack_peak[1][c]); };
+    const double bT = 8.0 * (double)bp.arena_peak[CLS_TRAJ] + pk(CLS_TRAJ);
+    const double bC = 8.0 * (double)bp.arena_peak[CLS_CONST] + pk(CLS_CONST);
+    const int64_t per = (int64_t)((plan->mem_cap - bC) / std::max(bT, 1.0));
+    if (per < 1) return set_error(PTN_ERR_TOO_LARGE, "one trajectory needs %.3g bytes (cap %.3g)", bT + bC, plan->mem_cap);
+    const int64_t Ec = std::min<int64_t>(per, n_traj);
+    if ((e = ws->arena[CLS_CONST].grow((size_t)(8.0 * bp.arena_peak[CLS_CONST] + 16))) ||
+        (e = ws->arena[CLS_TRAJ].grow((size_t)(8.0 * bp.arena_peak[CLS_TRAJ] * Ec + 16))) ||
+        (e = ws->err.grow(sizeof(int))) || (e = ws->h_small.grow(64)))
+        return e;
+    for (int r = 0; r < 2; r++) {
+        const double need = 4.0 * ((double)bp.pack_peak[r][CLS_CONST] + (double)bp.pack_peak[r][CLS_TRAJ] * Ec);
+        if (need > 0 && (e = ws->pack[r].grow((size_t)(need + need / 64) + 4096))) return e;
+    }
+    PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
+    GroupTable no_groups;
+    const int n = plan->n_qubits;
+    for (int64_t t0 = 0; t0 < n_traj; t0 += Ec) {
+        const int64_t nt = std::min(Ec, n_traj - t0);
+        ChunkCtx ctx;
+        ctx.vtab = reinterpret_cast<const float2*>(plan->d_var_table);
+        ctx.var_ids = traj->var_ids;
+        ctx.n_var_cols = traj->n_var_cols;
+        ctx.pad = 0;
+        ctx.chunk_traj = ws->ev_iota.as<int32_t>() + traj0 + t0;
+        ctx.net_tl = nullptr;
+        ctx.net_prefix = nullptr;
+        ctx.arena[CLS_CONST] = ws->arena[CLS_CONST].as<float2>();
+        ctx.arena[CLS_TRAJ] = ws->arena[CLS_TRAJ].as<float2>();
+        ctx.arena[CLS_NET] = ctx.arena[ARENA_ADJ] = ctx.arena[ARENA_LGRAD] = nullptr;
+        ctx.arena_inst[CLS_CONST] = 1;
+        ctx.arena_inst[CLS_TRAJ] = nt;
+        ctx.arena_inst[CLS_NET] = ctx.arena_inst[ARENA_ADJ] = ctx.arena_inst[ARENA_LGRAD] = 0;
+        for (size_t k = 0; k < bp.steps.size(); k++) {
+            const StepDesc& h = bp.steps[k];
+            StepTag tag(-2, (int)k);
+            const int64_t ni = h.out_cls == CLS_CONST ? 1 : nt;
+            if (h.kind != STEP_DIRECT) {
+                if ((e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(), no_groups,
+                                          precision, s)))
+                    return e;
+            } else {
+                launch_contract_step(ws->ev_steps.as<StepDesc>() + k, h, ctx, ni, s);
+            }
+        }
+        launch_amplitudes(ws->ev_root.as<RootRef>(), ctx, n, nt, reinterpret_cast<float2*>(amp_out) + (t0 << n), s);
+    }
+    PTN_CUDA(cudaGetLastError());
+    int* herr = reinterpret_cast<int*>(ws->h_small.as<int64_t>() + 4);
+    PTN_CUDA(cudaMemcpyAsync(herr, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PTN_CUDA(cudaStreamSynchronize(s));
+    if (*herr) return set_error(PTN_ERR_TIMEOUT, "amplitudes: a tensor-core step timed out (code %d)", *herr);
+    return PTN_OK;
+}
+
 ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const ptn_pauli_sum* obs, const double* theta,
                            int32_t n_theta, double* value_out, double* grad_out, ptn_stream stream) {
     clear_error();
@@ -667,22 +777,7 @@ ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const pt
     const int n = plan->n_qubits;
     const int64_t E = traj->n_unique;
     const int np = std::max(n_theta, 1);
-    // device copies of the expectation plan (once)
-    if (!ws->ev_steps.p) {
-        if ((e = ws->ev_steps.grow(sizeof(StepDesc) * std::max<size_t>(bp.steps.size(), 1))) ||
-            (e = ws->ev_bwd.grow(sizeof(StepDesc) * std::max<size_t>(bp.bwd.size(), 1))) ||
-            (e = ws->ev_root.grow(sizeof(RootRef))) ||
-            (e = ws->ev_pl.grow(sizeof(ParamLeaf) * std::max<size_t>(bp.pleaves.size(), 1))) ||
-            (e = ws->ev_dvt.grow(sizeof(float2) * std::max<int64_t>(bp.dvt_size, 1))))
-            return e;
-        PTN_CUDA(cudaMemcpy(ws->ev_steps.p, bp.steps.data(), sizeof(StepDesc) * bp.steps.size(), cudaMemcpyHostToDevice));
-        if (!bp.bwd.empty())
-            PTN_CUDA(cudaMemcpy(ws->ev_bwd.p, bp.bwd.data(), sizeof(StepDesc) * bp.bwd.size(), cudaMemcpyHostToDevice));
-        PTN_CUDA(cudaMemcpy(ws->ev_root.p, &bp.root, sizeof(RootRef), cudaMemcpyHostToDevice));
-        if (!bp.pleaves.empty())
-            PTN_CUDA(cudaMemcpy(ws->ev_pl.p, bp.pleaves.data(), sizeof(ParamLeaf) * bp.pleaves.size(),
-                                cudaMemcpyHostToDevice));
-    }
+    if ((e = upload_expval_plan(bp, ws))) return e;
     // merged tensors of the parametrised gates at theta, and their derivatives
     {
         std::vector<float> dvt(2 * std::max<int64_t>(bp.dvt_size, 1));

@@ -116,6 +116,7 @@ _SIGS = {
     "ptn_sample_shots_batch": [C.POINTER(ptn_batch_item), C.c_int32, C.POINTER(ptn_batch_opts), C.POINTER(_P),
                                C.POINTER(C.c_int), _P],
     "ptn_expval_grad": [_P, _P, C.POINTER(ptn_pauli_sum), C.POINTER(C.c_double), C.c_int32, _P, _P, _P],
+    "ptn_trajectory_amplitudes": [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P, _P],
     "ptn_stats_enable": [C.c_int32],
     "ptn_stats_reset": [],
     "ptn_stats_read": [C.POINTER(ptn_kernel_stat), C.c_int32, C.POINTER(C.c_int32)],
@@ -418,6 +419,15 @@ def ptn_expval_grad(plan, traj, terms, theta, value_out, grad_out, stream=None):
     thp = th.ctypes.data_as(C.POINTER(C.c_double)) if th.size else None
     _check(lib().ptn_expval_grad(plan.handle, traj.handle, C.byref(obs), thp, int(th.size), _ptr(value_out),
                                  _ptr(grad_out), _stream(stream)))
+
+
+def ptn_trajectory_amplitudes(plan, traj, traj0, n_traj, amp_out, precision=PTN_PREC_FP32, stream=None):
+    """<x|psi_i> for distinct error sets traj0 .. traj0 + n_traj - 1 into the
+    device complex64 tensor amp_out of shape [n_traj, 2^n] (include/ptn.h)."""
+    if int(amp_out.numel()) != n_traj << plan.n_qubits or amp_out.element_size() != 8:
+        raise ValueError("amp_out must be complex64 with n_traj * 2^n entries")
+    _check(lib().ptn_trajectory_amplitudes(plan.handle, traj.handle, int(traj0), int(n_traj), precision,
+                                           _ptr(amp_out), _stream(stream)))
 
 
 def ptn_shots_merge(shots, n_blocks, stream=None):

@@ -3,13 +3,13 @@ circuits of different qubit counts, depths, trajectory counts and shot
 budgets from the mixed workload, run concurrently.  Every item must give
 exactly the result of its own ptn_sample_shots call (same kernels, same
 Philox counters, so bit-identical), over-budget circuits must come back as
-PTN_ERR_TOO_LARGE without stopping the others, and one item is replayed
-against the oracle."""
+PTN_ERR_TOO_LARGE without stopping the others (one item is replayed against
+the oracle in test_gpu_replay.py)."""
 import numpy as np
 import pytest
 
 import workloads as W
-from oracle import sampling, statevector as sv
+
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -95,34 +95,3 @@ def test_batch_empty_and_bad_arguments():
     p2, t2 = _prepare(cfg)
     with pytest.raises(ptn.PtnError):
         ptn.ptn_sample_shots_batch([dict(plan=p1, traj=t2, seed=1, total_shots=10)])
-
-
-def test_batch_item_against_oracle_replay():
-    """The 20-qubit item of the mixed workload, replayed by the oracle with
-    complex128 state-vector marginals: identical shots except draws that an
-    FP32-vs-FP64 marginal difference moves across a CDF boundary (rare)."""
-    cfg = _c3(["c3_58_brickwork20q_d8"])[0]
-    circ, n = cfg["circuit"], cfg["circuit"].n_qubits
-    plan = ptn.ptn_plan_path(circ, cfg["block_sizes"], hypersamples=16, est_traj=cfg["n_traj"])
-    tr = ptn.ptn_presample_trajectories(plan, cfg["seed"], cfg["n_traj"], dedup=False, circuit_id=cfg["circuit_id"])
-    (st, shots), = ptn.ptn_sample_shots_batch([dict(plan=plan, traj=tr, seed=cfg["seed"],
-                                                    total_shots=cfg["total_shots"], circuit_id=cfg["circuit_id"])])
-    assert st == 0
-    t, bits, cnt = _host(shots)
-    kraus = tr.to_torch()[0].cpu().numpy()
-    probs = [np.abs(sv.trajectory_state(circ, kraus[i])) ** 2 for i in range(cfg["n_traj"])]
-    bl = plan.blocks
-
-    def marg(j, traj, prefix):
-        start, b = bl[j]
-        return np.stack([sv.block_marginals(probs[i], n, start, b)[int(s) & ((1 << start) - 1)]
-                         for i, s in zip(traj, prefix)])
-
-    rt, rb, rc, levels, m = sampling.nbs_proportional(marg, bl, cfg["seed"], cfg["n_traj"], circuit=cfg["circuit_id"],
-                                                      total_shots=cfg["total_shots"],
-                                                      mult=np.ones(cfg["n_traj"], np.int64))
-    got = {(int(a), int(b)): int(c) for a, b, c in zip(t, bits, cnt)}
-    want = {(int(a), int(b)): int(c) for a, b, c in zip(rt, rb, rc)}
-    diff = sum(abs(got.get(k, 0) - want.get(k, 0)) for k in set(got) | set(want))
-    assert diff <= 8, diff
-    assert cnt.sum() == rc.sum() == cfg["total_shots"]

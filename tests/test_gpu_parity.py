@@ -300,34 +300,6 @@ def test_sample_shots_c1_end_to_end():
         assert _tvd(pe, pq) < 3 / np.sqrt(N)
 
 
-def test_sample_shots_matches_oracle_replay_small():
-    """On a small circuit the GPU's NBS output equals the oracle's replay
-    except where an FP32-vs-FP64 marginal difference moves a draw across a CDF
-    boundary; such differences must be rare."""
-    rng = np.random.default_rng(77)
-    circ = W.attach_noise(W.brickwork_1d(8, 5, rng), [W.depolarizing_kraus(0.05)])
-    blocks = [3, 3, 2]
-    plan = ptn.ptn_plan_path(circ, blocks, hypersamples=8, est_traj=8, est_shots=4000)
-    tr = ptn.ptn_presample_trajectories(plan, 21, 8)
-    res = ptn.ptn_sample_shots(plan, tr, 99, shots_per_traj=500)
-    t, bits, cnt = [x.cpu().numpy() for x in res.to_torch()]
-    kraus = tr.to_torch()[0].cpu().numpy()
-    probs = [np.abs(sv.trajectory_state(circ, kraus[i])) ** 2 for i in range(8)]
-    bl = plan.blocks
-
-    def marg(j, traj, prefix):
-        start, b = bl[j]
-        return np.stack([sv.block_marginals(probs[i], 8, start, b)[int(s) & ((1 << start) - 1)]
-                         for i, s in zip(traj, prefix)])
-
-    rt, rb, rc, levels, m = sampling.nbs_proportional(marg, bl, 99, 8, shots=[500] * 8)
-    got = {(int(a), int(b)): int(c) for a, b, c in zip(t, bits, cnt)}
-    want = {(int(a), int(b)): int(c) for a, b, c in zip(rt, rb, rc)}
-    diff = sum(abs(got.get(k, 0) - want.get(k, 0)) for k in set(got) | set(want))
-    assert diff <= 4        # at most a couple of shots moved across a boundary
-    assert res.nets_per_block[0] == levels[0]
-
-
 def test_sample_shots_c2_proportional_total():
     """C2 at full size: 1e6 shots over 4096 trajectories (allocation by
     multiplicity x norm), blocks of 10."""
@@ -341,6 +313,32 @@ def test_sample_shots_c2_proportional_total():
     assert res.nets_per_block[1] <= 1_000_000 and res.nets_per_block[2] >= res.nets_per_block[1]
     assert np.all(np.diff(t) >= 0)
     assert len(set(zip(t.tolist(), bits.tolist()))) == len(t)
+
+
+def test_sample_shots_c2_distribution_vs_mps_mixture():
+    """30-qubit brickwork (depth 12, depolarizing + amplitude damping) on a
+    16-trajectory subset with 10^6 shots allocated in proportion to the
+    trajectory weights: each shot is an i.i.d. draw from the mixture
+    sum_i w_i p_i / sum_i w_i, so 4-qubit window marginals of the shots must lie
+    within TVD 3/sqrt(shots) of the exact-MPS mixture (16 outcomes: expected
+    TVD about 1.5/sqrt(shots))."""
+    cfg = W.config_c2()
+    circ = cfg["circuit"]
+    plan = _plan(cfg, hyper=16)
+    E, N = 16, 1_000_000
+    tr = ptn.ptn_presample_trajectories(plan, cfg["seed"] + 17, E)
+    res = ptn.ptn_sample_shots(plan, tr, cfg["seed"] + 17, total_shots=N)
+    t, bits, cnt = [x.cpu().numpy() for x in res.to_torch()]
+    assert cnt.sum() == N
+    kraus = tr.to_torch()[0].cpu().numpy()
+    states = [mps.trajectory_mps(circ, kraus[i]) for i in range(E)]
+    bits = bits.astype(np.uint64)
+    for start in (0, 8, 18, 26):
+        key = ((bits >> np.uint64(start)) & np.uint64(15)).astype(np.int64)
+        pe = np.bincount(key, weights=cnt, minlength=16) / N
+        pq = sum(st.window_marginal(start, 4) for st in states)   # sum_i w_i p_i (unnormalised)
+        pq = pq / pq.sum()
+        assert _tvd(pe, pq) < 3 / np.sqrt(N), (start, _tvd(pe, pq))
 
 
 def test_contract_tensor_core_steps_vs_statevector():

@@ -430,3 +430,55 @@ def test_expval_enumeration_equals_density_matrix():
     g_dm = G.density_grad_shift(circ, terms, th)
     np.testing.assert_allclose(g_traj, g_dm, atol=1e-12)
     assert np.abs(g_dm).max() > 1e-2
+
+
+def test_density_row_application_equals_column_loop():
+    """The density-matrix left action (one 2n-qubit gate application) equals
+    applying the gate to each column of rho separately."""
+    from oracle import densmat
+    rng = np.random.default_rng(8)
+    n = 4
+    rho = rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16))
+    for qubits in [(0,), (3,), (1, 2), (3, 0)]:
+        m = W.haar_u2(rng) if len(qubits) == 1 else np.kron(W.haar_u2(rng), W.haar_u2(rng)) @ W.CZ
+        loop = np.stack([sv.apply_gate(rho[:, c], n, qubits, m) for c in range(16)], axis=1)
+        np.testing.assert_allclose(densmat._apply_left(rho, n, qubits, m), loop, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_adjoint_gradients_match_parameter_shift(seed):
+    """Reverse-mode gradients (state vector per trajectory, and the density
+    matrix) equal the parameter-shift rule, which is exact for rotations, on
+    small noisy ansatz circuits with shared angles and amplitude damping."""
+    from oracle import gradient as G, pts as P
+    r = np.random.default_rng(seed)
+    th = r.standard_normal(5 * 2 * 2)
+    circ = W.attach_noise(W.hea_ring(5, 2, th), [W.depolarizing_kraus(0.1), W.amplitude_damping_kraus(0.2)])
+    # a shared angle: parameter 3 also drives gate 0's rotation
+    circ.gates[0].param_index = 3
+    terms = [(0.3, 0b00011), (-0.7, 0b10100), (0.25, 0b00001)]
+    rows, _ = P.presample(circ, 6, 40 + seed)
+    mult = np.arange(1, 7)
+    v_adj, g_adj = G.expval_grad_adjoint(circ, rows, mult, terms, th)
+    g_sh = G.expval_grad_shift(circ, rows, mult, terms, th)
+    assert abs(v_adj - G.expval(circ, rows, mult, terms, th)) < 1e-12
+    np.testing.assert_allclose(g_adj, g_sh, rtol=0, atol=1e-11)
+    vd, gd = G.density_grad_adjoint(circ, terms, th)
+    assert abs(vd - G.density_expval(circ, terms, th)) < 1e-12
+    np.testing.assert_allclose(gd, G.density_grad_shift(circ, terms, th), rtol=0, atol=1e-11)
+
+
+def test_mps_window_marginal_brute_force():
+    """Marginal of a window of qubits with every other qubit traced equals the
+    brute-force sum of |psi|^2 over the other qubits' outcomes."""
+    rng = np.random.default_rng(31)
+    circ = W.attach_noise(W.brickwork_1d(8, 6, rng), [W.depolarizing_kraus(0.1), W.amplitude_damping_kraus(0.2)])
+    kraus, _ = pts.presample(circ, 3, 9)
+    for t in range(3):
+        probs = np.abs(sv.trajectory_state(circ, kraus[t])) ** 2
+        m = mps.trajectory_mps(circ, kraus[t])
+        idx = np.arange(256)
+        for start, b in [(0, 3), (2, 4), (5, 3), (0, 8), (7, 1)]:
+            key = (idx >> start) & ((1 << b) - 1)
+            want = np.bincount(key, weights=probs, minlength=1 << b)
+            np.testing.assert_allclose(m.window_marginal(start, b), want, rtol=1e-10, atol=1e-14)

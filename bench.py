@@ -13,6 +13,14 @@ outside the timed region, as the paper's throughput definition excludes it).
 Multi-GPU (torchrun): every rank runs the full workload on its own
 trajectory seeds (weak scaling, no collective on the data path); value is the
 shots of all ranks over the slowest rank's time.
+
+Timing: the headline steps run uninstrumented except for CUDA events around
+the launches of the dominant kernel class (found by a fully instrumented pass
+of two steps before the timed region), which give its live average launch
+duration for the roofline line.  Tensor-core peaks of the formats the
+contraction uses (TF32, FP16) are measured here the same way as the BF16 peak
+of MEASURED_PEAKS.json (torch.matmul 8192^3: best of 10, and back to back for
+4 s).
 """
 import argparse
 import json
@@ -40,6 +48,9 @@ PRECISIONS = {
 # tensor-core steps run three MMAs per real product (hi*hi + hi*lo + lo*hi)
 SPLIT_TERMS = 3
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# DRAM bytes (read + write) per average launch of a kernel class, from the ncu
+# captures summarised under profiles/ (null where none matches the current kernel)
+TRAFFIC = {}
 
 
 def load_peaks():
@@ -131,40 +142,140 @@ def oracle_sample_run(cfg, n_traj_sample, shots_per_traj, seed_offset=0):
     return int(cnt.sum()), time.perf_counter() - t0
 
 
-def cpu_threads():
+def _oracle_task(args):
+    """One trajectory of the oracle pipeline (run in a worker process)."""
+    k, shots_per_traj = args
+    return oracle_sample_run(W.config_c2(), 1, shots_per_traj, seed_offset=k)
+
+
+class OraclePool:
+    """Worker processes for the CPU oracle, started with 'spawn' before any
+    CUDA call, each with one BLAS thread, so that `cores` trajectories run at
+    once on `cores` host cores."""
+
+    def __init__(self, cores):
+        import multiprocessing as mp
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        for k in keys:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(cores)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.cores = cores
+
+    def run(self, n_traj, shots_per_traj, seed0):
+        """Wall time of n_traj oracle trajectories spread over the workers."""
+        t0 = time.perf_counter()
+        out = self.pool.map(_oracle_task, [(seed0 + i, shots_per_traj) for i in range(n_traj)], chunksize=1)
+        return sum(o[0] for o in out), time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def host_cores():
     try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] + [1])
+        return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
 
 
+def cpu_baseline(pool, cfg, shots_per_traj):
+    """The oracle on a bounded sample: `pool.cores` trajectories per round on
+    all worker processes (2 rounds), and one trajectory on one process."""
+    pool.run(pool.cores, shots_per_traj, 50_000)          # warm-up (imports in the workers)
+    n = 2 * pool.cores
+    shots, sec = pool.run(n, shots_per_traj, 60_000)
+    s1, t1 = pool.pool.apply(_oracle_task, ((70_000, shots_per_traj),))
+    return {"value": shots / sec, "unit": "shots/s", "cores": pool.cores, "kind": "oracle",
+            "sample": f"{n} trajectories x {shots_per_traj} shots of the workload on {pool.cores} worker "
+                      f"processes (one BLAS thread each): exact MPS contraction + NBS replay, complex128",
+            "single_thread": {"value": s1 / t1, "unit": "shots/s", "cores": 1,
+                              "sample": f"1 trajectory x {shots_per_traj} shots on one process"}}
+
+
 def run_reference(args, rank):
-    """--impl reference: the CPU oracle as it stands, on bounded samples."""
+    """--impl reference: the CPU oracle as it stands, on bounded samples of the
+    workload, trajectories spread over worker processes on the host cores."""
     if rank != 0:
         return
     cfg = c2_config()
     shots_per_traj = cfg["total_shots"] // cfg["n_traj"]
-    n_sample = 2
-    for w in range(args.warmup):
-        oracle_sample_run(cfg, 1, shots_per_traj, seed_offset=1000 + w)
-    times, shots = [], 0
-    for k in range(args.steps):
-        s, t = oracle_sample_run(cfg, n_sample, shots_per_traj, seed_offset=k)
-        times.append(t)
-        shots += s
+    pool = OraclePool(min(host_cores(), 32))
+    n_sample = pool.cores
+    try:
+        for w in range(args.warmup):
+            pool.run(n_sample, shots_per_traj, 1000 + 100 * w)
+        times, shots = [], 0
+        for k in range(args.steps):
+            s_k, t_k = pool.run(n_sample, shots_per_traj, 10_000 + 100 * k)
+            times.append(t_k)
+            shots += s_k
+    finally:
+        pool.close()
     value = shots / sum(times)
+    sample = (f"{n_sample} trajectories x {shots_per_traj} shots per step on {pool.cores} worker processes "
+              f"(one BLAS thread each), exact MPS + NBS replay, complex128")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic",
             "config": {"workload": "c2_brickwork30_d12 (30 qubits, depth 12, dep 0.005 + AD 0.002, blocks 10/10/10)",
-                       "sample": f"{n_sample} trajectories x {shots_per_traj} shots per step"},
-            "cpu_baseline": {"value": value, "unit": "shots/s", "cores": cpu_threads(), "kind": "oracle",
-                             "sample": f"{n_sample} trajectories x {shots_per_traj} shots per step, exact MPS + NBS"},
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "shots/s", "cores": pool.cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def measure_tc_peaks(torch, sustain_s=4.0):
+    """Dense TF32 and FP16 tensor-core throughput of this GPU, measured like the
+    BF16 figures of MEASURED_PEAKS.json: torch.matmul 8192^3 (2 N^3 flops),
+    best of 10 (burst) and back to back for a few seconds (sustained)."""
+    N = 8192
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        for name, dt in (("tf32", torch.float32), ("fp16", torch.float16)):
+            a = torch.randn(N, N, device="cuda", dtype=dt)
+            b = torch.randn(N, N, device="cuda", dtype=dt)
+            for _ in range(3):
+                torch.matmul(a, b)
+            best = 1e9
+            for _ in range(10):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            torch.cuda.synchronize()
+            n_it, t0 = 0, time.perf_counter()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            while time.perf_counter() - t0 < sustain_s:
+                for _ in range(20):
+                    torch.matmul(a, b)
+                n_it += 20
+                torch.cuda.synchronize()
+            e1.record()
+            torch.cuda.synchronize()
+            out[f"{name}_tflops"] = 2.0 * N ** 3 / best / 1e12
+            out[f"{name}_tflops_sustained"] = 2.0 * N ** 3 * n_it / (e0.elapsed_time(e1) / 1e3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------- our arm ----
@@ -237,8 +348,13 @@ def main():
                     help="open a CUDA profiler range around the timed steps (for ncu --profile-from-start off)")
     ap.add_argument("--grad-calls", type=int, default=3,
                     help="timed ptn_expval_grad calls on the 16-qubit ansatz (0: skip)")
-    ap.add_argument("--mixed-batch", type=int, default=0, metavar="WORKERS",
+    ap.add_argument("--mixed-batch", type=int, default=4, metavar="WORKERS",
                     help="also run the 64-circuit mixed batch with this many concurrent circuits (0: skip)")
+    ap.add_argument("--no-precision-lines", action="store_true",
+                    help="skip the timed steps of the other tensor-core operand splits")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip measuring the TF32 / FP16 tensor-core peaks (the roofline then uses the "
+                         "BF16 peak x the nominal format ratio)")
     ap.add_argument("--n-traj", type=int, default=0,
                     help="trajectories per step (default: the workload's 4096; smaller values are for profiling)")
     ap.add_argument("--total-shots", type=int, default=0,
@@ -256,8 +372,14 @@ def main():
         run_reference(args, rank)
         return
 
+    # the oracle's worker processes are spawned before the first CUDA call
+    pool = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pool = OraclePool(min(host_cores(), 32))
+
     import torch
     torch.cuda.set_device(local)
+    tc_peaks = {} if args.no_peaks else measure_tc_peaks(torch)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -285,11 +407,31 @@ def main():
         del tr, res
     torch.cuda.synchronize()
 
+    # ---- instrumented pass (every launch bracketed by events): the per-kernel
+    # breakdown and the dominant kernel class; not part of the headline
+    n_instr = 2
+    ptn.ptn_stats_reset()
+    ptn.ptn_stats_enable(True)
+    instr_times = []
+    for k in range(n_instr):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tr, res = step(20_000 + k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        instr_times.append(a.elapsed_time(b) / 1e3)
+        del tr, res
+    ptn.ptn_stats_enable(False)
+    stats = ptn.ptn_stats_read()
+    dominant = max(stats, key=lambda k: stats[k]["ms"])
+
+    # ---- timed region: only the dominant class's launches carry events
     nets = None
     n_records = 0
     times = []
     ptn.ptn_stats_reset()
-    ptn.ptn_stats_enable(True)
+    ptn.ptn_stats_enable_only(dominant)
     with ClockSampler(local) as clk:
         if dist:
             dist.barrier()
@@ -313,11 +455,33 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
     ptn.ptn_stats_enable(False)
-    stats = ptn.ptn_stats_read()
+    live = ptn.ptn_stats_read()
     free_b, total_b = torch.cuda.mem_get_info()
     clocks = clk.summary()
     t_step = shard.max_over_ranks(float(np.mean(times)), dist, device="cuda")
     value = M * world / t_step
+
+    # ---- the other tensor-core operand splits, same workload, uninstrumented
+    other_prec = {}
+    if not args.no_precision_lines:
+        for pname, (pcode, perr) in PRECISIONS.items():
+            if pname == args.precision:
+                continue
+            pt = []
+            for k in range(max(2, min(args.steps, 4))):
+                flush.zero_()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                tr = ptn.ptn_presample_trajectories(plan, shard.rank_seed(cfg["seed"], rank, 30_000 + k), E)
+                res = ptn.ptn_sample_shots(plan, tr, cfg["seed"] + k, total_shots=M, precision=pcode)
+                b.record(stream)
+                torch.cuda.synchronize()
+                pt.append(a.elapsed_time(b) / 1e3)
+                del tr, res
+            tp = shard.max_over_ranks(float(np.mean(pt)), dist, device="cuda")
+            other_prec[pname] = {"value": M * world / tp, "unit": "shots/s", "ms_per_step": tp * 1e3,
+                                 "steps": len(pt), "error_vs_fp64": perr}
 
     # ---- end to end through the public API, result copied to pinned host memory
     e2e_times = []
@@ -367,7 +531,7 @@ def main():
     if args.grad_calls > 0:
         c5 = W.config_c5()
         gplan = ptn.ptn_plan_path(c5["circuit"], c5["block_sizes"], hypersamples=args.hypersamples,
-                                  est_traj=c5["n_traj"])
+                                  est_traj=c5["n_traj"], grad_checkpoint=True)
         gtr = ptn.ptn_presample_trajectories(gplan, c5["seed"], c5["n_traj"], dedup=True)
         nq = c5["circuit"].n_qubits
         terms = [(1.0 / nq, (1 << q) | (1 << ((q + 1) % nq))) for q in range(nq)]
@@ -382,7 +546,8 @@ def main():
         torch.cuda.synchronize()
         tg = (time.perf_counter() - t0) / args.grad_calls
         grad = {"workload": "c5_hea16_l6: 16-qubit ansatz, 6 layers RY RZ + CZ ring, 192 angles, depolarizing 0.01, "
-                            f"{c5['n_traj']} trajectories ({gtr.n_unique} distinct), O = mean Z_q Z_q+1",
+                            f"{c5['n_traj']} trajectories ({gtr.n_unique} distinct), O = mean Z_q Z_q+1, "
+                            "checkpointed intermediates",
                 "value": c5["n_traj"] / tg, "unit": "trajectory gradients/s", "ms_per_call": tg * 1e3,
                 "expval": float(gv.item())}
         del gplan, gtr
@@ -394,43 +559,50 @@ def main():
         del plan          # frees the brickwork workspace so the batch gets the device memory
         mixed = run_mixed_batch(ptn, shard, torch, dist, rank, world, args.hypersamples, args.mixed_batch)
 
-    # ---- roofline of every kernel class (from the library's per-launch events);
-    # the dominant one is the headline.  Tensor-core GEMMs are charged their
-    # algorithmic complex flops (8 per complex multiply-add) against the
-    # measured dense BF16 peak (sustained: the kernel runs inside a long step)
-    # scaled by the nominal ratio of the input format (TF32 = 1/2 of BF16) and
-    # divided by the three MMAs of the hi/lo split; everything else is charged
-    # algorithmic bytes against the measured HBM copy bandwidth.
+    # ---- rooflines.  Tensor-core GEMMs are charged their algorithmic complex
+    # flops (8 per complex multiply-add) against the dense peak of their input
+    # format measured above (sustained: the kernel runs inside a long step),
+    # divided by the three MMAs of the hi/lo split; every other kernel class is
+    # charged algorithmic bytes against the measured HBM copy bandwidth.  The
+    # headline is the dominant class, timed live inside the timed region; the
+    # per-class breakdown comes from the instrumented pass.
     peaks, peak_src = load_peaks()
-    fmt_ratio = 0.5 if args.precision == "fp32" else 1.0
-    tc_peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * fmt_ratio / SPLIT_TERMS
+    fmt = {"fp32": "tf32", "fp16x3": "fp16", "bf16x3": "bf16"}[args.precision]
+    if fmt == "bf16":
+        tc_base, tc_note = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), f"bf16 sustained ({peak_src})"
+    elif f"{fmt}_tflops_sustained" in tc_peaks:
+        tc_base, tc_note = tc_peaks[f"{fmt}_tflops_sustained"], f"{fmt} sustained (measured in this run)"
+    else:
+        ratio = 0.5 if fmt == "tf32" else 1.0
+        tc_base = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * ratio
+        tc_note = f"bf16 sustained x {ratio} nominal {fmt} ratio ({peak_src})"
+    tc_peak = tc_base / SPLIT_TERMS
 
-    def roof_of(name, s):
+    def roof_of(name, s, steps, step_seconds):
         sec = s["ms"] / 1e3
         if name == "contract_gemm":
             ach = s["alg_flops"] / sec / 1e12 if sec > 0 else 0.0
             r = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
-                 "peak_note": f"bf16 sustained x {fmt_ratio} / {SPLIT_TERMS} split terms ({peak_src})"}
+                 "peak_note": f"{tc_note} / {SPLIT_TERMS} split terms"}
         else:
             ach = s["alg_bytes"] / sec / 1e9 if sec > 0 else 0.0
             r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                  "peak_note": f"hbm copy ({peak_src})"}
-        r.update({"frac": r["achieved"] / r["peak"], "traffic": None,
-                  "launches_per_step": s["timed_launches"] / max(args.steps, 1),
-                  "ms_per_step": s["ms"] / max(args.steps, 1),
-                  "share_of_step": sec / max(sum(times), 1e-12)})
+        r.update({"frac": r["achieved"] / r["peak"], "traffic": TRAFFIC.get(name),
+                  "launches_per_step": s["timed_launches"] / max(steps, 1),
+                  "ms_per_step": s["ms"] / max(steps, 1),
+                  "share_of_step": sec / max(step_seconds, 1e-12)})
         return r
 
-    roofs = {k: roof_of(k, v) for k, v in stats.items() if v["ms"] > 0}
-    top = max(roofs.values(), key=lambda r: r["ms_per_step"]) if roofs else None
-    roof = dict(top) if top else None
-    launches = sum(v["launches"] for v in stats.values())
+    roofs = {k: roof_of(k, v, n_instr, sum(instr_times)) for k, v in stats.items() if v["ms"] > 0}
+    roof = roof_of(dominant, live[dominant], args.steps, sum(times))
+    roof["timing"] = "CUDA events around this class's launches inside the timed region"
+    launches = sum(v["launches"] for v in live.values())
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        shots, sec = oracle_sample_run(cfg, 2, M // E)
-        cpu = {"value": shots / sec, "unit": "shots/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"2 trajectories x {M // E} shots (exact MPS contraction + NBS replay, complex128)"}
+    if pool is not None:
+        cpu = cpu_baseline(pool, cfg, M // E)
+        pool.close()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
@@ -446,13 +618,17 @@ def main():
                            "precision": f"{args.precision}: complex64 storage, tensor-core operands split hi/lo "
                                         f"({args.precision}), fp64 CDF / log-probabilities",
                            "error_vs_fp64": PRECISIONS[args.precision][1]},
-                "e2e": e2e, "plain_path": plain, "expval_grad": grad, "mixed_batch": mixed, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "plain_path": plain, "other_precisions": other_prec, "expval_grad": grad,
+                "mixed_batch": mixed, "roofline": roof, "cpu_baseline": cpu,
                 "contractions_per_s": float(sum(nets or [0])) * world / t_step,
                 "distinct_records_per_s": float(n_records) * world / t_step,
-                "gpu_launches": int(launches), "clocks": clocks,
-                "kernels": {k: {"launches": v["launches"], "ms_per_step": r["ms_per_step"], "achieved": r["achieved"],
-                                "unit": r["unit"], "frac": r["frac"]} for k, r in roofs.items()
-                            for v in [stats[k]]}}
+                "gpu_launches": int(launches), "clocks": clocks, "tc_peaks_measured": tc_peaks,
+                "kernels_instrumented": {
+                    "note": f"{n_instr} extra steps with events around every launch "
+                            f"({1e3 * float(np.mean(instr_times)):.1f} ms per step there)",
+                    **{k: {"launches_per_step": r["launches_per_step"], "ms_per_step": r["ms_per_step"],
+                           "share": r["share_of_step"], "achieved": r["achieved"], "unit": r["unit"],
+                           "frac": r["frac"]} for k, r in roofs.items()}}}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

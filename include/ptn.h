@@ -418,6 +418,12 @@ typedef struct {
 } ptn_kernel_stat;
 
 ptn_status ptn_stats_enable(int32_t timing_on);
+/* Timing of one kernel class only (a name as reported by ptn_stats_read, e.g.
+ * "contract_gemm"): the other launches are only counted, so the timed class
+ * can be measured inside an otherwise uninstrumented run.  NULL or "" times
+ * every class; an unknown name returns PTN_ERR_INVALID_ARG.
+ * ptn_stats_enable(0) turns timing off. */
+ptn_status ptn_stats_enable_only(const char* kernel);
 ptn_status ptn_stats_reset(void);
 ptn_status ptn_stats_read(ptn_kernel_stat* out, int32_t cap, int32_t* n_out);
 

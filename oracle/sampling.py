@@ -156,3 +156,126 @@ def nbs_proportional(marginal_fn, blocks, seed, n_traj, circuit=0, shots=None,
         prefix = prefix[par] | (xs.astype(np.uint64) << np.uint64(start))
         counts = cs
     return traj, prefix, counts, levels, m
+
+
+# ------------------------------------------------ non-proportional NBS ----
+#
+# Paper, Sec. III-B (non-proportional case): every non-final batch draws one or
+# more shots per distinct prefix from its conditional marginal (the prefixes
+# branch at a user-set rate), and the final batch B_f, whose outcomes feed no
+# later contraction, is harvested in bulk from its 2^{b_f} population vector,
+# either by direct sampling (many shots drawn from it) or exhaustively (every
+# entry above a user threshold, optionally with its probability).
+#
+# Readings (points the paper leaves open):
+#
+# * branching: parent n of a non-final block draws `branch` shots (the same
+#   for every parent; 1 in the paper's experiments, Sec. IV-C), with the shot
+#   ranks and Philox counters of the proportional case; its distinct outcomes
+#   become the next block's prefixes;
+# * the final population vector of a network with b_f bits is quantised to
+#   64-bit integers, P_x = rint(max(p_x, 0) * 2^s), s = 62 - bits - e with
+#   max p = f * 2^e, f in [0.5, 1) (T = sum P_x < 2^62, so the running sum is
+#   exact in uint64; relative resolution 2^-(61 - b_f) of the largest entry,
+#   which keeps b_f up to 30 exact enough for direct draws and thresholds);
+# * direct sampling: each final network draws `final_shots` shots with the
+#   proportional counters (ranks continue within the trajectory), a draw
+#   taking r = floor(a T / 2^64) and the smallest x with r < C[x]; the
+#   distinct outcomes are returned with their counts;
+# * exhaustive sampling: the entries with P_x > 0 and P_x >= tau * T (FP64
+#   product; tau is the threshold on the conditional probability p(x |
+#   prefix)) are returned in increasing x with probability P_x / T (FP64).
+
+
+def quantise64(p):
+    """64-bit integer weights of one final population vector and their running
+    sum (Python ints held in uint64 arrays)."""
+    p = np.asarray(p, dtype=np.float64)
+    p = np.where(p > 0.0, p, 0.0)
+    n_bins = p.shape[-1]
+    bits = int(math.ceil(math.log2(n_bins))) if n_bins > 1 else 0
+    m = float(p.max())
+    if m <= 0.0:
+        raise ValueError("all-zero probability row")
+    _, e = math.frexp(m)
+    s = 62 - bits - e
+    P = np.rint(np.ldexp(p, s)).astype(np.uint64)
+    C = np.cumsum(P, dtype=np.uint64)
+    return P, C
+
+
+def inverse_cdf64(C, a):
+    """Smallest x with floor(a * T / 2^64) < C[x], T = C[-1] < 2^62."""
+    r = philox.mulhi64(a, np.uint64(int(C[-1])))
+    return np.searchsorted(C, r, side="right")
+
+
+def harvest_direct(p_rows, traj, prefix, start, n_shots, seed, block, circuit=0):
+    """Direct sampling of the final block: n_shots draws per network (ranks
+    continuing within each trajectory); returns (traj, bits, count) of the
+    distinct outcomes, networks in order, x increasing."""
+    tagw = philox.tag(philox.STREAM_SAMPLE, circuit, block)
+    counts = np.full(len(traj), int(n_shots), dtype=np.int64)
+    r0 = rank_offsets(traj, counts)
+    out_t, out_b, out_c = [], [], []
+    for n in range(len(traj)):
+        if n_shots == 0 or not np.any(np.asarray(p_rows[n]) > 0):
+            continue
+        _, C = quantise64(p_rows[n])
+        ranks = np.arange(int(r0[n]), int(r0[n]) + int(n_shots), dtype=np.uint64)
+        xs = inverse_cdf64(C, draw_words(ranks, np.uint64(int(traj[n])), tagw, seed))
+        hist = np.bincount(xs, minlength=len(C))
+        nz = np.nonzero(hist)[0]
+        out_t.extend([int(traj[n])] * len(nz))
+        out_b.extend([int(prefix[n]) | (int(x) << start) for x in nz])
+        out_c.extend(hist[nz].tolist())
+    return (np.array(out_t, dtype=np.int64), np.array(out_b, dtype=np.uint64),
+            np.array(out_c, dtype=np.int64))
+
+
+def harvest_exhaustive(p_rows, traj, prefix, start, tau):
+    """Exhaustive sampling of the final block: every entry with P_x > 0 and
+    P_x >= tau * T; returns (traj, bits, probability P_x / T)."""
+    out_t, out_b, out_p = [], [], []
+    for n in range(len(traj)):
+        if not np.any(np.asarray(p_rows[n]) > 0):
+            continue
+        P, C = quantise64(p_rows[n])
+        T = float(int(C[-1]))
+        keep = [x for x in range(len(P)) if int(P[x]) > 0 and float(int(P[x])) >= tau * T]
+        out_t.extend([int(traj[n])] * len(keep))
+        out_b.extend([int(prefix[n]) | (x << start) for x in keep])
+        out_p.extend([float(int(P[x])) / T for x in keep])
+    return (np.array(out_t, dtype=np.int64), np.array(out_b, dtype=np.uint64),
+            np.array(out_p, dtype=np.float64))
+
+
+def nbs_nonproportional(marginal_fn, blocks, seed, n_traj, branch=1, mode="exhaustive", final_shots=0,
+                        tau=0.0, circuit=0):
+    """Non-proportional NBS over all blocks: `branch` shots per parent on every
+    non-final block, then the final block harvested by direct sampling
+    (`final_shots` per network) or exhaustively (threshold `tau`).
+
+    Returns the final records ((traj, bits, count) or (traj, bits, probability))
+    and the number of networks contracted per block."""
+    traj = np.arange(n_traj, dtype=np.int64)
+    prefix = np.zeros(n_traj, dtype=np.uint64)
+    nets = []
+    for j, (start, b) in enumerate(blocks[:-1]):
+        nets.append(len(traj))
+        rows = marginal_fn(j, traj, prefix)
+        counts = np.full(len(traj), int(branch), dtype=np.int64)
+        par, xs, _ = sample_block(rows, traj, counts, rank_offsets(traj, counts), seed, j, circuit)
+        traj = traj[par]
+        prefix = prefix[par] | (xs.astype(np.uint64) << np.uint64(start))
+    jf = len(blocks) - 1
+    start, b = blocks[jf]
+    nets.append(len(traj))
+    rows = marginal_fn(jf, traj, prefix)
+    if mode == "direct":
+        rec = harvest_direct(rows, traj, prefix, start, final_shots, seed, jf, circuit)
+    elif mode == "exhaustive":
+        rec = harvest_exhaustive(rows, traj, prefix, start, tau)
+    else:
+        raise ValueError(mode)
+    return rec, nets

@@ -23,6 +23,7 @@ thread_local int t_block = -1, t_step = -1;
 struct State {
     std::mutex mu;
     bool timing = false;
+    int only = -1;               // time only this kernel class (-1: every class)
     int64_t launches[K_COUNT] = {};
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
@@ -58,7 +59,7 @@ StatScope::StatScope(int kid, cudaStream_t s, double bytes, double flops) : kid_
     State& g = st();
     std::lock_guard<std::mutex> lk(g.mu);
     g.launches[kid]++;
-    timing_ = g.timing;
+    timing_ = g.timing && (g.only < 0 || g.only == kid);
     if (timing_) {
         a_ = take_event();
         b_ = take_event();
@@ -84,6 +85,20 @@ extern "C" ptn_status ptn_stats_enable(int32_t on) {
     State& g = st();
     std::lock_guard<std::mutex> lk(g.mu);
     g.timing = on != 0;
+    g.only = -1;
+    return PTN_OK;
+}
+
+extern "C" ptn_status ptn_stats_enable_only(const char* kernel) {
+    if (!kernel || !*kernel) return ptn_stats_enable(1);
+    int kid = -1;
+    for (int k = 0; k < K_COUNT; k++)
+        if (strcmp(kernel, kNames[k]) == 0) kid = k;
+    if (kid < 0) return set_error(PTN_ERR_INVALID_ARG, "unknown kernel class '%s'", kernel);
+    State& g = st();
+    std::lock_guard<std::mutex> lk(g.mu);
+    g.timing = true;
+    g.only = kid;
     return PTN_OK;
 }
 

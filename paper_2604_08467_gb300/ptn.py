@@ -118,6 +118,7 @@ _SIGS = {
     "ptn_expval_grad": [_P, _P, C.POINTER(ptn_pauli_sum), C.POINTER(C.c_double), C.c_int32, _P, _P, _P],
     "ptn_trajectory_amplitudes": [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P, _P],
     "ptn_stats_enable": [C.c_int32],
+    "ptn_stats_enable_only": [C.c_char_p],
     "ptn_stats_reset": [],
     "ptn_stats_read": [C.POINTER(ptn_kernel_stat), C.c_int32, C.POINTER(C.c_int32)],
     "ptn_stats_read_steps": [C.POINTER(ptn_step_stat), C.c_int32, C.POINTER(C.c_int32)],
@@ -440,6 +441,11 @@ def ptn_shots_merge(shots, n_blocks, stream=None):
 
 def ptn_stats_enable(on=True):
     _check(lib().ptn_stats_enable(int(bool(on))))
+
+
+def ptn_stats_enable_only(kernel):
+    """Time only the launches of one kernel class (others are just counted)."""
+    _check(lib().ptn_stats_enable_only(kernel.encode() if kernel else None))
 
 
 def ptn_stats_reset():

@@ -482,3 +482,103 @@ def test_mps_window_marginal_brute_force():
             key = (idx >> start) & ((1 << b) - 1)
             want = np.bincount(key, weights=probs, minlength=1 << b)
             np.testing.assert_allclose(m.window_marginal(start, b), want, rtol=1e-10, atol=1e-14)
+
+
+# ------------------------------------------------ non-proportional NBS ----
+
+def test_quantise64_exact_and_close_to_the_row():
+    rng = np.random.default_rng(61)
+    for n_bins in (1, 2, 7, 1024, 1 << 16):
+        p = rng.exponential(size=n_bins) * np.exp(rng.uniform(-30, 0))
+        p[rng.random(n_bins) < 0.1] = 0.0
+        if not np.any(p > 0):
+            p[0] = 1.0
+        P, C = sampling.quantise64(p)
+        tot = sum(int(v) for v in P)
+        assert int(C[-1]) == tot < 2 ** 62 and int(P.max()) >= 2 ** 60 >> max(0, math.ceil(math.log2(n_bins)))
+        bits = math.ceil(math.log2(n_bins)) if n_bins > 1 else 0
+        err = np.abs(P.astype(np.float64) / tot - p / p.sum())
+        assert err.max() <= 2.0 ** (bits - 59) * (p.max() / p.sum()) + 1e-300
+
+
+def test_inverse_cdf64_brute_force():
+    rng = np.random.default_rng(62)
+    for _ in range(20):
+        p = rng.random(rng.integers(1, 40))
+        p[rng.random(len(p)) < 0.3] = 0.0
+        if not np.any(p > 0):
+            p[-1] = 0.5
+        P, C = sampling.quantise64(p)
+        T = int(C[-1])
+        a = rng.integers(0, 2 ** 63, size=200, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, size=200,
+                                                                                              dtype=np.uint64)
+        got = sampling.inverse_cdf64(C, a)
+        for ai, x in zip(a.tolist(), got.tolist()):
+            r = (int(ai) * T) >> 64
+            want = next(k for k in range(len(C)) if r < int(C[k]))
+            assert x == want and P[x] > 0
+
+
+def test_harvest_exhaustive_threshold_and_probabilities():
+    p = np.array([0.5, 0.0, 0.25, 0.125, 0.0625, 0.0625, 0.0, 0.0])
+    t, b, pr = sampling.harvest_exhaustive(p[None, :] * 3.0, np.array([4]), np.array([5], np.uint64), 3, 0.0)
+    assert t.tolist() == [4] * 5 and b.tolist() == [5 | (x << 3) for x in (0, 2, 3, 4, 5)]
+    np.testing.assert_allclose(pr, [0.5, 0.25, 0.125, 0.0625, 0.0625], rtol=1e-15)
+    t, b, pr = sampling.harvest_exhaustive(p[None, :], np.array([0]), np.array([0], np.uint64), 0, 0.1)
+    assert b.tolist() == [0, 2, 3]
+    onehot = np.zeros((1, 64))
+    onehot[0, 37] = 1e-20
+    t, b, pr = sampling.harvest_exhaustive(onehot, np.array([1]), np.array([0], np.uint64), 6, 0.5)
+    assert b.tolist() == [37 << 6] and pr.tolist() == [1.0]
+    # zero-norm network: no records
+    t, b, pr = sampling.harvest_exhaustive(np.zeros((1, 8)), np.array([0]), np.array([0], np.uint64), 0, 0.0)
+    assert len(t) == 0
+
+
+def test_harvest_direct_law_and_counts():
+    p = np.array([0.1, 0.4, 0.0, 0.2, 0.3])
+    rows = np.stack([p, p[::-1]])
+    t, b, c = sampling.harvest_direct(rows, np.array([0, 0]), np.array([1, 0], np.uint64), 1, 200_000, 5, 2)
+    assert c.sum() == 400_000 and np.all(np.diff(t) >= 0)
+    for n, row in enumerate(rows):
+        sel = (b & np.uint64(1)) == np.uint64(1 - n)
+        freq = np.zeros(5)
+        freq[(b[sel] >> np.uint64(1)).astype(np.int64)] = c[sel]
+        freq /= freq.sum()
+        assert np.abs(freq - row).max() < 0.005
+        assert freq[np.nonzero(row == 0)[0]].sum() == 0
+
+
+def test_nbs_nonproportional_branching_and_final_law():
+    """One shot per non-final block: every trajectory keeps exactly one prefix
+    per block, and the first block's outcomes follow its marginal; the
+    exhaustive final harvest of each network equals the exact conditional
+    distribution of the final block given that prefix."""
+    rng = np.random.default_rng(63)
+    circ = W.brickwork_1d(6, 4, rng)           # noiseless: every trajectory is the same state
+    psi = sv.pure_state(circ)
+    probs = np.abs(psi) ** 2
+    blocks = [(0, 2), (2, 2), (4, 2)]
+
+    def marg(j, traj, prefix):
+        start, b = blocks[j]
+        return np.stack([sv.block_marginals(probs, 6, start, b)[int(s) & ((1 << start) - 1)] for s in prefix])
+
+    E = 4000
+    (t, bits, pr), nets = sampling.nbs_nonproportional(marg, blocks, 77, E, branch=1, mode="exhaustive", tau=0.0)
+    assert nets == [E, E, E]
+    assert sorted(set(t.tolist())) == list(range(E))
+    first = (bits[np.r_[0, np.nonzero(np.diff(t))[0] + 1]] & np.uint64(3)).astype(np.int64)
+    freq = np.bincount(first, minlength=4) / E
+    assert np.abs(freq - sv.block_marginals(probs, 6, 0, 2)[0] / probs.sum()).max() < 0.03
+    for i in (0, 17, 3999):
+        sel = t == i
+        pre = int(bits[sel][0]) & 15
+        cond = sv.block_marginals(probs, 6, 4, 2)[pre]
+        cond = cond / cond.sum()
+        got = np.zeros(4)
+        got[(bits[sel] >> np.uint64(4)).astype(np.int64)] = pr[sel]
+        np.testing.assert_allclose(got, cond, rtol=1e-12, atol=1e-15)
+    # branch > 1 grows the prefix set; direct mode returns counts
+    (t2, b2, c2), nets2 = sampling.nbs_nonproportional(marg, blocks, 78, 10, branch=3, mode="direct", final_shots=50)
+    assert nets2[0] == 10 and nets2[1] >= 10 and nets2[2] >= nets2[1] and c2.sum() == 50 * nets2[2]

@@ -142,8 +142,8 @@ typedef struct {
  * contraction path per block (Sec. III-A), lowered to a list of batched
  * pairwise contractions.  Host only: needs no GPU (device tables are uploaded
  * on first use).  block_sizes may be NULL (then b = 10 blocks, the last one
- * taking the remainder); otherwise they must be in 1..14 and sum to
- * n_qubits. */
+ * taking the remainder); otherwise they must be in 1..14 (the last one in
+ * 1..30, for the non-proportional final-block harvest) and sum to n_qubits. */
 ptn_status ptn_plan_path(const ptn_circuit* circuit, const ptn_noise* noise,
                          const int32_t* block_sizes, int32_t n_blocks,
                          const ptn_plan_opts* opts, ptn_plan** plan_out);
@@ -178,6 +178,17 @@ void ptn_plan_destroy(ptn_plan* plan);
 ptn_status ptn_presample_trajectories(const ptn_plan* plan, uint64_t seed, int32_t circuit_id,
                                       int64_t n_traj, int32_t dedup, ptn_traj** traj_out,
                                       ptn_stream stream);
+
+/* Trajectories traj0 .. traj0 + n_traj - 1 of the draw ptn_presample_trajectories
+ * makes from the same seed (no dedup): trajectory traj0 + i uses the Philox
+ * counter (s, 0, traj0 + i, (1 << 24) | (circuit_id << 8)) and is row i of the
+ * result, whose `first` entries are traj0 + i.  Ranks that shard one job by
+ * trajectory range draw their ranges with this call (Sec. III: the method
+ * parallelises over error sets); their sampling calls then pass the global
+ * trajectory index (traj0 + row) as parent_traj so that every Philox counter
+ * is the one of the single-process run.  traj0 + n_traj <= 2^32. */
+ptn_status ptn_presample_range(const ptn_plan* plan, uint64_t seed, int32_t circuit_id, int64_t traj0, int64_t n_traj,
+                               ptn_traj** traj_out, ptn_stream stream);
 
 /* Device views of a ptn_traj (valid until ptn_traj_destroy): kraus [n][S]
  * uint8 row-major, logq [n] double, mult [n] int64 (1 without dedup), first
@@ -272,7 +283,16 @@ ptn_status ptn_sample_block_noalloc(const float* marg, int32_t b, int32_t start,
 ptn_status ptn_allocate_shots(const double* weights, int64_t n, int64_t total, uint64_t seed,
                               int32_t circuit_id, int64_t* m_out, ptn_stream stream);
 
-enum { PTN_PROPORTIONAL_FIXED = 0, PTN_PROPORTIONAL_TOTAL = 1 };
+/* Sampling modes (Sec. III-B).  The proportional modes keep the circuit's
+ * statistics; the non-proportional ones gather as much data as possible:
+ * every non-final block draws branch_shots shots per distinct prefix (the
+ * distinct outcomes become the next block's prefixes), and the final block,
+ * whose outcomes feed no later contraction, is harvested from its population
+ * vector, by direct sampling (final_shots draws per network) or exhaustively
+ * (every outcome x with p(x | prefix) >= threshold, with that probability).
+ * The final block of a plan may have up to 30 qubits for the non-proportional
+ * modes; the proportional modes need every block <= 14. */
+enum { PTN_PROPORTIONAL_FIXED = 0, PTN_PROPORTIONAL_TOTAL = 1, PTN_NONPROP_DIRECT = 2, PTN_NONPROP_EXHAUSTIVE = 3 };
 
 typedef struct {
     int32_t  mode;               /* PTN_PROPORTIONAL_FIXED or PTN_PROPORTIONAL_TOTAL */
@@ -286,6 +306,10 @@ typedef struct {
     int32_t  use_graphs;         /* must be 0: CUDA-graph capture of the step lists is not
                                     built (PTN_ERR_UNSUPPORTED otherwise) */
     int32_t  reserved;
+    int64_t  branch_shots;       /* NONPROP_*: shots drawn per prefix on every non-final block (>= 1) */
+    int64_t  final_shots;        /* NONPROP_DIRECT: shots drawn from every final-block network (>= 1) */
+    double   threshold;          /* NONPROP_EXHAUSTIVE: keep outcomes with p(x | prefix) >= threshold,
+                                    in [0, 1] */
 } ptn_sample_opts;
 
 /* Full proportional NBS over all blocks (Sec. III-B): block 1 contracts one
@@ -298,6 +322,19 @@ typedef struct {
 ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const ptn_sample_opts* opts,
                             ptn_shots** shots_out, ptn_stream stream);
 
+/* Non-proportional modes, final block: the population vector of a network
+ * (trajectory i, prefix s) with b_f bits is quantised to 64-bit integers
+ * P_x = rint(max(p_x, 0) 2^(62 - b_f - e)), max p = f 2^e with f in [0.5, 1),
+ * T = sum P_x (exact).  Exhaustive: the records are the x with P_x > 0 and
+ * (double)P_x >= threshold * (double)T, count 1.  Direct: shot rank r of the
+ * trajectory (ranks continue over its final networks in order, final_shots
+ * each) uses the Philox counter of ptn_sample_block and takes the smallest x
+ * with floor(a T / 2^64) < sum_{y <= x} P_y; the records are the distinct x
+ * with their counts.  Both give every record its probability
+ * p(x | s) = (double)P_x / (double)T (ptn_shots_probs).  Records are in
+ * canonical order (networks in order, x increasing); the final networks are
+ * contracted and harvested in sub-batches that fit half the memory cap. */
+
 /* Device views of the result (valid until ptn_shots_destroy) and, per block,
  * the number of networks contracted (host array of n_blocks, may be NULL). */
 ptn_status ptn_shots_info(const ptn_shots* shots, int64_t* n_out, const int32_t** traj,
@@ -307,6 +344,12 @@ ptn_status ptn_shots_info(const ptn_shots* shots, int64_t* n_out, const int32_t*
 /* Copy the result into caller-allocated device arrays of n_out entries. */
 ptn_status ptn_shots_copy(const ptn_shots* shots, int32_t* traj_out, uint64_t* bits_out, int64_t* count_out,
                           ptn_stream stream);
+
+/* Per-record probabilities p(x | prefix) of a non-proportional result: device
+ * view (NULL for proportional results) and a copy into a caller-allocated
+ * device double array of n_out entries (PTN_ERR_INVALID_ARG without them). */
+ptn_status ptn_shots_probs(const ptn_shots* shots, const double** prob);
+ptn_status ptn_shots_copy_probs(const ptn_shots* shots, double* prob_out, ptn_stream stream);
 
 void ptn_shots_destroy(ptn_shots* shots);
 

@@ -68,7 +68,7 @@ def uniform53(x0, x1):
 
 
 def mulhi64(a, t):
-    """floor(a * t / 2**64) for uint64 arrays a and t with t < 2**54, exact."""
+    """floor(a * t / 2**64) for uint64 arrays a and t, exact (carries tracked)."""
     a = np.asarray(a, np.uint64)
     t = np.asarray(t, np.uint64)
     a_hi, a_lo = a >> S32, a & MASK32

@@ -54,8 +54,10 @@ def completeness_error(kraus):
     return float(np.max(np.abs(s - np.eye(2))))
 
 
-def presample(circ, n_traj: int, seed: int, circuit_id: int = 0):
-    """Draw the Kraus index of every site of every trajectory.
+def presample(circ, n_traj: int, seed: int, circuit_id: int = 0, traj0: int = 0):
+    """Draw the Kraus index of every site of trajectories traj0 .. traj0 +
+    n_traj - 1 (trajectory i uses counter word i, so a range is the same rows
+    of a draw that starts at 0).
 
     Returns (kraus[E, S] uint8, logq[E] float64) where logq_i = sum over sites,
     in site order, of log q_{s, k_{i,s}}."""
@@ -63,7 +65,7 @@ def presample(circ, n_traj: int, seed: int, circuit_id: int = 0):
     k0, k1 = philox.key_of(seed)
     t = philox.tag(philox.STREAM_KRAUS, circuit_id, 0)
     s_idx, i_idx = np.meshgrid(np.arange(S, dtype=np.uint64),
-                               np.arange(n_traj, dtype=np.uint64))
+                               np.arange(traj0, traj0 + n_traj, dtype=np.uint64))
     x0, x1, _, _ = philox.philox4x32_10(s_idx, 0, i_idx, t, k0, k1)
     u = philox.uniform53(x0, x1)                           # [E, S]
     kraus = np.zeros((n_traj, S), dtype=np.uint8)

@@ -242,12 +242,14 @@ def harvest_exhaustive(p_rows, traj, prefix, start, tau):
             continue
         P, C = quantise64(p_rows[n])
         T = float(int(C[-1]))
-        keep = [x for x in range(len(P)) if int(P[x]) > 0 and float(int(P[x])) >= tau * T]
-        out_t.extend([int(traj[n])] * len(keep))
-        out_b.extend([int(prefix[n]) | (x << start) for x in keep])
-        out_p.extend([float(int(P[x])) / T for x in keep])
-    return (np.array(out_t, dtype=np.int64), np.array(out_b, dtype=np.uint64),
-            np.array(out_p, dtype=np.float64))
+        Pf = P.astype(np.float64)             # each P_x rounded to FP64, like float(int(P_x))
+        keep = np.nonzero((P > 0) & (Pf >= tau * T))[0]
+        out_t.append(np.full(len(keep), int(traj[n]), dtype=np.int64))
+        out_b.append(np.uint64(int(prefix[n])) | (keep.astype(np.uint64) << np.uint64(start)))
+        out_p.append(Pf[keep] / T)
+    if not out_t:
+        return np.zeros(0, np.int64), np.zeros(0, np.uint64), np.zeros(0, np.float64)
+    return np.concatenate(out_t), np.concatenate(out_b), np.concatenate(out_p)
 
 
 def nbs_nonproportional(marginal_fn, blocks, seed, n_traj, branch=1, mode="exhaustive", final_shots=0,

@@ -51,8 +51,11 @@ struct ChunkCtx {
 // ---- launchers (kernels_contract.cu)
 void launch_contract_step(const StepDesc* d_step, const StepDesc& h_step, const ChunkCtx& ctx,
                           int64_t n_inst, cudaStream_t s);
-void launch_finalize(const RootRef* d_root, const ChunkCtx& ctx, int b, int64_t n_net,
-                     float* marg, double* Z, cudaStream_t s);
+// marginal rows (real diagonal of the root) and their FP64 totals; part holds
+// n_net * finalize_tiles(b) doubles when finalize_tiles(b) > 1 (else unused)
+int64_t finalize_tiles(int b);
+void launch_finalize(const RootRef* d_root, const ChunkCtx& ctx, int b, int64_t n_net, float* marg, double* Z,
+                     double* part, cudaStream_t s);
 
 // ---- tensor-core steps (kernels_gemm.cu); err: device word set on a timeout
 // Networks of a chunk grouped by trajectory: group g holds networks
@@ -90,7 +93,8 @@ void launch_expval_reduce(const int64_t* mult, const double* F, const double* pa
                           double* value, double* grad, cudaStream_t s);
 
 // ---- launchers (kernels_sample.cu)
-void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, uint64_t seed,
+// trajectory traj0 + i of the draw is row i (Philox counter word 2 = traj0 + i)
+void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, int64_t traj0, uint64_t seed,
                       int32_t circuit, uint8_t* kraus, double* logq, cudaStream_t s);
 void launch_row_hash(const uint8_t* kraus, int64_t n, int32_t S, uint64_t* h, cudaStream_t s);
 void launch_first_occurrence(const uint8_t* kraus, const uint64_t* h, int64_t n, int32_t S,
@@ -122,6 +126,40 @@ void launch_run_flags(const uint64_t* key, int64_t n, int64_t* flag, cudaStream_
 void launch_run_starts(const int64_t* flag, const int64_t* excl, int64_t n, int64_t* start, cudaStream_t s);
 void launch_run_sum(const uint64_t* key, const int64_t* val, const int64_t* start, int64_t n_runs, int64_t n,
                     int32_t* traj_out, uint64_t* bits_out, int64_t* count_out, cudaStream_t s);
+
+// ---- final-block harvest of non-proportional sampling (kernels_harvest.cu)
+struct HarvestArgs {
+    const float* marg;          // [n_net][2^b] population vectors (unnormalised marginals)
+    int b, start;
+    int64_t n_net;
+    bool direct;                // true: `shots` draws per network; false: threshold `tau`
+    double tau;
+    const int32_t* traj;        // [n_net]
+    const uint64_t* prefix;     // [n_net]
+    const int64_t* rank0;       // [n_net] first shot rank of each network (direct)
+    int64_t shots;
+    uint64_t seed;
+    int circuit, block;
+};
+struct HarvestScratch {
+    unsigned* rowmax;           // [n_net]
+    unsigned long long* T;      // [n_net]
+    uint64_t* tcdf;             // [n_net][harvest_cdf_tiles(b)] (direct)
+    int64_t* tcnt;              // [n_net * harvest_tiles(b)]
+    int64_t* toff;              // [n_net * harvest_tiles(b)]
+    int64_t* scan_tmp;          // scan_tmp_elems(n_net * harvest_tiles(b))
+    unsigned* cnt;              // [n_net][2^b] (direct)
+};
+int64_t harvest_tiles(int b);
+int64_t harvest_cdf_tiles(int b);
+// rank0[i] = (i - first network of traj[i]) * shots; first: n_traj_max scratch
+void launch_harvest_ranks(const int32_t* traj, int64_t n, int64_t n_traj_max, int64_t shots,
+                          unsigned long long* first, int64_t* rank0, cudaStream_t s);
+// number of records of the networks (synchronises the stream), then the records
+int64_t run_harvest_count(const HarvestArgs& a, const HarvestScratch& h, int64_t* host_tmp, cudaStream_t s,
+                          ptn_status* st);
+void run_harvest_write(const HarvestArgs& a, const HarvestScratch& h, int32_t* otraj, uint64_t* obits,
+                       int64_t* ocount, double* oprob, cudaStream_t s);
 
 struct SampleScratch {
     int64_t* cap;        // [n_parent] min(count, 2^b)

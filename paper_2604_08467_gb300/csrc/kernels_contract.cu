@@ -332,35 +332,66 @@ static void launch_micro(const StepDesc* d_step, const ChunkCtx& ctx, int64_t n_
 }
 
 // marg[n][x] = Re(root_n[x]) (the double-layer diagonal), Z[n] = sum_x in FP64.
-__global__ void __launch_bounds__(256) k_finalize(const RootRef* __restrict__ groot, ChunkCtx c, int b,
-                                                  float* __restrict__ marg, double* __restrict__ Z) {
+// One block per (network, tile of kFinTile consecutive block outcomes x); a
+// thread takes kFinPer consecutive x and steps its root offset from x to x + 1
+// with delta[ctz(~x)] (delta[k] = stride[k] - sum of the strides below k).
+// Z is the FP64 sum of the tile (written directly when the block has one tile,
+// otherwise as a partial that k_finalize_sum adds in tile order).
+constexpr int kFinThreads = 256, kFinPer = 16, kFinTile = kFinThreads * kFinPer;
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const RootRef* __restrict__ groot, ChunkCtx c, int b,
+                                                          int64_t tiles, float* __restrict__ marg,
+                                                          double* __restrict__ Z, double* __restrict__ part) {
     __shared__ __align__(16) RootRef r;
-    __shared__ double red[256];
+    __shared__ int64_t delta[32];
+    __shared__ double red[kFinThreads / 32];
     {
         const int4* src = reinterpret_cast<const int4*>(groot);
         int4* dst = reinterpret_cast<int4*>(&r);
         for (int i = threadIdx.x; i < (int)(sizeof(RootRef) / sizeof(int4)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    const int64_t net = blockIdx.x;
+    if (threadIdx.x < 32) {
+        int64_t below = 0;
+        for (int t = 0; t < (int)threadIdx.x && t < b; t++) below += r.x_stride[t];
+        delta[threadIdx.x] = (int)threadIdx.x < b ? r.x_stride[threadIdx.x] - below : 0;
+    }
+    __syncthreads();
+    const int64_t net = blockIdx.x / tiles, tile = blockIdx.x - net * tiles;
     const float2* R = operand_ptr(r.op, CLS_NET, net, c);
     const int64_t nx = (int64_t)1 << b;
+    int64_t x = tile * kFinTile + (int64_t)threadIdx.x * kFinPer;
     double acc = 0.0;
-    for (int64_t x = threadIdx.x; x < nx; x += blockDim.x) {
+    if (x < nx) {
         int64_t off = 0;
         for (int t = 0; t < b; t++)
             if ((x >> t) & 1) off += r.x_stride[t];
-        const float v = R[off].x;
-        marg[net * nx + x] = v;
-        acc += (double)v;
+        float* out = marg + net * nx;
+        for (int k = 0; k < kFinPer && x < nx; k++, x++) {
+            const float v = R[off].x;
+            out[x] = v;
+            acc += (double)v;
+            off += delta[__ffsll(~x) - 1];
+        }
     }
-    red[threadIdx.x] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kFinThreads / 32; w++) t += red[w];
+        if (tiles == 1) Z[net] = t;
+        else part[blockIdx.x] = t;
     }
-    if (threadIdx.x == 0) Z[net] = red[0];
+}
+
+// Z[net] = sum of its tiles' partials, in tile order
+__global__ void k_finalize_sum(const double* __restrict__ part, int64_t tiles, int64_t n_net, double* __restrict__ Z) {
+    const int64_t net = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (net >= n_net) return;
+    double t = 0.0;
+    for (int64_t k = 0; k < tiles; k++) t += part[net * tiles + k];
+    Z[net] = t;
 }
 
 }  // namespace
@@ -418,11 +449,15 @@ void launch_contract_step(const StepDesc* d_step, const StepDesc& h, const Chunk
         k_contract_direct<int64_t><<<(unsigned)blocks, kDirThreads, 0, s>>>(d_step, ctx, n_inst);
 }
 
+int64_t finalize_tiles(int b) { return (((int64_t)1 << b) + kFinTile - 1) / kFinTile; }
+
 void launch_finalize(const RootRef* d_root, const ChunkCtx& ctx, int b, int64_t n_net, float* marg, double* Z,
-                     cudaStream_t s) {
+                     double* part, cudaStream_t s) {
     if (n_net <= 0) return;
+    const int64_t tiles = finalize_tiles(b);
     StatScope sc(K_FINALIZE, s, (double)n_net * (double)(1ll << b) * 12.0, 0.0);
-    k_finalize<<<(unsigned)n_net, 256, 0, s>>>(d_root, ctx, b, marg, Z);
+    k_finalize<<<(unsigned)(n_net * tiles), kFinThreads, 0, s>>>(d_root, ctx, b, tiles, marg, Z, part);
+    if (tiles > 1) k_finalize_sum<<<(unsigned)((n_net + 127) / 128), 128, 0, s>>>(part, tiles, n_net, Z);
 }
 
 }  // namespace ptn

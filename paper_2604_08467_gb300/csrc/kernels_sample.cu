@@ -21,14 +21,14 @@ namespace {
 constexpr int kScanTile = 2048;   // elements per block in the scan (1024 threads x 2)
 
 // ------------------------------------------------------------- presample --
-__global__ void k_presample(const SiteTable* __restrict__ sites, int32_t S, int64_t n_traj, uint2 key,
+__global__ void k_presample(const SiteTable* __restrict__ sites, int32_t S, int64_t n_traj, int64_t traj0, uint2 key,
                             uint32_t tagw, uint8_t* __restrict__ kraus) {
     const int64_t total = n_traj * S;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = g / S;
         const int32_t s = (int32_t)(g - i * S);
-        const uint4 x = philox4x32_10(make_uint4((uint32_t)s, 0u, (uint32_t)i, tagw), key);
+        const uint4 x = philox4x32_10(make_uint4((uint32_t)s, 0u, (uint32_t)(traj0 + i), tagw), key);
         const double u = (double)(word64(x) >> 11) * 0x1p-53;
         const SiteTable& T = sites[s];
         int k = 0;
@@ -348,12 +348,12 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 64) {
 
 }  // namespace
 
-void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, uint64_t seed, int32_t circuit,
-                      uint8_t* kraus, double* logq, cudaStream_t s) {
+void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, int64_t traj0, uint64_t seed,
+                      int32_t circuit, uint8_t* kraus, double* logq, cudaStream_t s) {
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     if (n_sites > 0) {
         StatScope sc(K_PRESAMPLE, s, (double)n_traj * n_sites, 0.0);
-        k_presample<<<grid_for(n_traj * n_sites, 256), 256, 0, s>>>(sites, n_sites, n_traj, key,
+        k_presample<<<grid_for(n_traj * n_sites, 256), 256, 0, s>>>(sites, n_sites, n_traj, traj0, key,
                                                                     philox_tag(STREAM_KRAUS, circuit, 0), kraus);
     }
     StatScope sc2(K_LOGQ, s, (double)n_traj * (n_sites + 8), 0.0);

@@ -1493,8 +1493,12 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
     }
     if ((int)bs.size() > kMaxBlocks) return set_error(PTN_ERR_INVALID_ARG, "too many blocks");
     int tot = 0;
-    for (int32_t v : bs) {
-        if (v < 1 || v > 14) return set_error(PTN_ERR_INVALID_ARG, "block sizes must be in 1..14");
+    for (size_t j = 0; j < bs.size(); j++) {
+        const int32_t v = bs[j];
+        const int32_t vmax = j + 1 == bs.size() ? kMaxFinalBlock : kMaxSampleBlock;
+        if (v < 1 || v > vmax)
+            return set_error(PTN_ERR_INVALID_ARG, "block sizes must be in 1..%d (the last block 1..%d)", kMaxSampleBlock,
+                             kMaxFinalBlock);
         tot += v;
     }
     if (tot != n) return set_error(PTN_ERR_INVALID_ARG, "block sizes sum to %d, circuit has %d qubits", tot, n);

@@ -26,6 +26,8 @@ constexpr int kMaxOut = 40;     // output bits of one contraction step
 constexpr int kMaxSum = 24;     // summed bits of one contraction step
 constexpr int kMaxSlice = 64;   // prefix (projected) bits read by one operand
 constexpr int kMaxBlocks = 64;
+constexpr int kMaxSampleBlock = 14;   // blocks sampled by conditional draws (marginal CDF in shared memory)
+constexpr int kMaxFinalBlock = 30;    // last block: harvested from its population vector in global memory
 constexpr int kMaxKraus = 16;
 
 // One operand of a batched pairwise contraction, as the kernels read it.
@@ -101,7 +103,7 @@ struct ParamLeaf {
 
 struct RootRef {             // where the block's final tensor lives
     OperandDesc op;          // read with NET addressing (slices applied)
-    int64_t x_stride[24];    // stride of block bit t in the root tensor
+    int64_t x_stride[32];    // stride of block bit t (or, for the whole-circuit state, qubit t) in the root
 };
 
 struct BlockPlan {

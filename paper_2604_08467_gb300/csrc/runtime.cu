@@ -132,6 +132,9 @@ struct PlanWorkspace {
     // expectation / gradient plans
     DevBuf arena_x[2];                    // ADJ, LGRAD arenas
     DevBuf ev_steps, ev_bwd, ev_root, ev_pl, ev_dvt, ev_terms, ev_F, ev_partial, ev_iota;
+    DevBuf zpart;                         // per-tile partial totals of large marginal rows
+    // final-block harvest of non-proportional sampling
+    DevBuf h_rowmax, h_T, h_tcdf, h_tcnt, h_toff, h_scan, h_cnt, h_rank0, h_first;
     HostBuf h_traj, h_chunk_traj, h_net_tl, h_small, h_grp;
     void release() {
         DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &marg, &Z, &w, &cdf, &m,
@@ -139,7 +142,8 @@ struct PlanWorkspace {
                          &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
                          &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err, &grp, &grp_cnt,
                          &grp_tile0, &grp_scan, &arena_x[0], &arena_x[1], &ev_steps,
-                         &ev_bwd, &ev_root, &ev_pl, &ev_dvt, &ev_terms, &ev_F, &ev_partial, &ev_iota};
+                         &ev_bwd, &ev_root, &ev_pl, &ev_dvt, &ev_terms, &ev_F, &ev_partial, &ev_iota, &zpart,
+                         &h_rowmax, &h_T, &h_tcdf, &h_tcnt, &h_toff, &h_scan, &h_cnt, &h_rank0, &h_first};
         for (DevBuf* b : all) b->release();
         h_grp.release();
         h_traj.release();
@@ -167,6 +171,7 @@ struct ptn_shots {
     int32_t* traj = nullptr;
     uint64_t* bits = nullptr;
     int64_t* count = nullptr;
+    double* prob = nullptr;              // non-proportional final-block harvest: p(x | prefix) per record
     std::vector<int64_t> nets_per_block;
 };
 
@@ -362,6 +367,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     }
     if ((e = ws->err.grow(sizeof(int)))) return e;
     if ((e = ws->h_small.grow(64))) return e;
+    if (finalize_tiles(bp.b) > 1 && (e = ws->zpart.grow(sizeof(double) * max_n * finalize_tiles(bp.b)))) return e;
     PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
     const RootRef* d_root = plan->d_roots + j;
     for (size_t ci = 0; ci < chunks.size(); ci++) {
@@ -400,7 +406,8 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
             }
         }
         StepTag tag(j, (int)bp.steps.size());
-        launch_finalize(d_root, ctx, bp.b, c.n_net, marg + c.net0 * ((int64_t)1 << bp.b), Z + c.net0, s);
+        launch_finalize(d_root, ctx, bp.b, c.n_net, marg + c.net0 * ((int64_t)1 << bp.b), Z + c.net0,
+                        ws->zpart.as<double>(), s);
     }
     PTN_CUDA(cudaGetLastError());
     // a tensor-core step that gave up a bounded wait reports it through the error word
@@ -487,9 +494,26 @@ void ptn_plan_destroy(ptn_plan* plan) {
     delete plan;
 }
 
+static ptn_status presample_impl(const ptn_plan* plan, uint64_t seed, int32_t circuit_id, int64_t traj0,
+                                 int64_t n_traj, int32_t dedup, ptn_traj** traj_out, ptn_stream stream);
+
 ptn_status ptn_presample_trajectories(const ptn_plan* plan, uint64_t seed, int32_t circuit_id, int64_t n_traj,
                                       int32_t dedup, ptn_traj** traj_out, ptn_stream stream) {
     clear_error();
+    return presample_impl(plan, seed, circuit_id, 0, n_traj, dedup, traj_out, stream);
+}
+
+ptn_status ptn_presample_range(const ptn_plan* plan, uint64_t seed, int32_t circuit_id, int64_t traj0, int64_t n_traj,
+                               ptn_traj** traj_out, ptn_stream stream) {
+    clear_error();
+    if (traj0 < 0 || traj0 + n_traj > ((int64_t)1 << 32))
+        return set_error(PTN_ERR_INVALID_ARG, "trajectory range [%lld, %lld) outside 0..2^32", (long long)traj0,
+                         (long long)(traj0 + n_traj));
+    return presample_impl(plan, seed, circuit_id, traj0, n_traj, 0, traj_out, stream);
+}
+
+static ptn_status presample_impl(const ptn_plan* plan, uint64_t seed, int32_t circuit_id, int64_t traj0,
+                                 int64_t n_traj, int32_t dedup, ptn_traj** traj_out, ptn_stream stream) {
     if (!plan || !traj_out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
     *traj_out = nullptr;
     if (n_traj < 1 || n_traj > (1 << 24)) return set_error(PTN_ERR_INVALID_ARG, "n_traj %lld out of 1..2^24", (long long)n_traj);
@@ -525,7 +549,7 @@ ptn_status ptn_presample_trajectories(const ptn_plan* plan, uint64_t seed, int32
     } while (0)
     TRY_CUDA(cudaMalloc(&kraus, std::max<size_t>((size_t)n_traj * S, 16)));
     TRY_CUDA(cudaMalloc(&logq, sizeof(double) * n_traj));
-    launch_presample(plan->d_site_tables, S, n_traj, seed, circuit_id, kraus, logq, s);
+    launch_presample(plan->d_site_tables, S, n_traj, traj0, seed, circuit_id, kraus, logq, s);
     TRY_CUDA(cudaGetLastError());
     if (!dedup) {
         t->n_unique = n_traj;
@@ -536,9 +560,9 @@ ptn_status ptn_presample_trajectories(const ptn_plan* plan, uint64_t seed, int32
         TRY_CUDA(cudaMalloc(&t->mult, sizeof(int64_t) * n_traj));
         TRY_CUDA(cudaMalloc(&t->first, sizeof(int64_t) * n_traj));
         launch_fill_i64(t->mult, 1, n_traj, s);
-        // first = identity
+        // first = the trajectory's index in the whole draw
         std::vector<int64_t> id(n_traj);
-        for (int64_t i = 0; i < n_traj; i++) id[i] = i;
+        for (int64_t i = 0; i < n_traj; i++) id[i] = traj0 + i;
         TRY_CUDA(cudaMemcpyAsync(t->first, id.data(), sizeof(int64_t) * n_traj, cudaMemcpyHostToDevice, s));
         TRY_CUDA(cudaStreamSynchronize(s));
     } else {
@@ -950,15 +974,212 @@ ptn_status ptn_sample_block(const float* marg, int32_t b, int32_t start, const i
     return PTN_OK;
 }
 
+// Non-proportional NBS (Sec. III-B): every non-final block draws branch_shots
+// shots per distinct prefix (its distinct outcomes become the next block's
+// prefixes); the final block's networks are contracted in sub-batches that fit
+// half the memory cap and each sub-batch's population vectors are harvested
+// at once (direct draws or threshold), the records appended in order.
+static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, const ptn_sample_opts* o,
+                                 ptn_shots** shots_out, cudaStream_t s) {
+    const bool direct = o->mode == PTN_NONPROP_DIRECT;
+    if (o->branch_shots < 1) return set_error(PTN_ERR_INVALID_ARG, "branch_shots must be >= 1");
+    if (direct && o->final_shots < 1) return set_error(PTN_ERR_INVALID_ARG, "final_shots must be >= 1");
+    if (!direct && !(o->threshold >= 0.0 && o->threshold <= 1.0))
+        return set_error(PTN_ERR_INVALID_ARG, "threshold must be in [0, 1]");
+    ptn_status e = ensure_device(plan);
+    if (e) return e;
+    PlanWorkspace* ws = workspace(plan);
+    const int64_t E = traj->n_unique;
+    const int nblk = (int)plan->blocks.size();
+    if ((e = ws->h_small.grow(64))) return e;
+    auto grow_level = [&](int k, int64_t cap) -> ptn_status {
+        ptn_status g;
+        if ((g = ws->lvl_traj[k].grow(sizeof(int32_t) * cap)) || (g = ws->lvl_prefix[k].grow(sizeof(uint64_t) * cap)) ||
+            (g = ws->lvl_count[k].grow(sizeof(int64_t) * cap)))
+            return g;
+        return PTN_OK;
+    };
+    int cur = 0;
+    int64_t n = E;
+    if ((e = grow_level(0, E))) return e;
+    launch_iota_i32(ws->lvl_traj[0].as<int32_t>(), E, s);
+    PTN_CUDA(cudaMemsetAsync(ws->lvl_prefix[0].p, 0, sizeof(uint64_t) * E, s));
+    std::vector<int64_t> nets;
+    for (int j = 0; j + 1 < nblk && n > 0; j++) {
+        const BlockPlan& bp = plan->blocks[j];
+        const int64_t nb = (int64_t)1 << bp.b;
+        if ((e = ws->marg.grow(sizeof(float) * n * nb)) || (e = ws->Z.grow(sizeof(double) * n))) return e;
+        e = contract_level(plan, traj, j, ws->lvl_traj[cur].as<int32_t>(), ws->lvl_prefix[cur].as<uint64_t>(), n,
+                           ws->marg.as<float>(), ws->Z.as<double>(), o->max_traj_per_chunk, o->precision, s);
+        if (e) return e;
+        launch_fill_i64(ws->lvl_count[cur].as<int64_t>(), o->branch_shots, n, s);
+        const int64_t child_cap = n * std::min<int64_t>(o->branch_shots, nb);
+        if ((e = grow_level(1 - cur, child_cap))) return e;
+        SampleScratch sc;
+        if ((e = alloc_sample_scratch(ws, n, E, child_cap, sc))) return e;
+        ptn_status st;
+        const int64_t nc = run_sample_block(ws->marg.as<float>(), bp.b, bp.start, ws->lvl_traj[cur].as<int32_t>(),
+                                            ws->lvl_prefix[cur].as<uint64_t>(), ws->lvl_count[cur].as<int64_t>(), n, E,
+                                            o->seed, o->circuit_id, j, ws->lvl_traj[1 - cur].as<int32_t>(),
+                                            ws->lvl_prefix[1 - cur].as<uint64_t>(), ws->lvl_count[1 - cur].as<int64_t>(),
+                                            child_cap, sc, ws->h_small.as<int64_t>(), s, &st);
+        if (st != PTN_OK) return st;
+        nets.push_back(n);
+        cur = 1 - cur;
+        n = nc;
+    }
+    // ---- final block
+    const int jf = nblk - 1;
+    const BlockPlan& bf = plan->blocks[jf];
+    const int64_t nx = (int64_t)1 << bf.b;
+    nets.push_back(n);
+    const int32_t* ftraj = ws->lvl_traj[cur].as<int32_t>();
+    const uint64_t* fprefix = ws->lvl_prefix[cur].as<uint64_t>();
+    if (direct && n > 0) {
+        if ((e = ws->h_rank0.grow(sizeof(int64_t) * n)) || (e = ws->h_first.grow(sizeof(uint64_t) * E))) return e;
+        launch_harvest_ranks(ftraj, n, E, o->final_shots, ws->h_first.as<unsigned long long>(),
+                             ws->h_rank0.as<int64_t>(), s);
+    }
+    const int64_t tiles = harvest_tiles(bf.b), tiles256 = harvest_cdf_tiles(bf.b);
+    const double per_net = 4.0 * nx + 8.0 + 8.0 * finalize_tiles(bf.b) + 12.0 + 16.0 * tiles + 8.0 * scan_tmp_elems(tiles) +
+                           (direct ? 4.0 * nx + 8.0 * tiles256 : 0.0);
+    const int64_t sub = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(0.5 * plan->mem_cap / per_net)));
+    if (n > 0) {
+        if ((e = ws->marg.grow(sizeof(float) * sub * nx)) || (e = ws->Z.grow(sizeof(double) * sub)) ||
+            (e = ws->h_rowmax.grow(sizeof(unsigned) * sub)) || (e = ws->h_T.grow(sizeof(uint64_t) * sub)) ||
+            (e = ws->h_tcnt.grow(sizeof(int64_t) * sub * tiles)) || (e = ws->h_toff.grow(sizeof(int64_t) * sub * tiles)) ||
+            (e = ws->h_scan.grow(sizeof(int64_t) * scan_tmp_elems(sub * tiles))))
+            return e;
+        if (direct && ((e = ws->h_tcdf.grow(sizeof(uint64_t) * sub * tiles256)) ||
+                       (e = ws->h_cnt.grow(sizeof(unsigned) * sub * nx))))
+            return e;
+    }
+    HarvestScratch hs;
+    hs.rowmax = ws->h_rowmax.as<unsigned>();
+    hs.T = ws->h_T.as<unsigned long long>();
+    hs.tcdf = ws->h_tcdf.as<uint64_t>();
+    hs.tcnt = ws->h_tcnt.as<int64_t>();
+    hs.toff = ws->h_toff.as<int64_t>();
+    hs.scan_tmp = ws->h_scan.as<int64_t>();
+    hs.cnt = ws->h_cnt.as<unsigned>();
+    struct Part {
+        int32_t* t;
+        uint64_t* b;
+        int64_t* c;
+        double* p;
+        int64_t n;
+    };
+    std::vector<Part> parts;
+    auto free_parts = [&]() {
+        for (Part& p : parts) {
+            cudaFree(p.t);
+            cudaFree(p.b);
+            cudaFree(p.c);
+            cudaFree(p.p);
+        }
+        parts.clear();
+    };
+    int64_t total = 0;
+    for (int64_t a = 0; a < n; a += sub) {
+        const int64_t m = std::min(sub, n - a);
+        e = contract_level(plan, traj, jf, ftraj + a, fprefix + a, m, ws->marg.as<float>(), ws->Z.as<double>(),
+                           o->max_traj_per_chunk, o->precision, s);
+        if (e) {
+            free_parts();
+            return e;
+        }
+        HarvestArgs ha;
+        ha.marg = ws->marg.as<float>();
+        ha.b = bf.b;
+        ha.start = bf.start;
+        ha.n_net = m;
+        ha.direct = direct;
+        ha.tau = o->threshold;
+        ha.traj = ftraj + a;
+        ha.prefix = fprefix + a;
+        ha.rank0 = direct ? ws->h_rank0.as<int64_t>() + a : nullptr;
+        ha.shots = o->final_shots;
+        ha.seed = o->seed;
+        ha.circuit = o->circuit_id;
+        ha.block = jf;
+        ptn_status st;
+        const int64_t nr = run_harvest_count(ha, hs, ws->h_small.as<int64_t>(), s, &st);
+        if (st != PTN_OK) {
+            free_parts();
+            return st;
+        }
+        if (nr == 0) continue;
+        Part p{nullptr, nullptr, nullptr, nullptr, nr};
+        cudaError_t ce;
+        if ((ce = cudaMalloc(&p.t, sizeof(int32_t) * nr)) != cudaSuccess ||
+            (ce = cudaMalloc(&p.b, sizeof(uint64_t) * nr)) != cudaSuccess ||
+            (ce = cudaMalloc(&p.c, sizeof(int64_t) * nr)) != cudaSuccess ||
+            (ce = cudaMalloc(&p.p, sizeof(double) * nr)) != cudaSuccess) {
+            parts.push_back(p);
+            free_parts();
+            return set_error(PTN_ERR_OOM, "harvest records (%lld): %s", (long long)nr, cudaGetErrorString(ce));
+        }
+        parts.push_back(p);
+        run_harvest_write(ha, hs, p.t, p.b, p.c, p.p, s);
+        total += nr;
+    }
+    ptn_shots* r = new ptn_shots();
+    r->n = total;
+    r->n_qubits = plan->n_qubits;
+    r->nets_per_block = nets;
+    const size_t mcap = std::max<int64_t>(total, 1);
+    cudaError_t ce;
+    if (parts.size() == 1) {
+        r->traj = parts[0].t;
+        r->bits = parts[0].b;
+        r->count = parts[0].c;
+        r->prob = parts[0].p;
+        parts.clear();
+    } else if ((ce = cudaMalloc(&r->traj, sizeof(int32_t) * mcap)) != cudaSuccess ||
+               (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * mcap)) != cudaSuccess ||
+               (ce = cudaMalloc(&r->count, sizeof(int64_t) * mcap)) != cudaSuccess ||
+               (ce = cudaMalloc(&r->prob, sizeof(double) * mcap)) != cudaSuccess) {
+        free_parts();
+        ptn_shots_destroy(r);
+        return set_error(PTN_ERR_OOM, "result allocation: %s", cudaGetErrorString(ce));
+    } else {
+        int64_t o_ = 0;
+        for (Part& p : parts) {
+            cudaMemcpyAsync(r->traj + o_, p.t, sizeof(int32_t) * p.n, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(r->bits + o_, p.b, sizeof(uint64_t) * p.n, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(r->count + o_, p.c, sizeof(int64_t) * p.n, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(r->prob + o_, p.p, sizeof(double) * p.n, cudaMemcpyDeviceToDevice, s);
+            o_ += p.n;
+        }
+        cudaStreamSynchronize(s);
+        free_parts();
+    }
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        ptn_shots_destroy(r);
+        return set_error(PTN_ERR_CUDA, "non-proportional sampling: %s", cudaGetErrorString(ce));
+    }
+    *shots_out = r;
+    return PTN_OK;
+}
+
 ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const ptn_sample_opts* o,
                             ptn_shots** shots_out, ptn_stream stream) {
     clear_error();
     if (!plan || !traj || !o || !shots_out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
     *shots_out = nullptr;
     if (traj->plan != plan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
+    if (o->use_graphs) return set_error(PTN_ERR_UNSUPPORTED, "CUDA-graph capture is not built");
+    if (o->mode == PTN_NONPROP_DIRECT || o->mode == PTN_NONPROP_EXHAUSTIVE)
+        return sample_nonprop(plan, traj, o, shots_out, (cudaStream_t)stream);
     if (o->mode != PTN_PROPORTIONAL_FIXED && o->mode != PTN_PROPORTIONAL_TOTAL)
         return set_error(PTN_ERR_UNSUPPORTED, "sampling mode %d", o->mode);
-    if (o->use_graphs) return set_error(PTN_ERR_UNSUPPORTED, "CUDA-graph capture is not built");
+    for (size_t j = 0; j < plan->blocks.size(); j++)
+        if (plan->blocks[j].b > kMaxSampleBlock)
+            return set_error(PTN_ERR_UNSUPPORTED,
+                             "block %zu has %d qubits; proportional sampling draws from blocks of at most %d "
+                             "(larger final blocks are harvested by the non-proportional modes)",
+                             j, plan->blocks[j].b, kMaxSampleBlock);
     int64_t total_cap;
     if (o->mode == PTN_PROPORTIONAL_FIXED) {
         if (o->shots_per_traj < 1) return set_error(PTN_ERR_INVALID_ARG, "shots_per_traj must be >= 1");
@@ -1279,11 +1500,27 @@ ptn_status ptn_shots_copy(const ptn_shots* r, int32_t* traj_out, uint64_t* bits_
     return PTN_OK;
 }
 
+ptn_status ptn_shots_probs(const ptn_shots* r, const double** prob) {
+    if (!r || !prob) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    *prob = r->prob;
+    return PTN_OK;
+}
+
+ptn_status ptn_shots_copy_probs(const ptn_shots* r, double* prob_out, ptn_stream stream) {
+    if (!r || !prob_out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    if (!r->prob) return set_error(PTN_ERR_INVALID_ARG, "these shots carry no probabilities");
+    if (r->n > 0)
+        PTN_CUDA(cudaMemcpyAsync(prob_out, r->prob, sizeof(double) * r->n, cudaMemcpyDeviceToDevice,
+                                 (cudaStream_t)stream));
+    return PTN_OK;
+}
+
 void ptn_shots_destroy(ptn_shots* r) {
     if (!r) return;
     cudaFree(r->traj);
     cudaFree(r->bits);
     cudaFree(r->count);
+    cudaFree(r->prob);
     delete r;
 }
 

@@ -22,7 +22,7 @@ PTN_OK = 0
 STATUS_NAMES = {0: "PTN_OK", 1: "PTN_ERR_INVALID_ARG", 2: "PTN_ERR_NOT_CPTP", 3: "PTN_ERR_TOO_LARGE",
                 4: "PTN_ERR_OOM", 5: "PTN_ERR_CUDA", 6: "PTN_ERR_TIMEOUT", 7: "PTN_ERR_UNSUPPORTED"}
 PTN_PREC_FP32, PTN_PREC_BF16X3, PTN_PREC_FP16X3 = 0, 1, 2
-PTN_PROPORTIONAL_FIXED, PTN_PROPORTIONAL_TOTAL = 0, 1
+PTN_PROPORTIONAL_FIXED, PTN_PROPORTIONAL_TOTAL, PTN_NONPROP_DIRECT, PTN_NONPROP_EXHAUSTIVE = 0, 1, 2, 3
 
 
 class PtnError(RuntimeError):
@@ -63,7 +63,8 @@ class ptn_plan_opts(C.Structure):
 class ptn_sample_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("circuit_id", C.c_int32), ("shots_per_traj", C.c_int64),
                 ("total_shots", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int32),
-                ("max_traj_per_chunk", C.c_int32), ("use_graphs", C.c_int32), ("reserved", C.c_int32)]
+                ("max_traj_per_chunk", C.c_int32), ("use_graphs", C.c_int32), ("reserved", C.c_int32),
+                ("branch_shots", C.c_int64), ("final_shots", C.c_int64), ("threshold", C.c_double)]
 
 
 class ptn_step_stat(C.Structure):
@@ -97,6 +98,7 @@ _SIGS = {
     "ptn_plan_describe": [_P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
     "ptn_plan_destroy": [_P],
     "ptn_presample_trajectories": [_P, C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.POINTER(_P), _P],
+    "ptn_presample_range": [_P, C.c_uint64, C.c_int32, C.c_int64, C.c_int64, C.POINTER(_P), _P],
     "ptn_traj_info": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(_P), C.POINTER(_P),
                       C.POINTER(_P), C.POINTER(_P)],
     "ptn_traj_copy": [_P, _P, _P, _P, _P, _P],
@@ -112,6 +114,8 @@ _SIGS = {
                        C.POINTER(C.c_int64), C.c_int32],
     "ptn_shots_copy": [_P, _P, _P, _P, _P],
     "ptn_shots_destroy": [_P],
+    "ptn_shots_probs": [_P, C.POINTER(_P)],
+    "ptn_shots_copy_probs": [_P, _P, _P],
     "ptn_shots_merge": [_P, C.POINTER(_P), _P],
     "ptn_sample_shots_batch": [C.POINTER(ptn_batch_item), C.c_int32, C.POINTER(ptn_batch_opts), C.POINTER(_P),
                                C.POINTER(C.c_int), _P],
@@ -279,6 +283,13 @@ class Shots:
         _check(lib().ptn_shots_copy(self.handle, _ptr(t), _ptr(b), _ptr(c), _stream(stream)))
         return t, b, c
 
+    def probs(self, stream=None):
+        """Per-record probabilities p(x | prefix) (non-proportional results)."""
+        import torch
+        p = torch.empty(self.n, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+        _check(lib().ptn_shots_copy_probs(self.handle, _ptr(p), _stream(stream)))
+        return p
+
     def __del__(self):
         if getattr(self, "handle", None) and _lib_handle is not None:
             _lib_handle.ptn_shots_destroy(self.handle)
@@ -307,6 +318,15 @@ def ptn_presample_trajectories(plan, seed, n_traj, dedup=False, circuit_id=0, st
     h = C.c_void_p()
     _check(lib().ptn_presample_trajectories(plan.handle, seed, circuit_id, n_traj, int(bool(dedup)),
                                             C.byref(h), _stream(stream)))
+    return Traj(h, plan)
+
+
+def ptn_presample_range(plan, seed, traj0, n_traj, circuit_id=0, stream=None):
+    """Trajectories traj0 .. traj0 + n_traj - 1 of the draw made from `seed`
+    (global Philox counters, no dedup)."""
+    h = C.c_void_p()
+    _check(lib().ptn_presample_range(plan.handle, seed, circuit_id, int(traj0), int(n_traj), C.byref(h),
+                                     _stream(stream)))
     return Traj(h, plan)
 
 
@@ -373,7 +393,20 @@ def _sample_opts(seed, shots_per_traj=None, total_shots=None, circuit_id=0, prec
                  max_traj_per_chunk=0):
     mode = PTN_PROPORTIONAL_FIXED if total_shots is None else PTN_PROPORTIONAL_TOTAL
     return ptn_sample_opts(mode, circuit_id, int(shots_per_traj or 0), int(total_shots or 0), seed, precision,
-                           max_traj_per_chunk, 0, 0)
+                           max_traj_per_chunk, 0, 0, 0, 0, 0.0)
+
+
+def ptn_sample_nonprop(plan, traj, seed, mode="exhaustive", branch_shots=1, final_shots=0, threshold=0.0,
+                       circuit_id=0, precision=PTN_PREC_FP32, max_traj_per_chunk=0, stream=None):
+    """Non-proportional NBS (include/ptn.h): branch_shots per prefix on the
+    non-final blocks, then the final block harvested directly (final_shots
+    draws per network) or exhaustively (p(x | prefix) >= threshold)."""
+    code = {"direct": PTN_NONPROP_DIRECT, "exhaustive": PTN_NONPROP_EXHAUSTIVE}[mode]
+    o = ptn_sample_opts(code, circuit_id, 0, 0, seed, precision, max_traj_per_chunk, 0, 0, int(branch_shots),
+                        int(final_shots), float(threshold))
+    h = C.c_void_p()
+    _check(lib().ptn_sample_shots(plan.handle, traj.handle, C.byref(o), C.byref(h), _stream(stream)))
+    return Shots(h, len(plan.block_sizes))
 
 
 def ptn_sample_shots_batch(items, n_workers=4, keep_workspaces=False, mem_budget_bytes=0.0, max_est_seconds=0.0,

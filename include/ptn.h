@@ -486,6 +486,16 @@ typedef struct {
 
 ptn_status ptn_stats_read_steps(ptn_step_stat* out, int32_t cap, int32_t* n_out);
 
+/* ---------------------------------------------------------- bounded waits -- */
+
+/* Wall-time limit of every pipeline wait inside the tensor-core contraction
+ * kernel (mbarrier waits between its TMA, MMA and epilogue roles), 2 s by
+ * default, for launches issued after the call (process-wide).  A wait that
+ * runs out makes its CTA stop issuing work, let its own copies and MMAs in
+ * flight finish, free its tensor memory and exit; the call then returns
+ * PTN_ERR_TIMEOUT and the device stays usable.  seconds in [0, 60]. */
+ptn_status ptn_set_wait_limit(double seconds);
+
 /* ------------------------------------------------------------- utilities -- */
 
 const char* ptn_status_string(ptn_status status);

@@ -31,6 +31,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 
 #include "kernels.cuh"
@@ -109,6 +110,7 @@ struct GemmArgs {
     float2* out;
     int64_t out_size;
     int* err;
+    uint64_t wait_ns;            // limit of every pipeline wait (ptn_set_wait_limit)
     const int8_t* exp_a;         // FP16 row exponents of A and B (see PackArgs), else null
     const int8_t* exp_b;
     int64_t m_stride[kMaxOut];
@@ -394,16 +396,16 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait (about 2 s of wall time); false when it gave up or another
-// thread of the block aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// Bounded wait (limit_ns of wall time, 2 s by default); false when it gave up
+// or another thread of the block aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0;; i++) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 255u) == 255u) {
             if (*abort) return false;
-            if (global_ns() - t0 > 2000000000ull) return false;
+            if (global_ns() - t0 > limit_ns) return false;
         }
     }
 }
@@ -580,7 +582,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 const TileInfo t = decode_tile(g, tile);
                 for (int kb = 0; kb < g.nkb; kb++, it++) {
                     const int s = (int)(it % kStages);
-                    if (it >= kStages && !mbar_wait(&empty[s], (uint32_t)((it / kStages) - 1) & 1u, abort)) {
+                    if (it >= kStages && !mbar_wait(&empty[s], (uint32_t)((it / kStages) - 1) & 1u, abort, g.wait_ns)) {
                         atomicExch(g.err, 1);
                         *abort = 1;
                         break;
@@ -593,19 +595,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                     tma_load_3d(st + 2 * kTileA + kTileB, &tmB, g.Kh + kb * kBK, t.n0, t.zb, &full[s]);   // B lo
                 }
             }
-            if (*abort) {
-                // let this CTA's own copies land before it exits: the last load of
-                // every stage is that stage's newest phase
-                const int64_t first = it > kStages ? it - kStages : 0;
-                for (int64_t j = first; j < it; j++) mbar_wait_plain(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
-            }
+            // let this CTA's own copies land before it exits (on every path: the
+            // MMA thread may have stopped early): the last load of every stage
+            // is that stage's newest phase
+            const int64_t first = it > kStages ? it - kStages : 0;
+            for (int64_t j = first; j < it; j++) mbar_wait_plain(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
             int64_t it = 0, lt = 0;
             for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x, lt++) {
-                if (lt > 0 && !mbar_wait(acc_empty, (uint32_t)((lt - 1) & 1), abort)) {
+                if (lt > 0 && !mbar_wait(acc_empty, (uint32_t)((lt - 1) & 1), abort, g.wait_ns)) {
                     atomicExch(g.err, 4);
                     *abort = 1;
                     break;
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 bool ok = true;
                 for (int kb = 0; kb < g.nkb; kb++, it++) {
                     const int s = (int)(it % kStages);
-                    if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, abort)) {
+                    if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, abort, g.wait_ns)) {
                         atomicExch(g.err, 2);
                         *abort = 1;
                         ok = false;
@@ -637,10 +638,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 if (!ok) break;
                 umma_commit(acc_full);        // accumulators complete for this tile
             }
-            if (*abort) {   // MMAs still in flight finish before TMEM is freed
-                umma_commit(drain);
-                mbar_wait_plain(drain, 0u);
-            }
+            // MMAs still in flight finish before TMEM is freed (on every path: the
+            // epilogue may have stopped early)
+            umma_commit(drain);
+            mbar_wait_plain(drain, 0u);
         }
         __syncwarp();
     } else {
@@ -649,7 +650,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         int64_t* noff = noff_all + (warp - 2) * (kBN / 2);
         const int n_acc = g.nkb < kAcc ? g.nkb : kAcc;
         int64_t lt = 0;
-        for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x, lt++) {
+        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, lt++) {
+            if (__shfl_sync(0xffffffffu, *abort, 0)) break;   // warp-uniform stop
             const TileInfo t = decode_tile(g, tile);
             for (int c = lane; c < kBN / 2; c += 32) {   // output offsets of this tile's complex columns
                 const int64_t n = (int64_t)(t.n0 / 2) + c;
@@ -659,9 +661,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 noff[c] = off;
             }
             __syncwarp();
-            if (!mbar_wait(acc_full, (uint32_t)(lt & 1), abort)) {
-                if (lane == 0) atomicExch(g.err, 3);
-                *abort = 1;
+            // one lane waits and the warp follows its outcome (lanes polling on
+            // their own could disagree when a wait gives up)
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(acc_full, (uint32_t)(lt & 1), abort, g.wait_ns) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) {
+                    atomicExch(g.err, 3);
+                    *abort = 1;
+                }
                 break;
             }
             __syncwarp();
@@ -733,6 +742,8 @@ __global__ void k_group_tiles(const int32_t* __restrict__ net0, int64_t n_groups
 }
 
 // ---------------------------------------------------------- host helpers --
+std::atomic<uint64_t> g_wait_ns{2000000000ull};   // limit of the GEMM's pipeline waits
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -850,6 +861,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     ga.out = ctx.arena[st.out_arena] + st.out_off * ctx.arena_inst[st.out_arena];
     ga.out_size = st.out_size;
     ga.err = err;
+    ga.wait_ns = g_wait_ns.load(std::memory_order_relaxed);
     const int64_t tot_a = pa.n_pinst * (1ll << nh) * M * (Kh / 2);
     const int64_t tot_b = pb.n_pinst * (1ll << nh) * N * (Kh / 2);
     cudaError_t e;
@@ -946,3 +958,10 @@ ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_i
 }
 
 }  // namespace ptn
+
+extern "C" ptn_status ptn_set_wait_limit(double seconds) {
+    if (!(seconds >= 0.0 && seconds <= 60.0))
+        return ptn::set_error(PTN_ERR_INVALID_ARG, "wait limit %g s outside 0..60", seconds);
+    ptn::g_wait_ns.store((uint64_t)(seconds * 1e9), std::memory_order_relaxed);
+    return PTN_OK;
+}

@@ -319,6 +319,104 @@ __global__ void __launch_bounds__(256) k_sample_parents(const float* __restrict_
     if (threadIdx.x == 0) ndist[n] = wpos;
 }
 
+// Blocks of up to 2^10 bins: one warp per parent, kSampWarps parents per CTA,
+// no CTA-wide barrier.  Lane l owns the bins [l * per, (l + 1) * per): the
+// row maximum is a shuffle reduction, the exact-integer CDF the lane's own
+// running sums plus a shuffle scan of the lane totals (exact in FP64 in any
+// order), the draws search the warp's CDF in shared memory and count into its
+// histogram, and the nonzero bins are compacted in x order through a shuffle
+// scan of the lanes' counts.  Same arithmetic and results as
+// k_sample_parents.
+constexpr int kSampWarps = 4;
+constexpr int kSampWarpMaxBits = 10;
+
+__device__ __forceinline__ double warp_excl_scan_f64(double v, int lane) {
+    double inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    return inc - v;
+}
+
+__global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
+    const float* __restrict__ marg, int b, int64_t n_parent, const int32_t* __restrict__ traj,
+    const int64_t* __restrict__ count, const int64_t* __restrict__ rank0, const int64_t* __restrict__ tmp_off,
+    int64_t tmp_cap, uint2 key, uint32_t tagw, int32_t* __restrict__ tmp_x, int64_t* __restrict__ tmp_c,
+    int64_t* __restrict__ ndist) {
+    extern __shared__ unsigned char smem[];
+    const int nb = 1 << b;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* C = reinterpret_cast<double*>(smem) + (int64_t)wib * nb;
+    unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<double*>(smem) + (int64_t)kSampWarps * nb) +
+                     (int64_t)wib * nb;
+    const int64_t n = (int64_t)blockIdx.x * kSampWarps + wib;
+    if (n >= n_parent) return;                 // the whole warp leaves together
+    const int64_t c = count[n];
+    if (c <= 0) {
+        if (lane == 0) ndist[n] = 0;
+        return;
+    }
+    const float* p = marg + n * (int64_t)nb;
+    const int per = nb >= 32 ? nb >> 5 : 1;
+    const int x0 = lane * per;
+    const int own = x0 < nb ? per : 0;
+    float m = 0.f;
+    for (int i = 0; i < own; i++) {
+        const float v = p[x0 + i];
+        m = fmaxf(m, v > 0.f ? v : 0.f);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e;
+    frexp((double)m, &e);
+    const int sigma = 52 - b - e;
+    double acc = 0.0;
+    for (int i = 0; i < own; i++) {
+        const float v = p[x0 + i];
+        acc += rint(ldexp((double)(v > 0.f ? v : 0.f), sigma));
+        C[x0 + i] = acc;
+        hist[x0 + i] = 0u;
+    }
+    const double before = warp_excl_scan_f64(acc, lane);
+    for (int i = 0; i < own; i++) C[x0 + i] += before;
+    __syncwarp();
+    const uint64_t T = (uint64_t)C[nb - 1];
+    if (T == 0) {   // zero-norm network: its shots cannot be drawn and are dropped
+        if (lane == 0) ndist[n] = 0;
+        return;
+    }
+    const uint32_t tr = (uint32_t)traj[n];
+    const int64_t r0 = rank0[n];
+    for (int64_t k = lane; k < c; k += 32) {
+        const uint64_t rank = (uint64_t)(r0 + k);
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)rank, (uint32_t)(rank >> 32), tr, tagw), key);
+        const double r = (double)__umul64hi(word64(w), T);
+        atomicAdd(&hist[cdf_search(C, nb, r)], 1u);
+    }
+    __syncwarp();
+    int mine = 0;
+    for (int i = 0; i < own; i++) mine += hist[x0 + i] != 0u;
+    int inc = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    int64_t pos = tmp_off[n] + (inc - mine);
+    for (int i = 0; i < own; i++) {
+        const unsigned h = hist[x0 + i];
+        if (h) {
+            // slots past tmp_cap are never written; the host reports the shortfall
+            if (pos < tmp_cap) {
+                tmp_x[pos] = x0 + i;
+                tmp_c[pos] = (int64_t)h;
+            }
+            pos++;
+        }
+    }
+    if (lane == 0) ndist[n] = total;
+}
+
 __global__ void k_emit_children(const int32_t* __restrict__ traj, const uint64_t* __restrict__ prefix,
                                 const int64_t* __restrict__ tmp_off, const int64_t* __restrict__ ndist,
                                 const int64_t* __restrict__ out_off, const int32_t* __restrict__ tmp_x,
@@ -448,13 +546,25 @@ int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptr
     k_rank0<<<grid_for(n_parent, 256, 1 << 30), 256, 0, s>>>(sc.excl, ptraj,
                                                             reinterpret_cast<const unsigned long long*>(sc.first),
                                                             n_parent, sc.rank0);
-    const size_t smem = (size_t)(((int64_t)1 << b) * (sizeof(double) + sizeof(unsigned int)));
-    if (smem > 32 * 1024) cudaFuncSetAttribute(k_sample_parents, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    StatScope st_sp(K_SAMPLE_PARENTS, s, (double)n_parent * ((double)((int64_t)1 << b) * 4.0 + 40.0), 0.0);
-    k_sample_parents<<<(unsigned)n_parent, 256, smem, s>>>(marg, b, ptraj, pcount, sc.rank0, sc.tmp_off, child_cap,
-                                                           key, philox_tag(STREAM_SAMPLE, circuit, block), sc.tmp_x,
-                                                           sc.tmp_c, sc.ndist);
+    {
+        StatScope st_sp(K_SAMPLE_PARENTS, s, (double)n_parent * ((double)((int64_t)1 << b) * 4.0 + 40.0), 0.0);
+        if (b <= kSampWarpMaxBits) {
+            // per warp: CDF (8 B) + histogram (4 B) per bin; 48 KB at 2^10 bins
+            const size_t smem = (size_t)kSampWarps * (((size_t)1 << b) * (sizeof(double) + sizeof(unsigned)));
+            k_sample_parents_warp<<<(unsigned)((n_parent + kSampWarps - 1) / kSampWarps), kSampWarps * 32, smem, s>>>(
+                marg, b, n_parent, ptraj, pcount, sc.rank0, sc.tmp_off, child_cap, key,
+                philox_tag(STREAM_SAMPLE, circuit, block), sc.tmp_x, sc.tmp_c, sc.ndist);
+        } else {
+            const size_t smem = (size_t)(((int64_t)1 << b) * (sizeof(double) + sizeof(unsigned int)));
+            if (smem > 32 * 1024)
+                cudaFuncSetAttribute(k_sample_parents, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_sample_parents<<<(unsigned)n_parent, 256, smem, s>>>(marg, b, ptraj, pcount, sc.rank0, sc.tmp_off,
+                                                                   child_cap, key,
+                                                                   philox_tag(STREAM_SAMPLE, circuit, block),
+                                                                   sc.tmp_x, sc.tmp_c, sc.ndist);
+        }
+    }
     launch_exclusive_scan(sc.ndist, sc.out_off, n_parent, sc.scan_tmp, s);
     cudaMemcpyAsync(host_tmp, sc.out_off + n_parent - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(host_tmp + 1, sc.ndist + n_parent - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);

@@ -121,6 +121,7 @@ _SIGS = {
                                C.POINTER(C.c_int), _P],
     "ptn_expval_grad": [_P, _P, C.POINTER(ptn_pauli_sum), C.POINTER(C.c_double), C.c_int32, _P, _P, _P],
     "ptn_trajectory_amplitudes": [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P, _P],
+    "ptn_set_wait_limit": [C.c_double],
     "ptn_stats_enable": [C.c_int32],
     "ptn_stats_enable_only": [C.c_char_p],
     "ptn_stats_reset": [],
@@ -470,6 +471,11 @@ def ptn_shots_merge(shots, n_blocks, stream=None):
     h = C.c_void_p()
     _check(lib().ptn_shots_merge(shots.handle, C.byref(h), _stream(stream)))
     return Shots(h, n_blocks)
+
+
+def ptn_set_wait_limit(seconds):
+    """Limit of the tensor-core kernel's pipeline waits (default 2 s)."""
+    _check(lib().ptn_set_wait_limit(float(seconds)))
 
 
 def ptn_stats_enable(on=True):

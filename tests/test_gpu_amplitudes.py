@@ -30,7 +30,9 @@ def _amps(plan, tr, t0, n, prec=ptn.PTN_PREC_FP32):
 
 
 def _rel(a, b):
-    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+    # a zero-norm trajectory (amplitude damping can annihilate a state) is
+    # compared absolutely: its amplitudes must vanish
+    return np.linalg.norm(a - b, axis=-1) / np.maximum(np.linalg.norm(b, axis=-1), 1e-12)
 
 
 CIRCUITS = [

@@ -486,6 +486,22 @@ typedef struct {
 
 ptn_status ptn_stats_read_steps(ptn_step_stat* out, int32_t cap, int32_t* n_out);
 
+/* ----------------------------------------------------- block-size tuning -- */
+
+/* Block-size autotuning (Sec. V-B, Fig. 7: the contraction cost per block
+ * changes by orders of magnitude with the block size, so b is a tuning
+ * parameter of each circuit).  For every candidate b (1..14) the circuit is
+ * planned with blocks of b qubits, the last taking the remainder, and a probe
+ * run is timed on the stream with CUDA events: pre-sampling probe_traj error
+ * sets (seed) and proportional NBS of probe_shots shots (FP32 mode), once to
+ * warm up and once timed.  seconds_out[i] (host, n_cand) receives the timed
+ * seconds of candidate i (+infinity if it could not be planned or run);
+ * *best_b the fastest candidate.  opts as for ptn_plan_path.  Synchronises
+ * the stream; returns the last failure if no candidate ran. */
+ptn_status ptn_tune_block_sizes(const ptn_circuit* circuit, const ptn_noise* noise, const int32_t* candidates,
+                                int32_t n_cand, const ptn_plan_opts* opts, int64_t probe_traj, int64_t probe_shots,
+                                uint64_t seed, int32_t* best_b, double* seconds_out, ptn_stream stream);
+
 /* ---------------------------------------------------------- bounded waits -- */
 
 /* Wall-time limit of every pipeline wait inside the tensor-core contraction

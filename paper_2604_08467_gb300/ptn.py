@@ -122,6 +122,9 @@ _SIGS = {
     "ptn_expval_grad": [_P, _P, C.POINTER(ptn_pauli_sum), C.POINTER(C.c_double), C.c_int32, _P, _P, _P],
     "ptn_trajectory_amplitudes": [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P, _P],
     "ptn_set_wait_limit": [C.c_double],
+    "ptn_tune_block_sizes": [C.POINTER(ptn_circuit), C.POINTER(ptn_noise), C.POINTER(C.c_int32), C.c_int32,
+                             C.POINTER(ptn_plan_opts), C.c_int64, C.c_int64, C.c_uint64, C.POINTER(C.c_int32),
+                             C.POINTER(C.c_double), _P],
     "ptn_stats_enable": [C.c_int32],
     "ptn_stats_enable_only": [C.c_char_p],
     "ptn_stats_reset": [],
@@ -471,6 +474,21 @@ def ptn_shots_merge(shots, n_blocks, stream=None):
     h = C.c_void_p()
     _check(lib().ptn_shots_merge(shots.handle, C.byref(h), _stream(stream)))
     return Shots(h, n_blocks)
+
+
+def ptn_tune_block_sizes(circ, candidates, probe_traj, probe_shots, seed=1, hypersamples=16, split_gates=1,
+                         plan_seed=1234, stream=None):
+    """Fastest block size among `candidates` by timed probe runs (include/ptn.h).
+    Returns (best b, [seconds per candidate])."""
+    c, nz, keep = circuit_structs(circ)
+    opts = ptn_plan_opts(hypersamples, split_gates, plan_seed, float(probe_traj), float(probe_shots), 0.0, 0, 0, 0, 0)
+    cand = (C.c_int32 * len(candidates))(*candidates)
+    secs = (C.c_double * len(candidates))()
+    best = C.c_int32(0)
+    _check(lib().ptn_tune_block_sizes(C.byref(c), C.byref(nz), cand, len(candidates), C.byref(opts), int(probe_traj),
+                                      int(probe_shots), seed, C.byref(best), secs, _stream(stream)))
+    del keep
+    return best.value, [secs[i] for i in range(len(candidates))]
 
 
 def ptn_set_wait_limit(seconds):

@@ -82,3 +82,14 @@ def test_plan_rejects_unknown_network_form():
     with pytest.raises(ptn.PtnError) as e:
         ptn.ptn_plan_path(circ, [4], hypersamples=2, network_form=3)
     assert e.value.status == INVALID
+
+
+def test_tune_block_sizes_argument_checks():
+    """Candidates outside 1..14, an empty list and probe sizes < 1 are refused
+    before any device work."""
+    rng = np.random.default_rng(42)
+    circ = W.attach_noise(W.brickwork_1d(6, 3, rng), [W.depolarizing_kraus(0.05)])
+    for cands, pt, ps in (([15], 4, 100), ([0, 2], 4, 100), ([2], 0, 100), ([2], 4, 0)):
+        with pytest.raises(ptn.PtnError) as e:
+            ptn.ptn_tune_block_sizes(circ, cands, probe_traj=pt, probe_shots=ps, stream=0)
+        assert e.value.status == 1

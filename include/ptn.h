@@ -83,21 +83,27 @@ typedef struct {
     const ptn_gate* gates;     /* host, n_gates entries, in circuit order */
 } ptn_circuit;
 
-/* A single-qubit noise channel given by its Kraus operators (Sec. II-A).
- * kraus holds n_kraus 2x2 complex128 matrices K[out][in], row-major (re, im). */
+/* A noise channel given by its Kraus operators (Sec. II-A): one-qubit
+ * (n_qubits 0 or 1: n_kraus 2x2 complex128 matrices K[out][in], row-major
+ * (re, im), 8 doubles each) or two-qubit (n_qubits 2: 4x4 matrices
+ * K[(o_a o_b)][(i_a i_b)], 32 doubles each, a the first qubit of the gate the
+ * site follows, as for ptn_gate; e.g. the two-qubit depolarizing channel of
+ * the paper's benchmarks, Sec. IV-B). */
 typedef struct {
     int32_t n_kraus;           /* 1 .. 16 */
-    const double* kraus;       /* host, n_kraus * 8 doubles */
+    int32_t n_qubits;          /* 0 or 1: one-qubit channel; 2: two-qubit channel */
+    const double* kraus;       /* host, n_kraus * 8 (or * 32) doubles */
 } ptn_channel;
 
 /* A noise site: channel `channel` acts on qubit `qubit` right after gate `gate`
- * (the paper couples channels to every coherent gate, Sec. IV-B).  Sites are
- * listed in application order: grouped by gate in circuit order; within a
- * gate, the sites of one qubit act in list order.  Site s is column s of the
+ * (the paper couples channels to every coherent gate, Sec. IV-B); a two-qubit
+ * channel acts on both qubits of its (two-qubit) gate and takes qubit = -1.
+ * Sites are listed in application order: grouped by gate in circuit order;
+ * within a gate, the sites act in list order.  Site s is column s of the
  * Kraus-index matrix. */
 typedef struct {
     int32_t gate;
-    int32_t qubit;             /* must be one of the gate's qubits */
+    int32_t qubit;             /* one of the gate's qubits; -1 for a two-qubit channel */
     int32_t channel;
 } ptn_site;
 
@@ -137,7 +143,9 @@ typedef struct {
 /* Build the plan: validates the channels (PTN_ERR_NOT_CPTP), builds the UPV
  * variant tables (every merged gate (N_a (x) N_b) d_l for every combination of
  * Kraus choices of its sites, N_q = product of K_k / sqrt(q_k), q_k =
- * Tr(K_k^dagger K_k) / 2), the double-layer marginal network of every block
+ * Tr(K_k^dagger K_k) / d with d = 2 or 4; a gate with a two-qubit channel merges
+ * every site's operator in application order and is not split by the
+ * operator-Schmidt option), the double-layer marginal network of every block
  * (prefix qubits projected, block qubits open, later qubits traced), and one
  * contraction path per block (Sec. III-A), lowered to a list of batched
  * pairwise contractions.  Host only: needs no GPU (device tables are uploaded

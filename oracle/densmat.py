@@ -41,7 +41,11 @@ def density_matrix(circ):
     for l, g in enumerate(circ.gates):
         rho = apply_unitary(rho, n, g.qubits, g.matrix)
         for s in sites_of[l]:
-            rho = apply_channel(rho, n, s.qubit, circ.channels[s.channel].kraus)
+            kr = circ.channels[s.channel].kraus
+            if s.qubit < 0:    # two-qubit channel on the gate's qubits
+                rho = sum(apply_unitary(rho, n, g.qubits, k) for k in kr)
+            else:
+                rho = apply_channel(rho, n, s.qubit, kr)
     return rho
 
 

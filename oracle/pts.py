@@ -24,15 +24,16 @@ from . import philox
 
 
 def kraus_probs(kraus):
-    """q_k = Tr(K_k^dagger K_k) / 2, summed as re*re + im*im over the entries in
-    row-major order (a fixed order, so every implementation gets the same bits)."""
+    """q_k = Tr(K_k^dagger K_k) / d (d = 2 or 4 for a one- or two-qubit
+    channel), summed as re*re + im*im over the entries in row-major order (a
+    fixed order, so every implementation gets the same bits)."""
     q = []
     for k in kraus:
         k = np.asarray(k, np.complex128)
         acc = 0.0
         for z in k.reshape(-1):
             acc = acc + (z.real * z.real + z.imag * z.imag)
-        q.append(acc / 2.0)
+        q.append(acc / float(k.shape[0]))
     return np.array(q, dtype=np.float64)
 
 
@@ -51,7 +52,7 @@ def kraus_cdf(kraus):
 def completeness_error(kraus):
     """max |sum_k K_k^dagger K_k - I| (zero for a trace-preserving channel)."""
     s = sum(np.conj(k).T @ k for k in kraus)
-    return float(np.max(np.abs(s - np.eye(2))))
+    return float(np.max(np.abs(s - np.eye(s.shape[0]))))
 
 
 def presample(circ, n_traj: int, seed: int, circuit_id: int = 0, traj0: int = 0):
@@ -130,11 +131,29 @@ def noise_operator(circ, sites, choices, qubit):
 
 
 def merged_gate(circ, l: int, choices, sites_of_gate=None):
-    """UPV merge of gate l with its sampled error operators: (N_a (x) N_b) d_l."""
+    """UPV merge of gate l with its sampled error operators: (N_a (x) N_b) d_l,
+    or, when a two-qubit channel acts on the gate, the product in application
+    order of every site's scaled operator (a one-qubit one embedded on its
+    qubit, the gate's first qubit being the high bit) times d_l."""
     g = circ.gates[l]
     sites = (sites_of_gate or gate_sites(circ))[l]
     if g.arity == 1:
         return noise_operator(circ, sites, choices, g.qubits[0]) @ g.matrix
+    if any(circ.sites[s].qubit < 0 for s in sites):
+        t = np.eye(4, dtype=np.complex128)
+        for s in sites:
+            site = circ.sites[s]
+            ch = circ.channels[site.channel]
+            k = int(choices[s])
+            op = ch.kraus[k] / np.sqrt(kraus_probs(ch.kraus)[k])
+            if site.qubit < 0:
+                e = op
+            elif site.qubit == g.qubits[0]:
+                e = np.kron(op, np.eye(2))
+            else:
+                e = np.kron(np.eye(2), op)
+            t = e @ t
+        return t @ g.matrix
     na = noise_operator(circ, sites, choices, g.qubits[0])
     nb = noise_operator(circ, sites, choices, g.qubits[1])
     return np.kron(na, nb) @ g.matrix

@@ -48,7 +48,7 @@ constexpr int kStages = 3;        // pipeline depth (4 tiles of 16 KB per stage)
 constexpr int kTileA = kBM * kRowBytes;
 constexpr int kTileB = kBN * kRowBytes;
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;
-constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 3072;   // align slack + stages + barriers/offsets
+constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 4096;   // align slack + stages + barriers/offsets/scales
 constexpr int kMaxPackBits = 40;
 // k-blocks are spread round-robin over kAcc TMEM accumulators that the
 // epilogue adds in FP32: the tensor core's FP32 accumulation truncates, so
@@ -549,6 +549,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
     int64_t* noff_all = reinterpret_cast<int64_t*>(tslot + 4);   // 4 epilogue warps x kBN / 2 column offsets
+    float* ucol_all = reinterpret_cast<float*>(noff_all + 4 * (kBN / 2));   // FP16: column scales 2^eb
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 32) {
@@ -648,17 +649,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         // epilogue warps 2..5: TMEM lane quadrant q = warp % 4 holds tile rows 32q..32q+31
         const int q = warp & 3;
         int64_t* noff = noff_all + (warp - 2) * (kBN / 2);
+        float* ucol = ucol_all + (warp - 2) * (kBN / 2);
         const int n_acc = g.nkb < kAcc ? g.nkb : kAcc;
         int64_t lt = 0;
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, lt++) {
             if (__shfl_sync(0xffffffffu, *abort, 0)) break;   // warp-uniform stop
             const TileInfo t = decode_tile(g, tile);
-            for (int c = lane; c < kBN / 2; c += 32) {   // output offsets of this tile's complex columns
+            for (int c = lane; c < kBN / 2; c += 32) {   // output offsets (and FP16 scales) of the tile's columns
                 const int64_t n = (int64_t)(t.n0 / 2) + c;
                 int64_t off = 0;
                 for (int i = 0; i < g.n_nb; i++)
                     if ((n >> i) & 1) off += g.n_stride[i];
                 noff[c] = off;
+                if (F == FMT_FP16)
+                    ucol[c] = 2 * n < g.N2 ? ldexpf(1.f, (int)g.exp_b[(int64_t)t.zb * (g.N2 >> 1) + n]) : 0.f;
             }
             __syncwarp();
             // one lane waits and the warp follows its outcome (lanes polling on
@@ -688,9 +692,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 if ((t.h >> i) & 1) moff += g.h_stride[i];
             const bool row_ok = row < t.row_end;
             float2* out = g.out + (row_ok ? out_inst : 0) * g.out_size + moff;
-            // FP16: A row and B column exponents (packed row indices za * M + row, zb * N + n)
-            const int ea = (F == FMT_FP16 && row_ok) ? (int)g.exp_a[(int64_t)t.za * g.M + row] : 0;
-            const int8_t* eb = F == FMT_FP16 ? g.exp_b + (int64_t)t.zb * (g.N2 >> 1) : nullptr;
+            // FP16: A row scale 2^ea (packed row index za * M + row); the product with
+            // the column scale 2^eb is exactly 2^(ea + eb)
+            const float urow = (F == FMT_FP16 && row_ok) ? ldexpf(1.f, (int)g.exp_a[(int64_t)t.za * g.M + row]) : 1.f;
 #pragma unroll 1
             for (int c0 = 0; c0 < kBN; c0 += 32) {
                 float v[32];
@@ -708,7 +712,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                     for (int j = 0; j < 16; j++) {
                         const int col = t.n0 + c0 + 2 * j;
                         if (col < g.N2) {
-                            const float u = F == FMT_FP16 ? ldexpf(1.f, ea + (int)eb[col >> 1]) : 1.f;
+                            const float u = F == FMT_FP16 ? urow * ucol[(c0 >> 1) + j] : 1.f;
                             out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j] * u, v[2 * j + 1] * u);
                         }
                     }
@@ -885,7 +889,8 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
             const int64_t tot = pk == &pa ? tot_a : tot_b;
             if (F == FMT_FP16 && Kh / 2 > kPackRegRow) {
                 const int64_t rows = pk->n_pinst << (pk->n_hb + pk->n_rb);
-                k_pack_long<F><<<(unsigned)(rows < 152 * 8 ? rows : 152 * 8), 256, 0, s>>>(*pk, ctx);
+                // few rows in flight, so the second pass over a row finds it in L2
+                k_pack_long<F><<<(unsigned)(rows < 152 * 3 ? rows : 152 * 3), 256, 0, s>>>(*pk, ctx);
             } else {
                 k_pack<F><<<grid_of(tot), 256, 0, s>>>(*pk, ctx);
             }

@@ -320,23 +320,22 @@ __global__ void __launch_bounds__(256) k_sample_parents(const float* __restrict_
 }
 
 // Blocks of up to 2^10 bins: one warp per parent, kSampWarps parents per CTA,
-// no CTA-wide barrier.  Lane l owns the bins [l * per, (l + 1) * per): the
-// row maximum is a shuffle reduction, the exact-integer CDF the lane's own
-// running sums plus a shuffle scan of the lane totals (exact in FP64 in any
-// order), the draws search the warp's CDF in shared memory and count into its
-// histogram, and the nonzero bins are compacted in x order through a shuffle
-// scan of the lanes' counts.  Same arithmetic and results as
-// k_sample_parents.
+// no CTA-wide barrier.  The row is read in coalesced rounds of 32 bins (lane l
+// holds bin 32 i + l of round i, kept in registers): the row maximum is a
+// shuffle reduction; the exact-integer CDF is built round by round with a
+// shuffle scan plus the running total (exact in FP64 in any order); the draws
+// search the warp's CDF in shared memory and count into its histogram; the
+// nonzero bins are compacted in x order with one ballot per round.  Same
+// arithmetic and results as k_sample_parents.
 constexpr int kSampWarps = 4;
 constexpr int kSampWarpMaxBits = 10;
 
-__device__ __forceinline__ double warp_excl_scan_f64(double v, int lane) {
-    double inc = v;
+__device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
     for (int o = 1; o < 32; o <<= 1) {
-        const double u = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += u;
+        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
     }
-    return inc - v;
+    return v;
 }
 
 __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
@@ -345,6 +344,7 @@ __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
     int64_t tmp_cap, uint2 key, uint32_t tagw, int32_t* __restrict__ tmp_x, int64_t* __restrict__ tmp_c,
     int64_t* __restrict__ ndist) {
     extern __shared__ unsigned char smem[];
+    constexpr int kMaxRounds = (1 << kSampWarpMaxBits) / 32;
     const int nb = 1 << b;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* C = reinterpret_cast<double*>(smem) + (int64_t)wib * nb;
@@ -358,27 +358,36 @@ __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
         return;
     }
     const float* p = marg + n * (int64_t)nb;
-    const int per = nb >= 32 ? nb >> 5 : 1;
-    const int x0 = lane * per;
-    const int own = x0 < nb ? per : 0;
+    const int rounds = (nb + 31) >> 5;
+    float v[kMaxRounds];
     float m = 0.f;
-    for (int i = 0; i < own; i++) {
-        const float v = p[x0 + i];
-        m = fmaxf(m, v > 0.f ? v : 0.f);
+#pragma unroll
+    for (int i = 0; i < kMaxRounds; i++) {
+        const int x = 32 * i + lane;
+        v[i] = 0.f;
+        if (i < rounds && x < nb) {
+            const float t = p[x];
+            v[i] = t > 0.f ? t : 0.f;
+        }
+        m = fmaxf(m, v[i]);
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     int e;
     frexp((double)m, &e);
     const int sigma = 52 - b - e;
-    double acc = 0.0;
-    for (int i = 0; i < own; i++) {
-        const float v = p[x0 + i];
-        acc += rint(ldexp((double)(v > 0.f ? v : 0.f), sigma));
-        C[x0 + i] = acc;
-        hist[x0 + i] = 0u;
+    double carry = 0.0;
+#pragma unroll
+    for (int i = 0; i < kMaxRounds; i++) {
+        if (i < rounds) {
+            const int x = 32 * i + lane;
+            const double inc = warp_incl_scan_f64(rint(ldexp((double)v[i], sigma)), lane);
+            if (x < nb) {
+                C[x] = carry + inc;
+                hist[x] = 0u;
+            }
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
     }
-    const double before = warp_excl_scan_f64(acc, lane);
-    for (int i = 0; i < own; i++) C[x0 + i] += before;
     __syncwarp();
     const uint64_t T = (uint64_t)C[nb - 1];
     if (T == 0) {   // zero-norm network: its shots cannot be drawn and are dropped
@@ -394,27 +403,23 @@ __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
         atomicAdd(&hist[cdf_search(C, nb, r)], 1u);
     }
     __syncwarp();
-    int mine = 0;
-    for (int i = 0; i < own; i++) mine += hist[x0 + i] != 0u;
-    int inc = mine;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += u;
-    }
-    const int total = __shfl_sync(0xffffffffu, inc, 31);
-    int64_t pos = tmp_off[n] + (inc - mine);
-    for (int i = 0; i < own; i++) {
-        const unsigned h = hist[x0 + i];
+    int64_t pos = tmp_off[n];
+    const unsigned below = (1u << lane) - 1u;
+    for (int i = 0; i < rounds; i++) {
+        const int x = 32 * i + lane;
+        const unsigned h = x < nb ? hist[x] : 0u;
+        const unsigned mask = __ballot_sync(0xffffffffu, h != 0u);
         if (h) {
+            const int64_t q = pos + __popc(mask & below);
             // slots past tmp_cap are never written; the host reports the shortfall
-            if (pos < tmp_cap) {
-                tmp_x[pos] = x0 + i;
-                tmp_c[pos] = (int64_t)h;
+            if (q < tmp_cap) {
+                tmp_x[q] = x;
+                tmp_c[q] = (int64_t)h;
             }
-            pos++;
         }
+        pos += __popc(mask);
     }
-    if (lane == 0) ndist[n] = total;
+    if (lane == 0) ndist[n] = pos - tmp_off[n];
 }
 
 __global__ void k_emit_children(const int32_t* __restrict__ traj, const uint64_t* __restrict__ prefix,

@@ -69,17 +69,18 @@ static M2 mul2(const M2& a, const M2& b) {
 }
 static M2 eye2() { return M2{cd(1), cd(0), cd(0), cd(1)}; }
 
-// q_k = Tr(K^dagger K) / 2 with the entries summed as re*re + im*im in
-// row-major order (a fixed order so every implementation gets the same bits).
-static double kraus_prob(const double* k) {
+// q_k = Tr(K^dagger K) / d (d = 2, or 4 for a two-qubit channel) with the
+// entries summed as re*re + im*im in row-major order (a fixed order so every
+// implementation gets the same bits).
+static double kraus_prob(const double* k, int d = 2) {
     double acc = 0.0;
-    for (int e = 0; e < 4; e++) {
+    for (int e = 0; e < d * d; e++) {
         double re = k[2 * e], im = k[2 * e + 1];
         double sq = re * re;
         sq = sq + im * im;
         acc = acc + sq;
     }
-    return acc / 2.0;
+    return acc / (double)d;
 }
 
 // One-sided (Hestenes) Jacobi SVD of a complex 4x4 matrix X = sum_r u_r s_r v_r^H.
@@ -1238,19 +1239,24 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
     int n_sites = nz ? nz->n_sites : 0;
     int n_ch = nz ? nz->n_channels : 0;
     plan->n_sites = n_sites;
+    auto ch_dim = [&](int k) { return nz->channels[k].n_qubits == 2 ? 4 : 2; };
     for (int k = 0; k < n_ch; k++) {
         const ptn_channel& ch = nz->channels[k];
         if (ch.n_kraus < 1 || ch.n_kraus > kMaxKraus || !ch.kraus)
             return set_error(PTN_ERR_INVALID_ARG, "channel %d: n_kraus %d", k, ch.n_kraus);
-        cd s[4] = {0, 0, 0, 0};
+        if (ch.n_qubits < 0 || ch.n_qubits > 2)
+            return set_error(PTN_ERR_INVALID_ARG, "channel %d: n_qubits %d", k, ch.n_qubits);
+        const int d = ch_dim(k);
+        std::vector<cd> s(d * d, cd(0)), m(d * d);
         for (int a = 0; a < ch.n_kraus; a++) {
-            cd m[4];
-            cd_from(ch.kraus + 8 * a, m, 4);
-            for (int i = 0; i < 2; i++)
-                for (int j = 0; j < 2; j++)
-                    s[i * 2 + j] += std::conj(m[i]) * m[j] + std::conj(m[2 + i]) * m[2 + j];
+            cd_from(ch.kraus + 2 * d * d * a, m.data(), d * d);
+            for (int i = 0; i < d; i++)
+                for (int j = 0; j < d; j++)
+                    for (int r = 0; r < d; r++) s[i * d + j] += std::conj(m[r * d + i]) * m[r * d + j];
         }
-        double err = std::max({std::abs(s[0] - 1.0), std::abs(s[1]), std::abs(s[2]), std::abs(s[3] - 1.0)});
+        double err = 0.0;
+        for (int i = 0; i < d; i++)
+            for (int j = 0; j < d; j++) err = std::max(err, std::abs(s[i * d + j] - (i == j ? 1.0 : 0.0)));
         if (err > 1e-10) return set_error(PTN_ERR_NOT_CPTP, "channel %d: |sum K^dag K - I| = %.3g", k, err);
     }
     int prev_gate = -1;
@@ -1259,8 +1265,13 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
         if (st.gate < 0 || st.gate >= c->n_gates || st.channel < 0 || st.channel >= n_ch)
             return set_error(PTN_ERR_INVALID_ARG, "site %d: bad gate or channel", s);
         const ptn_gate& g = c->gates[st.gate];
-        if (st.qubit != g.q0 && !(g.arity == 2 && st.qubit == g.q1))
+        if (ch_dim(st.channel) == 4) {
+            if (g.arity != 2 || st.qubit != -1)
+                return set_error(PTN_ERR_INVALID_ARG, "site %d: a two-qubit channel needs a two-qubit gate and qubit -1",
+                                 s);
+        } else if (st.qubit != g.q0 && !(g.arity == 2 && st.qubit == g.q1)) {
             return set_error(PTN_ERR_INVALID_ARG, "site %d: qubit not on its gate", s);
+        }
         if (st.gate < prev_gate) return set_error(PTN_ERR_INVALID_ARG, "sites must be grouped by gate in order");
         prev_gate = st.gate;
     }
@@ -1270,7 +1281,8 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
     std::vector<std::vector<double>> qtab(n_ch);
     for (int k = 0; k < n_ch; k++) {
         const ptn_channel& ch = nz->channels[k];
-        for (int a = 0; a < ch.n_kraus; a++) qtab[k].push_back(kraus_prob(ch.kraus + 8 * a));
+        const int d = ch_dim(k);
+        for (int a = 0; a < ch.n_kraus; a++) qtab[k].push_back(kraus_prob(ch.kraus + 2 * d * d * a, d));
     }
     for (int s = 0; s < n_sites; s++) {
         SiteTable& T = plan->site_tables[s];
@@ -1301,6 +1313,42 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
         double sc = q > 0 ? 1.0 / std::sqrt(q) : 0.0;
         M2 r;
         for (int i = 0; i < 4; i++) r[i] = m[i] * sc;
+        return r;
+    };
+
+    // scaled operator of site s as a 4x4 on its two-qubit gate's (a, b) = (q0, q1)
+    // (a one-qubit operator embedded on its qubit, a the high bit)
+    auto scaled_kraus4 = [&](int s, int k, const ptn_gate& g) {
+        const ptn_site& st = nz->sites[s];
+        const ptn_channel& ch = nz->channels[st.channel];
+        double q = qtab[st.channel][k];
+        double sc = q > 0 ? 1.0 / std::sqrt(q) : 0.0;
+        M4 r{};
+        if (ch_dim(st.channel) == 4) {
+            cd m[16];
+            cd_from(ch.kraus + 32 * k, m, 16);
+            for (int i = 0; i < 16; i++) r[i] = m[i] * sc;
+        } else {
+            const M2 N = scaled_kraus(s, k);
+            const bool on_a = st.qubit == g.q0;
+            for (int oa = 0; oa < 2; oa++)
+                for (int ob = 0; ob < 2; ob++)
+                    for (int ia = 0; ia < 2; ia++)
+                        for (int ib = 0; ib < 2; ib++) {
+                            cd v = on_a ? (ob == ib ? N[oa * 2 + ia] : cd(0)) : (oa == ia ? N[ob * 2 + ib] : cd(0));
+                            r[(oa * 2 + ob) * 4 + ia * 2 + ib] = v;
+                        }
+        }
+        return r;
+    };
+    auto mul4 = [](const M4& a, const M4& b) {
+        M4 r{};
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++) {
+                cd z = 0;
+                for (int k = 0; k < 4; k++) z += a[i * 4 + k] * b[k * 4 + j];
+                r[i * 4 + j] = z;
+            }
         return r;
     };
 
@@ -1392,7 +1440,9 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
             int rank = 0;
             for (int r = 0; r < 4; r++)
                 if (sv[r] > 1e-12 * std::max(sv[0], 1e-300)) rank++;
-            if (opts.split_gates && rank <= 2) {
+            bool two_qubit_noise = false;
+            for (int32_t s2 : gsites[l]) two_qubit_noise |= ch_dim(nz->sites[s2].channel) == 4;
+            if (opts.split_gates && rank <= 2 && !two_qubit_noise) {
                 int bond_bits = rank == 2 ? 1 : 0;
                 // left factor A_r[oa][ia] = (X V)[(oa ia), r] / sqrt(s_r); right B_r[ob][ib] = sqrt(s_r) conj(V[(ob ib), r])
                 for (int part = 1; part <= 2; part++) {
@@ -1438,6 +1488,18 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
                 L.legs.push_back(R_OUT_B);
                 L.legs.push_back(R_OUT_A);
                 finish_leaf(L, [&](int64_t v, const int32_t* rb) {
+                    if (two_qubit_noise) {   // every site's operator in application order, then the gate
+                        M4 T{};
+                        for (int i = 0; i < 4; i++) T[i * 4 + i] = 1.0;
+                        int64_t vv = v;
+                        for (size_t i = 0; i < L.sites.size(); i++) {
+                            const int k = (int)(vv % L.radix[i]);
+                            vv /= L.radix[i];
+                            T = mul4(scaled_kraus4(L.sites[i], k, g), T);
+                        }
+                        const M4 TM = mul4(T, M);
+                        return TM[(rb[R_OUT_A] * 2 + rb[R_OUT_B]) * 4 + rb[R_IN_A] * 2 + rb[R_IN_B]];
+                    }
                     M2 Na = noise_op(L, v, g.q0), Nb = noise_op(L, v, g.q1);
                     int ro = rb[R_OUT_A] * 2 + rb[R_OUT_B];
                     int ci = rb[R_IN_A] * 2 + rb[R_IN_B];

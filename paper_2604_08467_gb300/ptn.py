@@ -41,7 +41,7 @@ class ptn_circuit(C.Structure):
 
 
 class ptn_channel(C.Structure):
-    _fields_ = [("n_kraus", C.c_int32), ("kraus", C.POINTER(C.c_double))]
+    _fields_ = [("n_kraus", C.c_int32), ("n_qubits", C.c_int32), ("kraus", C.POINTER(C.c_double))]
 
 
 class ptn_site(C.Structure):
@@ -209,6 +209,7 @@ def circuit_structs(circ):
                               for K in ch.kraus]).astype(np.float64)
         kraus_arrays.append(arr)
         chans[k].n_kraus = len(ch.kraus)
+        chans[k].n_qubits = 2 if np.asarray(ch.kraus[0]).shape[0] == 4 else 1
         chans[k].kraus = arr.ctypes.data_as(C.POINTER(C.c_double))
     n_s = len(circ.sites)
     sites = (ptn_site * max(n_s, 1))()

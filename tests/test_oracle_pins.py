@@ -582,3 +582,64 @@ def test_nbs_nonproportional_branching_and_final_law():
     # branch > 1 grows the prefix set; direct mode returns counts
     (t2, b2, c2), nets2 = sampling.nbs_nonproportional(marg, blocks, 78, 10, branch=3, mode="direct", final_shots=50)
     assert nets2[0] == 10 and nets2[1] >= 10 and nets2[2] >= nets2[1] and c2.sum() == 50 * nets2[2]
+
+
+# ------------------------------------------- the paper's circuit family ----
+
+def test_two_qubit_depolarizing_closed_form():
+    """Completeness, nominal probabilities (1 - p, p/15 x 15) and the channel's
+    action on a random two-qubit state: (1 - p) rho + p/15 sum_{PQ != II}."""
+    p = 0.13
+    ch = W.depolarizing2_kraus(p)
+    assert pts.completeness_error(ch.kraus) < 1e-14
+    q = pts.kraus_probs(ch.kraus)
+    np.testing.assert_allclose(q, [1 - p] + [p / 15] * 15, rtol=1e-14)
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    rho = a @ a.conj().T
+    rho /= np.trace(rho)
+    out = sum(k @ rho @ k.conj().T for k in ch.kraus)
+    # the fully depolarizing part of a unit-trace state is I / 4: (1 - 16 p / 15) rho + 16 p / 15 * I / 4
+    want = (1 - 16 * p / 15) * rho + (16 * p / 15) * np.eye(4) / 4
+    np.testing.assert_allclose(out, want, atol=1e-14)
+
+
+def test_paper_family_trajectories_match_density_matrix():
+    """A 4-qubit member of the paper's random family (Pauli and two-qubit
+    depolarizing noise): the exact average over every Kraus assignment,
+    weighted by the nominal probabilities, of the merged-gate trajectory
+    states equals the density matrix of the channel evolution."""
+    import itertools
+    rng = np.random.default_rng(17)
+    circ = W.paper_random_circuit(4, 40, rng, frac_2q=0.5)
+    # a short prefix of the draw with two two-qubit and three one-qubit gates
+    keep = [l for l, g in enumerate(circ.gates) if g.arity == 2][:2] + \
+           [l for l, g in enumerate(circ.gates) if g.arity == 1][:3]
+    keep.sort()
+    gates = [circ.gates[l] for l in keep]
+    sites = [W.Site(i, s.qubit, s.channel) for i, l in enumerate(keep) for s in circ.sites if s.gate == l]
+    circ = W.Circuit(4, gates, circ.channels, sites)
+    assert sum(s.qubit < 0 for s in circ.sites) == 2 and sum(s.qubit >= 0 for s in circ.sites) == 3
+    rho = densmat.density_matrix(circ)
+    qs = [pts.kraus_probs(circ.channels[s.channel].kraus) for s in circ.sites]
+    acc = np.zeros((16, 16), dtype=np.complex128)
+    for choice in itertools.product(*[range(len(q)) for q in qs]):
+        w = np.prod([q[k] for q, k in zip(qs, choice)])
+        if w == 0:
+            continue
+        psi = sv.trajectory_state(circ, np.array(choice))
+        acc += w * np.outer(psi, psi.conj())
+    np.testing.assert_allclose(acc, rho, atol=1e-12)
+
+
+def test_merged_two_qubit_pauli_product():
+    """The merge of a two-qubit depolarizing Kraus choice 4a + b into its gate is
+    (P_a (x) P_b) G on the gate's (first, second) qubits."""
+    g = W.Gate((3, 2), np.kron(W.haar_u2(np.random.default_rng(1)), W.haar_u2(np.random.default_rng(2))) @ W.CZ)
+    ch = W.depolarizing2_kraus(0.2)
+    circ = W.Circuit(4, [g], [ch], [W.Site(0, -1, 0)])
+    P = [W.PAULI[c] for c in "IXYZ"]
+    for k in (0, 6, 15):
+        # K_k / sqrt(q_k) is the bare Pauli product (K_k = sqrt(q_k) P (x) Q)
+        m = pts.merged_gate(circ, 0, np.array([k]))
+        np.testing.assert_allclose(m, np.kron(P[k // 4], P[k % 4]) @ g.matrix, atol=1e-13)

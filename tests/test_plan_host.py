@@ -73,6 +73,8 @@ CASES = [
     ("idle_qubit", lambda r: W.attach_noise(W.Circuit(3, [W.Gate((0,), W.haar_u2(r)),
                                                           W.Gate((0, 1), W.CZ.copy())]),
                                             [W.amplitude_damping_kraus(0.4)]), [1, 2]),
+    # the paper's random family: Pauli errors and two-qubit depolarizing channels
+    ("paper8", lambda r: W.paper_random_circuit(8, 40, r, frac_2q=0.3), [3, 5]),
 ]
 
 

@@ -67,13 +67,17 @@ class Gate:
 @dataclass
 class Channel:
     name: str
-    kraus: List[np.ndarray]         # list of (2,2) complex128
+    kraus: List[np.ndarray]         # list of (2,2) complex128, or (4,4) for a two-qubit channel
+
+    @property
+    def n_qubits(self) -> int:
+        return 2 if np.asarray(self.kraus[0]).shape[0] == 4 else 1
 
 
 @dataclass
 class Site:
     gate: int
-    qubit: int
+    qubit: int                      # -1: a two-qubit channel on both qubits of its (two-qubit) gate
     channel: int
 
 
@@ -121,6 +125,29 @@ def depolarizing_kraus(p: float) -> Channel:
     z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
     a, b = np.sqrt(1.0 - p), np.sqrt(p / 3.0)
     return Channel(f"depolarizing({p})", [a * i2, b * x, b * y, b * z])
+
+
+PAULI = {"I": np.eye(2, dtype=np.complex128), "X": np.array([[0, 1], [1, 0]], dtype=np.complex128),
+         "Y": np.array([[0, -1j], [1j, 0]], dtype=np.complex128), "Z": np.diag([1.0, -1.0]).astype(np.complex128)}
+
+
+def pauli_channel(p: float, pauli: str) -> Channel:
+    """Single Pauli error: rho -> (1-p) rho + p P rho P."""
+    return Channel(f"pauli_{pauli}({p})", [np.sqrt(1.0 - p) * PAULI["I"], np.sqrt(p) * PAULI[pauli]])
+
+
+def depolarizing2_kraus(p: float) -> Channel:
+    """Two-qubit depolarizing channel rho -> (1-p) rho + p/15 sum over the 15
+    non-identity Pauli products P (x) Q of (P (x) Q) rho (P (x) Q); Kraus index
+    4 a + b for P = (I, X, Y, Z)[a] on the gate's first qubit (the high bit) and
+    Q = (I, X, Y, Z)[b] on its second."""
+    names = "IXYZ"
+    ks = []
+    for a in range(4):
+        for b in range(4):
+            c = np.sqrt(1.0 - p) if a == b == 0 else np.sqrt(p / 15.0)
+            ks.append(c * np.kron(PAULI[names[a]], PAULI[names[b]]))
+    return Channel(f"depolarizing2({p})", ks)
 
 
 def amplitude_damping_kraus(gamma: float) -> Channel:
@@ -204,6 +231,63 @@ def attach_noise(circ: Circuit, channels: Sequence[Channel]) -> Circuit:
                 sites.append(Site(l, q, c))
     circ.sites = sites
     return circ
+
+
+def _rx(theta: float) -> np.ndarray:
+    c, s_ = np.cos(theta / 2), np.sin(theta / 2)
+    return np.array([[c, -1j * s_], [-1j * s_, c]], dtype=np.complex128)
+
+
+def _controlled(u: np.ndarray) -> np.ndarray:
+    """Controlled-u with the control on the gate's first qubit (the high bit)."""
+    m = np.eye(4, dtype=np.complex128)
+    m[2:, 2:] = u
+    return m
+
+
+def paper_random_circuit(n: int, n_gates: int, rng: np.random.Generator, frac_2q: float = 0.2,
+                         p_range=(0.02, 0.2)) -> Circuit:
+    """Random circuits of the paper's benchmark family (Sec. IV-B): single-qubit
+    gates from {H, X, Y, Z, T, Rx} and, for a fraction frac_2q of the gates,
+    nearest-neighbour controlled gates from {CX, CY, CZ, CH, CRx} (control and
+    target order random); every single-qubit gate gets a single Pauli error
+    channel with a random Pauli and every two-qubit gate a two-qubit
+    depolarizing channel, with error probabilities drawn uniformly from p_range.
+    Rx angles are uniform in [0, 2 pi)."""
+    h = np.array([[1, 1], [1, -1]], dtype=np.complex128) / np.sqrt(2.0)
+    t = np.diag([1.0, np.exp(1j * np.pi / 4)]).astype(np.complex128)
+    gates, channels, sites = [], [], []
+    for l in range(n_gates):
+        p = float(rng.uniform(*p_range))
+        if n > 1 and rng.random() < frac_2q:
+            q = int(rng.integers(0, n - 1))
+            a, b = (q, q + 1) if rng.random() < 0.5 else (q + 1, q)
+            kind = int(rng.integers(0, 5))
+            u = [PAULI["X"], PAULI["Y"], PAULI["Z"], h, _rx(float(rng.uniform(0, 2 * np.pi)))][kind]
+            gates.append(Gate((a, b), _controlled(u)))
+            channels.append(depolarizing2_kraus(p))
+            sites.append(Site(l, -1, len(channels) - 1))
+        else:
+            q = int(rng.integers(0, n))
+            kind = int(rng.integers(0, 6))
+            u = [h, PAULI["X"], PAULI["Y"], PAULI["Z"], t, _rx(float(rng.uniform(0, 2 * np.pi)))][kind]
+            gates.append(Gate((q,), u))
+            channels.append(pauli_channel(p, "XYZ"[int(rng.integers(0, 3))]))
+            sites.append(Site(l, q, len(channels) - 1))
+    return Circuit(n, gates, channels, sites, layout="1d", name=f"paper_random_n{n}_g{n_gates}")
+
+
+def config_paper(n: int = 50, n_gates: int = 200, instance: int = 0) -> dict:
+    """One instance of the paper's random-circuit family (n qubits, n_gates
+    gates, 20% two-qubit, Pauli / two-qubit depolarizing noise p ~ U[0.02,
+    0.2]) with the paper's sampling parameters: blocks of b = 10 and a final
+    block taking the remainder up to 28 qubits, one shot per non-final block."""
+    rng = np.random.default_rng(circuit_seed(6, 1000 * n + n_gates + instance))
+    circ = paper_random_circuit(n, n_gates, rng)
+    b, bf = 10, min(28, n)
+    rest = n - bf
+    bs = [b] * (rest // b) + ([rest % b] if rest % b else []) + [bf]
+    return dict(name=f"paper_n{n}_g{n_gates}", circuit=circ, block_sizes=bs, seed=philox_seed(instance))
 
 
 # ---------------------------------------------------------------------------

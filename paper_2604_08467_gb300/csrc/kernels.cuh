@@ -29,6 +29,40 @@ __device__ __forceinline__ uint64_t word64(uint4 x) {
     return ((uint64_t)x.x << 32) | (uint64_t)x.y;
 }
 
+// Exact-integer quantisation of probabilities without FP64 arithmetic (the
+// GB300's FP64 rate is a small fraction of its integer rate): for a float p,
+// quant_pow2(p, s) = rint(max(p, 0) * 2^s) (rint: round half to even), the
+// value the FP64 expression gives, since p * 2^s is exact in FP64.  The
+// caller chooses s so that the result stays below 2^63.
+__device__ __forceinline__ uint64_t quant_pow2(float p, int s) {
+    if (!(p > 0.f)) return 0;
+    const uint32_t bits = __float_as_uint(p);
+    const int be = (int)((bits >> 23) & 0xFFu);
+    uint64_t m = bits & 0x7FFFFFu;
+    int E = -149;                      // subnormal: value = m * 2^-149
+    if (be) {
+        m |= 0x800000u;
+        E = be - 150;                  // normal: value = m * 2^(be - 150)
+    }
+    const int sh = E + s;
+    if (sh >= 0) return m << sh;
+    const int d = -sh;
+    if (d > 24) return 0;              // value < 0.5
+    uint64_t q = m >> d;
+    const uint64_t rem = m & ((1ull << d) - 1), half = 1ull << (d - 1);
+    if (rem > half || (rem == half && (q & 1ull))) q++;
+    return q;
+}
+// e with m = f * 2^e, f in [0.5, 1), as frexp((double)m) gives for a float m
+// >= 0 (0 for m = 0).
+__device__ __forceinline__ int frexp_exp(float m) {
+    const uint32_t bits = __float_as_uint(m);
+    const int be = (int)((bits >> 23) & 0xFFu);
+    if (be) return be - 126;
+    const uint32_t frac = bits & 0x7FFFFFu;
+    return frac ? (31 - __clz((int)frac)) - 148 : 0;
+}
+
 // Counter word 3: (stream << 24) | (circuit << 8) | block.
 enum { STREAM_KRAUS = 1, STREAM_ALLOC = 2, STREAM_SAMPLE = 3 };
 __host__ __device__ __forceinline__ uint32_t philox_tag(int stream, int circuit, int block) {
@@ -49,6 +83,13 @@ struct ChunkCtx {
 };
 
 // ---- launchers (kernels_contract.cu)
+// Small trajectory-class steps that run fused, a run of consecutive ones per
+// launch (one CTA per trajectory of the chunk): out <= 2^kSmallOutBits
+// elements, summed bits <= kSmallSumBits, operands <= 2^kSmallOpBits.
+constexpr int kSmallOutBits = 12, kSmallSumBits = 8, kSmallOpBits = 14;
+bool small_step(const StepDesc& h);
+void launch_small_steps(const StepDesc* d_steps, const StepDesc* h_steps, int n_steps, const ChunkCtx& ctx,
+                        int64_t n_traj, cudaStream_t s);
 void launch_contract_step(const StepDesc* d_step, const StepDesc& h_step, const ChunkCtx& ctx,
                           int64_t n_inst, cudaStream_t s);
 // marginal rows (real diagonal of the root) and their FP64 totals; part holds

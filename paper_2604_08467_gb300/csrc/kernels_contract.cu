@@ -394,7 +394,78 @@ __global__ void k_finalize_sum(const double* __restrict__ part, int64_t tiles, i
     Z[net] = t;
 }
 
+// A run of consecutive small trajectory-class steps (the gate-level start of a
+// block's path: outputs of at most 2^kSmallOutBits elements from operands of
+// at most 2^kSmallOpBits) in one launch: one CTA per trajectory of the chunk
+// walks the run in order, each step's descriptor staged in shared memory and
+// its outputs written to the arena, with a CTA barrier between steps (the
+// next step reads them back from L1/L2).  Every output is the same complex
+// multiply-add chain over the summed bits as in k_contract_direct.
+constexpr int kSmallThreads = 128;
+
+__global__ void __launch_bounds__(kSmallThreads) k_small_steps(const StepDesc* __restrict__ steps, int n_steps,
+                                                               ChunkCtx c) {
+    __shared__ __align__(16) StepDesc s;
+    const int64_t inst = blockIdx.x;
+    for (int k = 0; k < n_steps; k++) {
+        {
+            const int4* src = reinterpret_cast<const int4*>(steps + k);
+            int4* dst = reinterpret_cast<int4*>(&s);
+            for (int i = threadIdx.x; i < (int)(sizeof(StepDesc) / sizeof(int4)); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();   // descriptor staged; the previous step's outputs are visible
+        const float2* A = operand_ptr(s.op[0], CLS_TRAJ, inst, c);
+        const float2* B = operand_ptr(s.op[1], CLS_TRAJ, inst, c);
+        float2* out = c.arena[s.out_arena] + s.out_off * c.arena_inst[s.out_arena] + inst * s.out_size;
+        const float sa = s.op[0].conj ? -1.f : 1.f, sb = s.op[1].conj ? -1.f : 1.f;
+        const int nk = 1 << s.n_sum;
+        for (int64_t o = threadIdx.x; o < s.out_size; o += blockDim.x) {
+            int64_t oa = 0, ob = 0;
+            for (int p = 0; p < s.n_out; p++)
+                if ((o >> p) & 1) {
+                    oa += s.out_stride[0][p];
+                    ob += s.out_stride[1][p];
+                }
+            float2 acc = make_float2(0.f, 0.f);
+            for (int kk = 0; kk < nk; kk++) {
+                int64_t ka = oa, kb = ob;
+                for (int q = 0; q < s.n_sum; q++)
+                    if ((kk >> q) & 1) {
+                        ka += s.sum_stride[0][q];
+                        kb += s.sum_stride[1][q];
+                    }
+                const float2 x = A[ka], y = B[kb];
+                const float xi = sa * x.y, yi = sb * y.y;
+                acc.x = fmaf(x.x, y.x, acc.x);
+                acc.x = fmaf(-xi, yi, acc.x);
+                acc.y = fmaf(x.x, yi, acc.y);
+                acc.y = fmaf(xi, y.x, acc.y);
+            }
+            out[o] = acc;
+        }
+        __syncthreads();   // outputs written before the descriptor is replaced
+    }
+}
+
 }  // namespace
+
+bool small_step(const StepDesc& h) {
+    return h.kind == STEP_DIRECT && h.out_cls == CLS_TRAJ && h.n_out <= kSmallOutBits && h.n_sum <= kSmallSumBits &&
+           h.op[0].inst_size <= (1ll << kSmallOpBits) && h.op[1].inst_size <= (1ll << kSmallOpBits);
+}
+
+void launch_small_steps(const StepDesc* d_steps, const StepDesc* h_steps, int n_steps, const ChunkCtx& ctx,
+                        int64_t n_traj, cudaStream_t s) {
+    if (n_steps <= 0 || n_traj <= 0) return;
+    double bytes = 0.0, flops = 0.0;
+    for (int k = 0; k < n_steps; k++) {
+        const StepDesc& h = h_steps[k];
+        bytes += 8.0 * (double)n_traj * (double)(h.out_size + h.op[0].inst_size + h.op[1].inst_size);
+        flops += 8.0 * (double)n_traj * (double)h.out_size * (double)(1ll << h.n_sum);
+    }
+    StatScope sc(K_CONTRACT_SMALL, s, bytes, flops);
+    k_small_steps<<<(unsigned)n_traj, kSmallThreads, 0, s>>>(d_steps, n_steps, ctx);
+}
 
 void launch_contract_step(const StepDesc* d_step, const StepDesc& h, const ChunkCtx& ctx, int64_t n_inst,
                           cudaStream_t s) {

@@ -32,14 +32,11 @@ constexpr int kHThreads = 256, kHPer = 16, kHTile = kHThreads * kHPer;   // comp
 constexpr int kDTile = 256;                                              // CDF tile of direct draws
 
 __device__ __forceinline__ int pop_shift(unsigned rowmax_bits, int b) {
-    int e;
-    frexp((double)__uint_as_float(rowmax_bits), &e);
-    return 62 - b - e;
+    return 62 - b - frexp_exp(__uint_as_float(rowmax_bits));
 }
 
-__device__ __forceinline__ uint64_t pop_weight(float p, int s) {
-    return (uint64_t)rint(ldexp(p > 0.f ? (double)p : 0.0, s));
-}
+// rint(max(p, 0) 2^s) in integer arithmetic (quant_pow2: the FP64 value, exactly)
+__device__ __forceinline__ uint64_t pop_weight(float p, int s) { return quant_pow2(p, s); }
 
 __device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v) {
     const int lane = threadIdx.x & 31;

@@ -179,6 +179,17 @@ __global__ void __launch_bounds__(1024) k_quantise_cdf(const double* __restrict_
     }
 }
 
+// smallest x with r < C[x] (C non-decreasing, exact integers)
+__device__ __forceinline__ int64_t cdf_search_u64(const uint64_t* C, int64_t n, uint64_t r) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (r < C[mid]) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ int64_t cdf_search(const double* C, int64_t n, double r) {
     // smallest x with r < C[x]
     int64_t lo = 0, hi = n - 1;
@@ -249,11 +260,11 @@ __global__ void __launch_bounds__(256) k_sample_parents(const float* __restrict_
                                                         int64_t* __restrict__ tmp_c, int64_t* __restrict__ ndist) {
     extern __shared__ unsigned char smem[];
     const int64_t nb = (int64_t)1 << b;
-    double* C = reinterpret_cast<double*>(smem);                       // nb
+    uint64_t* C = reinterpret_cast<uint64_t*>(smem);                   // nb
     unsigned int* hist = reinterpret_cast<unsigned int*>(C + nb);      // nb
     __shared__ int64_t sh[257];
     __shared__ float fred[256];
-    __shared__ double carry;
+    __shared__ uint64_t carry;
     __shared__ int64_t wpos;
     const int64_t n = blockIdx.x;
     const int64_t c = count[n];
@@ -271,22 +282,20 @@ __global__ void __launch_bounds__(256) k_sample_parents(const float* __restrict_
         if ((int)threadIdx.x < s) fred[threadIdx.x] = fmaxf(fred[threadIdx.x], fred[threadIdx.x + s]);
         __syncthreads();
     }
-    int e;
-    frexp((double)fred[0], &e);
-    const int sigma = 52 - b - e;
-    if (threadIdx.x == 0) carry = 0.0;
+    const int sigma = 52 - b - frexp_exp(fred[0]);
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int64_t base = 0; base < nb; base += blockDim.x) {
         const int64_t x = base + threadIdx.x;
-        const double v = x < nb ? rint(ldexp((double)(p[x] > 0.f ? p[x] : 0.f), sigma)) : 0.0;
+        const uint64_t v = x < nb ? quant_pow2(p[x], sigma) : 0;
         int64_t tot;
         const int64_t ex = block_exclusive_scan((int64_t)v, sh, &tot);
-        if (x < nb) C[x] = carry + (double)(ex + (int64_t)v);
+        if (x < nb) C[x] = carry + (uint64_t)ex + v;
         __syncthreads();
-        if (threadIdx.x == 0) carry += (double)tot;
+        if (threadIdx.x == 0) carry += (uint64_t)tot;
         __syncthreads();
     }
-    const uint64_t T = (uint64_t)C[nb - 1];
+    const uint64_t T = C[nb - 1];
     if (T == 0) {   // zero-norm network: its shots cannot be drawn and are dropped
         if (threadIdx.x == 0) ndist[n] = 0;
         return;
@@ -296,8 +305,7 @@ __global__ void __launch_bounds__(256) k_sample_parents(const float* __restrict_
     for (int64_t k = threadIdx.x; k < c; k += blockDim.x) {
         const uint64_t rank = (uint64_t)(r0 + k);
         const uint4 w = philox4x32_10(make_uint4((uint32_t)rank, (uint32_t)(rank >> 32), tr, tagw), key);
-        const double r = (double)__umul64hi(word64(w), T);
-        atomicAdd(&hist[cdf_search(C, nb, r)], 1u);
+        atomicAdd(&hist[cdf_search_u64(C, nb, __umul64hi(word64(w), T))], 1u);
     }
     if (threadIdx.x == 0) wpos = 0;
     __syncthreads();
@@ -323,20 +331,22 @@ __global__ void __launch_bounds__(256) k_sample_parents(const float* __restrict_
 // no CTA-wide barrier.  The row is read in coalesced rounds of 32 bins (lane l
 // holds bin 32 i + l of round i, kept in registers): the row maximum is a
 // shuffle reduction; the exact-integer CDF is built round by round with a
-// shuffle scan plus the running total (exact in FP64 in any order); the draws
+// shuffle scan plus the running total in 64-bit integers (the values the FP64
+// rule defines, computed without FP64 arithmetic); the draws
 // search the warp's CDF in shared memory and count into its histogram; the
 // nonzero bins are compacted in x order with one ballot per round.  Same
 // arithmetic and results as k_sample_parents.
 constexpr int kSampWarps = 4;
 constexpr int kSampWarpMaxBits = 10;
 
-__device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
+__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v, int lane) {
     for (int o = 1; o < 32; o <<= 1) {
-        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        const uint64_t u = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += u;
     }
     return v;
 }
+
 
 __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
     const float* __restrict__ marg, int b, int64_t n_parent, const int32_t* __restrict__ traj,
@@ -347,8 +357,8 @@ __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
     constexpr int kMaxRounds = (1 << kSampWarpMaxBits) / 32;
     const int nb = 1 << b;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* C = reinterpret_cast<double*>(smem) + (int64_t)wib * nb;
-    unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<double*>(smem) + (int64_t)kSampWarps * nb) +
+    uint64_t* C = reinterpret_cast<uint64_t*>(smem) + (int64_t)wib * nb;
+    unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<uint64_t*>(smem) + (int64_t)kSampWarps * nb) +
                      (int64_t)wib * nb;
     const int64_t n = (int64_t)blockIdx.x * kSampWarps + wib;
     if (n >= n_parent) return;                 // the whole warp leaves together
@@ -372,15 +382,13 @@ __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
         m = fmaxf(m, v[i]);
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    int e;
-    frexp((double)m, &e);
-    const int sigma = 52 - b - e;
-    double carry = 0.0;
+    const int sigma = 52 - b - frexp_exp(m);
+    uint64_t carry = 0;
 #pragma unroll
     for (int i = 0; i < kMaxRounds; i++) {
         if (i < rounds) {
             const int x = 32 * i + lane;
-            const double inc = warp_incl_scan_f64(rint(ldexp((double)v[i], sigma)), lane);
+            const uint64_t inc = warp_incl_scan_u64(quant_pow2(v[i], sigma), lane);
             if (x < nb) {
                 C[x] = carry + inc;
                 hist[x] = 0u;
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
         }
     }
     __syncwarp();
-    const uint64_t T = (uint64_t)C[nb - 1];
+    const uint64_t T = C[nb - 1];
     if (T == 0) {   // zero-norm network: its shots cannot be drawn and are dropped
         if (lane == 0) ndist[n] = 0;
         return;
@@ -399,8 +407,7 @@ __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
     for (int64_t k = lane; k < c; k += 32) {
         const uint64_t rank = (uint64_t)(r0 + k);
         const uint4 w = philox4x32_10(make_uint4((uint32_t)rank, (uint32_t)(rank >> 32), tr, tagw), key);
-        const double r = (double)__umul64hi(word64(w), T);
-        atomicAdd(&hist[cdf_search(C, nb, r)], 1u);
+        atomicAdd(&hist[cdf_search_u64(C, nb, __umul64hi(word64(w), T))], 1u);
     }
     __syncwarp();
     int64_t pos = tmp_off[n];
@@ -556,12 +563,12 @@ int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptr
         StatScope st_sp(K_SAMPLE_PARENTS, s, (double)n_parent * ((double)((int64_t)1 << b) * 4.0 + 40.0), 0.0);
         if (b <= kSampWarpMaxBits) {
             // per warp: CDF (8 B) + histogram (4 B) per bin; 48 KB at 2^10 bins
-            const size_t smem = (size_t)kSampWarps * (((size_t)1 << b) * (sizeof(double) + sizeof(unsigned)));
+            const size_t smem = (size_t)kSampWarps * (((size_t)1 << b) * (sizeof(uint64_t) + sizeof(unsigned)));
             k_sample_parents_warp<<<(unsigned)((n_parent + kSampWarps - 1) / kSampWarps), kSampWarps * 32, smem, s>>>(
                 marg, b, n_parent, ptraj, pcount, sc.rank0, sc.tmp_off, child_cap, key,
                 philox_tag(STREAM_SAMPLE, circuit, block), sc.tmp_x, sc.tmp_c, sc.ndist);
         } else {
-            const size_t smem = (size_t)(((int64_t)1 << b) * (sizeof(double) + sizeof(unsigned int)));
+            const size_t smem = (size_t)(((int64_t)1 << b) * (sizeof(uint64_t) + sizeof(unsigned int)));
             if (smem > 32 * 1024)
                 cudaFuncSetAttribute(k_sample_parents, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_sample_parents<<<(unsigned)n_parent, 256, smem, s>>>(marg, b, ptraj, pcount, sc.rank0, sc.tmp_off,

@@ -396,6 +396,15 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         for (size_t st = 0; st < bp.steps.size(); st++) {
             const StepDesc& h = bp.steps[st];
             StepTag tag(j, (int)st);
+            if (small_step(h)) {   // a run of small trajectory-class steps: one fused launch
+                size_t en = st + 1;
+                while (en < bp.steps.size() && small_step(bp.steps[en])) en++;
+                if (en - st >= 2) {
+                    launch_small_steps(bp.d_steps + st, &bp.steps[st], (int)(en - st), ctx, c.n_traj, s);
+                    st = en - 1;
+                    continue;
+                }
+            }
             int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
             if (h.kind == STEP_GEMM || h.kind == STEP_GEMM_STACKED) {
                 e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(), gt,
@@ -751,6 +760,15 @@ ptn_status ptn_trajectory_amplitudes(const ptn_plan* cplan, const ptn_traj* traj
         for (size_t k = 0; k < bp.steps.size(); k++) {
             const StepDesc& h = bp.steps[k];
             StepTag tag(-2, (int)k);
+            if (small_step(h)) {   // a run of small trajectory-class steps: one fused launch
+                size_t en = k + 1;
+                while (en < bp.steps.size() && small_step(bp.steps[en])) en++;
+                if (en - k >= 2) {
+                    launch_small_steps(ws->ev_steps.as<StepDesc>() + k, &bp.steps[k], (int)(en - k), ctx, nt, s);
+                    k = en - 1;
+                    continue;
+                }
+            }
             const int64_t ni = h.out_cls == CLS_CONST ? 1 : nt;
             if (h.kind != STEP_DIRECT) {
                 if ((e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(), no_groups,
@@ -866,6 +884,15 @@ ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const pt
             for (size_t k = 0; k < steps.size(); k++) {
                 const StepDesc& h = steps[k];
                 StepTag tag(tag_block, (int)k);
+                if (small_step(h)) {   // a run of small trajectory-class steps: one fused launch
+                    size_t en = k + 1;
+                    while (en < steps.size() && small_step(steps[en])) en++;
+                    if (en - k >= 2) {
+                        launch_small_steps(d_steps + k, &steps[k], (int)(en - k), ctx, nt, s);
+                        k = en - 1;
+                        continue;
+                    }
+                }
                 const int64_t ni = h.out_cls == CLS_CONST ? 1 : nt;
                 if (h.kind != STEP_DIRECT) {
                     ptn_status ee = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(),

@@ -135,7 +135,9 @@ typedef struct {
                                   ket-only form (amplitudes of the block and later qubits, then
                                   the marginal as sum over later qubits of |a|^2); 2 ket-only
                                   wherever it has a path */
-    int32_t  reserved;
+    int32_t  fuse_max;         /* longest run of consecutive small trajectory-level steps (the
+                                  gate-level start of a path) executed by one launch, one CTA per
+                                  trajectory walking the run; 0 -> 1024, 1 -> one launch per step */
 } ptn_plan_opts;
 
 /* ------------------------------------------------------------- planning -- */

@@ -83,11 +83,7 @@ struct ChunkCtx {
 };
 
 // ---- launchers (kernels_contract.cu)
-// Small trajectory-class steps that run fused, a run of consecutive ones per
-// launch (one CTA per trajectory of the chunk): out <= 2^kSmallOutBits
-// elements, summed bits <= kSmallSumBits, operands <= 2^kSmallOpBits.
-constexpr int kSmallOutBits = 12, kSmallSumBits = 8, kSmallOpBits = 14;
-bool small_step(const StepDesc& h);
+// a run of small trajectory-class steps (small_step, fuse_prev) in one launch
 void launch_small_steps(const StepDesc* d_steps, const StepDesc* h_steps, int n_steps, const ChunkCtx& ctx,
                         int64_t n_traj, cudaStream_t s);
 void launch_contract_step(const StepDesc* d_step, const StepDesc& h_step, const ChunkCtx& ctx,

@@ -399,8 +399,12 @@ __global__ void k_finalize_sum(const double* __restrict__ part, int64_t tiles, i
 // at most 2^kSmallOpBits) in one launch: one CTA per trajectory of the chunk
 // walks the run in order, each step's descriptor staged in shared memory and
 // its outputs written to the arena, with a CTA barrier between steps (the
-// next step reads them back from L1/L2).  Every output is the same complex
-// multiply-add chain over the summed bits as in k_contract_direct.
+// next step reads them back from L1/L2).  A CTA touches only its own
+// trajectory's instances, and the planner admits a step into a run only if no
+// other CTA's instances can share its output's addresses (small_step,
+// fuse_prev), so the CTA barrier is the only ordering the run needs.  Every
+// output is the same complex multiply-add chain over the summed bits as in
+// k_contract_direct.
 constexpr int kSmallThreads = 128;
 
 __global__ void __launch_bounds__(kSmallThreads) k_small_steps(const StepDesc* __restrict__ steps, int n_steps,
@@ -448,11 +452,6 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_steps(const StepDesc* _
 }
 
 }  // namespace
-
-bool small_step(const StepDesc& h) {
-    return h.kind == STEP_DIRECT && h.out_cls == CLS_TRAJ && h.n_out <= kSmallOutBits && h.n_sum <= kSmallSumBits &&
-           h.op[0].inst_size <= (1ll << kSmallOpBits) && h.op[1].inst_size <= (1ll << kSmallOpBits);
-}
 
 void launch_small_steps(const StepDesc* d_steps, const StepDesc* h_steps, int n_steps, const ChunkCtx& ctx,
                         int64_t n_traj, cudaStream_t s) {

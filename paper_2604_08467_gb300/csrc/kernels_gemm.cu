@@ -92,6 +92,8 @@ struct PackArgs {
     void* dst;
     int8_t* row_exp;         // FP16: per packed row, the power-of-two exponent e of its largest
                              // |component| (the row is stored scaled by 2^-e), else null
+    const unsigned* row_max; // FP16 rows longer than kPackRegRow slots: the largest |component| of
+                             // every packed row (float bits), found by k_row_absmax; else null
 };
 
 struct GemmArgs {
@@ -193,7 +195,7 @@ __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, 
 // 32-bit pairs, consecutive lanes on consecutive slots.  FP16 rows are scaled
 // by 2^-e, e the exponent of the row's largest |component|: rows of up to 256
 // slots keep their values in registers between the max and the store pass;
-// longer rows go to k_pack_long (one block per row, second pass from cache).
+// longer rows take their maxima from a separate coalesced pass (k_row_absmax).
 constexpr int kKTab = 1024;
 constexpr int kPackRegRow = 256;   // longest FP16 row the warp kernel holds in registers
 
@@ -283,7 +285,21 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
         int64_t z, row;
         const float2* base = pack_row_base(a, c, jr, z, row);
         T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
-        if constexpr (F == FMT_FP16) {
+        if (F == FMT_FP16 && a.row_max) {
+            // long row: its largest |component| is known, one scaled pass
+            const int e = row_exponent(__uint_as_float(a.row_max[jr]));
+            const float sc = ldexpf(1.f, -e);
+            if (lane == 0) a.row_exp[jr] = (int8_t)e;
+            for (int64_t kc = l0; kc < kcp; kc += lstep) {
+                float re = 0.f, im = 0.f;
+                if (kc < kc_real) {
+                    const float2 v = base[kofs(a, ktab, kc)];
+                    re = v.x * sc;
+                    im = csign * v.y * sc;
+                }
+                pack_store<F>(a, d0, rowlen, kc, re, im);
+            }
+        } else if constexpr (F == FMT_FP16) {
             float2 v[kPackRegRow / 32];
             float mx = 0.f;
 #pragma unroll
@@ -316,54 +332,31 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
     }
 }
 
-// FP16 rows longer than kPackRegRow slots: one block per row, the block's
-// largest |component| first, then the scaled split (the second read of the
-// row hits the cache: a few hundred rows are in flight).
-template <int F>
-__global__ void __launch_bounds__(256) k_pack_long(const __grid_constant__ PackArgs a, const ChunkCtx c) {
-    using T = typename Fmt<F>::T;
+// Largest |component| of every packed row (float bits, atomicMax: the same
+// result in any order), for FP16 rows too long to hold in registers: a warp
+// takes 256 consecutive slots of one row, lanes on consecutive slots.
+constexpr int kAbsSeg = 256;
+__global__ void __launch_bounds__(256) k_row_absmax(const __grid_constant__ PackArgs a, const ChunkCtx c,
+                                                    unsigned* __restrict__ row_max) {
     __shared__ int64_t ktab[2 * kKTab];
-    __shared__ float red[8];
-    __shared__ int e_sh;
     build_ktab(a, ktab);
     __syncthreads();
-    T* dst = static_cast<T*>(a.dst);
-    const int64_t kcp = (int64_t)a.Kh / 2;
     const int64_t kc_real = (int64_t)1 << a.n_kb;
-    const int64_t rowlen = 2 * (int64_t)a.Kh;
+    const int64_t segs = (kc_real + kAbsSeg - 1) / kAbsSeg;
     const int64_t n_rows = a.n_pinst << (a.n_hb + a.n_rb);
-    const float csign = a.op.conj ? -1.f : 1.f;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    for (int64_t jr = blockIdx.x; jr < n_rows; jr += gridDim.x) {
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < n_rows * segs; w += warps) {
+        const int64_t jr = w / segs, seg = w - jr * segs;
         int64_t z, row;
         const float2* base = pack_row_base(a, c, jr, z, row);
-        T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
         float mx = 0.f;
-        for (int64_t kc = threadIdx.x; kc < kc_real; kc += blockDim.x) {
+        for (int64_t kc = seg * kAbsSeg + lane; kc < (seg + 1) * kAbsSeg && kc < kc_real; kc += 32) {
             const float2 v = base[kofs(a, ktab, kc)];
             mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) red[wib] = mx;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float m = red[0];
-            for (int i = 1; i < (int)(blockDim.x >> 5); i++) m = fmaxf(m, red[i]);
-            e_sh = row_exponent(m);
-            a.row_exp[jr] = (int8_t)e_sh;
-        }
-        __syncthreads();
-        const float sc = ldexpf(1.f, -e_sh);
-        for (int64_t kc = threadIdx.x; kc < kcp; kc += blockDim.x) {
-            float re = 0.f, im = 0.f;
-            if (kc < kc_real) {
-                const float2 v = base[kofs(a, ktab, kc)];
-                re = v.x * sc;
-                im = csign * v.y * sc;
-            }
-            pack_store<F>(a, d0, rowlen, kc, re, im);
-        }
-        __syncthreads();   // red / e_sh reused by the next row
+        if (lane == 0 && mx > 0.f) atomicMax(&row_max[jr], __float_as_uint(mx));
     }
 }
 
@@ -885,15 +878,17 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     {
         StatScope sc(K_PACK, s, 8.0 * (double)(tot_a + tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b, 0.0);
         // (grid_of sizes by complex slots; the kernels stride over rows)
-        for (const PackArgs* pk : {&pa, &pb}) {
+        for (PackArgs* pk : {&pa, &pb}) {
             const int64_t tot = pk == &pa ? tot_a : tot_b;
             if (F == FMT_FP16 && Kh / 2 > kPackRegRow) {
+                // long rows: their maxima first (one coalesced pass), then one scaled pass
                 const int64_t rows = pk->n_pinst << (pk->n_hb + pk->n_rb);
-                // few rows in flight, so the second pass over a row finds it in L2
-                k_pack_long<F><<<(unsigned)(rows < 152 * 3 ? rows : 152 * 3), 256, 0, s>>>(*pk, ctx);
-            } else {
-                k_pack<F><<<grid_of(tot), 256, 0, s>>>(*pk, ctx);
+                unsigned* rmax = reinterpret_cast<unsigned*>(pk->row_exp + ((rows + 255) & ~(int64_t)255));
+                cudaMemsetAsync(rmax, 0, sizeof(unsigned) * rows, s);
+                k_row_absmax<<<grid_of(tot), 256, 0, s>>>(*pk, ctx, rmax);
+                pk->row_max = rmax;
             }
+            k_pack<F><<<grid_of(tot), 256, 0, s>>>(*pk, ctx);
         }
     }
     CUtensorMap mA, mB;

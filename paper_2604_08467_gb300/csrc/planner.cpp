@@ -534,6 +534,48 @@ struct ArenaAlloc {   // first-fit offsets of live buffers in one arena
     }
 };
 
+// Set fuse_prev on the steps of a list that may join the fused launch of the
+// step before them: a run is a maximal sequence of small steps, cut wherever a
+// step's output range overlaps, without coinciding with it, a range of the
+// same arena read or written earlier in the run, or one of its operands
+// overlaps, without coinciding, an output written earlier in the run.  A
+// coinciding range holds the same instance at the same addresses, which only
+// the CTA of that instance touches, in order.
+static void mark_fusable_runs(std::vector<StepDesc>& steps) {
+    struct Rng {
+        int32_t arena;
+        int64_t off, size;
+        bool wrote;
+    };
+    std::vector<Rng> touched;
+    auto clash = [&](const Rng& r, bool writes) {
+        for (const Rng& t : touched) {
+            if (t.arena != r.arena || (!writes && !t.wrote)) continue;
+            const bool same = t.off == r.off && t.size == r.size;
+            if (!same && t.off < r.off + r.size && r.off < t.off + t.size) return true;
+        }
+        return false;
+    };
+    for (size_t i = 0; i < steps.size(); i++) {
+        StepDesc& st = steps[i];
+        st.fuse_prev = 0;
+        if (!small_step(st)) {
+            touched.clear();
+            continue;
+        }
+        const Rng out{st.out_arena, st.out_off, st.out_size, true};
+        std::vector<Rng> ins;
+        for (const OperandDesc& d : st.op)
+            if (d.mode == OP_BUF) ins.push_back({d.arena, d.arena_off, d.inst_size, false});
+        bool join = i > 0 && small_step(steps[i - 1]) && !clash(out, true);
+        for (const Rng& r : ins) join = join && !clash(r, false);
+        if (!join) touched.clear();
+        st.fuse_prev = join ? 1 : 0;
+        touched.insert(touched.end(), ins.begin(), ins.end());
+        touched.push_back(out);
+    }
+}
+
 // Lower a searched path to step descriptors.  expval: the network is the ket
 // state with every qubit open; the forward intermediates are kept (all of
 // them, or with checkpointing those crossing a segment boundary) and the
@@ -624,15 +666,29 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
     }
     int cur_step = 0;
     std::vector<int32_t> buf_step;   // producing step of every buffer
+    // Inside a run of small steps (one fused launch, one CTA per trajectory)
+    // a released slot is not reused before the run ends: the slot's other
+    // instances may still be read by other CTAs (mark_fusable_runs).
+    bool in_run = false;
+    std::vector<std::pair<int32_t, int64_t>> deferred;
+    auto release = [&](int32_t arena, int64_t off) {
+        if (in_run) deferred.push_back({arena, off});
+        else arenas[arena].release(off);
+    };
+    auto end_run = [&]() {
+        for (const auto& d : deferred) arenas[d.first].release(d.second);
+        deferred.clear();
+        in_run = false;
+    };
     auto consume = [&](const TRef& r) {
         if (r.mode != OP_BUF) return;
         BufInfo& bi = bufs[r.id];
         if (--bi.refs != 0) return;
         if (!expval) {
-            arenas[bi.arena].release(bi.off);
+            release(bi.arena, bi.off);
             return;
         }
-        if (ckpt && step_seg[buf_step[r.id]] == step_seg[cur_step]) arenas[bi.arena].release(bi.off);
+        if (ckpt && step_seg[buf_step[r.id]] == step_seg[cur_step]) release(bi.arena, bi.off);
     };
 
     int32_t root_id = s.root();
@@ -740,10 +796,16 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
                 st.sum_stride[o][p] = (int64_t)1 << q;
             }
         }
+        int64_t pf[2][3];
+        classify_step(st, pf, !plan->opts.simt_only);
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
+        if (!small_step(st)) end_run();
         // output buffer: allocate before releasing the operands
         BufInfo bi;
         bi.arena = C.cls;
         bi.off = arenas[C.cls].alloc(st.out_size);
+        in_run = small_step(st);
         bi.refs = mv.mc >= 0 ? 2 : 1;
         int32_t bid = (int32_t)bufs.size();
         bufs.push_back(bi);
@@ -769,10 +831,6 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
             for (auto& x : rm.layout) x = idx[x].mirror;
             ref[mv.mc] = rm;
         }
-        int64_t pf[2][3];
-        classify_step(st, pf, !plan->opts.simt_only);
-        for (int r = 0; r < 2; r++)
-            for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
         bp.steps.push_back(st);
         if (expval) recs.push_back({A, B, rc});
         cur_step++;
@@ -814,9 +872,15 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
             st.out_stride[0][p] = st.out_stride[1][p] = (int64_t)1 << pos_in(R.layout, xs[p]);
         for (size_t q = 0; q < rs.size(); q++)
             st.sum_stride[0][q] = st.sum_stride[1][q] = (int64_t)1 << pos_in(R.layout, rs[q]);
+        int64_t pf[2][3];
+        classify_step(st, pf, !plan->opts.simt_only);
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
+        if (!small_step(st)) end_run();
         BufInfo bi;
         bi.arena = cls;
         bi.off = arenas[cls].alloc(st.out_size);
+        in_run = small_step(st);
         bi.refs = 1;
         const int32_t bid = (int32_t)bufs.size();
         bufs.push_back(bi);
@@ -824,10 +888,6 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         st.out_arena = cls;
         st.out_off = bi.off;
         consume(R);
-        int64_t pf[2][3];
-        classify_step(st, pf, !plan->opts.simt_only);
-        for (int r = 0; r < 2; r++)
-            for (int k = 0; k < 3; k++) bp.pack_peak[r][k] = std::max(bp.pack_peak[r][k], pf[r][k]);
         bp.steps.push_back(st);
         cur_step++;
         {   // modelled cost of the closing step (the search did not see it)
@@ -845,6 +905,8 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         rn.layout = xs;
         R = rn;
     }
+    end_run();
+    mark_fusable_runs(bp.steps);
     ptn_status e = make_op(R, CLS_NET, bp.root.op);
     if (e) return e;
     for (int tb = 0; tb < b; tb++) bp.root.x_stride[tb] = -1;
@@ -986,6 +1048,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
         }
         adj.release(adj_off[C.id]);
     }
+    mark_fusable_runs(bp.bwd);
     bp.arena_peak[ARENA_ADJ] = adj.peak;
     bp.arena_peak[ARENA_LGRAD] = lg.peak;
     for (int k = 0; k < 3; k++) bp.arena_peak[k] = arenas[k].peak;   // recomputed buffers included
@@ -1226,6 +1289,8 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
     if (opts.est_shots <= 0) opts.est_shots = 1e6;
     if (opts.network_form < 0 || opts.network_form > 2)
         return set_error(PTN_ERR_INVALID_ARG, "network_form must be 0, 1 or 2");
+    if (opts.fuse_max < 0) return set_error(PTN_ERR_INVALID_ARG, "fuse_max must be >= 0");
+    if (opts.fuse_max == 0) opts.fuse_max = 1024;
     plan->opts = opts;
     plan->mem_cap = opts.mem_cap_bytes;
 
@@ -1642,8 +1707,9 @@ static void json_steps(std::string& s, const std::vector<StepDesc>& steps) {
         const StepDesc& st = steps[i];
         snprintf(buf, sizeof buf,
                  "%s{\"out_cls\":%d,\"n_out\":%d,\"n_sum\":%d,\"kind\":%d,\"gemm_a\":%d,\"out_arena\":%d,"
-                 "\"out_off\":%lld,\"ops\":[",
-                 i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.kind, st.gemm_a, st.out_arena, (long long)st.out_off);
+                 "\"out_off\":%lld,\"fuse_prev\":%d,\"ops\":[",
+                 i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.kind, st.gemm_a, st.out_arena, (long long)st.out_off,
+                 st.fuse_prev);
         s += buf;
         json_op(s, st.op[0]);
         s += ",";

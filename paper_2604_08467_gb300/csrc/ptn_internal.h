@@ -59,13 +59,30 @@ struct StepDesc {
     int32_t out_arena;
     int32_t kind;            // STEP_DIRECT or STEP_GEMM
     int32_t gemm_a;          // STEP_GEMM: which operand supplies the GEMM rows (the other is realified)
-    int32_t pad0, pad1;
+    int32_t fuse_prev;       // 1: may run in the same fused launch as the previous step (set by the planner)
+    int32_t pad1;
     int64_t out_size;        // 2^n_out
     int64_t out_off;         // offset of the output buffer in its arena (elements per instance)
     OperandDesc op[2];
     int64_t out_stride[2][kMaxOut];
     int64_t sum_stride[2][kMaxSum];
 };
+
+// Small trajectory-class steps run fused, a run of consecutive ones per launch
+// (one CTA per trajectory of the chunk walks the run): out <= 2^kSmallOutBits
+// elements, summed bits <= kSmallSumBits, operands <= 2^kSmallOpBits.  In
+// every arena the instances of one buffer are stored one after another
+// (offset x instances + instance x size), so two buffers whose per-instance
+// ranges overlap without coinciding share addresses across different
+// instances, i.e. across CTAs of a fused launch.  The planner therefore keeps
+// the buffers a run reads allocated until the run ends, and sets fuse_prev
+// only where a step's output range meets no range touched earlier in its run
+// other than itself.
+constexpr int kSmallOutBits = 12, kSmallSumBits = 8, kSmallOpBits = 14;
+inline bool small_step(const StepDesc& h) {
+    return h.kind == STEP_DIRECT && h.out_cls == CLS_TRAJ && h.n_out <= kSmallOutBits && h.n_sum <= kSmallSumBits &&
+           h.op[0].inst_size <= (1ll << kSmallOpBits) && h.op[1].inst_size <= (1ll << kSmallOpBits);
+}
 
 struct LeafInfo {
     int32_t gate;            // source gate, -1 for a |0> state

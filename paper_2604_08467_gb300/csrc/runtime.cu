@@ -398,7 +398,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
             StepTag tag(j, (int)st);
             if (small_step(h)) {   // a run of small trajectory-class steps: one fused launch
                 size_t en = st + 1;
-                while (en < bp.steps.size() && small_step(bp.steps[en])) en++;
+                while (en < bp.steps.size() && en - st < (size_t)plan->opts.fuse_max && bp.steps[en].fuse_prev) en++;
                 if (en - st >= 2) {
                     launch_small_steps(bp.d_steps + st, &bp.steps[st], (int)(en - st), ctx, c.n_traj, s);
                     st = en - 1;
@@ -762,7 +762,7 @@ ptn_status ptn_trajectory_amplitudes(const ptn_plan* cplan, const ptn_traj* traj
             StepTag tag(-2, (int)k);
             if (small_step(h)) {   // a run of small trajectory-class steps: one fused launch
                 size_t en = k + 1;
-                while (en < bp.steps.size() && small_step(bp.steps[en])) en++;
+                while (en < bp.steps.size() && en - k < (size_t)plan->opts.fuse_max && bp.steps[en].fuse_prev) en++;
                 if (en - k >= 2) {
                     launch_small_steps(ws->ev_steps.as<StepDesc>() + k, &bp.steps[k], (int)(en - k), ctx, nt, s);
                     k = en - 1;
@@ -886,7 +886,7 @@ ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const pt
                 StepTag tag(tag_block, (int)k);
                 if (small_step(h)) {   // a run of small trajectory-class steps: one fused launch
                     size_t en = k + 1;
-                    while (en < steps.size() && small_step(steps[en])) en++;
+                    while (en < steps.size() && en - k < (size_t)plan->opts.fuse_max && steps[en].fuse_prev) en++;
                     if (en - k >= 2) {
                         launch_small_steps(d_steps + k, &steps[k], (int)(en - k), ctx, nt, s);
                         k = en - 1;

@@ -23,9 +23,31 @@ def _bits_offsets(strides, n):
     return off
 
 
-def run_block(desc, j, kraus_rows, net_traj, net_prefix):
+def _runs(steps, schedule):
+    """Groups of steps executed together: single steps, or with a schedule the
+    fused runs (a small step followed by steps marked fuse_prev)."""
+    i = 0
+    while i < len(steps):
+        k = i + 1
+        if schedule is not None:
+            while k < len(steps) and steps[k].get("fuse_prev", 0):
+                k += 1
+        yield steps[i:k]
+        i = k
+
+
+def _order(n_inst, schedule):
+    return range(n_inst - 1, -1, -1) if schedule == "desc" else range(n_inst)
+
+
+def run_block(desc, j, kraus_rows, net_traj, net_prefix, schedule=None):
     """Marginals [n_net, 2^b] (complex64 arithmetic) of block j for the given
-    networks (net_traj non-decreasing), one chunk holding all of them."""
+    networks (net_traj non-decreasing), one chunk holding all of them.
+
+    schedule "asc" / "desc": every fused run of small steps is executed one
+    instance at a time, each instance walking the whole run before the next
+    starts (in ascending / descending instance order), the two extreme
+    interleavings of a fused launch's CTAs; the result must not change."""
     blk = desc["blocks"][j]
     vt = np.array(desc["var_table"], dtype=np.float32).view(np.complex64)
     vids = var_ids(desc, kraus_rows)
@@ -60,20 +82,26 @@ def run_block(desc, j, kraus_rows, net_traj, net_prefix):
         v = arr[base:base + d["inst_size"]]
         return np.conj(v) if d["conj"] else v
 
-    for st in blk["steps"]:
-        n_inst = inst_of[st["out_cls"]]
+    def one(st, inst):
         oa = _bits_offsets(st["out_stride"][0], st["n_out"])
         ob = _bits_offsets(st["out_stride"][1], st["n_out"])
         ka = _bits_offsets(st["sum_stride"][0], st["n_sum"])
         kb = _bits_offsets(st["sum_stride"][1], st["n_sum"])
         size = 1 << st["n_out"]
-        out = arenas[st["out_arena"]]
         obase = st["out_off"] * inst_of[st["out_arena"]]
-        for inst in range(n_inst):
-            A = operand(st["ops"][0], st["out_cls"], inst)
-            B = operand(st["ops"][1], st["out_cls"], inst)
-            val = (A[oa[:, None] + ka[None, :]] * B[ob[:, None] + kb[None, :]]).sum(axis=1)
-            out[obase + inst * size: obase + (inst + 1) * size] = val
+        A = operand(st["ops"][0], st["out_cls"], inst)
+        B = operand(st["ops"][1], st["out_cls"], inst)
+        val = (A[oa[:, None] + ka[None, :]] * B[ob[:, None] + kb[None, :]]).sum(axis=1)
+        arenas[st["out_arena"]][obase + inst * size: obase + (inst + 1) * size] = val
+
+    for run in _runs(blk["steps"], schedule):
+        if len(run) == 1:
+            for inst in range(inst_of[run[0]["out_cls"]]):
+                one(run[0], inst)
+            continue
+        for inst in _order(inst_of[run[0]["out_cls"]], schedule):
+            for st in run:
+                one(st, inst)
     root = blk["root"]
     xo = _bits_offsets(root["x_stride"], blk["b"])
     marg = np.zeros((n_net, 1 << blk["b"]), dtype=np.float64)
@@ -83,10 +111,11 @@ def run_block(desc, j, kraus_rows, net_traj, net_prefix):
     return marg
 
 
-def run_expval(desc, kraus_rows, w, var_table=None):
+def run_expval(desc, kraus_rows, w, var_table=None, schedule=None):
     """Replay of the expectation-value plan (ptn_plan_describe(detail=2)):
     forward steps, root adjoint w(x) conj(psi(x)), reversed steps.  Returns
-    (psi [n_traj, 2^n] in basis order, F [n_traj], {leaf: adjoint [n_traj, size]})."""
+    (psi [n_traj, 2^n] in basis order, F [n_traj], {leaf: adjoint [n_traj, size]}).
+    schedule: as in run_block."""
     ev = desc["expval"]
     n = desc["n_qubits"]
     vt = np.array(desc["var_table"] if var_table is None else var_table, dtype=np.float32).view(np.complex64)
@@ -105,21 +134,27 @@ def run_expval(desc, kraus_rows, w, var_table=None):
         v = arr[base:base + d["inst_size"]]
         return np.conj(v) if d["conj"] else v
 
+    def one(st, inst):
+        oa = _bits_offsets(st["out_stride"][0], st["n_out"])
+        ob = _bits_offsets(st["out_stride"][1], st["n_out"])
+        ka = _bits_offsets(st["sum_stride"][0], st["n_sum"])
+        kb = _bits_offsets(st["sum_stride"][1], st["n_sum"])
+        size = 1 << st["n_out"]
+        obase = st["out_off"] * inst_of[st["out_arena"]]
+        A = operand(st["ops"][0], inst)
+        B = operand(st["ops"][1], inst)
+        arenas[st["out_arena"]][obase + inst * size: obase + (inst + 1) * size] = \
+            (A[oa[:, None] + ka[None, :]] * B[ob[:, None] + kb[None, :]]).sum(axis=1)
+
     def execute(steps):
-        for st in steps:
-            n_inst = inst_of[st["out_cls"]]
-            oa = _bits_offsets(st["out_stride"][0], st["n_out"])
-            ob = _bits_offsets(st["out_stride"][1], st["n_out"])
-            ka = _bits_offsets(st["sum_stride"][0], st["n_sum"])
-            kb = _bits_offsets(st["sum_stride"][1], st["n_sum"])
-            size = 1 << st["n_out"]
-            out = arenas[st["out_arena"]]
-            obase = st["out_off"] * inst_of[st["out_arena"]]
-            for inst in range(n_inst):
-                A = operand(st["ops"][0], inst)
-                B = operand(st["ops"][1], inst)
-                out[obase + inst * size: obase + (inst + 1) * size] = \
-                    (A[oa[:, None] + ka[None, :]] * B[ob[:, None] + kb[None, :]]).sum(axis=1)
+        for run in _runs(steps, schedule):
+            if len(run) == 1:
+                for inst in range(inst_of[run[0]["out_cls"]]):
+                    one(run[0], inst)
+                continue
+            for inst in _order(inst_of[run[0]["out_cls"]], schedule):
+                for st in run:
+                    one(st, inst)
 
     execute(ev["steps"])
     root = ev["root"]

@@ -97,6 +97,8 @@ def test_lowered_plan_reproduces_oracle_marginals(name, make, bs, split, form):
         traj = np.repeat(np.arange(4), 3)
         prefix = prng.integers(0, 1 << start, size=len(traj)) if start else np.zeros(len(traj), int)
         got = run_block(desc, j, kraus, traj, prefix)
+        for sched in ("asc", "desc"):   # fused runs: one CTA per trajectory, any interleaving
+            assert np.array_equal(run_block(desc, j, kraus, traj, prefix, schedule=sched), got), (j, sched)
         want = _oracle_rows(circ, kraus, blocks, j, traj, prefix)
         err = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
         assert err < 2e-5, (name, j, err)
@@ -167,6 +169,10 @@ def test_expval_plan_replay(name, make, bs, split, ckpt):
     terms = [(0.7, 0b11), (-0.4, (1 << (n - 1)) | 1), (0.25, 0)]
     w = G.pauli_weights(n, terms)
     psi, F, grads = run_expval(desc, kraus, w)
+    for sched in ("asc", "desc"):   # fused runs: one CTA per trajectory, any interleaving
+        p2, F2, g2 = run_expval(desc, kraus, w, schedule=sched)
+        assert np.array_equal(p2, psi) and np.array_equal(F2, F), sched
+        assert all(np.array_equal(g2[k], grads[k]) for k in grads), sched
     for t in range(4):
         want = sv.trajectory_state(circ, kraus[t])
         err = np.linalg.norm(psi[t] - want)
@@ -187,6 +193,50 @@ def test_expval_plan_replay(name, make, bs, split, ckpt):
             lhs = np.sum(grads[p["leaf"]][t].astype(np.complex128) * lp[var])
             rhs = np.sum(w * np.conj(psi[t].astype(np.complex128)) * psi2[t])
             assert abs(lhs - rhs) < 1e-4 * max(1.0, abs(rhs)), (p["leaf"], t, lhs, rhs)
+
+
+def _fused_runs(steps):
+    runs, cur = [], []
+    for st in steps:
+        if st["fuse_prev"]:
+            cur.append(st)
+        else:
+            if len(cur) > 1:
+                runs.append(cur)
+            cur = [st]
+    if len(cur) > 1:
+        runs.append(cur)
+    return runs
+
+
+def test_fused_runs_share_no_addresses_across_trajectories():
+    """Instances of a buffer sit one after another in its arena (offset x
+    instances + instance x size), so two buffers of one fused run whose
+    per-instance ranges overlap without coinciding would share addresses
+    between different trajectories' CTAs.  Every pair of ranges of one run, at
+    least one of them written, is disjoint or identical; the runs of the
+    100-qubit workload stay long (the gate-level start of each block is one
+    launch); and a run starts only at a small direct trajectory-class step."""
+    c2 = W.config_c2()
+    plan = ptn.ptn_plan_path(c2["circuit"], c2["block_sizes"], hypersamples=8, est_traj=4096, est_shots=1e6)
+    d = plan.describe(1)
+    for blk in d["blocks"]:
+        runs = _fused_runs(blk["steps"])
+        assert max(len(r) for r in runs) >= 100
+        for run in runs:
+            rng = []
+            for st in run:
+                assert st["kind"] == 0 and st["out_cls"] == 1 and st["n_out"] <= 12 and st["n_sum"] <= 8
+                rng += [(o["arena"], o["arena_off"], o["inst_size"], False) for o in st["ops"] if o["mode"] == 1]
+                rng.append((st["out_arena"], st["out_off"], 1 << st["n_out"], True))
+            rng.sort()
+            for a in range(len(rng)):
+                for b in range(a + 1, len(rng)):
+                    x, y = rng[a], rng[b]
+                    if y[0] != x[0] or y[1] >= x[1] + x[2]:
+                        break
+                    if (x[3] or y[3]) and (x[1], x[2]) != (y[1], y[2]):
+                        raise AssertionError(f"fused run shares addresses: {x} {y}")
 
 
 def test_gemm_operands_have_contiguous_summed_bits():

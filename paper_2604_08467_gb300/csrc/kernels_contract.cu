@@ -59,7 +59,7 @@ __device__ __forceinline__ const float2* operand_ptr(const OperandDesc& d, int o
 constexpr int kDirThreads = 256;
 constexpr int kDirU = 4;
 template <typename OffT>
-__global__ void __launch_bounds__(kDirThreads, 3) k_contract_direct(const StepDesc* __restrict__ gstep, ChunkCtx c,
+__global__ void __launch_bounds__(kDirThreads, 3) k_contract_direct(const StepDesc* __restrict__ gstep, const __grid_constant__ ChunkCtx c,
                                                                  int64_t n_inst) {
     __shared__ __align__(16) StepDesc s;
     {
@@ -179,7 +179,7 @@ struct MicroBits {
     int32_t n_ins;
 };
 template <int RA, int RB>
-__global__ void __launch_bounds__(kDirThreads, 2) k_contract_micro(const StepDesc* __restrict__ gstep, ChunkCtx c,
+__global__ void __launch_bounds__(kDirThreads, 2) k_contract_micro(const StepDesc* __restrict__ gstep, const __grid_constant__ ChunkCtx c,
                                                                    int64_t n_inst, const MicroBits mb) {
     __shared__ __align__(16) StepDesc s;
     {
@@ -339,7 +339,7 @@ static void launch_micro(const StepDesc* d_step, const ChunkCtx& ctx, int64_t n_
 // otherwise as a partial that k_finalize_sum adds in tile order).
 constexpr int kFinThreads = 256, kFinPer = 16, kFinTile = kFinThreads * kFinPer;
 
-__global__ void __launch_bounds__(kFinThreads) k_finalize(const RootRef* __restrict__ groot, ChunkCtx c, int b,
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const RootRef* __restrict__ groot, const __grid_constant__ ChunkCtx c, int b,
                                                           int64_t tiles, float* __restrict__ marg,
                                                           double* __restrict__ Z, double* __restrict__ part) {
     __shared__ __align__(16) RootRef r;
@@ -408,7 +408,7 @@ __global__ void k_finalize_sum(const double* __restrict__ part, int64_t tiles, i
 constexpr int kSmallThreads = 128;
 
 __global__ void __launch_bounds__(kSmallThreads) k_small_steps(const StepDesc* __restrict__ steps, int n_steps,
-                                                               ChunkCtx c) {
+                                                               const __grid_constant__ ChunkCtx c) {
     __shared__ __align__(16) StepDesc s;
     const int64_t inst = blockIdx.x;
     for (int k = 0; k < n_steps; k++) {

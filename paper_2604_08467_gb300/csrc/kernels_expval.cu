@@ -16,7 +16,7 @@ namespace ptn {
 namespace {
 
 // one block per trajectory of the chunk
-__global__ void __launch_bounds__(256) k_observable(const RootRef* __restrict__ groot, ChunkCtx c, int n,
+__global__ void __launch_bounds__(256) k_observable(const RootRef* __restrict__ groot, const __grid_constant__ ChunkCtx c, int n,
                                                     const ObsTerm* __restrict__ terms, int n_terms,
                                                     int64_t root_adj_off, int64_t traj0, double* __restrict__ F) {
     __shared__ __align__(16) RootRef r;
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_observable(const RootRef* __restrict__ 
 }
 
 // one block per (trajectory of the chunk, parametrised leaf)
-__global__ void __launch_bounds__(128) k_leaf_grad(ChunkCtx c, const ParamLeaf* __restrict__ pl, int n_pl,
+__global__ void __launch_bounds__(128) k_leaf_grad(const __grid_constant__ ChunkCtx c, const ParamLeaf* __restrict__ pl, int n_pl,
                                                    const float2* __restrict__ dvt, int64_t traj0, int n_params,
                                                    double* __restrict__ partial) {
     __shared__ double red[128];
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_expval_reduce(const int64_t* __restrict
 }
 
 // amp[t][x] = psi_t(x) in qubit order (bit q of x = qubit q); one block per trajectory
-__global__ void __launch_bounds__(256) k_amplitudes(const RootRef* __restrict__ groot, ChunkCtx c, int n,
+__global__ void __launch_bounds__(256) k_amplitudes(const RootRef* __restrict__ groot, const __grid_constant__ ChunkCtx c, int n,
                                                     float2* __restrict__ amp) {
     __shared__ __align__(16) RootRef r;
     {

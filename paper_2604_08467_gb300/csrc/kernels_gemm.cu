@@ -13,8 +13,9 @@
 //         row 2n   = (re, -im) per k,  row 2n+1 = (im, re) per k, each [hi | lo];
 //     so that  A_row . B_row(2n) = Re C[m, n]  and  A_row . B_row(2n+1) = Im C[m, n];
 //  2. GEMM: D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T with FP32 accumulation
-//     in TMEM (the lo*lo term is dropped), D[m][2n + c] -> C[m, n], written
-//     through the step's output strides (any layout).
+//     in TMEM (the lo*lo term is dropped) over segments of at most kSegKb
+//     k-blocks, the segments added in FP32 by the epilogue; D[m][2n + c] ->
+//     C[m, n], written through the step's output strides (any layout).
 // Formats (the precision modes of the contraction):
 //  - TF32 (PTN_PREC_FP32): hi = x rounded to TF32, lo = (x - hi) rounded to
 //    TF32; |x - hi - lo| <= 2^-24 |x|, i.e. FP32-accurate products;
@@ -48,8 +49,13 @@ constexpr int kStages = 3;        // pipeline depth (4 tiles of 16 KB per stage)
 constexpr int kTileA = kBM * kRowBytes;
 constexpr int kTileB = kBN * kRowBytes;
 constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;
-constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 4096;   // align slack + stages + barriers/offsets/scales
+// epilogue staging for column-contiguous outputs: per epilogue warp a 32-row x
+// 16-column complex fragment (rows padded to 17 slots) and its 32 row offsets
+constexpr int kStgPitch = 17;
+constexpr int kStgBytes = 4 * (32 * kStgPitch * 8 + 32 * 8);
+constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 4096 + kStgBytes;   // align slack + stages + barriers/offsets/scales + staging
 constexpr int kMaxPackBits = 40;
+constexpr int kSegKb = 16;        // longest run of k-blocks accumulated in TMEM before the epilogue adds it
 // k-blocks are spread round-robin over kAcc TMEM accumulators that the
 // epilogue adds in FP32: the tensor core's FP32 accumulation truncates, so
 // shorter accumulation chains keep the contraction within FP32 accuracy.
@@ -90,17 +96,18 @@ struct PackArgs {
     int64_t h_stride[kMaxPackBits];
     int64_t k_stride[kMaxPackBits];
     void* dst;
-    int8_t* row_exp;         // FP16: per packed row, the power-of-two exponent e of its largest
-                             // |component| (the row is stored scaled by 2^-e), else null
-    const unsigned* row_max; // FP16 rows longer than kPackRegRow slots: the largest |component| of
-                             // every packed row (float bits), found by k_row_absmax; else null
+    int8_t* row_exp;         // FP16: per packed row and K segment (row-major [row][segment]) the
+                             // power-of-two exponent e of the segment's largest |component| (the
+                             // segment is stored scaled by 2^-e), else null
+    int32_t seg_slots;       // FP16: complex slots per K segment (the GEMM's kSegKb k-blocks)
 };
 
 struct GemmArgs {
     int32_t M, N2, Kh, nkb;
     int32_t n_h;
     int32_t a_pcls, b_pcls, out_cls;
-    int32_t n_mb, n_nb, n_hb, pad;
+    int32_t n_mb, n_nb, n_hb;
+    int32_t col_out;             // the lowest output bit is a column (N) bit: stores go column-contiguous
     int64_t tiles_m, tiles_n, n_inst, n_tiles;
     const int32_t* net_tl;
     // stacked mode: the rows of all networks of one trajectory form one GEMM
@@ -193,11 +200,13 @@ __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, 
 // levels (bits 0-9 and 10-19; bit 20 and up, rarely used, by a loop), so a
 // contiguous K axis turns into coalesced float2 loads.  Stores are float2 /
 // 32-bit pairs, consecutive lanes on consecutive slots.  FP16 rows are scaled
-// by 2^-e, e the exponent of the row's largest |component|: rows of up to 256
-// slots keep their values in registers between the max and the store pass;
-// longer rows take their maxima from a separate coalesced pass (k_row_absmax).
+// segment by segment: the GEMM accumulates K in segments of kSegKb k-blocks
+// (512 complex slots in FP16) and adds them in FP32, so a scale needs to be
+// uniform along one segment only.  Each (row, segment) is stored scaled by
+// 2^-e, e the exponent of its largest |component|, in one pass: a warp keeps
+// the segment in registers between the max and the store.
 constexpr int kKTab = 1024;
-constexpr int kPackRegRow = 256;   // longest FP16 row the warp kernel holds in registers
+constexpr int kPackRegRow = 512;   // longest FP16 K segment a warp holds in registers
 
 __device__ __forceinline__ void build_ktab(const PackArgs& a, int64_t* ktab) {
     const int n_lo = a.n_kb < 10 ? a.n_kb : 10;
@@ -260,7 +269,7 @@ __device__ __forceinline__ int row_exponent(float mx) {
 }
 
 template <int F>
-__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a, const ChunkCtx c) {
+__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a, const __grid_constant__ ChunkCtx c) {
     using T = typename Fmt<F>::T;
     __shared__ int64_t ktab[2 * kKTab];
     build_ktab(a, ktab);
@@ -278,47 +287,76 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
     const int64_t n_rows = a.n_pinst << (a.n_hb + a.n_rb);
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float csign = a.op.conj ? -1.f : 1.f;
-    // (FP16 rows span 32..kPackRegRow slots here, so rpw == 1 and the warp reduction sees one row)
+    if (F == FMT_FP16 && kc_real < 32) {
+        // short FP16 rows (fewer real slots than a warp, padded to 32): g =
+        // kc_real lanes per row, 32 / g rows per warp, the row maximum
+        // reduced within each lane group
+        const int lg = a.n_kb, g = 1 << lg;
+        const int sub_r = lane >> lg, l0r = lane & (g - 1);
+        for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); (w << (5 - lg)) < n_rows;
+             w += warps) {
+            const int64_t jr = (w << (5 - lg)) + sub_r;
+            const bool act = jr < n_rows;
+            float2 v = make_float2(0.f, 0.f);
+            int64_t z = 0, row = 0;
+            const float2* base = nullptr;
+            if (act) {
+                base = pack_row_base(a, c, jr, z, row);
+                v = base[kofs(a, ktab, l0r)];
+            }
+            float mx = fmaxf(fabsf(v.x), fabsf(v.y));
+            for (int o = g >> 1; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (!act) continue;
+            const int e = row_exponent(mx);
+            const float sc = ldexpf(1.f, -e);
+            if (l0r == 0) a.row_exp[jr] = (int8_t)e;
+            T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
+            pack_store<F>(a, d0, rowlen, l0r, v.x * sc, csign * v.y * sc);
+            for (int64_t kc = l0r + g; kc < kcp; kc += g) pack_store<F>(a, d0, rowlen, kc, 0.f, 0.f);   // padding
+        }
+        return;
+    }
+    if constexpr (F == FMT_FP16) {
+        // units of (row, K segment): a warp holds a segment of at most
+        // kPackRegRow slots in registers, reduces its largest |component|,
+        // and writes it scaled (rows span at least 32 slots: one unit per warp)
+        const int64_t seg = kcp < a.seg_slots ? kcp : a.seg_slots;
+        const int lseg = 63 - __clzll(seg);
+        const int64_t nseg = kcp >> lseg;
+        const int64_t units = n_rows << (lk - lseg);
+        for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < units; w += warps) {
+            const int64_t jr = w >> (lk - lseg), sg = w & (nseg - 1);
+            int64_t z, row;
+            const float2* base = pack_row_base(a, c, jr, z, row);
+            T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
+            const int64_t kc0 = sg << lseg;
+            float2 v[kPackRegRow / 32];
+            float mx = 0.f;
+#pragma unroll
+            for (int i = 0; i < kPackRegRow / 32; i++) {
+                const int64_t kc = kc0 + lane + 32 * i;
+                v[i] = make_float2(0.f, 0.f);
+                if (lane + 32 * i < seg && kc < kc_real) v[i] = base[kofs(a, ktab, kc)];
+                mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const int e = row_exponent(mx);
+            const float sc = ldexpf(1.f, -e);
+            if (lane == 0) a.row_exp[jr * nseg + sg] = (int8_t)e;
+#pragma unroll
+            for (int i = 0; i < kPackRegRow / 32; i++)
+                if (lane + 32 * i < seg)
+                    pack_store<F>(a, d0, rowlen, kc0 + lane + 32 * i, v[i].x * sc, csign * v[i].y * sc);
+        }
+        return;
+    }
     for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w * rpw < n_rows; w += warps) {
         const int64_t jr = w * rpw + sub;                // (pi, h, row), row fastest
         if (jr >= n_rows) continue;
         int64_t z, row;
         const float2* base = pack_row_base(a, c, jr, z, row);
         T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
-        if (F == FMT_FP16 && a.row_max) {
-            // long row: its largest |component| is known, one scaled pass
-            const int e = row_exponent(__uint_as_float(a.row_max[jr]));
-            const float sc = ldexpf(1.f, -e);
-            if (lane == 0) a.row_exp[jr] = (int8_t)e;
-            for (int64_t kc = l0; kc < kcp; kc += lstep) {
-                float re = 0.f, im = 0.f;
-                if (kc < kc_real) {
-                    const float2 v = base[kofs(a, ktab, kc)];
-                    re = v.x * sc;
-                    im = csign * v.y * sc;
-                }
-                pack_store<F>(a, d0, rowlen, kc, re, im);
-            }
-        } else if constexpr (F == FMT_FP16) {
-            float2 v[kPackRegRow / 32];
-            float mx = 0.f;
-#pragma unroll
-            for (int i = 0; i < kPackRegRow / 32; i++) {
-                const int64_t kc = l0 + 32 * i;
-                v[i] = make_float2(0.f, 0.f);
-                if (kc < kc_real) v[i] = base[kofs(a, ktab, kc)];
-                mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
-            }
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            const int e = row_exponent(mx);
-            const float sc = ldexpf(1.f, -e);
-            if (lane == 0) a.row_exp[jr] = (int8_t)e;
-#pragma unroll
-            for (int i = 0; i < kPackRegRow / 32; i++) {
-                const int64_t kc = l0 + 32 * i;
-                if (kc < kcp) pack_store<F>(a, d0, rowlen, kc, v[i].x * sc, csign * v[i].y * sc);
-            }
-        } else {
+        {
             for (int64_t kc = l0; kc < kcp; kc += lstep) {
                 float re = 0.f, im = 0.f;
                 if (kc < kc_real) {
@@ -332,38 +370,11 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
     }
 }
 
-// Largest |component| of every packed row (float bits, atomicMax: the same
-// result in any order), for FP16 rows too long to hold in registers: a warp
-// takes 256 consecutive slots of one row, lanes on consecutive slots.
-constexpr int kAbsSeg = 256;
-__global__ void __launch_bounds__(256) k_row_absmax(const __grid_constant__ PackArgs a, const ChunkCtx c,
-                                                    unsigned* __restrict__ row_max) {
-    __shared__ int64_t ktab[2 * kKTab];
-    build_ktab(a, ktab);
-    __syncthreads();
-    const int64_t kc_real = (int64_t)1 << a.n_kb;
-    const int64_t segs = (kc_real + kAbsSeg - 1) / kAbsSeg;
-    const int64_t n_rows = a.n_pinst << (a.n_hb + a.n_rb);
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < n_rows * segs; w += warps) {
-        const int64_t jr = w / segs, seg = w - jr * segs;
-        int64_t z, row;
-        const float2* base = pack_row_base(a, c, jr, z, row);
-        float mx = 0.f;
-        for (int64_t kc = seg * kAbsSeg + lane; kc < (seg + 1) * kAbsSeg && kc < kc_real; kc += 32) {
-            const float2 v = base[kofs(a, ktab, kc)];
-            mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
-        }
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0 && mx > 0.f) atomicMax(&row_max[jr], __float_as_uint(mx));
-    }
-}
-
 // ------------------------------------------------------------- PTX helpers --
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -390,16 +401,17 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 // Bounded wait (limit_ns of wall time, 2 s by default); false when it gave up
-// or another thread of the block aborted.
+// or another thread of the block aborted.  A limit of 0 gives up at the first
+// poll that finds the phase incomplete.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0;; i++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 255u) {
+        if ((i & 255u) == 0u) {   // first after a failed poll, then every 256 polls
             if (*abort) return false;
-            if (global_ns() - t0 > limit_ns) return false;
+            if (global_ns() - t0 >= limit_ns) return false;
         }
+        if (mbar_try_wait(bar, parity)) return true;
     }
 }
 // Bounded wait that ignores the abort flag (used to drain own async work).
@@ -474,15 +486,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// Store 32 columns of this warp's 32 TMEM lanes (one register per column) and
+// wait until the stores have completed.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+          "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+          "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 
 // Persistent warp-specialised GEMM: each CTA (one per SM) walks the tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 lane 0 streams the K-blocks
 // of all its tiles through the kStages shared-memory ring by TMA; warp 1
 // lane 0 issues tcgen05.mma into the TMEM accumulators; warps 2-5 (one per
-// TMEM lane quadrant) drain a finished tile while the producer already loads
-// the next one.  The MMA warp starts a tile only after the epilogue has
-// released the accumulators (acc_empty), and the epilogue starts after the
-// tile's last MMA completes (acc_full).  Every wait is bounded.
+// TMEM lane quadrant) drain a finished item (a tile, or one K segment of a
+// long tile) while the producer already loads the next one.  The MMA warp
+// starts an item only after the epilogue has released that item's accumulator
+// set (acc_empty), and the epilogue starts after the item's last MMA
+// completes (acc_full).  Every wait is bounded.
 constexpr int kGemmThreads = 192;
 struct TileInfo {
     int64_t inst, h, row_end;
@@ -536,13 +563,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     uint8_t* stage0 = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
     uint64_t* empty = full + kStages;
-    uint64_t* acc_full = empty + kStages;
-    uint64_t* acc_empty = acc_full + 1;
-    uint64_t* drain = acc_empty + 1;
+    uint64_t* acc_full = empty + kStages;   // per accumulator set
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
     int64_t* noff_all = reinterpret_cast<int64_t*>(tslot + 4);   // 4 epilogue warps x kBN / 2 column offsets
     float* ucol_all = reinterpret_cast<float*>(noff_all + 4 * (kBN / 2));   // FP16: column scales 2^eb
+    float2* stg_all = reinterpret_cast<float2*>(smem + kStages * kStageBytes + 4096);   // column-contiguous staging
+    int64_t* rbase_all = reinterpret_cast<int64_t*>(stg_all + 4 * 32 * kStgPitch);
+    // Work items are (tile, K segment) pairs.  A tile's k-blocks run in
+    // segments of at most kSegKb; the tensor core's accumulation truncates, so
+    // long chains drift: every segment is accumulated on its own and the
+    // epilogue adds the segments in FP32 (round to nearest), in order, into a
+    // running sum kept in TMEM columns [2 kBN, 3 kBN), then writes the tile
+    // once.  Segmented tiles use two accumulator sets of one accumulator, short
+    // contractions (at most 8 k-blocks) two sets of kAcc / 2 (the epilogue of
+    // one item overlaps the MMAs of the next); the others one set of kAcc.
+    const int seg_kb = g.nkb > kSegKb ? kSegKb : g.nkb;
+    const int n_seg = (g.nkb + seg_kb - 1) / seg_kb;
+    const int n_sets = (g.nkb <= 8 || n_seg > 1) ? 2 : 1;
+    const int acc_per = n_seg > 1 ? 1 : kAcc / n_sets;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 32) {
@@ -550,8 +591,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 4);   // one arrival per epilogue warp
+        for (int k = 0; k < 2; k++) {
+            mbar_init(&acc_full[k], 1);
+            mbar_init(&acc_empty[k], 4);   // one arrival per epilogue warp
+        }
         mbar_init(drain, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -599,38 +642,46 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     } else if (warp == 1) {
         if (lane == 0) {
             int64_t it = 0, lt = 0;
-            for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x, lt++) {
-                if (lt > 0 && !mbar_wait(acc_empty, (uint32_t)((lt - 1) & 1), abort, g.wait_ns)) {
-                    atomicExch(g.err, 4);
-                    *abort = 1;
-                    break;
-                }
-                tc_fence_after();
-                bool ok = true;
-                for (int kb = 0; kb < g.nkb; kb++, it++) {
-                    const int s = (int)(it % kStages);
-                    if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, abort, g.wait_ns)) {
-                        atomicExch(g.err, 2);
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort && ok; tile += gridDim.x) {
+                for (int sg = 0; sg < n_seg && ok; sg++, lt++) {
+                    const int set = (int)(lt % n_sets);
+                    // this set's previous item has been drained by the epilogue
+                    if (lt >= n_sets &&
+                        !mbar_wait(&acc_empty[set], (uint32_t)((lt / n_sets - 1) & 1), abort, g.wait_ns)) {
+                        atomicExch(g.err, 4);
                         *abort = 1;
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(stage0 + s * kStageBytes);
-                    const uint32_t sal = sa + kTileA, sb = sa + 2 * kTileA, sbl = sb + kTileB;
-                    const uint32_t acc = tmem + (uint32_t)((kb % kAcc) * kBN);
-                    const bool fresh = kb < kAcc;
+                    const int kb0 = sg * seg_kb, kb1 = kb0 + seg_kb < g.nkb ? kb0 + seg_kb : g.nkb;
+                    for (int kb = kb0; kb < kb1; kb++, it++) {
+                        const int s = (int)(it % kStages);
+                        if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, abort, g.wait_ns)) {
+                            atomicExch(g.err, 2);
+                            *abort = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(stage0 + s * kStageBytes);
+                        const uint32_t sal = sa + kTileA, sb = sa + 2 * kTileA, sbl = sb + kTileB;
+                        const int j = kb - kb0;
+                        const uint32_t acc = tmem + (uint32_t)((set * acc_per + j % acc_per) * kBN);
+                        const bool fresh = j < acc_per;
 #pragma unroll
-                    for (int kk = 0; kk < kRowBytes / 32; kk++) {   // 32 bytes of K per MMA
-                        const uint32_t o = kk * 32;
-                        umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sb + o), (fresh && kk == 0) ? 0u : 1u);
-                        umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
-                        umma<F>(acc, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
+                        for (int kk = 0; kk < kRowBytes / 32; kk++) {   // 32 bytes of K per MMA
+                            const uint32_t o = kk * 32;
+                            umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sb + o), (fresh && kk == 0) ? 0u : 1u);
+                            umma<F>(acc, sdesc_sw128(sa + o), sdesc_sw128(sbl + o), 1u);
+                            umma<F>(acc, sdesc_sw128(sal + o), sdesc_sw128(sb + o), 1u);
+                        }
+                        umma_commit(&empty[s]);   // stage free once these MMAs have read it
                     }
-                    umma_commit(&empty[s]);   // stage free once these MMAs have read it
+                    if (!ok) break;
+                    umma_commit(&acc_full[set]);  // accumulators complete for this item
                 }
-                if (!ok) break;
-                umma_commit(acc_full);        // accumulators complete for this tile
             }
             // MMAs still in flight finish before TMEM is freed (on every path: the
             // epilogue may have stopped early)
@@ -643,35 +694,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         const int q = warp & 3;
         int64_t* noff = noff_all + (warp - 2) * (kBN / 2);
         float* ucol = ucol_all + (warp - 2) * (kBN / 2);
-        const int n_acc = g.nkb < kAcc ? g.nkb : kAcc;
+        float2* stg = stg_all + (warp - 2) * 32 * kStgPitch;
+        int64_t* rbase = rbase_all + (warp - 2) * 32;
         int64_t lt = 0;
-        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, lt++) {
+        bool live = true;
+        for (int64_t tile = blockIdx.x; tile < n_tiles && live; tile += gridDim.x) {
             if (__shfl_sync(0xffffffffu, *abort, 0)) break;   // warp-uniform stop
             const TileInfo t = decode_tile(g, tile);
-            for (int c = lane; c < kBN / 2; c += 32) {   // output offsets (and FP16 scales) of the tile's columns
+            for (int c = lane; c < kBN / 2; c += 32) {   // output offsets of the tile's columns
                 const int64_t n = (int64_t)(t.n0 / 2) + c;
                 int64_t off = 0;
                 for (int i = 0; i < g.n_nb; i++)
                     if ((n >> i) & 1) off += g.n_stride[i];
                 noff[c] = off;
-                if (F == FMT_FP16)
-                    ucol[c] = 2 * n < g.N2 ? ldexpf(1.f, (int)g.exp_b[(int64_t)t.zb * (g.N2 >> 1) + n]) : 0.f;
             }
-            __syncwarp();
-            // one lane waits and the warp follows its outcome (lanes polling on
-            // their own could disagree when a wait gives up)
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait(acc_full, (uint32_t)(lt & 1), abort, g.wait_ns) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
-                if (lane == 0) {
-                    atomicExch(g.err, 3);
-                    *abort = 1;
-                }
-                break;
-            }
-            __syncwarp();
-            tc_fence_after();
             const int64_t row = (int64_t)t.m0 + q * 32 + lane;
             int64_t m = row, out_inst = t.inst;
             if (g.stacked) {
@@ -685,35 +721,130 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 if ((t.h >> i) & 1) moff += g.h_stride[i];
             const bool row_ok = row < t.row_end;
             float2* out = g.out + (row_ok ? out_inst : 0) * g.out_size + moff;
-            // FP16: A row scale 2^ea (packed row index za * M + row); the product with
-            // the column scale 2^eb is exactly 2^(ea + eb)
-            const float urow = (F == FMT_FP16 && row_ok) ? ldexpf(1.f, (int)g.exp_a[(int64_t)t.za * g.M + row]) : 1.f;
-#pragma unroll 1
-            for (int c0 = 0; c0 < kBN; c0 += 32) {
-                float v[32];
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-#pragma unroll
-                for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
-                for (int a = 1; a < n_acc; a++) {
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * kBN + c0), r);
-#pragma unroll
-                    for (int j = 0; j < 32; j++) v[j] += __uint_as_float(r[j]);
+            if (g.col_out) rbase[lane] = row_ok ? out_inst * g.out_size + moff : -1;
+            __syncwarp();
+            for (int sg = 0; sg < n_seg; sg++, lt++) {
+                const int set = (int)(lt % n_sets);
+                const uint32_t acc0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(set * acc_per * kBN);
+                const int seg_len = (sg + 1) * seg_kb < g.nkb ? seg_kb : g.nkb - sg * seg_kb;
+                const int n_acc = seg_len < acc_per ? seg_len : acc_per;
+                const bool add = sg > 0;   // later segments add to the running sum
+                // FP16: the segment's A row scale 2^ea (packed row za * M + row) and
+                // column scales 2^eb; their product 2^(ea + eb) is exact
+                float urow = 1.f;
+                if (F == FMT_FP16) {
+                    for (int c = lane; c < kBN / 2; c += 32) {
+                        const int64_t n = (int64_t)(t.n0 / 2) + c;
+                        ucol[c] = 2 * n < g.N2
+                                      ? ldexpf(1.f, (int)g.exp_b[((int64_t)t.zb * (g.N2 >> 1) + n) * n_seg + sg])
+                                      : 0.f;
+                    }
+                    if (row_ok) urow = ldexpf(1.f, (int)g.exp_a[((int64_t)t.za * g.M + row) * n_seg + sg]);
+                    __syncwarp();
                 }
-                if (row_ok) {
+                // one lane waits and the warp follows its outcome (lanes polling on
+                // their own could disagree when a wait gives up)
+                int ok = 1;
+                if (lane == 0) ok = mbar_wait(&acc_full[set], (uint32_t)((lt / n_sets) & 1), abort, g.wait_ns) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) {
+                        atomicExch(g.err, 3);
+                        *abort = 1;
+                    }
+                    live = false;
+                    break;
+                }
+                __syncwarp();
+                tc_fence_after();
+                // one chunk of 32 columns of this thread's row: v[2j], v[2j+1] = complex
+                // column (c0 / 2 + j), written through the output strides
+                auto store_chunk = [&](int c0, const float* v) {
+                    if (g.col_out) {
+                        // column-contiguous output: the warp's 32 x 16 fragment goes
+                        // through shared memory, then 16 lanes store 16 consecutive
+                        // columns of one row (two rows per store instruction)
 #pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const int col = t.n0 + c0 + 2 * j;
-                        if (col < g.N2) {
-                            const float u = F == FMT_FP16 ? urow * ucol[(c0 >> 1) + j] : 1.f;
-                            out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j] * u, v[2 * j + 1] * u);
+                        for (int j = 0; j < 16; j++) stg[lane * kStgPitch + j] = make_float2(v[2 * j], v[2 * j + 1]);
+                        __syncwarp();
+                        const int cc = lane & 15;
+                        const bool col_ok = t.n0 + c0 + 2 * cc < g.N2;
+                        const int64_t no = noff[(c0 >> 1) + cc];
+#pragma unroll 4
+                        for (int i = 0; i < 16; i++) {
+                            const int rr = 2 * i + (lane >> 4);
+                            const int64_t rb = rbase[rr];
+                            if (rb >= 0 && col_ok) g.out[rb + no] = stg[rr * kStgPitch + cc];
+                        }
+                        __syncwarp();
+                    } else if (row_ok) {
+#pragma unroll
+                        for (int j = 0; j < 16; j++) {
+                            const int col = t.n0 + c0 + 2 * j;
+                            if (col < g.N2) out[noff[(c0 >> 1) + j]] = make_float2(v[2 * j], v[2 * j + 1]);
+                        }
+                    }
+                };
+                if (n_seg == 1) {
+#pragma unroll 1
+                    for (int c0 = 0; c0 < kBN; c0 += 32) {
+                        float v[32];
+                        uint32_t r[32];
+                        tmem_ld32(acc0 + (uint32_t)c0, r);
+#pragma unroll
+                        for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
+                        for (int a = 1; a < n_acc; a++) {
+                            tmem_ld32(acc0 + (uint32_t)(a * kBN + c0), r);
+#pragma unroll
+                            for (int j = 0; j < 32; j++) v[j] += __uint_as_float(r[j]);
+                        }
+                        if (F == FMT_FP16) {
+#pragma unroll
+                            for (int j = 0; j < 16; j++) {
+                                const float u = urow * ucol[(c0 >> 1) + j];
+                                v[2 * j] *= u;
+                                v[2 * j + 1] *= u;
+                            }
+                        }
+                        store_chunk(c0, v);
+                    }
+                } else {
+                    // segmented: add this segment to the running sum in TMEM; the
+                    // last one writes the tile
+#pragma unroll 1
+                    for (int c0 = 0; c0 < kBN; c0 += 32) {
+                        float v[32];
+                        uint32_t r[32];
+                        tmem_ld32(acc0 + (uint32_t)c0, r);
+#pragma unroll
+                        for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
+                        if (F == FMT_FP16) {
+#pragma unroll
+                            for (int j = 0; j < 16; j++) {
+                                const float u = urow * ucol[(c0 >> 1) + j];
+                                v[2 * j] *= u;
+                                v[2 * j + 1] *= u;
+                            }
+                        }
+                        const uint32_t sa = tmem + ((uint32_t)(q * 32) << 16) + 2 * kBN + (uint32_t)c0;
+                        if (add) {
+                            tmem_ld32(sa, r);
+#pragma unroll
+                            for (int j = 0; j < 32; j++) v[j] += __uint_as_float(r[j]);
+                        }
+                        if (sg + 1 < n_seg) {
+#pragma unroll
+                            for (int j = 0; j < 32; j++) r[j] = __float_as_uint(v[j]);
+                            tmem_st32(sa, r);
+                        } else {
+                            store_chunk(c0, v);
                         }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[set]);   // accumulators read: this set may take the next item
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);   // accumulators read: the next tile may start
         }
     }
     tc_fence_before();
@@ -851,6 +982,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     ga.n_mb = nm;
     ga.n_nb = nn;
     ga.n_hb = nh;
+    ga.col_out = (nn > 0 && ga.n_stride[0] == 1) ? 1 : 0;
     ga.tiles_m = (M + kBM - 1) / kBM;
     ga.tiles_n = (2 * N + kBN - 1) / kBN;
     ga.n_inst = n_inst;
@@ -873,6 +1005,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
         pb.row_exp = after(pack_b, pb.n_pinst * (1ll << nh) * 2 * N);   // B rows are realified pairs
         ga.exp_a = pa.row_exp;
         ga.exp_b = pb.row_exp;
+        pa.seg_slots = pb.seg_slots = kSegKb * kBK / 2;
         if (Kh / 2 < 32) return set_error(PTN_ERR_INVALID_ARG, "internal: FP16 rows shorter than a warp");
     }
     {
@@ -880,14 +1013,6 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
         // (grid_of sizes by complex slots; the kernels stride over rows)
         for (PackArgs* pk : {&pa, &pb}) {
             const int64_t tot = pk == &pa ? tot_a : tot_b;
-            if (F == FMT_FP16 && Kh / 2 > kPackRegRow) {
-                // long rows: their maxima first (one coalesced pass), then one scaled pass
-                const int64_t rows = pk->n_pinst << (pk->n_hb + pk->n_rb);
-                unsigned* rmax = reinterpret_cast<unsigned*>(pk->row_exp + ((rows + 255) & ~(int64_t)255));
-                cudaMemsetAsync(rmax, 0, sizeof(unsigned) * rows, s);
-                k_row_absmax<<<grid_of(tot), 256, 0, s>>>(*pk, ctx, rmax);
-                pk->row_max = rmax;
-            }
             k_pack<F><<<grid_of(tot), 256, 0, s>>>(*pk, ctx);
         }
     }

@@ -86,8 +86,11 @@ def test_c2_marginal_error_by_precision(prec):
     from oracle import mps
     cfg = W.config_c2()
     circ = cfg["circuit"]
-    plan = ptn.ptn_plan_path(circ, cfg["block_sizes"], hypersamples=16, est_traj=cfg["n_traj"],
+    plan = ptn.ptn_plan_path(circ, cfg["block_sizes"], hypersamples=100, est_traj=cfg["n_traj"],
                              est_shots=cfg["total_shots"])
+    # the benchmark's plan: its middle block packs rows of 2^14 complex slots
+    # (FP16: one row over a cluster of four CTAs)
+    assert max(s["n_sum"] for s in plan.describe(1)["blocks"][1]["steps"] if s["kind"]) >= 13
     tr = ptn.ptn_presample_trajectories(plan, cfg["seed"], cfg["n_traj"])
     kraus = tr.to_torch()[0].cpu().numpy()
     pick = [0, 2049, 4095]

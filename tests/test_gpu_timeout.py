@@ -18,8 +18,9 @@ TIMEOUT = 6
 
 def test_wait_limit_zero_times_out_and_device_recovers():
     cfg = W.config_c2()
-    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=8, est_traj=4096, est_shots=1e6)
-    assert plan.describe()["blocks"][1]["n_gemm"] > 0
+    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=100, est_traj=4096, est_shots=1e6)
+    # a tensor-core step with a long contraction (the epilogue waits for many MMAs)
+    assert max(s["n_sum"] for s in plan.describe(1)["blocks"][1]["steps"] if s["kind"]) >= 10
     tr = ptn.ptn_presample_trajectories(plan, 3, 8)
     traj = torch.tensor(np.repeat(np.arange(8), 4), dtype=torch.int32, device="cuda")
     prefix = torch.tensor(np.random.default_rng(1).integers(0, 1 << 10, size=32), dtype=torch.int64, device="cuda")

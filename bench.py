@@ -51,9 +51,14 @@ PRECISIONS = {
 # tensor-core steps run three MMAs per real product (hi*hi + hi*lo + lo*hi)
 SPLIT_TERMS = 3
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# DRAM bytes (read + write) per average launch of a kernel class, from the ncu
-# captures summarised under profiles/ (null where none matches the current kernel)
-TRAFFIC = {}
+# DRAM bytes (read + write) over algorithmic bytes, measured by ncu on the
+# 64-trajectory case of this workload (profiles/k_gemm_c2_64traj.md,
+# profiles/k_pack_c2_64traj.md: two GEMM and two pack launches of the middle
+# block); a class's roofline traffic per launch is this ratio times its
+# algorithmic bytes per launch in the timed run.  Classes without a capture
+# of the current kernel report null.
+TRAFFIC_RATIO = {"contract_gemm": (12.930 + 6.394) / (12.10 + 6.44),
+                 "gemm_pack": (6.791 + 12.835) / (6.84 + 12.88)}
 
 
 def load_peaks():
@@ -591,7 +596,10 @@ def main():
             ach = s["alg_bytes"] / sec / 1e9 if sec > 0 else 0.0
             r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                  "peak_note": f"hbm copy ({peak_src})"}
-        r.update({"frac": r["achieved"] / r["peak"], "traffic": TRAFFIC.get(name),
+        tr = TRAFFIC_RATIO.get(name)
+        r.update({"frac": r["achieved"] / r["peak"],
+                  "traffic": tr * s["alg_bytes"] / max(s["timed_launches"], 1) if tr else None,
+                  "traffic_unit": "bytes per launch (ncu DRAM/algorithmic ratio x algorithmic bytes)" if tr else None,
                   "launches_per_step": s["timed_launches"] / max(steps, 1),
                   "ms_per_step": s["ms"] / max(steps, 1),
                   "share_of_step": sec / max(step_seconds, 1e-12)})

@@ -288,6 +288,41 @@ def measure_tc_peaks(torch, sustain_s=4.0):
 
 # ------------------------------------------------------------- our arm ----
 
+def run_nonprop(ptn, shard, torch, rank, n_traj, hypersamples, steps=3, warmup=1):
+    """Non-proportional NBS (Sec. III-B) on the paper's own circuit family
+    (Sec. IV-B): a 50-qubit, 200-gate random circuit, blocks 10/10/2 with one
+    shot per prefix and a 28-qubit final block harvested exhaustively
+    (p(x | prefix) >= 1e-6), FP16x3.  Metric: unique labelled bitstrings
+    (distinct (trajectory, bitstring) records) per second."""
+    cfg = W.config_paper(50, 200)
+    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=hypersamples, est_traj=n_traj,
+                             est_shots=n_traj, network_form=1)
+    stream = torch.cuda.current_stream()
+    times, recs, nets = [], 0, None
+    for k in range(warmup + steps):
+        tr = ptn.ptn_presample_trajectories(plan, shard.rank_seed(cfg["seed"], rank, 500 + k), n_traj)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        res = ptn.ptn_sample_nonprop(plan, tr, 77 + k, mode="exhaustive", threshold=1e-6,
+                                     precision=ptn.PTN_PREC_FP16X3)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            times.append(a.elapsed_time(b) / 1e3)
+            recs += res.n
+            nets = res.nets_per_block
+        del tr, res
+    t = float(np.sum(times))
+    return {"workload": f"{cfg['name']}: paper's random family (H X Y Z T Rx, 20% CX CY CZ CH CRx nearest "
+                        f"neighbour, Pauli / two-qubit depolarizing noise p ~ U[0.02, 0.2]), {n_traj} trajectories, "
+                        f"blocks {cfg['block_sizes']}, one shot per prefix, exhaustive final block "
+                        "p(x | prefix) >= 1e-6, fp16x3",
+            "value": recs / t, "unit": "unique bitstrings/s", "ms_per_step": 1e3 * t / len(times),
+            "steps": len(times), "records_per_step": recs // len(times), "nets_per_block": nets,
+            "contractions_per_s": float(sum(nets or [0])) * len(times) / t}
+
+
 def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers):
     """Plans (untimed), pre-samples (untimed) and runs the mixed batch through
     ptn_sample_shots_batch, once with one circuit in flight and once with
@@ -358,6 +393,8 @@ def main():
                     help="timed ptn_expval_grad calls on the 16-qubit ansatz (0: skip)")
     ap.add_argument("--mixed-batch", type=int, default=4, metavar="WORKERS",
                     help="also run the 64-circuit mixed batch with this many concurrent circuits (0: skip)")
+    ap.add_argument("--nonprop-traj", type=int, default=256,
+                    help="trajectories of the non-proportional sub-line on the paper's 50-qubit family (0: skip)")
     ap.add_argument("--no-precision-lines", action="store_true",
                     help="skip the timed steps of the other tensor-core operand splits")
     ap.add_argument("--no-peaks", action="store_true",
@@ -562,6 +599,8 @@ def main():
 
     # ---- mixed-circuit batch: 64 circuits of 20-40 qubits, 1D or 6x5 grid,
     # depth 8-16, 16-8192 trajectories, 1e3-1e6 shots (the batching workload)
+    nonprop = run_nonprop(ptn, shard, torch, rank, args.nonprop_traj, args.hypersamples) if args.nonprop_traj > 0 else None
+
     mixed = None
     if args.mixed_batch > 0:
         del plan          # frees the brickwork workspace so the batch gets the device memory
@@ -630,7 +669,7 @@ def main():
                                         f"({args.precision}), fp64 CDF / log-probabilities",
                            "error_vs_fp64": PRECISIONS[args.precision][1]},
                 "e2e": e2e, "plain_path": plain, "other_precisions": other_prec, "expval_grad": grad,
-                "mixed_batch": mixed, "roofline": roof, "cpu_baseline": cpu,
+                "mixed_batch": mixed, "nonprop": nonprop, "roofline": roof, "cpu_baseline": cpu,
                 "contractions_per_s": float(sum(nets or [0])) * world / t_step,
                 "distinct_records_per_s": float(n_records) * world / t_step,
                 "gpu_launches": int(launches), "clocks": clocks, "tc_peaks_measured": tc_peaks,

@@ -148,6 +148,47 @@ def test_nonprop_direct_b24_against_oracle():
     assert c.sum() == 20000 * nets[-1]
 
 
+@pytest.mark.parametrize("prec", [ptn.PTN_PREC_FP32, ptn.PTN_PREC_FP16X3])
+def test_paper50_final28_records_against_mps(prec):
+    """The benchmarked non-proportional configuration at full size: a 50-qubit,
+    200-gate member of the paper's family, blocks 10/10/2/28, one shot per
+    prefix and an exhaustive harvest of the 2^28-entry final blocks
+    (threshold 1e-6).  The non-final draws and the harvest replay exactly on
+    the GPU's marginals of the first blocks (checked by the smaller cases
+    above); here sampled records are checked one by one against the exact-MPS
+    oracle: p(x | prefix) = |<prefix x|psi>|^2 / p(prefix), both from the
+    trajectory's MPS, and the kept mass of every network is at most 1."""
+    from oracle import mps
+    cfg = W.config_paper(50, 200)
+    assert cfg["block_sizes"] == [10, 10, 2, 28]
+    E = 4
+    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=100, est_traj=E, est_shots=E,
+                             network_form=1)
+    tr = ptn.ptn_presample_trajectories(plan, cfg["seed"], E)
+    kraus = tr.to_torch()[0].cpu().numpy()
+    res = ptn.ptn_sample_nonprop(plan, tr, 77, mode="exhaustive", threshold=1e-6, precision=prec)
+    t, b, c, p = _records(res)
+    assert res.nets_per_block == [E, E, E, E]
+    assert len(t) > 1000 * E and np.all(c == 1) and np.all(p >= 1e-6)
+    start = 22
+    for i in range(E):
+        sel = np.nonzero(t == i)[0]
+        assert len(sel) > 0 and p[sel].sum() <= 1.0 + 1e-9
+        pre = {int(x) & ((1 << start) - 1) for x in b[sel]}
+        assert len(pre) == 1                       # one shot per prefix: one final network per trajectory
+        st = mps.trajectory_mps(cfg["circuit"], kraus[i])
+        s_pre = pre.pop()
+        p_pre = float(st.block_marginal(start, 0, s_pre)[0])
+        pick = np.random.default_rng(i).choice(sel, size=min(100, len(sel)), replace=False)
+        for r in pick:
+            bits = int(b[r])
+            v = np.ones((1, 1), dtype=np.complex128)
+            for q in range(50):
+                v = v @ st.t[q][:, (bits >> q) & 1, :]
+            want = float(abs(v[0, 0]) ** 2) / p_pre
+            assert abs(p[r] - want) <= 1e-3 * want + 1e-8, (i, bits, p[r], want)
+
+
 def test_nonprop_argument_checks():
     rng = np.random.default_rng(3)
     circ = W.attach_noise(W.brickwork_1d(6, 3, rng), [W.depolarizing_kraus(0.05)])

@@ -53,7 +53,8 @@ constexpr int kStageBytes = 2 * kTileA + 2 * kTileB;
 // 16-column complex fragment (rows padded to 17 slots) and its 32 row offsets
 constexpr int kStgPitch = 17;
 constexpr int kStgBytes = 4 * (32 * kStgPitch * 8 + 32 * 8);
-constexpr int kGemmSmem = 1024 + kStages * kStageBytes + 4096 + kStgBytes;   // align slack + stages + barriers/offsets/scales + staging
+constexpr int kTabBytes = 8192;   // barriers, TMEM slot, per-warp column offsets and FP16 column scales
+constexpr int kGemmSmem = 1024 + kStages * kStageBytes + kTabBytes + kStgBytes;   // align slack + stages + tables + staging
 constexpr int kMaxPackBits = 40;
 constexpr int kSegKb = 16;        // longest run of k-blocks accumulated in TMEM before the epilogue adds it
 // k-blocks are spread round-robin over kAcc TMEM accumulators that the
@@ -510,7 +511,7 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 // starts an item only after the epilogue has released that item's accumulator
 // set (acc_empty), and the epilogue starts after the item's last MMA
 // completes (acc_full).  Every wait is bounded.
-constexpr int kGemmThreads = 192;
+constexpr int kGemmThreads = 320;   // producer, MMA, 8 epilogue warps
 struct TileInfo {
     int64_t inst, h, row_end;
     int m0, n0, za, zb;
@@ -568,9 +569,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     uint64_t* drain = acc_empty + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-    int64_t* noff_all = reinterpret_cast<int64_t*>(tslot + 4);   // 4 epilogue warps x kBN / 2 column offsets
-    float* ucol_all = reinterpret_cast<float*>(noff_all + 4 * (kBN / 2));   // FP16: column scales 2^eb
-    float2* stg_all = reinterpret_cast<float2*>(smem + kStages * kStageBytes + 4096);   // column-contiguous staging
+    int64_t* noff_all = reinterpret_cast<int64_t*>(tslot + 4);   // 8 epilogue warps x kBN / 2 column offsets
+    float* ucol_all = reinterpret_cast<float*>(noff_all + 8 * (kBN / 2));   // FP16: column scales 2^eb
+    float2* stg_all = reinterpret_cast<float2*>(smem + kStages * kStageBytes + kTabBytes);   // column-contiguous staging
     int64_t* rbase_all = reinterpret_cast<int64_t*>(stg_all + 4 * 32 * kStgPitch);
     // Work items are (tile, K segment) pairs.  A tile's k-blocks run in
     // segments of at most kSegKb; the tensor core's accumulation truncates, so
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         }
         for (int k = 0; k < 2; k++) {
             mbar_init(&acc_full[k], 1);
-            mbar_init(&acc_empty[k], 4);   // one arrival per epilogue warp
+            mbar_init(&acc_empty[k], g.col_out ? 4 : 8);   // one arrival per working epilogue warp
         }
         mbar_init(drain, 1);
         *abort = 0;
@@ -690,18 +691,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         }
         __syncwarp();
     } else {
-        // epilogue warps 2..5: TMEM lane quadrant q = warp % 4 holds tile rows 32q..32q+31
-        const int q = warp & 3;
-        int64_t* noff = noff_all + (warp - 2) * (kBN / 2);
-        float* ucol = ucol_all + (warp - 2) * (kBN / 2);
-        float2* stg = stg_all + (warp - 2) * 32 * kStgPitch;
-        int64_t* rbase = rbase_all + (warp - 2) * 32;
+        // epilogue warps 2..9: TMEM lane quadrant q = warp % 4 holds tile rows
+        // 32q..32q+31; two warps per quadrant drain half of the tile's columns
+        // each (one warp per SM sub-partition leaves its load and store
+        // latencies exposed).  Column-contiguous outputs, which go through the
+        // staging buffers, use warps 2..5 only, each over all columns.
+        const int ew = warp - 2, q = warp & 3;
+        const int n_epi = g.col_out ? 4 : 8;
+        const int c_lo = g.col_out ? 0 : (ew >> 2) * (kBN / 2), c_hi = g.col_out ? kBN : c_lo + kBN / 2;
+        int64_t* noff = noff_all + ew * (kBN / 2);
+        float* ucol = ucol_all + ew * (kBN / 2);
+        float2* stg = stg_all + (ew & 3) * 32 * kStgPitch;
+        int64_t* rbase = rbase_all + (ew & 3) * 32;
         int64_t lt = 0;
-        bool live = true;
+        bool live = ew < n_epi;
         for (int64_t tile = blockIdx.x; tile < n_tiles && live; tile += gridDim.x) {
             if (__shfl_sync(0xffffffffu, *abort, 0)) break;   // warp-uniform stop
             const TileInfo t = decode_tile(g, tile);
-            for (int c = lane; c < kBN / 2; c += 32) {   // output offsets of the tile's columns
+            for (int c = c_lo / 2 + lane; c < c_hi / 2; c += 32) {   // output offsets of this warp's columns
                 const int64_t n = (int64_t)(t.n0 / 2) + c;
                 int64_t off = 0;
                 for (int i = 0; i < g.n_nb; i++)
@@ -733,7 +740,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 // column scales 2^eb; their product 2^(ea + eb) is exact
                 float urow = 1.f;
                 if (F == FMT_FP16) {
-                    for (int c = lane; c < kBN / 2; c += 32) {
+                    for (int c = c_lo / 2 + lane; c < c_hi / 2; c += 32) {
                         const int64_t n = (int64_t)(t.n0 / 2) + c;
                         ucol[c] = 2 * n < g.N2
                                       ? ldexpf(1.f, (int)g.exp_b[((int64_t)t.zb * (g.N2 >> 1) + n) * n_seg + sg])
@@ -787,7 +794,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 };
                 if (n_seg == 1) {
 #pragma unroll 1
-                    for (int c0 = 0; c0 < kBN; c0 += 32) {
+                    for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
                         float v[32];
                         uint32_t r[32];
                         tmem_ld32(acc0 + (uint32_t)c0, r);
@@ -812,7 +819,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                     // segmented: add this segment to the running sum in TMEM; the
                     // last one writes the tile
 #pragma unroll 1
-                    for (int c0 = 0; c0 < kBN; c0 += 32) {
+                    for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
                         float v[32];
                         uint32_t r[32];
                         tmem_ld32(acc0 + (uint32_t)c0, r);

@@ -43,7 +43,7 @@ METRIC = "noisy-circuit shots/sec on 1 GB300, batched vs plain path, at stated e
 PRECISIONS = {
     "fp32": (0, "1.5e-5 on networks of the benchmarked 30-qubit plan, every block (tests/test_gpu_precision.py), "
                 "8.4e-6 on the 16-qubit grid slice"),
-    "bf16x3": (1, "2.3e-5 on networks of the benchmarked 30-qubit plan (tests/test_gpu_precision.py), "
+    "bf16x3": (1, "2.0e-5 on networks of the benchmarked 30-qubit plan (tests/test_gpu_precision.py), "
                   "1.5e-5 on the 16-qubit grid slice"),
     "fp16x3": (2, "1.3e-5 on networks of the benchmarked 30-qubit plan, every block (tests/test_gpu_precision.py), "
                   "5.6e-6 on the 16-qubit grid slice"),
@@ -296,7 +296,7 @@ def run_nonprop(ptn, shard, torch, rank, n_traj, hypersamples, steps=3, warmup=1
     (distinct (trajectory, bitstring) records) per second."""
     cfg = W.config_paper(50, 200)
     plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=hypersamples, est_traj=n_traj,
-                             est_shots=n_traj, network_form=1)
+                             est_shots=n_traj)
     stream = torch.cuda.current_stream()
     times, recs, nets = [], 0, None
     for k in range(warmup + steps):
@@ -323,11 +323,15 @@ def run_nonprop(ptn, shard, torch, rank, n_traj, hypersamples, steps=3, warmup=1
             "contractions_per_s": float(sum(nets or [0])) * len(times) / t}
 
 
+MIXED_MAX_EST_S = 15.0   # per-circuit time budget of the mixed batch (modelled seconds)
+
+
 def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers):
     """Plans (untimed), pre-samples (untimed) and runs the mixed batch through
     ptn_sample_shots_batch, once with one circuit in flight and once with
     `workers`; circuits beyond the planner's limits or the memory cap count as
-    failed (TOO_LARGE), as do those whose modelled time exceeds 120 s.  With
+    failed (TOO_LARGE), as do those whose modelled contraction time exceeds
+    MIXED_MAX_EST_S seconds (the 6x5 grids: 20 s to 5e7 s modelled).  With
     several ranks, the circuits are shared out by modelled cost (longest
     first, no collective on the data path)."""
     cfgs = W.config_c3()
@@ -355,7 +359,7 @@ def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers)
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = ptn.ptn_sample_shots_batch(items, n_workers=nw, max_est_seconds=120.0)
+        out = ptn.ptn_sample_shots_batch(items, n_workers=nw, max_est_seconds=MIXED_MAX_EST_S)
         torch.cuda.synchronize()
         dt = shard.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
         ok = [it for it, (st, _) in zip(items, out) if st == 0]

@@ -130,15 +130,19 @@ typedef struct {
     int32_t  grad_checkpoint;  /* ptn_expval_grad: 0 keep every forward intermediate; 1 keep only
                                   those crossing segments of ~sqrt(steps) steps and recompute the
                                   rest segment by segment on the reversed path */
-    int32_t  network_form;     /* sampling networks: 0 the double layer <psi|P|psi> of every block;
-                                  1 per block the cheaper (modelled) of the double layer and the
-                                  ket-only form (amplitudes of the block and later qubits, then
-                                  the marginal as sum over later qubits of |a|^2); 2 ket-only
-                                  wherever it has a path */
+    int32_t  network_form;     /* sampling networks (PTN_FORM_*): AUTO (0) per block the cheaper
+                                  (modelled) of the double layer and the ket-only form;
+                                  DOUBLE_LAYER (1) <psi|P|psi> for every block; KET_ONLY (2) the
+                                  amplitudes of the block and later qubits, then the marginal as
+                                  the sum over later qubits of |a|^2, wherever it has a path */
     int32_t  fuse_max;         /* longest run of consecutive small trajectory-level steps (the
                                   gate-level start of a path) executed by one launch, one CTA per
                                   trajectory walking the run; 0 -> 1024, 1 -> one launch per step */
 } ptn_plan_opts;
+
+/* Network forms of the block marginals (Sec. II-B; the ket-only form gives the
+ * same marginal, see ptn_plan_opts.network_form). */
+enum { PTN_FORM_AUTO = 0, PTN_FORM_DOUBLE_LAYER = 1, PTN_FORM_KET_ONLY = 2 };
 
 /* ------------------------------------------------------------- planning -- */
 

@@ -1642,21 +1642,21 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
         D = std::max(D, E);
         BlockPlan bp;
         ptn_status e = PTN_OK;
-        if (opts.network_form == 0) {
+        if (opts.network_form == PTN_FORM_DOUBLE_LAYER) {
             e = search_and_lower(plan, net, (int)j, start, b, E, j == 0 ? E : D, rng, bp, false);
         } else {
             // ket-only form (amplitudes of the block and later qubits, closing |.|^2
-            // step), alone (form 2) or against the double layer (form 1) by
+            // step), alone (KET_ONLY) or against the double layer (AUTO) by
             // modelled time; either falls back to the double layer without a path
             // (the ket-only search draws from its own stream, so the double-layer
-            // path is the one form 0 finds)
+            // path is the one DOUBLE_LAYER finds)
             BlockNet knet;
             build_block_net(plan, n, start, b, true, knet);
             BlockPlan bk, bd;
             std::mt19937_64 krng(rng);   // a copy: rng itself is not advanced
             const ptn_status ek = search_and_lower(plan, knet, (int)j, start, b, E, j == 0 ? E : D, krng, bk, false);
             ptn_status ed = PTN_ERR_TOO_LARGE;
-            if (opts.network_form == 1 || ek != PTN_OK)
+            if (opts.network_form == PTN_FORM_AUTO || ek != PTN_OK)
                 ed = search_and_lower(plan, net, (int)j, start, b, E, j == 0 ? E : D, rng, bd, false);
             if (ek == PTN_OK && (ed != PTN_OK || bk.est_time <= bd.est_time)) {
                 bp = std::move(bk);

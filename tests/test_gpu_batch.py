@@ -56,19 +56,20 @@ def test_batch_matches_individual_calls():
 
 
 def test_batch_over_budget_items_fail_alone():
-    """Grid circuits beyond the memory cap or the time model come back as
-    TOO_LARGE; the 1D circuits in the same batch still complete."""
+    """Grid circuits beyond the time budget (modelled 19.3 s and 98.9 s against
+    15 s) or the memory cap come back as TOO_LARGE; the 1D circuits in the
+    same batch still complete."""
     cfgs = _c3(["c3_3_grid6x5_d8", "c3_58_brickwork20q_d8", "c3_0_grid6x5_d10", "c3_62_brickwork30q_d9"])
     prepared = [_prepare(c) for c in cfgs]
     items = [dict(plan=p, traj=t, seed=c["seed"], total_shots=c["total_shots"], circuit_id=c["circuit_id"])
              for c, (p, t) in zip(cfgs, prepared)]
-    out = ptn.ptn_sample_shots_batch(items, n_workers=2, max_est_seconds=60.0)
+    out = ptn.ptn_sample_shots_batch(items, n_workers=2, max_est_seconds=15.0)
     st = [s for s, _ in out]
     assert st[0] == TOO_LARGE and st[2] == TOO_LARGE
     assert st[1] == 0 and st[3] == 0
     for k in (1, 3):
         assert _host(out[k][1])[2].sum() == cfgs[k]["total_shots"]
-    # without the time guard the grids still fail, on the memory cap
+    # without the time guard the first grid (28 GB per trajectory) fails on the memory cap
     out2 = ptn.ptn_sample_shots_batch(items[:1], n_workers=4, mem_budget_bytes=8e9)
     assert out2[0][0] == TOO_LARGE
 

@@ -2,8 +2,9 @@
 lowered as the ket network of the block and later qubits (prefix projected)
 plus a closing step that sums |a|^2 over the later qubits must give the same
 marginals as the double layer, within the same norm-wise 2e-5 bound against
-the complex128 oracle.  Form 1 picks per block the cheaper of the two forms
-by the cost model, form 2 takes the ket-only form wherever it has a path."""
+the complex128 oracle.  Form 0 (AUTO) picks per block the cheaper of the two
+forms by the cost model, form 2 takes the ket-only form wherever it has a
+path."""
 import numpy as np
 import pytest
 
@@ -45,7 +46,7 @@ SMALL = [
 ]
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [0, 1, 2])
 @pytest.mark.parametrize("name,make,bs", SMALL, ids=[c[0] for c in SMALL])
 def test_forms_small_circuits(name, make, bs, form):
     rng = np.random.default_rng(len(name) * 7919)
@@ -67,7 +68,7 @@ def test_forms_small_circuits(name, make, bs, form):
         np.testing.assert_allclose(Z, want.sum(axis=1), rtol=2e-5, atol=1e-12)
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [0, 1, 2])
 def test_forms_c1_all_blocks(form):
     """12-qubit brickwork (depth 8, 64 trajectories): block 1 for every
     trajectory, block 2 for ragged prefix sets, in the ket-only forms."""
@@ -96,13 +97,13 @@ def test_forms_c1_all_blocks(form):
 
 
 def test_form1_c2_sampled_networks_vs_mps():
-    """30-qubit brickwork (depth 12, 4096 trajectories) planned with form 1,
+    """30-qubit brickwork (depth 12, 4096 trajectories) planned with form AUTO,
     whose last block takes the ket-only form; sampled networks of every block
     against the exact-MPS oracle, launched over the full trajectory set."""
     cfg = W.config_c2()
     circ = cfg["circuit"]
     plan = ptn.ptn_plan_path(circ, cfg["block_sizes"], hypersamples=16, est_traj=cfg["n_traj"],
-                             est_shots=cfg["total_shots"], network_form=1)
+                             est_shots=cfg["total_shots"], network_form=0)
     kb = _ket_blocks(plan)
     assert kb[-1] == 1
     tr = ptn.ptn_presample_trajectories(plan, cfg["seed"], cfg["n_traj"])

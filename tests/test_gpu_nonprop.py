@@ -71,8 +71,7 @@ CASES = [
 @pytest.mark.parametrize("name,make,bs,E,branch", CASES, ids=[c[0] for c in CASES])
 def test_nonprop_exact_replay_and_c128_agreement(name, make, bs, E, branch, mode):
     circ = make(np.random.default_rng(len(name) * 101))
-    plan = ptn.ptn_plan_path(circ, bs, hypersamples=8, est_traj=E, est_shots=E * branch ** (len(bs) - 1),
-                             network_form=1)
+    plan = ptn.ptn_plan_path(circ, bs, hypersamples=8, est_traj=E, est_shots=E * branch ** (len(bs) - 1))
     tr = ptn.ptn_presample_trajectories(plan, 23, E)
     kw = dict(final_shots=700) if mode == "direct" else dict(threshold=0.004)
     res = ptn.ptn_sample_nonprop(plan, tr, 0xBEEF, mode=mode, branch_shots=branch, **kw)
@@ -115,7 +114,7 @@ def test_nonprop_large_final_block_subbatched():
     several sub-batches: records equal the oracle's on the GPU's marginals."""
     cfg = W.config_c2()
     E = 24
-    plan = ptn.ptn_plan_path(cfg["circuit"], [10, 20], hypersamples=16, est_traj=E, est_shots=E, network_form=1,
+    plan = ptn.ptn_plan_path(cfg["circuit"], [10, 20], hypersamples=16, est_traj=E, est_shots=E,
                              mem_cap_bytes=1.5e8)
     tr = ptn.ptn_presample_trajectories(plan, cfg["seed"], E)
     res = ptn.ptn_sample_nonprop(plan, tr, 99, mode="exhaustive", threshold=2e-6)
@@ -137,7 +136,7 @@ def test_nonprop_direct_b24_against_oracle():
     rng = np.random.default_rng(2626)
     circ = W.attach_noise(W.brickwork_1d(26, 8, rng), [W.depolarizing_kraus(0.01)])
     E = 3
-    plan = ptn.ptn_plan_path(circ, [2, 24], hypersamples=16, est_traj=E, est_shots=E, network_form=1)
+    plan = ptn.ptn_plan_path(circ, [2, 24], hypersamples=16, est_traj=E, est_shots=E)
     tr = ptn.ptn_presample_trajectories(plan, 5, E)
     res = ptn.ptn_sample_nonprop(plan, tr, 1234, mode="direct", branch_shots=2, final_shots=20000)
     t, b, c, p = _records(res)
@@ -162,8 +161,7 @@ def test_paper50_final28_records_against_mps(prec):
     cfg = W.config_paper(50, 200)
     assert cfg["block_sizes"] == [10, 10, 2, 28]
     E = 4
-    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=100, est_traj=E, est_shots=E,
-                             network_form=1)
+    plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=100, est_traj=E, est_shots=E)
     tr = ptn.ptn_presample_trajectories(plan, cfg["seed"], E)
     kraus = tr.to_torch()[0].cpu().numpy()
     res = ptn.ptn_sample_nonprop(plan, tr, 77, mode="exhaustive", threshold=1e-6, precision=prec)

@@ -63,7 +63,7 @@ def test_paper_family_50q_vs_mps_and_nonprop_replay():
     circ = cfg["circuit"]
     bs = [10, 10, 10, 20]
     E = 12
-    plan = ptn.ptn_plan_path(circ, bs, hypersamples=16, est_traj=E, est_shots=E, network_form=1)
+    plan = ptn.ptn_plan_path(circ, bs, hypersamples=16, est_traj=E, est_shots=E)
     tr = ptn.ptn_presample_trajectories(plan, cfg["seed"], E)
     kraus = tr.to_torch()[0].cpu().numpy()
     pick = [0, 7]

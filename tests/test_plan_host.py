@@ -79,11 +79,11 @@ CASES = [
 
 
 @pytest.mark.parametrize("name,make,bs", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("split,form", [(1, 0), (0, 0), (1, 2), (0, 1)])
+@pytest.mark.parametrize("split,form", [(1, 1), (0, 1), (1, 2), (0, 0)])
 def test_lowered_plan_reproduces_oracle_marginals(name, make, bs, split, form):
-    """form 0: double-layer networks; 2: ket-only networks (amplitudes of the
-    block and later qubits, then the closing |.|^2 step); 1: the cheaper of the
-    two per block."""
+    """form 1 (DOUBLE_LAYER): double-layer networks; 2 (KET_ONLY): ket-only
+    networks (amplitudes of the block and later qubits, then the closing |.|^2
+    step); 0 (AUTO): the cheaper of the two per block."""
     rng = np.random.default_rng(zlib.crc32(name.encode()))
     circ = make(rng)
     n = circ.n_qubits

@@ -134,8 +134,12 @@ void launch_expval_reduce(const int64_t* mult, const double* F, const double* pa
 void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, int64_t traj0, uint64_t seed,
                       int32_t circuit, uint8_t* kraus, double* logq, cudaStream_t s);
 void launch_row_hash(const uint8_t* kraus, int64_t n, int32_t S, uint64_t* h, cudaStream_t s);
-void launch_first_occurrence(const uint8_t* kraus, const uint64_t* h, int64_t n, int32_t S,
-                             int64_t* first, cudaStream_t s);
+// first[i] = smallest index whose Kraus row equals row i, from the (hash, index)
+// pairs sorted stably by hash (idx: indices in sorted order) and the run
+// flags / exclusive scan / run starts of the sorted hashes
+void launch_first_in_run(const uint8_t* kraus, int32_t S, const int64_t* idx, const int64_t* flag, const int64_t* excl,
+                         const int64_t* start, int64_t n, int64_t* first, cudaStream_t s);
+void launch_iota_i64(int64_t* p, int64_t n, cudaStream_t s);
 void launch_dedup_compact(const uint8_t* kraus, const double* logq, const int64_t* first,
                           const int64_t* uid, int64_t n, int32_t S, uint8_t* kraus_u,
                           double* logq_u, int64_t* mult_u, int64_t* first_u, cudaStream_t s);

@@ -56,23 +56,39 @@ __global__ void k_row_hash(const uint8_t* __restrict__ kraus, int64_t n, int32_t
     h[i] = v;
 }
 
-// first[i] = smallest j <= i whose row equals row i
-__global__ void k_first_occurrence(const uint8_t* __restrict__ kraus, const uint64_t* __restrict__ h, int64_t n,
-                                   int32_t S, int64_t* __restrict__ first) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint64_t hi = h[i];
-    int64_t f = i;
-    for (int64_t j = 0; j < i; j++) {
-        if (h[j] != hi) continue;
-        bool eq = true;
-        for (int32_t s = 0; s < S && eq; s++) eq = kraus[j * S + s] == kraus[i * S + s];
-        if (eq) {
-            f = j;
-            break;
+// Rows with equal hashes are contiguous after a stable sort of (hash, index)
+// pairs, in increasing index order: first[i] = smallest j whose row equals
+// row i is the run's first index when the rows match (always, unless two
+// different rows share a hash), else the first matching index further along
+// the run (a hash collision: compared row by row).  p: position in the sorted
+// order; run = inclusive count of run starts up to p, minus one.
+__device__ __forceinline__ bool rows_equal(const uint8_t* __restrict__ kraus, int64_t a, int64_t b, int32_t S) {
+    const uint8_t* ra = kraus + a * S;
+    const uint8_t* rb = kraus + b * S;
+    for (int32_t s = 0; s < S; s++)
+        if (ra[s] != rb[s]) return false;
+    return true;
+}
+__global__ void k_first_in_run(const uint8_t* __restrict__ kraus, int32_t S, const int64_t* __restrict__ idx,
+                               const int64_t* __restrict__ flag, const int64_t* __restrict__ excl,
+                               const int64_t* __restrict__ start, int64_t n, int64_t* __restrict__ first) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r0 = start[excl[p] + flag[p] - 1];
+        const int64_t i = idx[p];
+        int64_t f = i;
+        for (int64_t q = r0; q < p; q++) {
+            if (rows_equal(kraus, idx[q], i, S)) {
+                f = idx[q];
+                break;
+            }
         }
+        first[i] = f;
     }
-    first[i] = f;
+}
+
+__global__ void k_iota_i64(int64_t* p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = i;
 }
 
 __global__ void k_flags_first(const int64_t* __restrict__ first, int64_t n, int64_t* __restrict__ flags) {
@@ -473,9 +489,12 @@ void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, i
 void launch_row_hash(const uint8_t* kraus, int64_t n, int32_t S, uint64_t* h, cudaStream_t s) {
     k_row_hash<<<grid_for(n, 128, 1 << 30), 128, 0, s>>>(kraus, n, S, h);
 }
-void launch_first_occurrence(const uint8_t* kraus, const uint64_t* h, int64_t n, int32_t S, int64_t* first,
-                             cudaStream_t s) {
-    k_first_occurrence<<<grid_for(n, 128, 1 << 30), 128, 0, s>>>(kraus, h, n, S, first);
+void launch_first_in_run(const uint8_t* kraus, int32_t S, const int64_t* idx, const int64_t* flag, const int64_t* excl,
+                         const int64_t* start, int64_t n, int64_t* first, cudaStream_t s) {
+    if (n > 0) k_first_in_run<<<grid_for(n, 128, 1 << 30), 128, 0, s>>>(kraus, S, idx, flag, excl, start, n, first);
+}
+void launch_iota_i64(int64_t* p, int64_t n, cudaStream_t s) {
+    if (n > 0) k_iota_i64<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(p, n);
 }
 void launch_flags_first(const int64_t* first, int64_t n, int64_t* flags, cudaStream_t s) {
     k_flags_first<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(first, n, flags);

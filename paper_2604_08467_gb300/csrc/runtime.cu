@@ -526,7 +526,6 @@ static ptn_status presample_impl(const ptn_plan* plan, uint64_t seed, int32_t ci
     if (!plan || !traj_out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
     *traj_out = nullptr;
     if (n_traj < 1 || n_traj > (1 << 24)) return set_error(PTN_ERR_INVALID_ARG, "n_traj %lld out of 1..2^24", (long long)n_traj);
-    if (dedup && n_traj > (1 << 17)) return set_error(PTN_ERR_UNSUPPORTED, "dedup supports up to 2^17 trajectories");
     ptn_status e = ensure_device(plan);
     if (e) return e;
     cudaStream_t s = (cudaStream_t)stream;
@@ -575,16 +574,41 @@ static ptn_status presample_impl(const ptn_plan* plan, uint64_t seed, int32_t ci
         TRY_CUDA(cudaMemcpyAsync(t->first, id.data(), sizeof(int64_t) * n_traj, cudaMemcpyHostToDevice, s));
         TRY_CUDA(cudaStreamSynchronize(s));
     } else {
-        uint64_t* h = nullptr;
-        int64_t *first = nullptr, *flags = nullptr, *uid = nullptr, *tmp = nullptr;
+        // first occurrence of every Kraus row: rows hashed, (hash, index) pairs
+        // sorted stably by hash (the radix sort of the shot merge), each row
+        // compared with the first row of its run of equal hashes
+        uint64_t *h = nullptr, *h2 = nullptr;
+        int64_t *first = nullptr, *flags = nullptr, *uid = nullptr, *tmp = nullptr, *ix = nullptr, *ix2 = nullptr,
+                *hist = nullptr, *excl = nullptr, *start = nullptr;
         int64_t n_u = 0;
+        const int64_t nh = radix_hist_elems(n_traj);
         TRY_CUDA(cudaMalloc(&h, sizeof(uint64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&h2, sizeof(uint64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&ix, sizeof(int64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&ix2, sizeof(int64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&hist, sizeof(int64_t) * nh));
+        TRY_CUDA(cudaMalloc(&excl, sizeof(int64_t) * n_traj));
+        TRY_CUDA(cudaMalloc(&start, sizeof(int64_t) * n_traj));
         TRY_CUDA(cudaMalloc(&first, sizeof(int64_t) * n_traj));
         TRY_CUDA(cudaMalloc(&flags, sizeof(int64_t) * n_traj));
         TRY_CUDA(cudaMalloc(&uid, sizeof(int64_t) * n_traj));
-        TRY_CUDA(cudaMalloc(&tmp, sizeof(int64_t) * scan_tmp_elems(n_traj)));
+        TRY_CUDA(cudaMalloc(&tmp, sizeof(int64_t) * std::max(scan_tmp_elems(n_traj), scan_tmp_elems(nh))));
         launch_row_hash(kraus, n_traj, S, h, s);
-        launch_first_occurrence(kraus, h, n_traj, S, first, s);
+        launch_iota_i64(ix, n_traj, s);
+        {
+            uint64_t* k[2] = {h, h2};
+            int64_t* v[2] = {ix, ix2};
+            int cur = 0;
+            for (int shift = 0; shift < 64; shift += 8) {
+                launch_radix_pass(k[cur], v[cur], n_traj, shift, hist, tmp, k[1 - cur], v[1 - cur], s);
+                cur = 1 - cur;
+            }
+            // 8 passes: the sorted pairs are back in (h, ix)
+            launch_run_flags(h, n_traj, flags, s);
+            launch_exclusive_scan(flags, excl, n_traj, tmp, s);
+            launch_run_starts(flags, excl, n_traj, start, s);
+            launch_first_in_run(kraus, S, ix, flags, excl, start, n_traj, first, s);
+        }
         launch_flags_first(first, n_traj, flags, s);
         launch_exclusive_scan(flags, uid, n_traj, tmp, s);
         int64_t last[2];
@@ -601,6 +625,12 @@ static ptn_status presample_impl(const ptn_plan* plan, uint64_t seed, int32_t ci
         launch_dedup_compact(kraus, logq, first, uid, n_traj, S, t->kraus, t->logq, t->mult, t->first, s);
         TRY_CUDA(cudaStreamSynchronize(s));
         cudaFree(h);
+        cudaFree(h2);
+        cudaFree(ix);
+        cudaFree(ix2);
+        cudaFree(hist);
+        cudaFree(excl);
+        cudaFree(start);
         cudaFree(first);
         cudaFree(flags);
         cudaFree(uid);

@@ -46,6 +46,26 @@ def test_presample_dedup_matches_oracle():
         assert mu.sum() == 300 and len(mu) < 300
 
 
+def test_presample_dedup_large_against_oracle():
+    """Dedup by hash sort at 200,000 trajectories (past what a pairwise search
+    handles): the 12-qubit brickwork at p = 0.01 over 184 sites leaves about
+    16% of the rows error-free, so one run of equal rows holds ~31k entries.
+    The deduplicated rows, multiplicities and first indices equal the oracle's
+    dedup of the same draw (the undeduplicated rows, which are bit-exact with
+    the oracle's pre-sampling in the tests above)."""
+    cfg = W.config_c1()
+    plan = _plan(cfg, hyper=2)
+    N = 200_000
+    full = ptn.ptn_presample_trajectories(plan, 4242, N, dedup=False)
+    rows, lq_all = [x.cpu().numpy() for x in full.to_torch()[:2]]
+    tr = ptn.ptn_presample_trajectories(plan, 4242, N, dedup=True)
+    kr, lq, mu, fi = [x.cpu().numpy() for x in tr.to_torch()]
+    ku, lu, mult, first = pts.dedup(rows, lq_all)
+    assert np.array_equal(kr, ku) and np.array_equal(mu, mult) and np.array_equal(fi, first)
+    assert np.array_equal(lq, lu)
+    assert mu.sum() == N and mu.max() > 20_000 and len(mu) < N
+
+
 def test_presample_edge_single_trajectory_and_circuit_id():
     cfg = W.config_c1()
     plan = _plan(cfg, hyper=2)

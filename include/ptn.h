@@ -317,8 +317,14 @@ typedef struct {
     int32_t  precision;          /* PTN_PREC_* */
     int32_t  max_traj_per_chunk; /* 0: as many as the memory cap allows; 1: the plain
                                     per-trajectory path (one trajectory per launch) */
-    int32_t  use_graphs;         /* must be 0: CUDA-graph capture of the step lists is not
-                                    built (PTN_ERR_UNSUPPORTED otherwise) */
+    int32_t  use_graphs;         /* 1: every chunk's contraction (all steps of the block and the
+                                    marginal finalisation) is recorded on a private stream and
+                                    launched as one CUDA graph on the caller's stream; the
+                                    block's executable graph stays in the plan's workspace and is
+                                    updated in place for the next chunk or call, re-instantiated
+                                    when the launch sequence changes shape.  Results equal those
+                                    of 0; per-launch timing statistics are not taken inside
+                                    graphs (launch counts are). */
     int32_t  reserved;
     int64_t  branch_shots;       /* NONPROP_*: shots drawn per prefix on every non-final block (>= 1) */
     int64_t  final_shots;        /* NONPROP_DIRECT: shots drawn from every final-block network (>= 1) */

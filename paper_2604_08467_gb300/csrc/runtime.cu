@@ -136,7 +136,19 @@ struct PlanWorkspace {
     // final-block harvest of non-proportional sampling
     DevBuf h_rowmax, h_T, h_tcdf, h_tcnt, h_toff, h_scan, h_cnt, h_rank0, h_first;
     HostBuf h_traj, h_chunk_traj, h_net_tl, h_small, h_grp;
+    // CUDA-graph execution of a block's chunk (ptn_sample_opts.use_graphs): the
+    // capture stream and one executable graph per block, updated in place
+    cudaStream_t cap_stream = nullptr;
+    std::vector<cudaGraphExec_t> gexec;
+    void release_graphs() {
+        for (auto& x : gexec)
+            if (x) cudaGraphExecDestroy(x);
+        gexec.clear();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        cap_stream = nullptr;
+    }
     void release() {
+        release_graphs();
         DevBuf* all[] = {&arena[0], &arena[1], &arena[2], &chunk_traj, &net_tl, &marg, &Z, &w, &cdf, &m,
                          &lvl_traj[0], &lvl_traj[1], &lvl_prefix[0], &lvl_prefix[1], &lvl_count[0], &lvl_count[1],
                          &s_cap, &s_tmp_off, &s_rank0, &s_excl, &s_first, &s_ndist, &s_out_off, &s_tmp_x,
@@ -266,7 +278,7 @@ struct Chunk {
 // Contract n_net networks of block j; marg/Z outputs are device arrays.
 ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const int32_t* d_net_traj,
                           const uint64_t* d_net_prefix, int64_t n_net, float* marg, double* Z, int max_traj_chunk,
-                          int precision, cudaStream_t s) {
+                          int precision, cudaStream_t s, bool graphs = false) {
     if (n_net <= 0) return PTN_OK;
     if (precision != PTN_PREC_FP32 && precision != PTN_PREC_BF16X3 && precision != PTN_PREC_FP16X3)
         return set_error(PTN_ERR_INVALID_ARG, "unknown precision mode %d", precision);
@@ -370,8 +382,25 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     if (finalize_tiles(bp.b) > 1 && (e = ws->zpart.grow(sizeof(double) * max_n * finalize_tiles(bp.b)))) return e;
     PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
     const RootRef* d_root = plan->d_roots + j;
+    if (graphs) {
+        if (!ws->cap_stream) PTN_CUDA(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+        if (ws->gexec.size() < plan->blocks.size()) ws->gexec.resize(plan->blocks.size(), nullptr);
+    }
     for (size_t ci = 0; ci < chunks.size(); ci++) {
         const Chunk& c = chunks[ci];
+        // With graphs, the chunk's launches are recorded on the capture stream
+        // (nothing runs while recording) and the graph is launched on s.
+        cudaStream_t ls = s;
+        if (graphs) {
+            PTN_CUDA(cudaStreamBeginCapture(ws->cap_stream, cudaStreamCaptureModeRelaxed));
+            ls = ws->cap_stream;
+        }
+        auto end_capture = [&]() {
+            if (!graphs) return;
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(ws->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+        };
         GroupTable gt;
         gt.n_groups = c.n_traj;
         gt.h_net0 = hg + grp_off[ci];
@@ -400,7 +429,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
                 size_t en = st + 1;
                 while (en < bp.steps.size() && en - st < (size_t)plan->opts.fuse_max && bp.steps[en].fuse_prev) en++;
                 if (en - st >= 2) {
-                    launch_small_steps(bp.d_steps + st, &bp.steps[st], (int)(en - st), ctx, c.n_traj, s);
+                    launch_small_steps(bp.d_steps + st, &bp.steps[st], (int)(en - st), ctx, c.n_traj, ls);
                     st = en - 1;
                     continue;
                 }
@@ -408,15 +437,43 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
             int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
             if (h.kind == STEP_GEMM || h.kind == STEP_GEMM_STACKED) {
                 e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(), gt,
-                                     precision, s);
-                if (e) return e;
+                                     precision, ls);
+                if (e) {
+                    end_capture();
+                    return e;
+                }
             } else {
-                launch_contract_step(bp.d_steps + st, h, ctx, ni, s);
+                launch_contract_step(bp.d_steps + st, h, ctx, ni, ls);
             }
         }
-        StepTag tag(j, (int)bp.steps.size());
-        launch_finalize(d_root, ctx, bp.b, c.n_net, marg + c.net0 * ((int64_t)1 << bp.b), Z + c.net0,
-                        ws->zpart.as<double>(), s);
+        {
+            StepTag tag(j, (int)bp.steps.size());
+            launch_finalize(d_root, ctx, bp.b, c.n_net, marg + c.net0 * ((int64_t)1 << bp.b), Z + c.net0,
+                            ws->zpart.as<double>(), ls);
+        }
+        if (graphs) {
+            // the block's executable graph takes the new chunk's parameters in
+            // place; a chunk whose launch sequence differs in shape (other
+            // launch counts) gets a fresh executable
+            cudaGraph_t g = nullptr;
+            PTN_CUDA(cudaStreamEndCapture(ws->cap_stream, &g));
+            cudaGraphExec_t& x = ws->gexec[j];
+            if (x) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(x, g, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(x);
+                    x = nullptr;
+                }
+            }
+            cudaError_t ge = x ? cudaSuccess : cudaGraphInstantiate(&x, g, 0);
+            cudaGraphDestroy(g);
+            if (ge != cudaSuccess) {
+                x = nullptr;
+                return set_error(PTN_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(ge));
+            }
+            PTN_CUDA(cudaGraphLaunch(x, s));
+        }
     }
     PTN_CUDA(cudaGetLastError());
     // a tensor-core step that gave up a bounded wait reports it through the error word
@@ -1067,7 +1124,8 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
         const int64_t nb = (int64_t)1 << bp.b;
         if ((e = ws->marg.grow(sizeof(float) * n * nb)) || (e = ws->Z.grow(sizeof(double) * n))) return e;
         e = contract_level(plan, traj, j, ws->lvl_traj[cur].as<int32_t>(), ws->lvl_prefix[cur].as<uint64_t>(), n,
-                           ws->marg.as<float>(), ws->Z.as<double>(), o->max_traj_per_chunk, o->precision, s);
+                           ws->marg.as<float>(), ws->Z.as<double>(), o->max_traj_per_chunk, o->precision, s,
+                           o->use_graphs != 0);
         if (e) return e;
         launch_fill_i64(ws->lvl_count[cur].as<int64_t>(), o->branch_shots, n, s);
         const int64_t child_cap = n * std::min<int64_t>(o->branch_shots, nb);
@@ -1140,7 +1198,7 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
     for (int64_t a = 0; a < n; a += sub) {
         const int64_t m = std::min(sub, n - a);
         e = contract_level(plan, traj, jf, ftraj + a, fprefix + a, m, ws->marg.as<float>(), ws->Z.as<double>(),
-                           o->max_traj_per_chunk, o->precision, s);
+                           o->max_traj_per_chunk, o->precision, s, o->use_graphs != 0);
         if (e) {
             free_parts();
             return e;
@@ -1226,7 +1284,7 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     if (!plan || !traj || !o || !shots_out) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
     *shots_out = nullptr;
     if (traj->plan != plan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
-    if (o->use_graphs) return set_error(PTN_ERR_UNSUPPORTED, "CUDA-graph capture is not built");
+    if (o->use_graphs != 0 && o->use_graphs != 1) return set_error(PTN_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
     if (o->mode == PTN_NONPROP_DIRECT || o->mode == PTN_NONPROP_EXHAUSTIVE)
         return sample_nonprop(plan, traj, o, shots_out, (cudaStream_t)stream);
     if (o->mode != PTN_PROPORTIONAL_FIXED && o->mode != PTN_PROPORTIONAL_TOTAL)
@@ -1268,7 +1326,8 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
         const int64_t nb = (int64_t)1 << bp.b;
         if ((e = ws->marg.grow(sizeof(float) * n * nb)) || (e = ws->Z.grow(sizeof(double) * n))) return e;
         e = contract_level(plan, traj, (int)j, ws->lvl_traj[cur].as<int32_t>(), ws->lvl_prefix[cur].as<uint64_t>(), n,
-                           ws->marg.as<float>(), ws->Z.as<double>(), o->max_traj_per_chunk, o->precision, s);
+                           ws->marg.as<float>(), ws->Z.as<double>(), o->max_traj_per_chunk, o->precision, s,
+                           o->use_graphs != 0);
         if (e) return e;
         if (j == 0 && o->mode == PTN_PROPORTIONAL_TOTAL) {
             if ((e = ws->w.grow(sizeof(double) * E)) || (e = ws->cdf.grow(sizeof(double) * E))) return e;

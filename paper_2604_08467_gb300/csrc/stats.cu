@@ -60,6 +60,10 @@ StatScope::StatScope(int kid, cudaStream_t s, double bytes, double flops) : kid_
     std::lock_guard<std::mutex> lk(g.mu);
     g.launches[kid]++;
     timing_ = g.timing && (g.only < 0 || g.only == kid);
+    if (timing_) {   // launches recorded into a CUDA graph are counted, not timed
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) timing_ = false;
+    }
     if (timing_) {
         a_ = take_event();
         b_ = take_event();

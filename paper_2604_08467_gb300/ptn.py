@@ -403,12 +403,12 @@ def _sample_opts(seed, shots_per_traj=None, total_shots=None, circuit_id=0, prec
 
 
 def ptn_sample_nonprop(plan, traj, seed, mode="exhaustive", branch_shots=1, final_shots=0, threshold=0.0,
-                       circuit_id=0, precision=PTN_PREC_FP32, max_traj_per_chunk=0, stream=None):
+                       circuit_id=0, precision=PTN_PREC_FP32, max_traj_per_chunk=0, use_graphs=0, stream=None):
     """Non-proportional NBS (include/ptn.h): branch_shots per prefix on the
     non-final blocks, then the final block harvested directly (final_shots
     draws per network) or exhaustively (p(x | prefix) >= threshold)."""
     code = {"direct": PTN_NONPROP_DIRECT, "exhaustive": PTN_NONPROP_EXHAUSTIVE}[mode]
-    o = ptn_sample_opts(code, circuit_id, 0, 0, seed, precision, max_traj_per_chunk, 0, 0, int(branch_shots),
+    o = ptn_sample_opts(code, circuit_id, 0, 0, seed, precision, max_traj_per_chunk, int(use_graphs), 0, int(branch_shots),
                         int(final_shots), float(threshold))
     h = C.c_void_p()
     _check(lib().ptn_sample_shots(plan.handle, traj.handle, C.byref(o), C.byref(h), _stream(stream)))

@@ -522,6 +522,27 @@ ptn_status ptn_tune_block_sizes(const ptn_circuit* circuit, const ptn_noise* noi
                                 int32_t n_cand, const ptn_plan_opts* opts, int64_t probe_traj, int64_t probe_shots,
                                 uint64_t seed, int32_t* best_b, double* seconds_out, ptn_stream stream);
 
+/* Tile-shape autotuning of the SIMT contraction steps (the steps that do not
+ * go to the tensor cores and do not run in a fused gate-level run): each such
+ * step computes a micro-tile of up to 2^ra x 2^rb outputs per thread, spanned
+ * by output bits along which only one operand varies (ra, rb <= 2, ra = rb = 0
+ * the plain direct kernel).  Every block is contracted once on a probe of
+ * min(n_probe, unique trajectories, what one chunk holds) networks (one per
+ * trajectory, prefix 0) to fill its intermediates; then each step is launched
+ * under every feasible (ra, rb), timed over `reps` launches with CUDA events
+ * on the stream after one warm-up, and the fastest shape is stored in the
+ * plan for later calls if it beats the default shape (the most tile bits) by
+ * more than 5%.  The probe should be as large as the chunks of the intended
+ * runs: a shape that wins on few instances can lose on many.
+ * Timing does not depend on the data, and a step's output never aliases its
+ * operands, so the repeated launches leave the intermediates intact.  The
+ * arithmetic of each output (its multiply-add chain over the summed bits) is
+ * the same for every shape.  *n_tuned_out (may be NULL): steps timed;
+ * *n_changed_out (may be NULL): steps whose fastest shape differs from the
+ * default.  Synchronises the stream.  n_probe >= 1, reps in 1..100. */
+ptn_status ptn_tune_tiles(ptn_plan* plan, const ptn_traj* traj, int64_t n_probe, int32_t reps, int32_t* n_tuned_out,
+                          int32_t* n_changed_out, ptn_stream stream);
+
 /* ---------------------------------------------------------- bounded waits -- */
 
 /* Wall-time limit of every pipeline wait inside the tensor-core contraction

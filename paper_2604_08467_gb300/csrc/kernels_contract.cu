@@ -491,10 +491,11 @@ void launch_contract_step(const StepDesc* d_step, const StepDesc& h, const Chunk
     MicroBits mb;
     memset(&mb, 0, sizeof mb);
     int ra = 0, rb = 0;
+    const int ra_max = h.tile ? (h.tile - 1) / 3 : 2, rb_max = h.tile ? (h.tile - 1) % 3 : 2;
     for (int p = h.n_out - 1; p >= 0; p--) {
         const bool va = h.out_stride[0][p] != 0, vb = h.out_stride[1][p] != 0;
-        if (va && !vb && ra < 2) mb.ta[ra++] = p;
-        else if (vb && !va && rb < 2) mb.tb[rb++] = p;
+        if (va && !vb && ra < ra_max) mb.ta[ra++] = p;
+        else if (vb && !va && rb < rb_max) mb.tb[rb++] = p;
     }
     if (off32 && ra + rb > 0) {
         for (int j = 0; j < ra; j++) mb.ins[mb.n_ins++] = mb.ta[j];

@@ -60,7 +60,9 @@ struct StepDesc {
     int32_t kind;            // STEP_DIRECT or STEP_GEMM
     int32_t gemm_a;          // STEP_GEMM: which operand supplies the GEMM rows (the other is realified)
     int32_t fuse_prev;       // 1: may run in the same fused launch as the previous step (set by the planner)
-    int32_t pad1;
+    int32_t tile;            // SIMT micro-tile of a direct step (ptn_tune_tiles): 0 the default (up to
+                             // 2 x 2 bits), else 1 + 3 ra + rb with ra, rb <= 2 the most tile bits taken
+                             // from operand 0 / 1 (ra = rb = 0: the plain direct kernel)
     int64_t out_size;        // 2^n_out
     int64_t out_off;         // offset of the output buffer in its arena (elements per instance)
     OperandDesc op[2];

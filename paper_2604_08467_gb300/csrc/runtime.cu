@@ -741,6 +741,145 @@ void ptn_traj_destroy(ptn_traj* t) {
     delete t;
 }
 
+ptn_status ptn_tune_tiles(ptn_plan* plan, const ptn_traj* traj, int64_t n_probe, int32_t reps, int32_t* n_tuned_out,
+                          int32_t* n_changed_out, ptn_stream stream) {
+    clear_error();
+    if (!plan || !traj) return set_error(PTN_ERR_INVALID_ARG, "NULL argument");
+    if (traj->plan != plan) return set_error(PTN_ERR_INVALID_ARG, "trajectories belong to another plan");
+    if (n_probe < 1 || reps < 1 || reps > 100) return set_error(PTN_ERR_INVALID_ARG, "n_probe >= 1, reps in 1..100");
+    ptn_status e = ensure_device(plan);
+    if (e) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    PlanWorkspace* ws = workspace(plan);
+    int32_t* d_traj = nullptr;
+    uint64_t* d_prefix = nullptr;
+    float* marg = nullptr;
+    double* Z = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto release_probe = [&]() {
+        cudaFree(d_traj);
+        cudaFree(d_prefix);
+        cudaFree(marg);
+        cudaFree(Z);
+        d_traj = nullptr;
+        d_prefix = nullptr;
+        marg = nullptr;
+        Z = nullptr;
+    };
+    auto fail = [&](ptn_status st) {
+        release_probe();
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return st;
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(set_error(PTN_ERR_CUDA, "tile tuning events"));
+    int32_t tuned = 0, changed = 0;
+    for (size_t j = 0; j < plan->blocks.size(); j++) {
+        BlockPlan& bp = plan->blocks[j];
+        // probe in the shape of a real chunk: k networks per trajectory (the
+        // plan's modelled networks per trajectory, distinct prefixes), as many
+        // trajectories as n_probe and one chunk allow
+        int64_t k = 1;
+        if (bp.start > 0 && bp.est_mult_traj > 0) {
+            const double r = bp.est_mult_net / bp.est_mult_traj;
+            k = std::max<int64_t>(1, (int64_t)std::llround(r));
+            if (bp.start < 40) k = std::min<int64_t>(k, (int64_t)1 << bp.start);
+        }
+        auto pk = [&](int c) { return 4.0 * (double)(bp.pack_peak[0][c] + bp.pack_peak[1][c]); };
+        const double bT = 8.0 * (double)bp.arena_peak[CLS_TRAJ] + pk(CLS_TRAJ);
+        const double bN = 8.0 * (double)bp.arena_peak[CLS_NET] + 4.0 + 8.0 + pk(CLS_NET);
+        const double bC = 8.0 * (double)bp.arena_peak[CLS_CONST] + pk(CLS_CONST);
+        const int64_t fit = (int64_t)((plan->mem_cap - bC) / (bT + (double)k * bN));
+        const int64_t nt = std::min(std::min<int64_t>(n_probe, traj->n_unique), fit);
+        if (nt < 1) continue;
+        const int64_t nn = nt * k;
+        std::vector<int32_t> ht(nn);
+        std::vector<uint64_t> hp(nn);
+        for (int64_t t = 0; t < nt; t++)
+            for (int64_t q = 0; q < k; q++) {
+                ht[t * k + q] = (int32_t)t;
+                hp[t * k + q] = (uint64_t)q;
+            }
+        if (cudaMalloc(&d_traj, sizeof(int32_t) * nn) != cudaSuccess ||
+            cudaMalloc(&d_prefix, sizeof(uint64_t) * nn) != cudaSuccess ||
+            cudaMalloc(&marg, sizeof(float) * nn * ((int64_t)1 << bp.b)) != cudaSuccess ||
+            cudaMalloc(&Z, sizeof(double) * nn) != cudaSuccess)
+            return fail(set_error(PTN_ERR_OOM, "tile tuning buffers"));
+        if (cudaMemcpyAsync(d_traj, ht.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(d_prefix, hp.data(), sizeof(uint64_t) * nn, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(set_error(PTN_ERR_CUDA, "tile tuning setup"));
+        if ((e = contract_level(plan, traj, (int)j, d_traj, d_prefix, nn, marg, Z, 0, PTN_PREC_FP32, s)))
+            return fail(e);
+        ChunkCtx ctx;
+        memset(&ctx, 0, sizeof ctx);
+        ctx.vtab = reinterpret_cast<const float2*>(plan->d_var_table);
+        ctx.var_ids = traj->var_ids;
+        ctx.n_var_cols = traj->n_var_cols;
+        ctx.chunk_traj = ws->chunk_traj.as<int32_t>();
+        ctx.net_tl = ws->net_tl.as<int32_t>();
+        ctx.net_prefix = d_prefix;
+        for (int a = 0; a < 3; a++) ctx.arena[a] = ws->arena[a].as<float2>();
+        ctx.arena_inst[CLS_CONST] = 1;
+        ctx.arena_inst[CLS_TRAJ] = nt;
+        ctx.arena_inst[CLS_NET] = nn;
+        for (size_t st = 0; st < bp.steps.size(); st++) {
+            StepDesc& h = bp.steps[st];
+            if (small_step(h)) {   // fused runs are not tuned (one launch walks the whole run)
+                size_t en = st + 1;
+                while (en < bp.steps.size() && en - st < (size_t)plan->opts.fuse_max && bp.steps[en].fuse_prev) en++;
+                if (en - st >= 2) {
+                    st = en - 1;
+                    continue;
+                }
+            }
+            if (h.kind != STEP_DIRECT) continue;
+            int ra_av = 0, rb_av = 0;
+            for (int q = 0; q < h.n_out; q++) {
+                const bool va = h.out_stride[0][q] != 0, vb = h.out_stride[1][q] != 0;
+                if (va && !vb) ra_av++;
+                else if (vb && !va) rb_av++;
+            }
+            ra_av = std::min(ra_av, 2);
+            rb_av = std::min(rb_av, 2);
+            const int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? nt : nn);
+            // the default shape first; another shape replaces it only if it is
+            // more than 5% faster (timing noise does not move the choice)
+            const int def = 1 + 3 * ra_av + rb_av;
+            int best = def;
+            float best_ms = INFINITY, def_ms = INFINITY;
+            for (int cand = -1; cand < (ra_av + 1) * (rb_av + 1); cand++) {
+                const int ra = cand < 0 ? ra_av : cand / (rb_av + 1), rb = cand < 0 ? rb_av : cand % (rb_av + 1);
+                if (cand >= 0 && ra == ra_av && rb == rb_av) continue;
+                StepDesc h2 = h;
+                h2.tile = 1 + 3 * ra + rb;
+                launch_contract_step(bp.d_steps + st, h2, ctx, ni, s);   // warm-up
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps; r++) launch_contract_step(bp.d_steps + st, h2, ctx, ni, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess)
+                    return fail(set_error(PTN_ERR_CUDA, "tile tuning: %s", cudaGetErrorString(cudaGetLastError())));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (cand < 0) def_ms = ms;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = h2.tile;
+                }
+            }
+            if (best_ms > 0.95f * def_ms) best = def;
+            tuned++;
+            if (best != def) changed++;
+            h.tile = best;
+        }
+        release_probe();
+    }
+    fail(PTN_OK);
+    if (n_tuned_out) *n_tuned_out = tuned;
+    if (n_changed_out) *n_changed_out = changed;
+    return PTN_OK;
+}
+
 ptn_status ptn_contract_batch(const ptn_plan* plan, const ptn_traj* traj, int32_t block, const int32_t* net_traj,
                               const uint64_t* net_prefix, int64_t n_net, int32_t precision, float* marg_out,
                               double* Z_out, ptn_stream stream) {

@@ -122,6 +122,8 @@ _SIGS = {
     "ptn_expval_grad": [_P, _P, C.POINTER(ptn_pauli_sum), C.POINTER(C.c_double), C.c_int32, _P, _P, _P],
     "ptn_trajectory_amplitudes": [_P, _P, C.c_int64, C.c_int64, C.c_int32, _P, _P],
     "ptn_set_wait_limit": [C.c_double],
+    "ptn_tune_tiles": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                       C.c_void_p],
     "ptn_tune_block_sizes": [C.POINTER(ptn_circuit), C.POINTER(ptn_noise), C.POINTER(C.c_int32), C.c_int32,
                              C.POINTER(ptn_plan_opts), C.c_int64, C.c_int64, C.c_uint64, C.POINTER(C.c_int32),
                              C.POINTER(C.c_double), _P],
@@ -492,6 +494,16 @@ def ptn_tune_block_sizes(circ, candidates, probe_traj, probe_shots, seed=1, hype
                                       int(probe_shots), seed, C.byref(best), secs, _stream(stream)))
     del keep
     return best.value, [secs[i] for i in range(len(candidates))]
+
+
+def ptn_tune_tiles(plan, traj, n_probe=64, reps=3, stream=None):
+    """Time every SIMT step of the plan under each micro-tile shape on a probe
+    of n_probe networks and keep the fastest (include/ptn.h).  Returns
+    (steps timed, steps whose shape changed from the default)."""
+    nt, nc = C.c_int32(0), C.c_int32(0)
+    _check(lib().ptn_tune_tiles(plan.handle, traj.handle, int(n_probe), int(reps), C.byref(nt), C.byref(nc),
+                                _stream(stream)))
+    return nt.value, nc.value
 
 
 def ptn_set_wait_limit(seconds):

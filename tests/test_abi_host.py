@@ -93,3 +93,8 @@ def test_tune_block_sizes_argument_checks():
         with pytest.raises(ptn.PtnError) as e:
             ptn.ptn_tune_block_sizes(circ, cands, probe_traj=pt, probe_shots=ps, stream=0)
         assert e.value.status == 1
+
+
+def test_tune_tiles_argument_checks():
+    lib = ptn.lib()
+    assert lib.ptn_tune_tiles(None, None, 8, 2, None, None, None) == 1   # NULL handles

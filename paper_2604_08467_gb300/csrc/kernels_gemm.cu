@@ -228,14 +228,30 @@ __device__ __forceinline__ int64_t kofs(const PackArgs& a, const int64_t* ktab, 
     return off;
 }
 // Operand address of packed row jr = (pi * nh + h) * nrow + row; z = pi * nh + h.
-__device__ __forceinline__ const float2* pack_row_base(const PackArgs& a, const ChunkCtx& c, int64_t jr, int64_t& z,
-                                                      int64_t& row) {
+// Row offsets from a two-level table like the K offsets (row bits 0-9 and
+// 10-19; bit 20 and up by a loop): short rows would otherwise spend most of
+// their time forming their base address.
+__device__ __forceinline__ void build_rtab(const PackArgs& a, int64_t* rtab) {
+    const int n_lo = a.n_rb < 10 ? a.n_rb : 10;
+    const int n_mid = a.n_rb < 20 ? a.n_rb - n_lo : 10;
+    for (int i = threadIdx.x; i < 2 * kKTab; i += blockDim.x) {
+        const int lvl = i >= kKTab, v = i & (kKTab - 1);
+        int64_t off = 0;
+        const int nb = lvl ? n_mid : n_lo, b0 = lvl ? 10 : 0;
+        for (int t = 0; t < nb; t++)
+            if ((v >> t) & 1) off += a.r_stride[b0 + t];
+        rtab[i] = off;
+    }
+}
+__device__ __forceinline__ const float2* pack_row_base(const PackArgs& a, const ChunkCtx& c, const int64_t* rtab,
+                                                      int64_t jr, int64_t& z, int64_t& row) {
     row = jr & (((int64_t)1 << a.n_rb) - 1);
     z = jr >> a.n_rb;
     const int64_t h = z & (((int64_t)1 << a.n_hb) - 1);
     const int64_t pi = z >> a.n_hb;
     const float2* base = pack_operand_ptr(a.op, a.pcls, pi, c);
-    for (int i = 0; i < a.n_rb; i++)
+    base += rtab[row & (kKTab - 1)] + rtab[kKTab + ((row >> 10) & (kKTab - 1))];
+    for (int i = 20; i < a.n_rb; i++)
         if ((row >> i) & 1) base += a.r_stride[i];
     for (int i = 0; i < a.n_hb; i++)
         if ((h >> i) & 1) base += a.h_stride[i];
@@ -273,7 +289,9 @@ template <int F>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a, const __grid_constant__ ChunkCtx c) {
     using T = typename Fmt<F>::T;
     __shared__ int64_t ktab[2 * kKTab];
+    __shared__ int64_t rtab[2 * kKTab];
     build_ktab(a, ktab);
+    build_rtab(a, rtab);
     __syncthreads();
     T* dst = static_cast<T*>(a.dst);
     const int lk = 31 - __clz(a.Kh / 2);                // log2 complex slots per half row
@@ -302,7 +320,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
             int64_t z = 0, row = 0;
             const float2* base = nullptr;
             if (act) {
-                base = pack_row_base(a, c, jr, z, row);
+                base = pack_row_base(a, c, rtab, jr, z, row);
                 v = base[kofs(a, ktab, l0r)];
             }
             float mx = fmaxf(fabsf(v.x), fabsf(v.y));
@@ -328,7 +346,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
         for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < units; w += warps) {
             const int64_t jr = w >> (lk - lseg), sg = w & (nseg - 1);
             int64_t z, row;
-            const float2* base = pack_row_base(a, c, jr, z, row);
+            const float2* base = pack_row_base(a, c, rtab, jr, z, row);
             T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
             const int64_t kc0 = sg << lseg;
             float2 v[kPackRegRow / 32];
@@ -355,7 +373,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
         const int64_t jr = w * rpw + sub;                // (pi, h, row), row fastest
         if (jr >= n_rows) continue;
         int64_t z, row;
-        const float2* base = pack_row_base(a, c, jr, z, row);
+        const float2* base = pack_row_base(a, c, rtab, jr, z, row);
         T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
         {
             for (int64_t kc = l0; kc < kcp; kc += lstep) {

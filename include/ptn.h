@@ -220,6 +220,13 @@ void ptn_traj_destroy(ptn_traj* traj);
 
 /* ---------------------------------------------------------- contraction -- */
 
+/* Precision of the tensor-core contraction steps (the SIMT steps are FP32):
+ * FP32: TF32 hi/lo operands, three MMAs per product, FP32-accurate;
+ * BF16X3 / FP16X3: BF16 or FP16 hi/lo operands (FP16 scaled by a power of two
+ * per row and K segment), three MMAs per product.  In every mode K is
+ * accumulated in segments added in FP32, and a contraction over at most 16
+ * complex terms runs with TF32 hi/lo operands (one 128-byte K-block without
+ * padding). */
 enum { PTN_PREC_FP32 = 0, PTN_PREC_BF16X3 = 1, PTN_PREC_FP16X3 = 2 };
 
 /* Contract n_net block-`block` networks with the block's shared path

@@ -1099,6 +1099,13 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
 ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
                             int* err, const GroupTable& grp, int precision,
                             cudaStream_t s) {
+    // Contractions of at most 16 complex terms run in TF32 hi/lo in every mode:
+    // they fill one 128-byte K-block of TF32 exactly where a 16-bit K-block
+    // would be half padding, and their time is the epilogue's (FP16 adds
+    // per-row and per-column scales there); TF32 hi/lo is FP32-accurate.
+    if (precision != PTN_PREC_FP32 && st.n_sum <= 4 &&
+        (precision == PTN_PREC_BF16X3 || precision == PTN_PREC_FP16X3))
+        precision = PTN_PREC_FP32;
     switch (precision) {
         case PTN_PREC_FP32: return run_gemm<FMT_TF32>(st, ctx, n_inst, pack_a, pack_b, err, grp, s);
         case PTN_PREC_BF16X3: return run_gemm<FMT_BF16>(st, ctx, n_inst, pack_a, pack_b, err, grp, s);

@@ -57,8 +57,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # block); a class's roofline traffic per launch is this ratio times its
 # algorithmic bytes per launch in the timed run.  Classes without a capture
 # of the current kernel report null.
-TRAFFIC_RATIO = {"contract_gemm": (12.930 + 6.394) / (12.10 + 6.44),
-                 "gemm_pack": (6.791 + 12.835) / (6.84 + 12.88)}
+TRAFFIC_RATIO = {"contract_gemm": (14.089 + 6.385) / (12.10 + 6.44),
+                 "gemm_pack": (6.792 + 12.834) / (6.84 + 12.88)}
 
 
 def load_peaks():

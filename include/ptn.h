@@ -13,7 +13,10 @@
  *      counts (non-degenerate batched sampling, proportional case, Sec. III-B).
  *
  * Conventions used by every call:
- *   - qubit q is bit q of a bitstring (uint64, n <= 64 qubits);
+ *   - qubit q is bit q of a bitstring; a bitstring (or prefix) of an n-qubit
+ *     plan is W = ceil(n / 64) little-endian uint64 words, bit q being bit
+ *     q % 64 of word q / 64 (n <= 256; W = 1 for n <= 64, a plain uint64);
+ *     arrays of bitstrings hold W consecutive words per entry;
  *   - block j covers qubits [start_j, start_j + b_j), start_0 = 0, ascending;
  *     a block-local outcome x has bit t = qubit start_j + t;
  *   - complex numbers are (re, im) pairs; host inputs are complex128, device
@@ -232,7 +235,8 @@ enum { PTN_PREC_FP32 = 0, PTN_PREC_BF16X3 = 1, PTN_PREC_FP16X3 = 2 };
 /* Contract n_net block-`block` networks with the block's shared path
  * (Sec. III-A) and write their unnormalised marginals (Sec. II-B):
  *   marg_out[n][x] = <psi_i| P_s (x) |x><x| (x) I |psi_i>,  i = net_traj[n],
- *   s = the bits of net_prefix[n] below start_block (higher bits ignored),
+ *   s = the bits of prefix n below start_block (higher bits ignored); net_prefix
+ *   holds W words per network (the plan's bitstring width, see the conventions),
  *   Z_out[n] = sum_x marg_out[n][x] accumulated in FP64.
  * net_traj (device int32, indices into the ptn_traj's distinct error sets) must
  * be non-decreasing.  marg_out: device float [n_net][2^b_block]; Z_out: device
@@ -258,8 +262,9 @@ ptn_status ptn_contract_batch(const ptn_plan* plan, const ptn_traj* traj, int32_
  * children (traj, prefix | x << start, count) to the device arrays child_*
  * (capacity child_cap >= sum_n min(count_n, 2^b); a smaller capacity returns
  * PTN_ERR_INVALID_ARG and writes no child).  Parents must be grouped by
- * trajectory.  Writes the number of children to *n_child (host); synchronises
- * the stream. */
+ * trajectory.  Prefixes here are single uint64 words (start + b <= 64); plans
+ * of more than 64 qubits sample through ptn_sample_shots.  Writes the number
+ * of children to *n_child (host); synchronises the stream. */
 ptn_status ptn_sample_block(const float* marg, int32_t b, int32_t start,
                             const int32_t* parent_traj, const uint64_t* parent_prefix,
                             const int64_t* parent_count, int64_t n_parent,
@@ -363,12 +368,14 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
  * contracted and harvested in sub-batches that fit half the memory cap. */
 
 /* Device views of the result (valid until ptn_shots_destroy) and, per block,
- * the number of networks contracted (host array of n_blocks, may be NULL). */
+ * the number of networks contracted (host array of n_blocks, may be NULL).
+ * bits holds W words per record (the plan's bitstring width). */
 ptn_status ptn_shots_info(const ptn_shots* shots, int64_t* n_out, const int32_t** traj,
                           const uint64_t** bits, const int64_t** count,
                           int64_t* nets_per_block, int32_t cap_blocks);
 
-/* Copy the result into caller-allocated device arrays of n_out entries. */
+/* Copy the result into caller-allocated device arrays of n_out entries
+ * (bits_out: n_out x W words). */
 ptn_status ptn_shots_copy(const ptn_shots* shots, int32_t* traj_out, uint64_t* bits_out, int64_t* count_out,
                           ptn_stream stream);
 

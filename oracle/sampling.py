@@ -123,6 +123,23 @@ def allocate_shots(weights, total, seed, circuit=0):
     return m
 
 
+# Bitstrings are plain integers: uint64 arrays while every block ends below
+# bit 64, arrays of Python integers (dtype object) for wider circuits.
+def _is_wide(blocks):
+    return any(start + b > 64 for start, b in blocks)
+
+
+def _zero_prefix(n, wide):
+    return np.array([0] * n, dtype=object) if wide else np.zeros(n, dtype=np.uint64)
+
+
+def _child_prefix(pre, xs, start, wide):
+    """prefix | (x << start) for every parent prefix and outcome."""
+    if not wide:
+        return pre | (np.asarray(xs).astype(np.uint64) << np.uint64(start))
+    return np.array([int(p) | (int(x) << start) for p, x in zip(pre, xs)], dtype=object)
+
+
 def nbs_proportional(marginal_fn, blocks, seed, n_traj, circuit=0, shots=None,
                      total_shots=None, mult=None):
     """Proportional NBS over all blocks.
@@ -135,7 +152,8 @@ def nbs_proportional(marginal_fn, blocks, seed, n_traj, circuit=0, shots=None,
     Returns (traj, bits, count) of the final level in canonical order, the
     per-block numbers of parents D_j and the allocation m."""
     all_traj = np.arange(n_traj, dtype=np.int64)
-    rows0 = marginal_fn(0, all_traj, np.zeros(n_traj, dtype=np.uint64))
+    wide = _is_wide(blocks)
+    rows0 = marginal_fn(0, all_traj, _zero_prefix(n_traj, wide))
     if shots is None:
         z = np.asarray(rows0, dtype=np.float64).sum(axis=1)
         w = z * (np.ones(n_traj) if mult is None else np.asarray(mult, np.float64))
@@ -144,7 +162,7 @@ def nbs_proportional(marginal_fn, blocks, seed, n_traj, circuit=0, shots=None,
         m = np.asarray(shots, dtype=np.int64)
     keep = m > 0
     traj = all_traj[keep]
-    prefix = np.zeros(len(traj), dtype=np.uint64)
+    prefix = _zero_prefix(len(traj), wide)
     counts = m[keep]
     levels = []
     for j, (start, b) in enumerate(blocks):
@@ -153,7 +171,7 @@ def nbs_proportional(marginal_fn, blocks, seed, n_traj, circuit=0, shots=None,
         r0 = rank_offsets(traj, counts)
         par, xs, cs = sample_block(rows, traj, counts, r0, seed, j, circuit)
         traj = traj[par]
-        prefix = prefix[par] | (xs.astype(np.uint64) << np.uint64(start))
+        prefix = _child_prefix(prefix[par], xs, start, wide)
         counts = cs
     return traj, prefix, counts, levels, m
 
@@ -229,7 +247,8 @@ def harvest_direct(p_rows, traj, prefix, start, n_shots, seed, block, circuit=0)
         out_t.extend([int(traj[n])] * len(nz))
         out_b.extend([int(prefix[n]) | (int(x) << start) for x in nz])
         out_c.extend(hist[nz].tolist())
-    return (np.array(out_t, dtype=np.int64), np.array(out_b, dtype=np.uint64),
+    wide = start + (len(p_rows[0]) - 1).bit_length() > 64 if len(p_rows) else False
+    return (np.array(out_t, dtype=np.int64), np.array(out_b, dtype=object if wide else np.uint64),
             np.array(out_c, dtype=np.int64))
 
 
@@ -245,7 +264,10 @@ def harvest_exhaustive(p_rows, traj, prefix, start, tau):
         Pf = P.astype(np.float64)             # each P_x rounded to FP64, like float(int(P_x))
         keep = np.nonzero((P > 0) & (Pf >= tau * T))[0]
         out_t.append(np.full(len(keep), int(traj[n]), dtype=np.int64))
-        out_b.append(np.uint64(int(prefix[n])) | (keep.astype(np.uint64) << np.uint64(start)))
+        if start + (len(P) - 1).bit_length() > 64:
+            out_b.append(np.array([int(prefix[n]) | (int(x) << start) for x in keep], dtype=object))
+        else:
+            out_b.append(np.uint64(int(prefix[n])) | (keep.astype(np.uint64) << np.uint64(start)))
         out_p.append(Pf[keep] / T)
     if not out_t:
         return np.zeros(0, np.int64), np.zeros(0, np.uint64), np.zeros(0, np.float64)
@@ -261,7 +283,8 @@ def nbs_nonproportional(marginal_fn, blocks, seed, n_traj, branch=1, mode="exhau
     Returns the final records ((traj, bits, count) or (traj, bits, probability))
     and the number of networks contracted per block."""
     traj = np.arange(n_traj, dtype=np.int64)
-    prefix = np.zeros(n_traj, dtype=np.uint64)
+    wide = _is_wide(blocks)
+    prefix = _zero_prefix(n_traj, wide)
     nets = []
     for j, (start, b) in enumerate(blocks[:-1]):
         nets.append(len(traj))
@@ -269,7 +292,7 @@ def nbs_nonproportional(marginal_fn, blocks, seed, n_traj, branch=1, mode="exhau
         counts = np.full(len(traj), int(branch), dtype=np.int64)
         par, xs, _ = sample_block(rows, traj, counts, rank_offsets(traj, counts), seed, j, circuit)
         traj = traj[par]
-        prefix = prefix[par] | (xs.astype(np.uint64) << np.uint64(start))
+        prefix = _child_prefix(prefix[par], xs, start, wide)
     jf = len(blocks) - 1
     start, b = blocks[jf]
     nets.append(len(traj))

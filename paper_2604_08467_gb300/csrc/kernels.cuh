@@ -69,15 +69,30 @@ __host__ __device__ __forceinline__ uint32_t philox_tag(int stream, int circuit,
     return ((uint32_t)(stream & 0xFF) << 24) | ((uint32_t)(circuit & 0xFFFF) << 8) | (uint32_t)(block & 0xFF);
 }
 
+// Bitstrings of n qubits are W = ceil(n / 64) little-endian 64-bit words (bit q
+// of the string is bit q % 64 of word q / 64).
+__device__ __forceinline__ uint64_t bits_get(const uint64_t* w, int q) { return (w[q >> 6] >> (q & 63)) & 1ull; }
+// dst = src with the outcome x of a block placed at bit `start` (those bits of
+// src are zero); x may straddle two words
+__device__ __forceinline__ void bits_put(uint64_t* dst, const uint64_t* src, int n_words, uint64_t x, int start) {
+    const int w0 = start >> 6, sh = start & 63;
+    for (int w = 0; w < n_words; w++) {
+        uint64_t v = src[w];
+        if (w == w0) v |= x << sh;
+        else if (w == w0 + 1 && sh) v |= x >> (64 - sh);
+        dst[w] = v;
+    }
+}
+
 // Per-chunk execution context of a block's step list.
 struct ChunkCtx {
     const float2* vtab;         // merged-gate variant table
     const int32_t* var_ids;     // [traj][n_var_cols] variant of every multi-variant leaf
     int32_t n_var_cols;
-    int32_t pad;
+    int32_t n_words;            // 64-bit words per prefix (ceil(n_qubits / 64))
     const int32_t* chunk_traj;  // local trajectory -> global (index into var_ids)
     const int32_t* net_tl;      // network -> local trajectory
-    const uint64_t* net_prefix; // network -> prefix bits
+    const uint64_t* net_prefix; // network -> prefix bits, n_words little-endian words each
     float2* arena[N_ARENAS];    // CONST, TRAJ, NET (+ ADJ, LGRAD for gradients) arenas
     int64_t arena_inst[N_ARENAS];   // instances of each arena in this chunk
 };
@@ -164,6 +179,14 @@ int64_t radix_hist_elems(int64_t n);
 void launch_radix_pass(const uint64_t* key, const int64_t* val, int64_t n, int shift, int64_t* hist, int64_t* scan_tmp,
                        uint64_t* key_out, int64_t* val_out, cudaStream_t s);
 void launch_run_flags(const uint64_t* key, int64_t n, int64_t* flag, cudaStream_t s);
+// multi-word bitstrings ([n][n_words] records sorted as indices idx)
+void launch_gather_word(const uint64_t* bits, const int64_t* idx, int n_words, int w, int64_t n, uint64_t* key,
+                        cudaStream_t s);
+void launch_run_flags_words(const uint64_t* bits, const int64_t* idx, int n_words, int64_t n, int64_t* flag,
+                            cudaStream_t s);
+void launch_run_sum_words(const uint64_t* bits, const int64_t* count, const int64_t* idx, int n_words,
+                          const int64_t* start, int64_t n_runs, int64_t n, int32_t* traj_out, uint64_t* bits_out,
+                          int64_t* count_out, cudaStream_t s);
 void launch_run_starts(const int64_t* flag, const int64_t* excl, int64_t n, int64_t* start, cudaStream_t s);
 void launch_run_sum(const uint64_t* key, const int64_t* val, const int64_t* start, int64_t n_runs, int64_t n,
                     int32_t* traj_out, uint64_t* bits_out, int64_t* count_out, cudaStream_t s);
@@ -176,7 +199,8 @@ struct HarvestArgs {
     bool direct;                // true: `shots` draws per network; false: threshold `tau`
     double tau;
     const int32_t* traj;        // [n_net]
-    const uint64_t* prefix;     // [n_net]
+    const uint64_t* prefix;     // [n_net][n_words]
+    int n_words;                // 64-bit words per prefix and per output bitstring
     const int64_t* rank0;       // [n_net] first shot rank of each network (direct)
     int64_t shots;
     uint64_t seed;
@@ -219,6 +243,7 @@ int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptr
                          const uint64_t* pprefix, const int64_t* pcount, int64_t n_parent,
                          int64_t n_traj_max, uint64_t seed, int circuit, int block,
                          int32_t* ctraj, uint64_t* cprefix, int64_t* ccount, int64_t child_cap,
-                         const SampleScratch& sc, int64_t* host_tmp, cudaStream_t s, ptn_status* st);
+                         const SampleScratch& sc, int64_t* host_tmp, cudaStream_t s, ptn_status* st,
+                         int n_words = 1);   // prefix words (pprefix / cprefix hold n_words per entry)
 
 }  // namespace ptn

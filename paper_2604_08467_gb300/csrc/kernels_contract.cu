@@ -42,9 +42,9 @@ __device__ __forceinline__ const float2* operand_ptr(const OperandDesc& d, int o
         p = c.arena[d.arena] + d.arena_off * c.arena_inst[d.arena] + oi * d.inst_size;
     }
     if (d.n_slice) {
-        const uint64_t pre = c.net_prefix[net];
+        const uint64_t* pre = c.net_prefix + net * c.n_words;
         int64_t off = 0;
-        for (int s = 0; s < d.n_slice; s++) off += (int64_t)((pre >> d.slice_qubit[s]) & 1ull) * d.slice_stride[s];
+        for (int s = 0; s < d.n_slice; s++) off += (int64_t)bits_get(pre, d.slice_qubit[s]) * d.slice_stride[s];
         p += off;
     }
     return p;

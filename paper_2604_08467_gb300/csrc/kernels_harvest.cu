@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kHThreads) k_harvest_write(const float* __rest
                                                              const unsigned* __restrict__ cnt,
                                                              const int64_t* __restrict__ toff,
                                                              const int32_t* __restrict__ traj,
-                                                             const uint64_t* __restrict__ prefix,
+                                                             const uint64_t* __restrict__ prefix, int n_words,
                                                              int32_t* __restrict__ otraj, uint64_t* __restrict__ obits,
                                                              int64_t* __restrict__ ocount, double* __restrict__ oprob) {
     __shared__ int64_t wtot[kHThreads / 32];
@@ -254,13 +254,14 @@ __global__ void __launch_bounds__(kHThreads) k_harvest_write(const float* __rest
     int64_t pos = toff[blockIdx.x] + inc - c;
     for (int w = 0; w < (int)(threadIdx.x >> 5); w++) pos += wtot[w];
     const int32_t t = traj[net];
-    const uint64_t pre = prefix[net];
+    const uint64_t* pre = prefix + net * n_words;
     while (mask) {
         const int k = __ffs(mask) - 1;
         mask &= mask - 1;
         const int64_t x = x0 + k;
         otraj[pos] = t;
-        obits[pos] = pre | ((uint64_t)x << start);
+        if (n_words == 1) obits[pos] = pre[0] | ((uint64_t)x << start);
+        else bits_put(obits + pos * n_words, pre, n_words, (uint64_t)x, start);
         ocount[pos] = kDirect ? (int64_t)cn[x] : 1;
         oprob[pos] = (double)pop_weight(p[x], s) / Td;
         pos++;
@@ -338,10 +339,10 @@ void run_harvest_write(const HarvestArgs& a, const HarvestScratch& h, int32_t* o
     StatScope sc(K_HARVEST, s, (a.direct ? 8.0 : 4.0) * (double)a.n_net * (double)((int64_t)1 << a.b), 0.0);
     if (a.direct)
         k_harvest_write<true><<<grid, kHThreads, 0, s>>>(a.marg, a.b, a.start, tiles, h.rowmax, h.T, a.tau, h.cnt,
-                                                         h.toff, a.traj, a.prefix, otraj, obits, ocount, oprob);
+                                                         h.toff, a.traj, a.prefix, a.n_words, otraj, obits, ocount, oprob);
     else
         k_harvest_write<false><<<grid, kHThreads, 0, s>>>(a.marg, a.b, a.start, tiles, h.rowmax, h.T, a.tau, h.cnt,
-                                                          h.toff, a.traj, a.prefix, otraj, obits, ocount, oprob);
+                                                          h.toff, a.traj, a.prefix, a.n_words, otraj, obits, ocount, oprob);
 }
 
 }  // namespace ptn

@@ -72,6 +72,42 @@ __global__ void k_run_sum(const uint64_t* __restrict__ key, const int64_t* __res
     }
 }
 
+// Multi-word bitstrings (n_words > 1): records are sorted as indices, one
+// word at a time from the least significant (LSD, every pass stable), so the
+// final order is lexicographic by the whole string.
+__global__ void k_gather_word(const uint64_t* __restrict__ bits, const int64_t* __restrict__ idx, int n_words, int w,
+                              int64_t n, uint64_t* __restrict__ key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        key[i] = bits[idx[i] * n_words + w];
+}
+
+__global__ void k_run_flags_words(const uint64_t* __restrict__ bits, const int64_t* __restrict__ idx, int n_words,
+                                  int64_t n, int64_t* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t f = i == 0;
+        if (i) {
+            const uint64_t *a = bits + idx[i] * n_words, *b = bits + idx[i - 1] * n_words;
+            for (int w = 0; w < n_words; w++) f |= a[w] != b[w];
+        }
+        flag[i] = f;
+    }
+}
+
+// one thread per run: its bitstring and the sum of its counts (in input order)
+__global__ void k_run_sum_words(const uint64_t* __restrict__ bits, const int64_t* __restrict__ count,
+                                const int64_t* __restrict__ idx, int n_words, const int64_t* __restrict__ start,
+                                int64_t n_runs, int64_t n, int32_t* __restrict__ traj_out,
+                                uint64_t* __restrict__ bits_out, int64_t* __restrict__ count_out) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_runs; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = start[r], b = r + 1 < n_runs ? start[r + 1] : n;
+        int64_t c = 0;
+        for (int64_t i = a; i < b; i++) c += count[idx[i]];
+        traj_out[r] = -1;
+        for (int w = 0; w < n_words; w++) bits_out[r * n_words + w] = bits[idx[a] * n_words + w];
+        count_out[r] = c;
+    }
+}
+
 unsigned blocks_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b > 152 * 64) b = 152 * 64;
@@ -106,6 +142,27 @@ void launch_run_sum(const uint64_t* key, const int64_t* val, const int64_t* star
     if (n_runs <= 0) return;
     StatScope sc(K_MISC, s, 16.0 * (double)n + 20.0 * (double)n_runs, 0.0);
     k_run_sum<<<blocks_for(n_runs, 256), 256, 0, s>>>(key, val, start, n_runs, n, traj_out, bits_out, count_out);
+}
+
+void launch_gather_word(const uint64_t* bits, const int64_t* idx, int n_words, int w, int64_t n, uint64_t* key,
+                        cudaStream_t s) {
+    StatScope sc(K_MISC, s, 24.0 * (double)n, 0.0);
+    k_gather_word<<<blocks_for(n, 256), 256, 0, s>>>(bits, idx, n_words, w, n, key);
+}
+
+void launch_run_flags_words(const uint64_t* bits, const int64_t* idx, int n_words, int64_t n, int64_t* flag,
+                            cudaStream_t s) {
+    StatScope sc(K_MISC, s, (16.0 * n_words + 16.0) * (double)n, 0.0);
+    k_run_flags_words<<<blocks_for(n, 256), 256, 0, s>>>(bits, idx, n_words, n, flag);
+}
+
+void launch_run_sum_words(const uint64_t* bits, const int64_t* count, const int64_t* idx, int n_words,
+                          const int64_t* start, int64_t n_runs, int64_t n, int32_t* traj_out, uint64_t* bits_out,
+                          int64_t* count_out, cudaStream_t s) {
+    if (n_runs <= 0) return;
+    StatScope sc(K_MISC, s, 24.0 * (double)n + (12.0 + 8.0 * n_words) * (double)n_runs, 0.0);
+    k_run_sum_words<<<blocks_for(n_runs, 256), 256, 0, s>>>(bits, count, idx, n_words, start, n_runs, n, traj_out,
+                                                           bits_out, count_out);
 }
 
 }  // namespace ptn

@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(kSampWarps * 32) k_sample_parents_warp(
 __global__ void k_emit_children(const int32_t* __restrict__ traj, const uint64_t* __restrict__ prefix,
                                 const int64_t* __restrict__ tmp_off, const int64_t* __restrict__ ndist,
                                 const int64_t* __restrict__ out_off, const int32_t* __restrict__ tmp_x,
-                                const int64_t* __restrict__ tmp_c, int start, int64_t n,
+                                const int64_t* __restrict__ tmp_c, int start, int64_t n, int n_words,
                                 int32_t* __restrict__ ctraj, uint64_t* __restrict__ cprefix,
                                 int64_t* __restrict__ ccount) {
     // one warp per parent
@@ -457,10 +457,19 @@ __global__ void k_emit_children(const int32_t* __restrict__ traj, const uint64_t
     if (w >= n) return;
     const int64_t nd = ndist[w], src = tmp_off[w], dst = out_off[w];
     const int32_t t = traj[w];
-    const uint64_t pre = prefix[w];
+    if (n_words == 1) {
+        const uint64_t pre = prefix[w];
+        for (int64_t k = lane; k < nd; k += 32) {
+            ctraj[dst + k] = t;
+            cprefix[dst + k] = pre | ((uint64_t)tmp_x[src + k] << start);
+            ccount[dst + k] = tmp_c[src + k];
+        }
+        return;
+    }
+    const uint64_t* pre = prefix + w * n_words;
     for (int64_t k = lane; k < nd; k += 32) {
         ctraj[dst + k] = t;
-        cprefix[dst + k] = pre | ((uint64_t)tmp_x[src + k] << start);
+        bits_put(cprefix + (dst + k) * n_words, pre, n_words, (uint64_t)tmp_x[src + k], start);
         ccount[dst + k] = tmp_c[src + k];
     }
 }
@@ -566,7 +575,7 @@ void launch_scale_i64(const int64_t* a, int64_t k, int64_t n, int64_t* out, cuda
 int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptraj, const uint64_t* pprefix,
                          const int64_t* pcount, int64_t n_parent, int64_t n_traj_max, uint64_t seed, int circuit,
                          int block, int32_t* ctraj, uint64_t* cprefix, int64_t* ccount, int64_t child_cap,
-                         const SampleScratch& sc, int64_t* host_tmp, cudaStream_t s, ptn_status* st) {
+                         const SampleScratch& sc, int64_t* host_tmp, cudaStream_t s, ptn_status* st, int n_words) {
     *st = PTN_OK;
     if (n_parent <= 0) return 0;
     cudaMemsetAsync(sc.first, 0xFF, sizeof(int64_t) * n_traj_max, s);
@@ -617,7 +626,7 @@ int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptr
     StatScope st_em(K_EMIT, s, (double)n_child * 32.0, 0.0);
     k_emit_children<<<grid_for(n_parent * 32, 256, 1 << 30), 256, 0, s>>>(ptraj, pprefix, sc.tmp_off, sc.ndist,
                                                                           sc.out_off, sc.tmp_x, sc.tmp_c, start,
-                                                                          n_parent, ctraj, cprefix, ccount);
+                                                                          n_parent, n_words, ctraj, cprefix, ccount);
     return n_child;
 }
 

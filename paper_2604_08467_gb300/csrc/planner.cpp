@@ -1278,7 +1278,7 @@ static void cd_from(const double* p, cd* out, int n) {
 ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* block_sizes,
                       int32_t n_blocks, const ptn_plan_opts* o, ptn_plan* plan) {
     auto t0 = std::chrono::steady_clock::now();
-    if (!c || !c->gates || c->n_qubits < 1 || c->n_qubits > 64 || c->n_gates < 0)
+    if (!c || !c->gates || c->n_qubits < 1 || c->n_qubits > kMaxQubits || c->n_gates < 0)
         return set_error(PTN_ERR_INVALID_ARG, "invalid circuit");
     const int n = c->n_qubits;
     plan->n_qubits = n;

@@ -26,6 +26,7 @@ constexpr int kMaxOut = 40;     // output bits of one contraction step
 constexpr int kMaxSum = 24;     // summed bits of one contraction step
 constexpr int kMaxSlice = 64;   // prefix (projected) bits read by one operand
 constexpr int kMaxBlocks = 64;
+constexpr int kMaxQubits = 256;      // bitstrings of ceil(n / 64) 64-bit words (4 at most)
 constexpr int kMaxSampleBlock = 14;   // blocks sampled by conditional draws (marginal CDF in shared memory)
 constexpr int kMaxFinalBlock = 30;    // last block: harvested from its population vector in global memory
 constexpr int kMaxKraus = 16;

@@ -180,8 +180,9 @@ struct ptn_traj {
 struct ptn_shots {
     int64_t n = 0;
     int32_t n_qubits = 64;
+    int32_t n_words = 1;                 // 64-bit words per bitstring (ceil(n_qubits / 64))
     int32_t* traj = nullptr;
-    uint64_t* bits = nullptr;
+    uint64_t* bits = nullptr;            // [n][n_words]
     int64_t* count = nullptr;
     double* prob = nullptr;              // non-proportional final-block harvest: p(x | prefix) per record
     std::vector<int64_t> nets_per_block;
@@ -412,7 +413,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         ctx.vtab = reinterpret_cast<const float2*>(plan->d_var_table);
         ctx.var_ids = tr->var_ids;
         ctx.n_var_cols = tr->n_var_cols;
-        ctx.pad = 0;
+        ctx.n_words = (plan->n_qubits + 63) / 64;
         ctx.chunk_traj = ws->chunk_traj.as<int32_t>() + c.traj0;
         ctx.net_tl = ws->net_tl.as<int32_t>() + c.net0;
         ctx.net_prefix = d_net_prefix + c.net0;
@@ -751,6 +752,7 @@ ptn_status ptn_tune_tiles(ptn_plan* plan, const ptn_traj* traj, int64_t n_probe,
     if (e) return e;
     cudaStream_t s = (cudaStream_t)stream;
     PlanWorkspace* ws = workspace(plan);
+    const int W = (plan->n_qubits + 63) / 64;
     int32_t* d_traj = nullptr;
     uint64_t* d_prefix = nullptr;
     float* marg = nullptr;
@@ -795,19 +797,19 @@ ptn_status ptn_tune_tiles(ptn_plan* plan, const ptn_traj* traj, int64_t n_probe,
         if (nt < 1) continue;
         const int64_t nn = nt * k;
         std::vector<int32_t> ht(nn);
-        std::vector<uint64_t> hp(nn);
+        std::vector<uint64_t> hp(nn * W, 0);
         for (int64_t t = 0; t < nt; t++)
             for (int64_t q = 0; q < k; q++) {
                 ht[t * k + q] = (int32_t)t;
-                hp[t * k + q] = (uint64_t)q;
+                hp[(t * k + q) * W] = (uint64_t)q;
             }
         if (cudaMalloc(&d_traj, sizeof(int32_t) * nn) != cudaSuccess ||
-            cudaMalloc(&d_prefix, sizeof(uint64_t) * nn) != cudaSuccess ||
+            cudaMalloc(&d_prefix, sizeof(uint64_t) * nn * W) != cudaSuccess ||
             cudaMalloc(&marg, sizeof(float) * nn * ((int64_t)1 << bp.b)) != cudaSuccess ||
             cudaMalloc(&Z, sizeof(double) * nn) != cudaSuccess)
             return fail(set_error(PTN_ERR_OOM, "tile tuning buffers"));
         if (cudaMemcpyAsync(d_traj, ht.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(d_prefix, hp.data(), sizeof(uint64_t) * nn, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            cudaMemcpyAsync(d_prefix, hp.data(), sizeof(uint64_t) * nn * W, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(set_error(PTN_ERR_CUDA, "tile tuning setup"));
         if ((e = contract_level(plan, traj, (int)j, d_traj, d_prefix, nn, marg, Z, 0, PTN_PREC_FP32, s)))
             return fail(e);
@@ -819,6 +821,7 @@ ptn_status ptn_tune_tiles(ptn_plan* plan, const ptn_traj* traj, int64_t n_probe,
         ctx.chunk_traj = ws->chunk_traj.as<int32_t>();
         ctx.net_tl = ws->net_tl.as<int32_t>();
         ctx.net_prefix = d_prefix;
+        ctx.n_words = W;
         for (int a = 0; a < 3; a++) ctx.arena[a] = ws->arena[a].as<float2>();
         ctx.arena_inst[CLS_CONST] = 1;
         ctx.arena_inst[CLS_TRAJ] = nt;
@@ -973,7 +976,7 @@ ptn_status ptn_trajectory_amplitudes(const ptn_plan* cplan, const ptn_traj* traj
         ctx.vtab = reinterpret_cast<const float2*>(plan->d_var_table);
         ctx.var_ids = traj->var_ids;
         ctx.n_var_cols = traj->n_var_cols;
-        ctx.pad = 0;
+        ctx.n_words = 1;
         ctx.chunk_traj = ws->ev_iota.as<int32_t>() + traj0 + t0;
         ctx.net_tl = nullptr;
         ctx.net_prefix = nullptr;
@@ -1094,7 +1097,7 @@ ptn_status ptn_expval_grad(const ptn_plan* cplan, const ptn_traj* traj, const pt
         ctx.vtab = reinterpret_cast<const float2*>(plan->d_var_table);
         ctx.var_ids = traj->var_ids;
         ctx.n_var_cols = traj->n_var_cols;
-        ctx.pad = 0;
+        ctx.n_words = 1;
         ctx.chunk_traj = ws->ev_iota.as<int32_t>() + t0;
         ctx.net_tl = nullptr;
         ctx.net_prefix = nullptr;
@@ -1242,12 +1245,13 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
     ptn_status e = ensure_device(plan);
     if (e) return e;
     PlanWorkspace* ws = workspace(plan);
+    const int W = (plan->n_qubits + 63) / 64;   // words per prefix
     const int64_t E = traj->n_unique;
     const int nblk = (int)plan->blocks.size();
     if ((e = ws->h_small.grow(64))) return e;
     auto grow_level = [&](int k, int64_t cap) -> ptn_status {
         ptn_status g;
-        if ((g = ws->lvl_traj[k].grow(sizeof(int32_t) * cap)) || (g = ws->lvl_prefix[k].grow(sizeof(uint64_t) * cap)) ||
+        if ((g = ws->lvl_traj[k].grow(sizeof(int32_t) * cap)) || (g = ws->lvl_prefix[k].grow(sizeof(uint64_t) * cap * W)) ||
             (g = ws->lvl_count[k].grow(sizeof(int64_t) * cap)))
             return g;
         return PTN_OK;
@@ -1256,7 +1260,7 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
     int64_t n = E;
     if ((e = grow_level(0, E))) return e;
     launch_iota_i32(ws->lvl_traj[0].as<int32_t>(), E, s);
-    PTN_CUDA(cudaMemsetAsync(ws->lvl_prefix[0].p, 0, sizeof(uint64_t) * E, s));
+    PTN_CUDA(cudaMemsetAsync(ws->lvl_prefix[0].p, 0, sizeof(uint64_t) * E * W, s));
     std::vector<int64_t> nets;
     for (int j = 0; j + 1 < nblk && n > 0; j++) {
         const BlockPlan& bp = plan->blocks[j];
@@ -1276,7 +1280,7 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
                                             ws->lvl_prefix[cur].as<uint64_t>(), ws->lvl_count[cur].as<int64_t>(), n, E,
                                             o->seed, o->circuit_id, j, ws->lvl_traj[1 - cur].as<int32_t>(),
                                             ws->lvl_prefix[1 - cur].as<uint64_t>(), ws->lvl_count[1 - cur].as<int64_t>(),
-                                            child_cap, sc, ws->h_small.as<int64_t>(), s, &st);
+                                            child_cap, sc, ws->h_small.as<int64_t>(), s, &st, W);
         if (st != PTN_OK) return st;
         nets.push_back(n);
         cur = 1 - cur;
@@ -1336,7 +1340,7 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
     int64_t total = 0;
     for (int64_t a = 0; a < n; a += sub) {
         const int64_t m = std::min(sub, n - a);
-        e = contract_level(plan, traj, jf, ftraj + a, fprefix + a, m, ws->marg.as<float>(), ws->Z.as<double>(),
+        e = contract_level(plan, traj, jf, ftraj + a, fprefix + a * W, m, ws->marg.as<float>(), ws->Z.as<double>(),
                            o->max_traj_per_chunk, o->precision, s, o->use_graphs != 0);
         if (e) {
             free_parts();
@@ -1350,7 +1354,8 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
         ha.direct = direct;
         ha.tau = o->threshold;
         ha.traj = ftraj + a;
-        ha.prefix = fprefix + a;
+        ha.prefix = fprefix + a * W;
+        ha.n_words = W;
         ha.rank0 = direct ? ws->h_rank0.as<int64_t>() + a : nullptr;
         ha.shots = o->final_shots;
         ha.seed = o->seed;
@@ -1366,7 +1371,7 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
         Part p{nullptr, nullptr, nullptr, nullptr, nr};
         cudaError_t ce;
         if ((ce = cudaMalloc(&p.t, sizeof(int32_t) * nr)) != cudaSuccess ||
-            (ce = cudaMalloc(&p.b, sizeof(uint64_t) * nr)) != cudaSuccess ||
+            (ce = cudaMalloc(&p.b, sizeof(uint64_t) * nr * W)) != cudaSuccess ||
             (ce = cudaMalloc(&p.c, sizeof(int64_t) * nr)) != cudaSuccess ||
             (ce = cudaMalloc(&p.p, sizeof(double) * nr)) != cudaSuccess) {
             parts.push_back(p);
@@ -1380,6 +1385,7 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
     ptn_shots* r = new ptn_shots();
     r->n = total;
     r->n_qubits = plan->n_qubits;
+    r->n_words = W;
     r->nets_per_block = nets;
     const size_t mcap = std::max<int64_t>(total, 1);
     cudaError_t ce;
@@ -1390,7 +1396,7 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
         r->prob = parts[0].p;
         parts.clear();
     } else if ((ce = cudaMalloc(&r->traj, sizeof(int32_t) * mcap)) != cudaSuccess ||
-               (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * mcap)) != cudaSuccess ||
+               (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * mcap * W)) != cudaSuccess ||
                (ce = cudaMalloc(&r->count, sizeof(int64_t) * mcap)) != cudaSuccess ||
                (ce = cudaMalloc(&r->prob, sizeof(double) * mcap)) != cudaSuccess) {
         free_parts();
@@ -1400,7 +1406,7 @@ static ptn_status sample_nonprop(const ptn_plan* plan, const ptn_traj* traj, con
         int64_t o_ = 0;
         for (Part& p : parts) {
             cudaMemcpyAsync(r->traj + o_, p.t, sizeof(int32_t) * p.n, cudaMemcpyDeviceToDevice, s);
-            cudaMemcpyAsync(r->bits + o_, p.b, sizeof(uint64_t) * p.n, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(r->bits + o_ * W, p.b, sizeof(uint64_t) * p.n * W, cudaMemcpyDeviceToDevice, s);
             cudaMemcpyAsync(r->count + o_, p.c, sizeof(int64_t) * p.n, cudaMemcpyDeviceToDevice, s);
             cudaMemcpyAsync(r->prob + o_, p.p, sizeof(double) * p.n, cudaMemcpyDeviceToDevice, s);
             o_ += p.n;
@@ -1446,10 +1452,11 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     if (e) return e;
     cudaStream_t s = (cudaStream_t)stream;
     PlanWorkspace* ws = workspace(plan);
+    const int W = (plan->n_qubits + 63) / 64;   // words per prefix
     const int64_t E = traj->n_unique;
     const int64_t lvl_cap = std::max(E, total_cap);
     for (int k = 0; k < 2; k++) {
-        if ((e = ws->lvl_traj[k].grow(sizeof(int32_t) * lvl_cap)) || (e = ws->lvl_prefix[k].grow(sizeof(uint64_t) * lvl_cap)) ||
+        if ((e = ws->lvl_traj[k].grow(sizeof(int32_t) * lvl_cap)) || (e = ws->lvl_prefix[k].grow(sizeof(uint64_t) * lvl_cap * W)) ||
             (e = ws->lvl_count[k].grow(sizeof(int64_t) * lvl_cap)))
             return e;
     }
@@ -1457,7 +1464,7 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     int cur = 0;
     int64_t n = E;
     launch_iota_i32(ws->lvl_traj[0].as<int32_t>(), E, s);
-    PTN_CUDA(cudaMemsetAsync(ws->lvl_prefix[0].p, 0, sizeof(uint64_t) * E, s));
+    PTN_CUDA(cudaMemsetAsync(ws->lvl_prefix[0].p, 0, sizeof(uint64_t) * E * W, s));
     if (o->mode == PTN_PROPORTIONAL_FIXED) launch_scale_i64(traj->mult, o->shots_per_traj, E, ws->lvl_count[0].as<int64_t>(), s);
     std::vector<int64_t> nets;
     for (size_t j = 0; j < plan->blocks.size() && n > 0; j++) {
@@ -1481,7 +1488,7 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
                                       ws->lvl_prefix[cur].as<uint64_t>(), ws->lvl_count[cur].as<int64_t>(), n, E,
                                       o->seed, o->circuit_id, (int)j, ws->lvl_traj[1 - cur].as<int32_t>(),
                                       ws->lvl_prefix[1 - cur].as<uint64_t>(), ws->lvl_count[1 - cur].as<int64_t>(),
-                                      lvl_cap, sc, ws->h_small.as<int64_t>(), s, &st);
+                                      lvl_cap, sc, ws->h_small.as<int64_t>(), s, &st, W);
         if (st != PTN_OK) return st;
         nets.push_back(n);
         cur = 1 - cur;
@@ -1490,10 +1497,11 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     ptn_shots* r = new ptn_shots();
     r->n = n;
     r->n_qubits = plan->n_qubits;
+    r->n_words = W;
     r->nets_per_block = nets;
     size_t m = std::max<int64_t>(n, 1);
     cudaError_t ce;
-    if ((ce = cudaMalloc(&r->traj, sizeof(int32_t) * m)) != cudaSuccess || (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * m)) != cudaSuccess ||
+    if ((ce = cudaMalloc(&r->traj, sizeof(int32_t) * m)) != cudaSuccess || (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * m * W)) != cudaSuccess ||
         (ce = cudaMalloc(&r->count, sizeof(int64_t) * m)) != cudaSuccess) {
         cudaFree(r->traj);
         cudaFree(r->bits);
@@ -1503,7 +1511,7 @@ ptn_status ptn_sample_shots(const ptn_plan* plan, const ptn_traj* traj, const pt
     }
     if (n > 0) {
         PTN_CUDA(cudaMemcpyAsync(r->traj, ws->lvl_traj[cur].p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-        PTN_CUDA(cudaMemcpyAsync(r->bits, ws->lvl_prefix[cur].p, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+        PTN_CUDA(cudaMemcpyAsync(r->bits, ws->lvl_prefix[cur].p, sizeof(uint64_t) * n * W, cudaMemcpyDeviceToDevice, s));
         PTN_CUDA(cudaMemcpyAsync(r->count, ws->lvl_count[cur].p, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s));
     }
     PTN_CUDA(cudaGetLastError());
@@ -1666,7 +1674,9 @@ ptn_status ptn_shots_merge(const ptn_shots* in, ptn_shots** out, ptn_stream stre
     const int64_t n = in->n;
     ptn_shots* r = new ptn_shots();
     r->n_qubits = in->n_qubits;
+    r->n_words = in->n_words;
     r->nets_per_block = in->nets_per_block;
+    const int W = in->n_words;
     int64_t n_runs = 0;
     std::vector<void*> tmp;
     auto fail = [&](ptn_status st) {
@@ -1694,15 +1704,30 @@ ptn_status ptn_shots_merge(const ptn_shots* in, ptn_shots** out, ptn_stream stre
         int64_t* start = static_cast<int64_t*>(alloc(8 * n));
         if (!k[0] || !k[1] || !v[0] || !v[1] || !hist || !scan || !flag || !excl || !start)
             return fail(set_error(PTN_ERR_OOM, "merge scratch"));
-        cudaError_t ce = cudaMemcpyAsync(k[0], in->bits, 8 * n, cudaMemcpyDeviceToDevice, s);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(v[0], in->count, 8 * n, cudaMemcpyDeviceToDevice, s);
-        if (ce != cudaSuccess) return fail(set_error(PTN_ERR_CUDA, "merge copy: %s", cudaGetErrorString(ce)));
+        cudaError_t ce = cudaSuccess;
         int cur = 0;
-        for (int shift = 0; shift < in->n_qubits; shift += 8) {
-            launch_radix_pass(k[cur], v[cur], n, shift, hist, scan, k[1 - cur], v[1 - cur], s);
-            cur = 1 - cur;
+        if (W == 1) {
+            ce = cudaMemcpyAsync(k[0], in->bits, 8 * n, cudaMemcpyDeviceToDevice, s);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(v[0], in->count, 8 * n, cudaMemcpyDeviceToDevice, s);
+            if (ce != cudaSuccess) return fail(set_error(PTN_ERR_CUDA, "merge copy: %s", cudaGetErrorString(ce)));
+            for (int shift = 0; shift < in->n_qubits; shift += 8) {
+                launch_radix_pass(k[cur], v[cur], n, shift, hist, scan, k[1 - cur], v[1 - cur], s);
+                cur = 1 - cur;
+            }
+            launch_run_flags(k[cur], n, flag, s);
+        } else {
+            // record indices sorted word by word, least significant word first
+            launch_iota_i64(v[0], n, s);
+            for (int w = 0; w < W; w++) {
+                launch_gather_word(in->bits, v[cur], W, w, n, k[cur], s);
+                const int top = std::min(64, in->n_qubits - 64 * w);
+                for (int shift = 0; shift < top; shift += 8) {
+                    launch_radix_pass(k[cur], v[cur], n, shift, hist, scan, k[1 - cur], v[1 - cur], s);
+                    cur = 1 - cur;
+                }
+            }
+            launch_run_flags_words(in->bits, v[cur], W, n, flag, s);
         }
-        launch_run_flags(k[cur], n, flag, s);
         launch_exclusive_scan(flag, excl, n, scan, s);
         launch_run_starts(flag, excl, n, start, s);
         int64_t last[2];
@@ -1713,10 +1738,11 @@ ptn_status ptn_shots_merge(const ptn_shots* in, ptn_shots** out, ptn_stream stre
         n_runs = last[0] + last[1];
         size_t m = std::max<int64_t>(n_runs, 1);
         if ((ce = cudaMalloc(&r->traj, sizeof(int32_t) * m)) != cudaSuccess ||
-            (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * m)) != cudaSuccess ||
+            (ce = cudaMalloc(&r->bits, sizeof(uint64_t) * m * W)) != cudaSuccess ||
             (ce = cudaMalloc(&r->count, sizeof(int64_t) * m)) != cudaSuccess)
             return fail(set_error(PTN_ERR_OOM, "merge result: %s", cudaGetErrorString(ce)));
-        launch_run_sum(k[cur], v[cur], start, n_runs, n, r->traj, r->bits, r->count, s);
+        if (W == 1) launch_run_sum(k[cur], v[cur], start, n_runs, n, r->traj, r->bits, r->count, s);
+        else launch_run_sum_words(in->bits, in->count, v[cur], W, start, n_runs, n, r->traj, r->bits, r->count, s);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(set_error(PTN_ERR_CUDA, "merge: %s", cudaGetErrorString(ce)));
     } else {
@@ -1749,7 +1775,8 @@ ptn_status ptn_shots_copy(const ptn_shots* r, int32_t* traj_out, uint64_t* bits_
     cudaStream_t s = (cudaStream_t)stream;
     if (r->n > 0) {
         if (traj_out) PTN_CUDA(cudaMemcpyAsync(traj_out, r->traj, sizeof(int32_t) * r->n, cudaMemcpyDeviceToDevice, s));
-        if (bits_out) PTN_CUDA(cudaMemcpyAsync(bits_out, r->bits, sizeof(uint64_t) * r->n, cudaMemcpyDeviceToDevice, s));
+        if (bits_out)
+            PTN_CUDA(cudaMemcpyAsync(bits_out, r->bits, sizeof(uint64_t) * r->n * r->n_words, cudaMemcpyDeviceToDevice, s));
         if (count_out) PTN_CUDA(cudaMemcpyAsync(count_out, r->count, sizeof(int64_t) * r->n, cudaMemcpyDeviceToDevice, s));
     }
     return PTN_OK;

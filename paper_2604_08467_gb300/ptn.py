@@ -272,9 +272,37 @@ class Traj:
             self.handle = None
 
 
+def words_of(n_qubits):
+    """64-bit words per bitstring of an n-qubit plan."""
+    return (int(n_qubits) + 63) // 64
+
+
+def bits_to_int(words):
+    """The Python integer of one bitstring given as its little-endian words."""
+    w = [int(x) & 0xFFFFFFFFFFFFFFFF for x in (words if hasattr(words, "__len__") else [words])]
+    return sum(x << (64 * i) for i, x in enumerate(w))
+
+
+def int_to_words(values, n_words):
+    """int64 array [len(values), n_words] of the little-endian words of each
+    Python integer (for prefixes of wide plans)."""
+    import numpy as np
+    out = np.zeros((len(values), n_words), dtype=np.uint64)
+    for i, v in enumerate(values):
+        v = int(v)
+        for w in range(n_words):
+            out[i, w] = (v >> (64 * w)) & 0xFFFFFFFFFFFFFFFF
+    return out.view(np.int64)
+
+
 class Shots:
-    def __init__(self, handle, n_blocks):
+    """A sampling result.  Bitstrings are n_words = ceil(n_qubits / 64)
+    little-endian uint64 words each (held as int64); to_torch gives them as
+    [n] for one word and [n, n_words] otherwise."""
+
+    def __init__(self, handle, n_blocks, n_words=1):
         self.handle = handle
+        self.n_words = int(n_words)
         n = C.c_int64(0)
         nets = (C.c_int64 * max(n_blocks, 1))()
         _check(lib().ptn_shots_info(handle, C.byref(n), None, None, None, nets, n_blocks))
@@ -285,7 +313,7 @@ class Shots:
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         t = torch.empty(self.n, dtype=torch.int32, device=dev)
-        b = torch.empty(self.n, dtype=torch.int64, device=dev)
+        b = torch.empty((self.n, self.n_words) if self.n_words > 1 else (self.n,), dtype=torch.int64, device=dev)
         c = torch.empty(self.n, dtype=torch.int64, device=dev)
         _check(lib().ptn_shots_copy(self.handle, _ptr(t), _ptr(b), _ptr(c), _stream(stream)))
         return t, b, c
@@ -341,6 +369,11 @@ def ptn_presample_range(plan, seed, traj0, n_traj, circuit_id=0, stream=None):
 def ptn_contract_batch(plan, traj, block, net_traj, net_prefix, marg_out, Z_out, precision=PTN_PREC_FP32,
                        stream=None):
     n = int(net_traj.numel())
+    w = words_of(plan.n_qubits)
+    if int(net_prefix.numel()) < n * w:
+        raise ValueError(f"net_prefix needs {w} words per network ({n * w} entries)")
+    if int(marg_out.numel()) < n << plan.block_sizes[block] or int(Z_out.numel()) < n:
+        raise ValueError("marg_out / Z_out shorter than n_net networks need")
     _check(lib().ptn_contract_batch(plan.handle, traj.handle, block, _ptr(net_traj), _ptr(net_prefix), n,
                                     precision, _ptr(marg_out), _ptr(Z_out), _stream(stream)))
 
@@ -394,7 +427,7 @@ def ptn_sample_shots(plan, traj, seed, shots_per_traj=None, total_shots=None, ci
     o.use_graphs = use_graphs
     h = C.c_void_p()
     _check(lib().ptn_sample_shots(plan.handle, traj.handle, C.byref(o), C.byref(h), _stream(stream)))
-    return Shots(h, len(plan.block_sizes))
+    return Shots(h, len(plan.block_sizes), words_of(plan.n_qubits))
 
 
 def _sample_opts(seed, shots_per_traj=None, total_shots=None, circuit_id=0, precision=PTN_PREC_FP32,
@@ -414,7 +447,7 @@ def ptn_sample_nonprop(plan, traj, seed, mode="exhaustive", branch_shots=1, fina
                         int(final_shots), float(threshold))
     h = C.c_void_p()
     _check(lib().ptn_sample_shots(plan.handle, traj.handle, C.byref(o), C.byref(h), _stream(stream)))
-    return Shots(h, len(plan.block_sizes))
+    return Shots(h, len(plan.block_sizes), words_of(plan.n_qubits))
 
 
 def ptn_sample_shots_batch(items, n_workers=4, keep_workspaces=False, mem_budget_bytes=0.0, max_est_seconds=0.0,
@@ -438,7 +471,8 @@ def ptn_sample_shots_batch(items, n_workers=4, keep_workspaces=False, mem_budget
     res = []
     for i, it in enumerate(items):
         if sts[i] == PTN_OK:
-            res.append((PTN_OK, Shots(C.c_void_p(outs[i]), len(it["plan"].block_sizes))))
+            res.append((PTN_OK, Shots(C.c_void_p(outs[i]), len(it["plan"].block_sizes),
+                                      words_of(it["plan"].n_qubits))))
         else:
             res.append((sts[i], None))
     return res
@@ -477,7 +511,7 @@ def ptn_shots_merge(shots, n_blocks, stream=None):
     bitstring, increasing bits, traj = -1."""
     h = C.c_void_p()
     _check(lib().ptn_shots_merge(shots.handle, C.byref(h), _stream(stream)))
-    return Shots(h, n_blocks)
+    return Shots(h, n_blocks, shots.n_words)
 
 
 def ptn_tune_block_sizes(circ, candidates, probe_traj, probe_shots, seed=1, hypersamples=16, split_gates=1,

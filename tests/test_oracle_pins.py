@@ -643,3 +643,34 @@ def test_merged_two_qubit_pauli_product():
         # K_k / sqrt(q_k) is the bare Pauli product (K_k = sqrt(q_k) P (x) Q)
         m = pts.merged_gate(circ, 0, np.array([k]))
         np.testing.assert_allclose(m, np.kron(P[k // 4], P[k % 4]) @ g.matrix, atol=1e-13)
+
+
+def test_wide_bitstrings_shift_block_outcomes():
+    """Bitstrings past bit 63 (circuits of more than 64 qubits) are Python
+    integers.  With marginals that do not depend on the prefix, moving blocks
+    2 and 3 from bits 4 and 8 to bits 64 and 130 moves their outcomes there
+    and changes nothing else: the draws depend on trajectory, shot rank and
+    block index only, and the canonical order is by block outcomes."""
+    from oracle import sampling
+    rng = np.random.default_rng(5)
+    rows = [rng.random((1, 16)) + 0.05 for _ in range(3)]
+
+    def mf(j, traj, prefix):
+        return np.repeat(rows[j], len(traj), axis=0)
+
+    narrow, wide = [(0, 4), (4, 4), (8, 4)], [(0, 4), (64, 4), (130, 4)]
+
+    def widen(bits):
+        b = int(bits)
+        return (b & 15) | (((b >> 4) & 15) << 64) | (((b >> 8) & 15) << 130)
+
+    tn, bn, cn, ln, _ = sampling.nbs_proportional(mf, narrow, 77, 6, shots=[40, 0, 13, 7, 25, 3])
+    tw, bw, cw, lw, _ = sampling.nbs_proportional(mf, wide, 77, 6, shots=[40, 0, 13, 7, 25, 3])
+    assert bw.dtype == object and any(int(x) >> 64 for x in bw)
+    assert np.array_equal(tn, tw) and np.array_equal(cn, cw) and ln == lw
+    assert [widen(x) for x in bn] == [int(x) for x in bw]
+    for mode, kw in (("exhaustive", dict(tau=0.02)), ("direct", dict(final_shots=50))):
+        (rt, rb, rv), nn = sampling.nbs_nonproportional(mf, narrow, 9, 5, branch=2, mode=mode, **kw)
+        (wt, wb, wv), nw = sampling.nbs_nonproportional(mf, wide, 9, 5, branch=2, mode=mode, **kw)
+        assert nn == nw and np.array_equal(rt, wt) and np.array_equal(rv, wv)
+        assert [widen(x) for x in rb] == [int(x) for x in wb]

@@ -288,13 +288,13 @@ def measure_tc_peaks(torch, sustain_s=4.0):
 
 # ------------------------------------------------------------- our arm ----
 
-def run_nonprop(ptn, shard, torch, rank, n_traj, hypersamples, steps=3, warmup=1):
+def run_nonprop(ptn, shard, torch, rank, n_traj, hypersamples, n=50, n_gates=200, steps=3, warmup=1):
     """Non-proportional NBS (Sec. III-B) on the paper's own circuit family
-    (Sec. IV-B): a 50-qubit, 200-gate random circuit, blocks 10/10/2 with one
-    shot per prefix and a 28-qubit final block harvested exhaustively
-    (p(x | prefix) >= 1e-6), FP16x3.  Metric: unique labelled bitstrings
-    (distinct (trajectory, bitstring) records) per second."""
-    cfg = W.config_paper(50, 200)
+    (Sec. IV-B): an n-qubit random circuit of n_gates gates, blocks of 10 with
+    one shot per prefix and a final block of up to 28 qubits harvested
+    exhaustively (p(x | prefix) >= 1e-6), FP16x3.  Metric: unique labelled
+    bitstrings (distinct (trajectory, bitstring) records) per second."""
+    cfg = W.config_paper(n, n_gates)
     plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=hypersamples, est_traj=n_traj,
                              est_shots=n_traj)
     stream = torch.cuda.current_stream()
@@ -321,6 +321,63 @@ def run_nonprop(ptn, shard, torch, rank, n_traj, hypersamples, steps=3, warmup=1
             "value": recs / t, "unit": "unique bitstrings/s", "ms_per_step": 1e3 * t / len(times),
             "steps": len(times), "records_per_step": recs // len(times), "nets_per_block": nets,
             "contractions_per_s": float(sum(nets or [0])) * len(times) / t}
+
+
+PRECISION_IDS = {"fp32": "PTN_PREC_FP32", "fp16x3": "PTN_PREC_FP16X3", "bf16x3": "PTN_PREC_BF16X3"}
+
+
+def run_block_contraction(ptn, torch, hypersamples, b, batches, precisions, n=100, n_gates=600, reps=5):
+    """Contraction time of one block of b qubits (the paper's contraction time
+    per batch, Sec. V-B) on its 100-qubit, 600-gate family: every block of b
+    qubits of a plan with uniform blocks of b (the remainder last) contracted for
+    `batch` networks of distinct trajectories with random prefixes; mean
+    CUDA-event time per block over the plan's full-size blocks.  Metric:
+    contracted qubits per second, b / (time per network).  A block of more
+    than 14 qubits can only be the final one (the conditional sampling of a
+    non-final block holds 2^b entries in shared memory), so such a b is timed
+    as the final block behind blocks of 10."""
+    circ = W.config_paper(n, n_gates)["circuit"]
+    rng = np.random.default_rng(n_gates)
+    if b <= 14:
+        bs = [b] * (n // b) + ([n % b] if n % b else [])
+    else:   # blocks of more than 14 qubits are sampled only as the final block
+        bs = [10] * ((n - b) // 10) + ([(n - b) % 10] if (n - b) % 10 else []) + [b]
+    plan = ptn.ptn_plan_path(circ, bs, hypersamples=hypersamples, est_traj=max(batches), est_shots=max(batches))
+    nw = ptn.words_of(n)
+    stream = torch.cuda.current_stream()
+    out = []
+    for batch in batches:
+        tr = ptn.ptn_presample_trajectories(plan, 4242, batch)
+        nt = torch.arange(batch, dtype=torch.int32, device="cuda")
+        marg = torch.empty((batch, 1 << b), dtype=torch.float32, device="cuda")
+        Z = torch.empty(batch, dtype=torch.float64, device="cuda")
+        for prec in precisions:
+            pid = getattr(ptn, PRECISION_IDS[prec])
+            per_block = []
+            for j, (start, bj) in enumerate(plan.blocks):
+                if bj != b:
+                    continue
+                pre = [int.from_bytes(rng.bytes(8 * nw), "little") & ((1 << start) - 1) for _ in range(batch)]
+                npre = torch.from_numpy(ptn.int_to_words(pre, nw).copy()).cuda()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(reps + 2)]
+                torch.cuda.synchronize()
+                for a, e in ev:
+                    a.record(stream)
+                    ptn.ptn_contract_batch(plan, tr, j, nt, npre, marg, Z, precision=pid)
+                    e.record(stream)
+                torch.cuda.synchronize()
+                per_block.append(float(np.mean([a.elapsed_time(e) for a, e in ev[2:]])))
+            ms = float(np.mean(per_block))
+            out.append({"b": b, "networks": batch, "precision": prec, "ms_per_block": ms,
+                        "ms_per_block_min_max": [min(per_block), max(per_block)], "blocks_timed": len(per_block),
+                        "us_per_network": 1e3 * ms / batch, "value": b * batch / (ms / 1e3),
+                        "unit": "contracted qubits/s"})
+        del tr, marg, Z
+    return {"workload": f"paper_n{n}_g{n_gates}: paper's random family, blocks {bs}, each block contracted for "
+                        "a batch of networks (distinct trajectories, random prefixes), CUDA events, "
+                        f"{reps} timed of {reps + 2} calls per block",
+            "lines": out}
 
 
 MIXED_MAX_EST_S = 15.0   # per-circuit time budget of the mixed batch (modelled seconds)
@@ -398,7 +455,11 @@ def main():
     ap.add_argument("--mixed-batch", type=int, default=4, metavar="WORKERS",
                     help="also run the 64-circuit mixed batch with this many concurrent circuits (0: skip)")
     ap.add_argument("--nonprop-traj", type=int, default=256,
-                    help="trajectories of the non-proportional sub-line on the paper's 50-qubit family (0: skip)")
+                    help="trajectories of the non-proportional sub-lines on the paper's family (0: skip)")
+    ap.add_argument("--nonprop-sizes", default="50x200,100x600,200x1000",
+                    help="qubits x gates of the non-proportional sub-lines")
+    ap.add_argument("--block-b", default="10,24",
+                    help="block sizes of the per-block contraction sub-line at 100 qubits, 600 gates ('': skip)")
     ap.add_argument("--no-precision-lines", action="store_true",
                     help="skip the timed steps of the other tensor-core operand splits")
     ap.add_argument("--no-peaks", action="store_true",
@@ -603,7 +664,16 @@ def main():
 
     # ---- mixed-circuit batch: 64 circuits of 20-40 qubits, 1D or 6x5 grid,
     # depth 8-16, 16-8192 trajectories, 1e3-1e6 shots (the batching workload)
-    nonprop = run_nonprop(ptn, shard, torch, rank, args.nonprop_traj, args.hypersamples) if args.nonprop_traj > 0 else None
+    nonprop = None
+    if args.nonprop_traj > 0:
+        nonprop = [run_nonprop(ptn, shard, torch, rank, args.nonprop_traj, args.hypersamples, n=int(a), n_gates=int(g))
+                   for a, g in (x.split("x") for x in args.nonprop_sizes.split(",") if x)]
+    block_contraction = None
+    if args.block_b:
+        block_contraction = [run_block_contraction(ptn, torch, args.hypersamples, int(b),
+                                                   [1, 256] if int(b) <= 16 else [1],
+                                                   ["fp32", "fp16x3"] if int(b) <= 16 else ["fp32"])
+                             for b in args.block_b.split(",") if b]
 
     mixed = None
     if args.mixed_batch > 0:
@@ -673,7 +743,7 @@ def main():
                                         f"({args.precision}), fp64 CDF / log-probabilities",
                            "error_vs_fp64": PRECISIONS[args.precision][1]},
                 "e2e": e2e, "plain_path": plain, "other_precisions": other_prec, "expval_grad": grad,
-                "mixed_batch": mixed, "nonprop": nonprop, "roofline": roof, "cpu_baseline": cpu,
+                "mixed_batch": mixed, "nonprop": nonprop, "block_contraction": block_contraction, "roofline": roof, "cpu_baseline": cpu,
                 "contractions_per_s": float(sum(nets or [0])) * world / t_step,
                 "distinct_records_per_s": float(n_records) * world / t_step,
                 "gpu_launches": int(launches), "clocks": clocks, "tc_peaks_measured": tc_peaks,

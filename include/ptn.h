@@ -81,7 +81,7 @@ typedef struct {
 } ptn_gate;
 
 typedef struct {
-    int32_t n_qubits;          /* 1 .. 64 */
+    int32_t n_qubits;          /* 1 .. 256 */
     int32_t n_gates;
     const ptn_gate* gates;     /* host, n_gates entries, in circuit order */
 } ptn_circuit;
@@ -141,6 +141,13 @@ typedef struct {
     int32_t  fuse_max;         /* longest run of consecutive small trajectory-level steps (the
                                   gate-level start of a path) executed by one launch, one CTA per
                                   trajectory walking the run; 0 -> 1024, 1 -> one launch per step */
+    int32_t  cache_intermediates; /* 1: intermediate caching across error sets (Sec. VI): every
+                                  trajectory-level step outside the fused runs (at least 4096
+                                  multiply-adds and 128 outputs per trajectory) is computed once
+                                  per group of a
+                                  chunk's trajectories that agree on every variant column of its
+                                  subtree, and read through a per-chunk representative table;
+                                  results are bit-identical to 0 (no caching) */
 } ptn_plan_opts;
 
 /* Network forms of the block marginals (Sec. II-B; the ket-only form gives the

@@ -24,7 +24,8 @@ CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler",
 
 CPP_SOURCES = ["planner.cpp"]
 CU_SOURCES = ["runtime.cu", "kernels_contract.cu", "kernels_sample.cu", "kernels_gemm.cu", "stats.cu", "noalloc.cu",
-              "kernels_expval.cu", "kernels_merge.cu", "kernels_harvest.cu", "tune.cu"]
+              "kernels_expval.cu", "kernels_merge.cu", "kernels_harvest.cu", "tune.cu",
+              "kernels_cache.cu"]
 
 
 def _sources():

@@ -95,7 +95,47 @@ struct ChunkCtx {
     const uint64_t* net_prefix; // network -> prefix bits, n_words little-endian words each
     float2* arena[N_ARENAS];    // CONST, TRAJ, NET (+ ADJ, LGRAD for gradients) arenas
     int64_t arena_inst[N_ARENAS];   // instances of each arena in this chunk
+    // intermediate caching (StepDesc.cache / OperandDesc.cache), null when off:
+    // cache_rep[k * cache_n + tl] the representative of local trajectory tl for
+    // cache slot k (the first trajectory of the chunk with the same variants on
+    // the slot's columns), cache_list[k * cache_n + i] the i-th representative
+    const int32_t* cache_rep = nullptr;
+    const int32_t* cache_list = nullptr;
+    int64_t cache_n = 0;
 };
+
+// Instance of a TRAJ-class buffer that local trajectory tl reads.
+__device__ __forceinline__ int64_t rep_inst(const OperandDesc& d, int64_t tl, const ChunkCtx& c) {
+    return (d.cache > 0 && c.cache_rep) ? (int64_t)c.cache_rep[(int64_t)(d.cache - 1) * c.cache_n + tl] : tl;
+}
+// Trajectory computed by the i-th instance of a launch of a step with cache id `cache`.
+__device__ __forceinline__ int64_t step_inst(int32_t cache, int64_t i, const ChunkCtx& c) {
+    return (cache > 0 && c.cache_list) ? (int64_t)c.cache_list[(int64_t)(cache - 1) * c.cache_n + i] : i;
+}
+
+// ---- intermediate caching (kernels_cache.cu)
+// Per trajectory (of a ptn_traj) its non-zero variant entries, in column
+// order: cnt holds n + 1 int64 (exclusive-scanned into the row pointers).
+void launch_nz_count(const int32_t* var_ids, int64_t n, int32_t n_cols, int64_t* cnt, cudaStream_t s);
+void launch_nz_fill(const int32_t* var_ids, int64_t n, int32_t n_cols, const int64_t* ptr, int32_t* col,
+                    int32_t* val, cudaStream_t s);
+struct CacheArgs {
+    int32_t n_cache = 0, words = 0;   // cache slots of the block; 32-bit words per column bitmap
+    int64_t n = 0;                    // trajectories of the chunk
+    int64_t P = 0;                    // hash-table entries per slot (a power of two >= 2n)
+    const int32_t* chunk_traj = nullptr;   // local -> global trajectory
+    const int64_t* nz_ptr = nullptr;       // per global trajectory: its non-zero variant entries
+    const int32_t* nz_col = nullptr;
+    const int32_t* nz_val = nullptr;
+    const uint32_t* bits = nullptr;        // [n_cache][words] column bitmaps
+    uint64_t* h = nullptr;                 // [n_cache][n][2] key halves
+    unsigned long long* keys = nullptr;    // [n_cache][P]
+    int32_t* first = nullptr;              // [n_cache][P]
+    int32_t* rep = nullptr;                // [n_cache][n] representative of every trajectory
+    int32_t* list = nullptr;               // [n_cache][n] representatives in increasing order
+    int32_t* cnt = nullptr;                // [n_cache] representatives per slot
+};
+void launch_cache_tables(const CacheArgs& a, cudaStream_t s);
 
 // ---- launchers (kernels_contract.cu)
 // a run of small trajectory-class steps (small_step, fuse_prev) in one launch

@@ -38,7 +38,7 @@ __device__ __forceinline__ const float2* operand_ptr(const OperandDesc& d, int o
         }
         p = c.vtab + d.leaf_base + var * d.inst_size;
     } else {
-        const int64_t oi = d.cls == CLS_CONST ? 0 : (d.cls == CLS_TRAJ ? tl : net);
+        const int64_t oi = d.cls == CLS_CONST ? 0 : (d.cls == CLS_TRAJ ? rep_inst(d, tl, c) : net);
         p = c.arena[d.arena] + d.arena_off * c.arena_inst[d.arena] + oi * d.inst_size;
     }
     if (d.n_slice) {
@@ -101,7 +101,10 @@ __global__ void __launch_bounds__(kDirThreads, 3) k_contract_direct(const StepDe
     const int lane = threadIdx.x & 31;
     const int64_t n_tiles = (total + 32 * kDirU - 1) / (32 * kDirU);
     const int64_t warps = (int64_t)gridDim.x * (kDirThreads / 32);
-    int64_t cur_inst = -1, cur_hi = -1;
+    // A cached step runs over the chunk's representatives: instance i writes
+    // trajectory step_inst(i), odelta = (that - i) << n_out (cached steps have
+    // n_out >= 7, so a tile of 128 outputs lies within one instance).
+    int64_t cur_inst = -1, cur_hi = -1, odelta = 0;
     OffT hia = 0, hib = 0;
     const float2 *A = nullptr, *B = nullptr;
     for (int64_t tile = (int64_t)blockIdx.x * (kDirThreads / 32) + (threadIdx.x >> 5); tile < n_tiles; tile += warps) {
@@ -116,8 +119,10 @@ __global__ void __launch_bounds__(kDirThreads, 3) k_contract_direct(const StepDe
             const int64_t inst = gg >> s.n_out;
             const int64_t o = gg & mask;
             if (inst != cur_inst) {
-                A = operand_ptr(s.op[0], s.out_cls, inst, c);
-                B = operand_ptr(s.op[1], s.out_cls, inst, c);
+                const int64_t tl = step_inst(s.cache, inst, c);
+                odelta = (tl - inst) << s.n_out;
+                A = operand_ptr(s.op[0], s.out_cls, tl, c);
+                B = operand_ptr(s.op[1], s.out_cls, tl, c);
                 cur_inst = inst;
             }
             const int64_t hi = o >> lowb;
@@ -163,7 +168,7 @@ __global__ void __launch_bounds__(kDirThreads, 3) k_contract_direct(const StepDe
 #pragma unroll
         for (int u = 0; u < kDirU; u++) {
             const int64_t g = tile * (32 * kDirU) + u * 32 + lane;
-            if (g < total) outbase[g] = acc[u];
+            if (g < total) outbase[g + odelta] = acc[u];
         }
     }
 }
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_contract_micro(const StepDes
     const int64_t n_hi = (int64_t)1 << (nk - klo);
     const float sa = s.op[0].conj ? -1.f : 1.f, sb = s.op[1].conj ? -1.f : 1.f;
     float2* outbase = c.arena[s.out_arena] + s.out_off * c.arena_inst[s.out_arena];
-    int64_t cur_inst = -1, cur_hi = -1;
+    int64_t cur_inst = -1, cur_hi = -1, cur_tl = 0;
     int32_t hia = 0, hib = 0;
     const float2 *A = nullptr, *B = nullptr;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
@@ -255,8 +260,9 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_contract_micro(const StepDes
             o = ((o >> cbit) << (cbit + 1)) | (o & (((int64_t)1 << cbit) - 1));
         }
         if (inst != cur_inst) {
-            A = operand_ptr(s.op[0], s.out_cls, inst, c);
-            B = operand_ptr(s.op[1], s.out_cls, inst, c);
+            cur_tl = step_inst(s.cache, inst, c);   // a cached step runs over representatives
+            A = operand_ptr(s.op[0], s.out_cls, cur_tl, c);
+            B = operand_ptr(s.op[1], s.out_cls, cur_tl, c);
             cur_inst = inst;
         }
         const int64_t hi = o >> lowb;
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(kDirThreads, 2) k_contract_micro(const StepDes
                     }
             }
         }
-        float2* out = outbase + inst * s.out_size + o;
+        float2* out = outbase + cur_tl * s.out_size + o;
 #pragma unroll
         for (int i = 0; i < NA; i++)
 #pragma unroll
@@ -478,11 +484,13 @@ void launch_contract_step(const StepDesc* d_step, const StepDesc& h, const Chunk
     const bool off32 = h.op[0].inst_size < (1ll << 31) && h.op[1].inst_size < (1ll << 31) &&
                        h.out_size < (1ll << 31);
     // algorithmic traffic: every distinct operand element once, the output once
+    // (a cached step reads the operands of its n_inst representatives only)
     double bytes = 8.0 * (double)total;
+    const double n_traj_read = (h.cache > 0 && ctx.cache_list) ? (double)n_inst : (double)ctx.arena_inst[CLS_TRAJ];
     for (int o = 0; o < 2; o++) {
         const OperandDesc& d = h.op[o];
-        double inst = d.mode == OP_LEAF ? (d.leaf_col >= 0 ? (double)ctx.arena_inst[CLS_TRAJ] : 1.0)
-                                        : (double)ctx.arena_inst[d.cls];
+        double inst = d.mode == OP_LEAF ? (d.leaf_col >= 0 ? n_traj_read : 1.0)
+                                        : (d.cls == CLS_TRAJ ? n_traj_read : (double)ctx.arena_inst[d.cls]);
         bytes += 8.0 * inst * (double)d.inst_size;
     }
     const double flops = 8.0 * (double)total * (double)(1ll << h.n_sum);

@@ -101,6 +101,7 @@ struct PackArgs {
                              // power-of-two exponent e of the segment's largest |component| (the
                              // segment is stored scaled by 2^-e), else null
     int32_t seg_slots;       // FP16: complex slots per K segment (the GEMM's kSegKb k-blocks)
+    const int32_t* inst_map; // cached step: packed instance i is local trajectory inst_map[i] (else i)
 };
 
 struct GemmArgs {
@@ -123,6 +124,7 @@ struct GemmArgs {
     uint64_t wait_ns;            // limit of every pipeline wait (ptn_set_wait_limit)
     const int8_t* exp_a;         // FP16 row exponents of A and B (see PackArgs), else null
     const int8_t* exp_b;
+    const int32_t* out_map;      // cached step: instance i writes local trajectory out_map[i] (else i)
     int64_t m_stride[kMaxOut];
     int64_t n_stride[kMaxOut];
     int64_t h_stride[kMaxOut];
@@ -182,7 +184,7 @@ __device__ __forceinline__ const float2* pack_operand_ptr(const OperandDesc& d, 
         if (d.leaf_col >= 0) var = c.var_ids[(int64_t)c.chunk_traj[tl] * c.n_var_cols + d.leaf_col];
         p = c.vtab + d.leaf_base + var * d.inst_size;
     } else {
-        const int64_t oi = d.cls == CLS_CONST ? 0 : (d.cls == CLS_TRAJ ? tl : net);
+        const int64_t oi = d.cls == CLS_CONST ? 0 : (d.cls == CLS_TRAJ ? rep_inst(d, tl, c) : net);
         p = c.arena[d.arena] + d.arena_off * c.arena_inst[d.arena] + oi * d.inst_size;
     }
     if (pcls == CLS_NET && d.n_slice) {
@@ -248,7 +250,7 @@ __device__ __forceinline__ const float2* pack_row_base(const PackArgs& a, const 
     row = jr & (((int64_t)1 << a.n_rb) - 1);
     z = jr >> a.n_rb;
     const int64_t h = z & (((int64_t)1 << a.n_hb) - 1);
-    const int64_t pi = z >> a.n_hb;
+    const int64_t pi = a.inst_map ? (int64_t)a.inst_map[z >> a.n_hb] : z >> a.n_hb;
     const float2* base = pack_operand_ptr(a.op, a.pcls, pi, c);
     base += rtab[row & (kKTab - 1)] + rtab[kKTab + ((row >> 10) & (kKTab - 1))];
     for (int i = 20; i < a.n_rb; i++)
@@ -734,7 +736,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
                 noff[c] = off;
             }
             const int64_t row = (int64_t)t.m0 + q * 32 + lane;
-            int64_t m = row, out_inst = t.inst;
+            int64_t m = row, out_inst = g.out_map ? (int64_t)g.out_map[t.inst] : t.inst;
             if (g.stacked) {
                 out_inst = row >> g.m_bits;
                 m = row & (((int64_t)1 << g.m_bits) - 1);
@@ -980,7 +982,12 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     }
     const int64_t M = (int64_t)1 << nm, N = (int64_t)1 << nn, Kc = (int64_t)1 << st.n_sum;
     const int64_t Kh = ((2 * Kc + kBK - 1) / kBK) * kBK;
-    const int64_t inst_of[3] = {1, ctx.arena_inst[CLS_TRAJ], ctx.arena_inst[CLS_NET]};
+    // A cached step (trajectory class, never stacked) runs over the chunk's
+    // representatives of its slot: its trajectory-class operands are packed
+    // for those instances only and its tiles write their trajectories' outputs.
+    const int32_t* cmap = (st.cache > 0 && ctx.cache_list) ? ctx.cache_list + (int64_t)(st.cache - 1) * ctx.cache_n
+                                                           : nullptr;
+    const int64_t inst_of[3] = {1, cmap ? n_inst : ctx.arena_inst[CLS_TRAJ], ctx.arena_inst[CLS_NET]};
     pa.op = st.op[a];
     pb.op = st.op[b];
     pa.pcls = pack_class(st.op[a], st.out_cls);
@@ -994,6 +1001,8 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     pa.Kh = pb.Kh = (int32_t)Kh;
     pa.n_pinst = inst_of[pa.pcls];
     pb.n_pinst = inst_of[pb.pcls];
+    pa.inst_map = pa.pcls == CLS_TRAJ ? cmap : nullptr;
+    pb.inst_map = pb.pcls == CLS_TRAJ ? cmap : nullptr;
     pa.dst = pack_a;
     pb.dst = pack_b;
     ga.M = (int32_t)M;
@@ -1014,6 +1023,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     ga.net_tl = ctx.net_tl;
     ga.out = ctx.arena[st.out_arena] + st.out_off * ctx.arena_inst[st.out_arena];
     ga.out_size = st.out_size;
+    ga.out_map = cmap;
     ga.err = err;
     ga.wait_ns = g_wait_ns.load(std::memory_order_relaxed);
     const int64_t tot_a = pa.n_pinst * (1ll << nh) * M * (Kh / 2);

@@ -32,6 +32,7 @@
 #include <cstring>
 #include <array>
 #include <functional>
+#include <map>
 #include <queue>
 #include <random>
 #include <unordered_map>
@@ -576,6 +577,59 @@ static void mark_fusable_runs(std::vector<StepDesc>& steps) {
     }
 }
 
+// Intermediate caching across error sets (Sec. VI).  A trajectory-class
+// step's output depends only on the variants its subtree's leaves take, i.e.
+// on the trajectory's entries in the variant columns of those leaves, so all
+// trajectories that agree on these columns share one output.  Walking the
+// steps in order, a step's column set is the union of its operands' sets: a
+// leaf contributes its own column, a buffer the set of the step that wrote it
+// (found by its arena address, which no other live buffer shares).  A
+// trajectory-class step outside the fused runs of small steps (a CTA of a run
+// computes every step of the run for its own trajectory) with at least kCacheMinWork
+// multiply-adds and 2^kCacheMinOutBits outputs per instance (a SIMT tile of
+// 128 outputs then lies within one instance) gets a cache slot and its column
+// bitmap; every later read of its buffer, the root's included, records the slot.
+constexpr double kCacheMinWork = 4096.0;
+constexpr int kCacheMinOutBits = 7;
+static void assign_cache(const ptn_plan* plan, BlockPlan& bp) {
+    const int words = (plan->n_var_cols + 31) / 32;
+    using Bits = std::vector<uint32_t>;
+    std::map<std::pair<int32_t, int64_t>, std::pair<Bits, int32_t>> written;   // (arena, offset) -> (columns, cache)
+    bp.n_cache = 0;
+    bp.cache_words = words;
+    bp.cache_bits.clear();
+    auto read = [&](OperandDesc& d, Bits& acc) {
+        d.cache = 0;
+        if (d.mode == OP_LEAF) {
+            if (d.leaf_col >= 0) acc[d.leaf_col >> 5] |= 1u << (d.leaf_col & 31);
+            return;
+        }
+        auto it = written.find({d.arena, d.arena_off});
+        if (it == written.end()) return;
+        if (d.cls == CLS_TRAJ) d.cache = it->second.second;
+        for (int w = 0; w < words; w++) acc[w] |= it->second.first[w];
+    };
+    for (size_t i = 0; i < bp.steps.size(); i++) {
+        StepDesc& st = bp.steps[i];
+        Bits acc(words, 0u);
+        for (OperandDesc& d : st.op) read(d, acc);
+        st.cache = 0;
+        const bool varies = std::any_of(acc.begin(), acc.end(), [](uint32_t w) { return w != 0; });
+        // a small step joins a fused run if it is marked fuse_prev or the next one
+        // is (fuse_max = 1: every step is launched on its own)
+        const bool fused = plan->opts.fuse_max > 1 && small_step(st) &&
+                           (st.fuse_prev || (i + 1 < bp.steps.size() && bp.steps[i + 1].fuse_prev));
+        if (st.out_cls == CLS_TRAJ && st.kind != STEP_GEMM_STACKED && !fused && varies &&
+            st.n_out >= kCacheMinOutBits && std::ldexp(1.0, st.n_out + st.n_sum) >= kCacheMinWork) {
+            st.cache = ++bp.n_cache;
+            bp.cache_bits.insert(bp.cache_bits.end(), acc.begin(), acc.end());
+        }
+        written[{st.out_arena, st.out_off}] = {std::move(acc), st.cache};
+    }
+    Bits root(words, 0u);
+    read(bp.root.op, root);
+}
+
 // Lower a searched path to step descriptors.  expval: the network is the ket
 // state with every qubit open; the forward intermediates are kept (all of
 // them, or with checkpointing those crossing a segment boundary) and the
@@ -917,7 +971,10 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
     for (int tb = 0; tb < b; tb++)
         if (bp.root.x_stride[tb] < 0) return set_error(PTN_ERR_INVALID_ARG, "internal: root misses an open bit");
     for (int k = 0; k < 3; k++) bp.arena_peak[k] = arenas[k].peak;
-    if (!expval) return PTN_OK;
+    if (!expval) {
+        if (plan->opts.cache_intermediates) assign_cache(plan, bp);
+        return PTN_OK;
+    }
 
     // ---- reversed path (reverse-mode differentiation of the contraction tree).
     // The ket network is holomorphic in its tensors, so for a step
@@ -1291,6 +1348,8 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
         return set_error(PTN_ERR_INVALID_ARG, "network_form must be 0, 1 or 2");
     if (opts.fuse_max < 0) return set_error(PTN_ERR_INVALID_ARG, "fuse_max must be >= 0");
     if (opts.fuse_max == 0) opts.fuse_max = 1024;
+    if (opts.cache_intermediates < 0 || opts.cache_intermediates > 1)
+        return set_error(PTN_ERR_INVALID_ARG, "cache_intermediates must be 0 or 1");
     plan->opts = opts;
     plan->mem_cap = opts.mem_cap_bytes;
 
@@ -1679,9 +1738,9 @@ static void json_op(std::string& s, const OperandDesc& d) {
     char buf[256];
     snprintf(buf, sizeof buf,
              "{\"mode\":%d,\"cls\":%d,\"conj\":%d,\"arena\":%d,\"inst_size\":%lld,\"arena_off\":%lld,"
-             "\"leaf_base\":%lld,\"leaf_col\":%d,\"slices\":[",
+             "\"leaf_base\":%lld,\"leaf_col\":%d,\"cache\":%d,\"slices\":[",
              d.mode, d.cls, d.conj, d.arena, (long long)d.inst_size, (long long)d.arena_off, (long long)d.leaf_base,
-             d.leaf_col);
+             d.leaf_col, d.cache);
     s += buf;
     for (int k = 0; k < d.n_slice; k++) {
         snprintf(buf, sizeof buf, "%s[%d,%lld]", k ? "," : "", d.slice_qubit[k], (long long)d.slice_stride[k]);
@@ -1707,9 +1766,9 @@ static void json_steps(std::string& s, const std::vector<StepDesc>& steps) {
         const StepDesc& st = steps[i];
         snprintf(buf, sizeof buf,
                  "%s{\"out_cls\":%d,\"n_out\":%d,\"n_sum\":%d,\"kind\":%d,\"gemm_a\":%d,\"out_arena\":%d,"
-                 "\"out_off\":%lld,\"fuse_prev\":%d,\"ops\":[",
+                 "\"out_off\":%lld,\"fuse_prev\":%d,\"cache\":%d,\"ops\":[",
                  i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.kind, st.gemm_a, st.out_arena, (long long)st.out_off,
-                 st.fuse_prev);
+                 st.fuse_prev, st.cache);
         s += buf;
         json_op(s, st.op[0]);
         s += ",";
@@ -1747,13 +1806,26 @@ std::string describe_plan(const ptn_plan* p, int detail) {
                  "%s{\"start\":%d,\"b\":%d,\"ket_only\":%d,\"n_gemm\":%d,\"n_steps\":%zu,\"steps_const\":%d,\"steps_traj\":%d,\"steps_net\":%d,"
                  "\"max_out_bits\":%lld,\"arena_const\":%lld,\"arena_traj\":%lld,\"arena_net\":%lld,"
                  "\"macs_const\":%.6e,\"macs_traj\":%.6e,\"macs_net\":%.6e,\"bytes_traj\":%.6e,\"bytes_net\":%.6e,"
-                 "\"est_time\":%.6e,\"mult_traj\":%.1f,\"mult_net\":%.1f",
+                 "\"est_time\":%.6e,\"mult_traj\":%.1f,\"mult_net\":%.1f,\"n_cache\":%d",
                  j ? "," : "", b.start, b.b, b.ket_only, n_gemm, b.steps.size(), cnt[0], cnt[1], cnt[2], (long long)maxout,
                  (long long)b.arena_peak[0], (long long)b.arena_peak[1], (long long)b.arena_peak[2], b.est_macs[0],
                  b.est_macs[1], b.est_macs[2], b.est_bytes[1], b.est_bytes[2], b.est_time, b.est_mult_traj,
-                 b.est_mult_net);
+                 b.est_mult_net, b.n_cache);
         s += buf;
         if (detail) {
+            s += ",\"cache_cols\":[";
+            for (int k = 0; k < b.n_cache; k++) {
+                s += k ? ",[" : "[";
+                bool first = true;
+                for (int c = 0; c < p->n_var_cols; c++)
+                    if ((b.cache_bits[(size_t)k * b.cache_words + (c >> 5)] >> (c & 31)) & 1u) {
+                        snprintf(buf, sizeof buf, "%s%d", first ? "" : ",", c);
+                        s += buf;
+                        first = false;
+                    }
+                s += "]";
+            }
+            s += "]";
             s += ",\"steps\":";
             json_steps(s, b.steps);
             s += ",\"root\":{\"op\":";

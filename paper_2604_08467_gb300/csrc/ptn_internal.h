@@ -42,6 +42,10 @@ struct OperandDesc {
     int64_t leaf_base;       // OP_LEAF: element offset of variant 0 in the variant table
     int32_t leaf_col;        // OP_LEAF: column of the variant index table, -1 = single variant
     int32_t n_slice;         // projected bits fixed from the network's prefix (NET steps)
+    int32_t cache;           // OP_BUF of class TRAJ: 1 + cache slot of the step that wrote it (that
+                             // step computed only representative trajectories: read instance
+                             // rep[slot][tl]); 0 = every trajectory has its own instance
+    int32_t reserved_c[3];
     int32_t slice_qubit[kMaxSlice];
     int64_t slice_stride[kMaxSlice];
 };
@@ -64,6 +68,11 @@ struct StepDesc {
     int32_t tile;            // SIMT micro-tile of a direct step (ptn_tune_tiles): 0 the default (up to
                              // 2 x 2 bits), else 1 + 3 ra + rb with ra, rb <= 2 the most tile bits taken
                              // from operand 0 / 1 (ra = rb = 0: the plain direct kernel)
+    int32_t cache;           // 1 + cache slot of a trajectory-class step whose output is shared by
+                             // the trajectories that agree on every variant column of its subtree
+                             // (intermediate caching across error sets, Sec. VI): it runs over the
+                             // chunk's representative trajectories only; 0 = not cached
+    int32_t reserved_s[3];
     int64_t out_size;        // 2^n_out
     int64_t out_off;         // offset of the output buffer in its arena (elements per instance)
     OperandDesc op[2];
@@ -125,6 +134,10 @@ struct RootRef {             // where the block's final tensor lives
     OperandDesc op;          // read with NET addressing (slices applied)
     int64_t x_stride[32];    // stride of block bit t (or, for the whole-circuit state, qubit t) in the root
 };
+// The kernels copy descriptors into shared memory 16 bytes at a time.
+static_assert(sizeof(OperandDesc) % 16 == 0, "OperandDesc must be a multiple of 16 bytes");
+static_assert(sizeof(StepDesc) % 16 == 0, "StepDesc must be a multiple of 16 bytes");
+static_assert(sizeof(RootRef) % 16 == 0, "RootRef must be a multiple of 16 bytes");
 
 struct BlockPlan {
     int32_t start = 0, b = 0;
@@ -139,6 +152,12 @@ struct BlockPlan {
     double est_mult_traj = 0, est_mult_net = 0;
     int32_t n_leaves_used = 0;
     std::string path_summary;
+    // intermediate caching (ptn_plan_opts.cache_intermediates): per cached step
+    // (slot k = StepDesc.cache - 1) the variant columns its output depends on,
+    // a bitmap of cache_words 32-bit words
+    int32_t n_cache = 0, cache_words = 0;
+    std::vector<uint32_t> cache_bits;
+    uint32_t* d_cache_bits = nullptr;
     // device copy
     StepDesc* d_steps = nullptr;
     // expectation/gradient plans only: the reversed path and its targets

@@ -135,7 +135,9 @@ struct PlanWorkspace {
     DevBuf zpart;                         // per-tile partial totals of large marginal rows
     // final-block harvest of non-proportional sampling
     DevBuf h_rowmax, h_T, h_tcdf, h_tcnt, h_toff, h_scan, h_cnt, h_rank0, h_first;
-    HostBuf h_traj, h_chunk_traj, h_net_tl, h_small, h_grp;
+    // intermediate caching: key halves, hash tables, representatives, lists, counts
+    DevBuf c_h, c_keys, c_first, c_rep, c_list, c_cnt;
+    HostBuf h_traj, h_chunk_traj, h_net_tl, h_small, h_grp, h_ccnt;
     // CUDA-graph execution of a block's chunk (ptn_sample_opts.use_graphs): the
     // capture stream and one executable graph per block, updated in place
     cudaStream_t cap_stream = nullptr;
@@ -155,9 +157,11 @@ struct PlanWorkspace {
                          &s_tmp_c, &s_scan, &zero_prefix, &pack[0], &pack[1], &err, &grp, &grp_cnt,
                          &grp_tile0, &grp_scan, &arena_x[0], &arena_x[1], &ev_steps,
                          &ev_bwd, &ev_root, &ev_pl, &ev_dvt, &ev_terms, &ev_F, &ev_partial, &ev_iota, &zpart,
-                         &h_rowmax, &h_T, &h_tcdf, &h_tcnt, &h_toff, &h_scan, &h_cnt, &h_rank0, &h_first};
+                         &h_rowmax, &h_T, &h_tcdf, &h_tcnt, &h_toff, &h_scan, &h_cnt, &h_rank0, &h_first,
+                         &c_h, &c_keys, &c_first, &c_rep, &c_list, &c_cnt};
         for (DevBuf* b : all) b->release();
         h_grp.release();
+        h_ccnt.release();
         h_traj.release();
         h_chunk_traj.release();
         h_net_tl.release();
@@ -174,6 +178,11 @@ struct ptn_traj {
     int64_t* mult = nullptr;
     int64_t* first = nullptr;
     int32_t* var_ids = nullptr;
+    // non-zero variant entries per trajectory (intermediate caching), built on
+    // first use: row pointers (n_unique + 1), columns, variants
+    int64_t* nz_ptr = nullptr;
+    int32_t* nz_col = nullptr;
+    int32_t* nz_val = nullptr;
     const ptn_plan* plan = nullptr;
 };
 
@@ -218,6 +227,11 @@ ptn_status ensure_device(const ptn_plan* cplan) {
         size_t by = bp.steps.size() * sizeof(StepDesc);
         PTN_CUDA(cudaMalloc(&bp.d_steps, std::max(by, (size_t)16)));
         if (by) PTN_CUDA(cudaMemcpy(bp.d_steps, bp.steps.data(), by, cudaMemcpyHostToDevice));
+        if (!bp.cache_bits.empty()) {
+            const size_t cb = bp.cache_bits.size() * sizeof(uint32_t);
+            PTN_CUDA(cudaMalloc(&bp.d_cache_bits, cb));
+            PTN_CUDA(cudaMemcpy(bp.d_cache_bits, bp.cache_bits.data(), cb, cudaMemcpyHostToDevice));
+        }
     }
     std::vector<RootRef> roots;
     for (auto& bp : plan->blocks) roots.push_back(bp.root);
@@ -275,6 +289,43 @@ struct Chunk {
     int64_t net0, n_net;     // networks [net0, net0 + n_net)
     int64_t traj0, n_traj;   // entries [traj0, traj0 + n_traj) of the chunk_traj list
 };
+
+// The non-zero variant entries of every trajectory (CSR over var_ids), made
+// once per trajectory set on first use by a cached step.
+ptn_status ensure_nz(const ptn_traj* ctr, cudaStream_t s) {
+    ptn_traj* tr = const_cast<ptn_traj*>(ctr);
+    if (tr->nz_ptr) return PTN_OK;
+    const int64_t n = tr->n_unique;
+    int64_t* ptr = nullptr;
+    int64_t* tmp = nullptr;
+    int32_t *col = nullptr, *val = nullptr;
+    auto fail = [&](cudaError_t e) {
+        cudaFree(ptr);
+        cudaFree(tmp);
+        cudaFree(col);
+        cudaFree(val);
+        return set_error(PTN_ERR_CUDA, "variant entry lists: %s", cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&ptr, sizeof(int64_t) * (n + 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&tmp, sizeof(int64_t) * scan_tmp_elems(n + 1))) != cudaSuccess) return fail(e);
+    launch_nz_count(tr->var_ids, n, tr->n_var_cols, ptr, s);
+    launch_exclusive_scan(ptr, ptr, n + 1, tmp, s);
+    int64_t total = 0;
+    if ((e = cudaMemcpyAsync(&total, ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMalloc(&col, sizeof(int32_t) * std::max<int64_t>(total, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&val, sizeof(int32_t) * std::max<int64_t>(total, 1))) != cudaSuccess)
+        return fail(e);
+    launch_nz_fill(tr->var_ids, n, tr->n_var_cols, ptr, col, val, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    cudaFree(tmp);
+    tr->nz_ptr = ptr;
+    tr->nz_col = col;
+    tr->nz_val = val;
+    return PTN_OK;
+}
 
 // Contract n_net networks of block j; marg/Z outputs are device arrays.
 ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const int32_t* d_net_traj,
@@ -381,6 +432,21 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     if ((e = ws->err.grow(sizeof(int)))) return e;
     if ((e = ws->h_small.grow(64))) return e;
     if (finalize_tiles(bp.b) > 1 && (e = ws->zpart.grow(sizeof(double) * max_n * finalize_tiles(bp.b)))) return e;
+    // intermediate caching: tables sized for the largest chunk
+    const bool caching = plan->opts.cache_intermediates && bp.n_cache > 0 && max_t >= 2;
+    auto table_size = [](int64_t n) {
+        int64_t P = 1;
+        while (P < 2 * n) P <<= 1;
+        return P;
+    };
+    if (caching) {
+        const int64_t nc = bp.n_cache, P = table_size(max_t);
+        if ((e = ensure_nz(tr, s)) || (e = ws->c_h.grow(sizeof(uint64_t) * 2 * nc * max_t)) ||
+            (e = ws->c_keys.grow(sizeof(unsigned long long) * nc * P)) || (e = ws->c_first.grow(sizeof(int32_t) * nc * P)) ||
+            (e = ws->c_rep.grow(sizeof(int32_t) * nc * max_t)) || (e = ws->c_list.grow(sizeof(int32_t) * nc * max_t)) ||
+            (e = ws->c_cnt.grow(sizeof(int32_t) * nc)) || (e = ws->h_ccnt.grow(sizeof(int32_t) * nc)))
+            return e;
+    }
     PTN_CUDA(cudaMemsetAsync(ws->err.p, 0, sizeof(int), s));
     const RootRef* d_root = plan->d_roots + j;
     if (graphs) {
@@ -389,6 +455,33 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
     }
     for (size_t ci = 0; ci < chunks.size(); ci++) {
         const Chunk& c = chunks[ci];
+        // Cached steps run over the chunk's representatives: their tables and
+        // counts are made (and the counts read back) before the chunk's steps
+        // are launched or recorded.
+        const int32_t* ccnt = nullptr;
+        if (caching && c.n_traj >= 2) {
+            CacheArgs ca;
+            ca.n_cache = bp.n_cache;
+            ca.words = bp.cache_words;
+            ca.n = c.n_traj;
+            ca.P = table_size(c.n_traj);
+            ca.chunk_traj = ws->chunk_traj.as<int32_t>() + c.traj0;
+            ca.nz_ptr = tr->nz_ptr;
+            ca.nz_col = tr->nz_col;
+            ca.nz_val = tr->nz_val;
+            ca.bits = bp.d_cache_bits;
+            ca.h = ws->c_h.as<uint64_t>();
+            ca.keys = ws->c_keys.as<unsigned long long>();
+            ca.first = ws->c_first.as<int32_t>();
+            ca.rep = ws->c_rep.as<int32_t>();
+            ca.list = ws->c_list.as<int32_t>();
+            ca.cnt = ws->c_cnt.as<int32_t>();
+            launch_cache_tables(ca, s);
+            int32_t* hc = ws->h_ccnt.as<int32_t>();
+            PTN_CUDA(cudaMemcpyAsync(hc, ca.cnt, sizeof(int32_t) * bp.n_cache, cudaMemcpyDeviceToHost, s));
+            PTN_CUDA(cudaStreamSynchronize(s));
+            ccnt = hc;
+        }
         // With graphs, the chunk's launches are recorded on the capture stream
         // (nothing runs while recording) and the graph is launched on s.
         cudaStream_t ls = s;
@@ -423,6 +516,11 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         ctx.arena_inst[CLS_CONST] = 1;
         ctx.arena_inst[CLS_TRAJ] = c.n_traj;
         ctx.arena_inst[CLS_NET] = c.n_net;
+        if (ccnt) {
+            ctx.cache_rep = ws->c_rep.as<int32_t>();
+            ctx.cache_list = ws->c_list.as<int32_t>();
+            ctx.cache_n = c.n_traj;
+        }
         for (size_t st = 0; st < bp.steps.size(); st++) {
             const StepDesc& h = bp.steps[st];
             StepTag tag(j, (int)st);
@@ -436,6 +534,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
                 }
             }
             int64_t ni = h.out_cls == CLS_CONST ? 1 : (h.out_cls == CLS_TRAJ ? c.n_traj : c.n_net);
+            if (ccnt && h.cache > 0) ni = ccnt[h.cache - 1];
             if (h.kind == STEP_GEMM || h.kind == STEP_GEMM_STACKED) {
                 e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(), gt,
                                      precision, ls);
@@ -554,7 +653,10 @@ void ptn_plan_destroy(ptn_plan* plan) {
         cudaFree(plan->d_leaf_site_ptr);
         cudaFree(plan->d_leaf_site_idx);
         cudaFree(plan->d_leaf_site_mul);
-        for (auto& b : plan->blocks) cudaFree(b.d_steps);
+        for (auto& b : plan->blocks) {
+            cudaFree(b.d_steps);
+            cudaFree(b.d_cache_bits);
+        }
         cudaFree(plan->d_roots);
     }
     delete plan->expval;
@@ -734,6 +836,9 @@ ptn_status ptn_traj_copy(const ptn_traj* t, uint8_t* kraus_out, double* logq_out
 
 void ptn_traj_destroy(ptn_traj* t) {
     if (!t) return;
+    cudaFree(t->nz_ptr);
+    cudaFree(t->nz_col);
+    cudaFree(t->nz_val);
     cudaFree(t->kraus);
     cudaFree(t->logq);
     cudaFree(t->mult);

@@ -34,7 +34,8 @@ State& st() {
 }
 const char* kNames[K_COUNT] = {"contract_direct", "contract_gemm", "finalize", "presample", "logq",
                                "dedup", "var_ids", "scan", "alloc_shots", "sample_parents",
-                               "emit_children", "gemm_pack", "expval", "misc", "harvest", "contract_small"};
+                               "emit_children", "gemm_pack", "expval", "misc", "harvest", "contract_small",
+                               "cache_tables"};
 cudaEvent_t take_event() {
     State& s = st();
     if (!s.pool.empty()) {

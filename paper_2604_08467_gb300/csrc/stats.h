@@ -9,7 +9,7 @@ namespace ptn {
 
 enum KernelId {
     K_CONTRACT_DIRECT = 0, K_CONTRACT_GEMM, K_FINALIZE, K_PRESAMPLE, K_LOGQ, K_DEDUP, K_VAR_IDS, K_SCAN,
-    K_ALLOC, K_SAMPLE_PARENTS, K_EMIT, K_PACK, K_EXPVAL, K_MISC, K_HARVEST, K_CONTRACT_SMALL, K_COUNT
+    K_ALLOC, K_SAMPLE_PARENTS, K_EMIT, K_PACK, K_EXPVAL, K_MISC, K_HARVEST, K_CONTRACT_SMALL, K_CACHE, K_COUNT
 };
 
 // Path step the calling thread is launching (recorded with each timed launch).

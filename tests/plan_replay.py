@@ -40,14 +40,33 @@ def _order(n_inst, schedule):
     return range(n_inst - 1, -1, -1) if schedule == "desc" else range(n_inst)
 
 
-def run_block(desc, j, kraus_rows, net_traj, net_prefix, schedule=None):
+def cache_reps(desc, j, vids, chunk_traj):
+    """Per cache slot of block j, the representative of every local trajectory:
+    the first trajectory of the chunk with the same variants on the columns the
+    planner lists for the slot (computed here from those lists directly)."""
+    reps = []
+    for cols in desc["blocks"][j]["cache_cols"]:
+        first, rep = {}, []
+        for tl, g in enumerate(chunk_traj):
+            key = tuple(int(v) for v in vids[g, cols])
+            rep.append(first.setdefault(key, tl))
+        reps.append(rep)
+    return reps
+
+
+def run_block(desc, j, kraus_rows, net_traj, net_prefix, schedule=None, cache=False):
     """Marginals [n_net, 2^b] (complex64 arithmetic) of block j for the given
     networks (net_traj non-decreasing), one chunk holding all of them.
 
     schedule "asc" / "desc": every fused run of small steps is executed one
     instance at a time, each instance walking the whole run before the next
     starts (in ascending / descending instance order), the two extreme
-    interleavings of a fused launch's CTAs; the result must not change."""
+    interleavings of a fused launch's CTAs; the result must not change.
+
+    cache: intermediate caching as the planner marked it: a cached step is
+    computed for its slot's representative trajectories only (the other
+    instances of its output are filled with NaN) and every operand that records
+    a slot reads the representative's instance."""
     blk = desc["blocks"][j]
     vt = np.array(desc["var_table"], dtype=np.float32).view(np.complex64)
     vids = var_ids(desc, kraus_rows)
@@ -60,6 +79,7 @@ def run_block(desc, j, kraus_rows, net_traj, net_prefix, schedule=None):
         net_tl[n] = len(chunk_traj) - 1
     n_traj, n_net = len(chunk_traj), len(net_traj)
     inst_of = {0: 1, 1: n_traj, 2: n_net}
+    reps = cache_reps(desc, j, vids, chunk_traj) if cache else None
     arenas = [np.zeros(max(blk["arena_const"], 1), np.complex64),
               np.zeros(max(blk["arena_traj"] * n_traj, 1), np.complex64),
               np.zeros(max(blk["arena_net"] * n_net, 1), np.complex64)]
@@ -75,6 +95,8 @@ def run_block(desc, j, kraus_rows, net_traj, net_prefix, schedule=None):
             arr, base = vt, d["leaf_base"] + var * d["inst_size"]
         else:
             oi = 0 if d["cls"] == 0 else (tl if d["cls"] == 1 else net)
+            if reps is not None and d["cls"] == 1 and d.get("cache", 0):
+                oi = reps[d["cache"] - 1][tl]
             arr = arenas[d["arena"]]
             base = d["arena_off"] * inst_of[d["arena"]] + oi * d["inst_size"]
         for q, st in d["slices"]:
@@ -96,8 +118,15 @@ def run_block(desc, j, kraus_rows, net_traj, net_prefix, schedule=None):
 
     for run in _runs(blk["steps"], schedule):
         if len(run) == 1:
-            for inst in range(inst_of[run[0]["out_cls"]]):
-                one(run[0], inst)
+            st = run[0]
+            k = st.get("cache", 0) if reps is not None else 0
+            for inst in range(inst_of[st["out_cls"]]):
+                if k and reps[k - 1][inst] != inst:
+                    size = 1 << st["n_out"]
+                    obase = st["out_off"] * inst_of[st["out_arena"]] + inst * size
+                    arenas[st["out_arena"]][obase:obase + size] = np.nan
+                else:
+                    one(st, inst)
             continue
         for inst in _order(inst_of[run[0]["out_cls"]], schedule):
             for st in run:

@@ -181,6 +181,7 @@ void launch_cache_tables(const CacheArgs& a, cudaStream_t s) {
     k_cache_keys<<<grid, 256, 0, s>>>(a);
     k_cache_rep<<<grid, 256, 0, s>>>(a);
     k_cache_list<<<(unsigned)a.n_cache, kListThreads, 0, s>>>(a);
+    count_launches(K_CACHE, 2);   // three kernels under one scope
 }
 
 }  // namespace ptn

@@ -536,6 +536,7 @@ void launch_finalize(const RootRef* d_root, const ChunkCtx& ctx, int b, int64_t 
     const int64_t tiles = finalize_tiles(b);
     StatScope sc(K_FINALIZE, s, (double)n_net * (double)(1ll << b) * 12.0, 0.0);
     k_finalize<<<(unsigned)(n_net * tiles), kFinThreads, 0, s>>>(d_root, ctx, b, tiles, marg, Z, part);
+    if (tiles > 1) count_launches(K_FINALIZE);
     if (tiles > 1) k_finalize_sum<<<(unsigned)((n_net + 127) / 128), 128, 0, s>>>(part, tiles, n_net, Z);
 }
 

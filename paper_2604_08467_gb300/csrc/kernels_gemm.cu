@@ -1050,6 +1050,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
             const int64_t tot = pk == &pa ? tot_a : tot_b;
             k_pack<F><<<grid_of(tot), 256, 0, s>>>(*pk, ctx);
         }
+        count_launches(K_PACK);   // two pack kernels under one scope
     }
     CUtensorMap mA, mB;
     int64_t blocks = ga.tiles_m * ga.tiles_n * n_inst * (1ll << nh);
@@ -1073,6 +1074,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
             acc += ((r + kBM - 1) / kBM) * ga.tiles_n;
         }
         blocks = acc;
+        count_launches(K_MISC);
         k_group_tiles<<<(unsigned)((grp.n_groups + 256) / 256), 256, 0, s>>>(grp.d_net0, grp.n_groups, nm,
                                                                               ga.tiles_n, grp.d_cnt);
         launch_exclusive_scan(grp.d_cnt, grp.d_tile0, grp.n_groups + 1, grp.d_scan, s);

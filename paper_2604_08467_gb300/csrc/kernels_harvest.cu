@@ -282,6 +282,7 @@ void launch_harvest_ranks(const int32_t* traj, int64_t n, int64_t n_traj_max, in
                           int64_t* rank0, cudaStream_t s) {
     if (n <= 0) return;
     cudaMemsetAsync(first, 0xFF, sizeof(unsigned long long) * n_traj_max, s);
+    count_launches(K_HARVEST, 2);
     k_first_net<<<grid1(n, 256), 256, 0, s>>>(traj, n, first);
     k_rank0_uniform<<<grid1(n, 256), 256, 0, s>>>(traj, first, n, shots, rank0);
 }
@@ -296,6 +297,7 @@ int64_t run_harvest_count(const HarvestArgs& a, const HarvestScratch& h, int64_t
     cudaMemsetAsync(h.T, 0, sizeof(unsigned long long) * a.n_net, s);
     {
         StatScope sc(K_HARVEST, s, 8.0 * (double)a.n_net * (double)nx, 0.0);
+        count_launches(K_HARVEST);   // two kernels under one scope
         k_row_max<<<grid, kHThreads, 0, s>>>(a.marg, a.b, tiles, h.rowmax);
         k_pop_sums<<<grid, kHThreads, 0, s>>>(a.marg, a.b, tiles, h.rowmax, h.T, a.direct ? h.tcdf : nullptr,
                                                tiles256);
@@ -303,6 +305,7 @@ int64_t run_harvest_count(const HarvestArgs& a, const HarvestScratch& h, int64_t
     if (a.direct) {
         StatScope sc(K_HARVEST, s, 16.0 * (double)a.n_net * (double)tiles256 + 8.0 * (double)a.n_net * (double)nx +
                                        1024.0 * (double)a.n_net * (double)a.shots, 0.0);
+        count_launches(K_HARVEST);
         k_tile_cdf<<<(unsigned)a.n_net, 1024, 0, s>>>(h.tcdf, tiles256);
         cudaMemsetAsync(h.cnt, 0, sizeof(unsigned) * a.n_net * nx, s);
         const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));

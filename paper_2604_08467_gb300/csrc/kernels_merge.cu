@@ -120,6 +120,7 @@ void launch_radix_pass(const uint64_t* key, const int64_t* val, int64_t n, int s
                        uint64_t* key_out, int64_t* val_out, cudaStream_t s) {
     const int64_t n_seg = (n + kSeg - 1) / kSeg;
     StatScope sc(K_MISC, s, 32.0 * (double)n, 0.0);
+    count_launches(K_MISC);   // two kernels under one scope
     k_seg_hist<<<(unsigned)((n_seg + 127) / 128), 128, 0, s>>>(key, n, shift, n_seg, hist);
     launch_exclusive_scan(hist, hist, 256 * n_seg, scan_tmp, s);
     k_seg_scatter<<<(unsigned)((n_seg + 127) / 128), 128, 0, s>>>(key, val, n, shift, n_seg, hist, key_out, val_out);

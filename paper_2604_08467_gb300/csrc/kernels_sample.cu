@@ -496,21 +496,26 @@ void launch_presample(const SiteTable* sites, int32_t n_sites, int64_t n_traj, i
 }
 
 void launch_row_hash(const uint8_t* kraus, int64_t n, int32_t S, uint64_t* h, cudaStream_t s) {
+    count_launches(K_DEDUP);
     k_row_hash<<<grid_for(n, 128, 1 << 30), 128, 0, s>>>(kraus, n, S, h);
 }
 void launch_first_in_run(const uint8_t* kraus, int32_t S, const int64_t* idx, const int64_t* flag, const int64_t* excl,
                          const int64_t* start, int64_t n, int64_t* first, cudaStream_t s) {
+    if (n > 0) count_launches(K_DEDUP);
     if (n > 0) k_first_in_run<<<grid_for(n, 128, 1 << 30), 128, 0, s>>>(kraus, S, idx, flag, excl, start, n, first);
 }
 void launch_iota_i64(int64_t* p, int64_t n, cudaStream_t s) {
+    if (n > 0) count_launches(K_MISC);
     if (n > 0) k_iota_i64<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(p, n);
 }
 void launch_flags_first(const int64_t* first, int64_t n, int64_t* flags, cudaStream_t s) {
+    count_launches(K_DEDUP);
     k_flags_first<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(first, n, flags);
 }
 void launch_dedup_compact(const uint8_t* kraus, const double* logq, const int64_t* first, const int64_t* uid,
                           int64_t n, int32_t S, uint8_t* kraus_u, double* logq_u, int64_t* mult_u, int64_t* first_u,
                           cudaStream_t s) {
+    count_launches(K_DEDUP);
     k_dedup_compact<<<grid_for(n, 128, 1 << 30), 128, 0, s>>>(kraus, logq, first, uid, n, S, kraus_u, logq_u,
                                                               reinterpret_cast<unsigned long long*>(mult_u), first_u);
 }
@@ -540,6 +545,7 @@ void launch_exclusive_scan(const int64_t* in, int64_t* out, int64_t n, int64_t* 
     }
     int64_t* sums = tmp;
     int64_t* offs = tmp + tiles;
+    count_launches(K_SCAN);   // the scope counts one of this level's two kernels
     k_scan_tiles<<<(unsigned)tiles, 1024, 0, s>>>(in, out, n, sums);
     launch_exclusive_scan(sums, offs, tiles, tmp + 2 * tiles + 2, s);
     k_scan_add<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(out, n, offs);
@@ -553,6 +559,7 @@ void launch_alloc_shots(const double* w, int64_t n, int64_t total, uint64_t seed
     k_quantise_cdf<<<1, 1024, 0, s>>>(w, n, bits, cdf_tmp);
     cudaMemsetAsync(m, 0, sizeof(int64_t) * n, s);
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    if (total > 0) count_launches(K_ALLOC);
     if (total > 0)
         k_alloc_draw<<<grid_for(total, 256), 256, 0, s>>>(cdf_tmp, n, total, key,
                                                           philox_tag(STREAM_ALLOC, circuit, 0),
@@ -560,15 +567,19 @@ void launch_alloc_shots(const double* w, int64_t n, int64_t total, uint64_t seed
 }
 
 void launch_mult_times_z(const int64_t* mult, const double* Z, int64_t n, double* w, cudaStream_t s) {
+    count_launches(K_MISC);
     k_mult_times_z<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(mult, Z, n, w);
 }
 void launch_fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s) {
+    if (n > 0) count_launches(K_MISC);
     if (n > 0) k_fill_i64<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(p, v, n);
 }
 void launch_iota_i32(int32_t* p, int64_t n, cudaStream_t s) {
+    if (n > 0) count_launches(K_MISC);
     if (n > 0) k_iota_i32<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(p, n);
 }
 void launch_scale_i64(const int64_t* a, int64_t k, int64_t n, int64_t* out, cudaStream_t s) {
+    if (n > 0) count_launches(K_MISC);
     if (n > 0) k_scale_i64<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(a, k, n, out);
 }
 
@@ -579,6 +590,7 @@ int64_t run_sample_block(const float* marg, int b, int start, const int32_t* ptr
     *st = PTN_OK;
     if (n_parent <= 0) return 0;
     cudaMemsetAsync(sc.first, 0xFF, sizeof(int64_t) * n_traj_max, s);
+    count_launches(K_MISC, 2);   // k_sample_prep, k_rank0
     k_sample_prep<<<grid_for(n_parent, 256, 1 << 30), 256, 0, s>>>(pcount, n_parent, b, ptraj, sc.cap,
                                                                   reinterpret_cast<unsigned long long*>(sc.first));
     launch_exclusive_scan(sc.cap, sc.tmp_off, n_parent, sc.scan_tmp, s);

@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "kernels.cuh"
+#include "stats.h"
 
 namespace ptn {
 void clear_error();
@@ -120,6 +121,7 @@ extern "C" ptn_status ptn_sample_block_noalloc(const float* marg, int32_t b, int
     if (e == cudaSuccess) {
         int64_t blocks = (n_parent + 255) / 256;
         if (blocks > 1024) blocks = 1024;
+        count_launches(K_MISC);
         k_check_parents<<<(unsigned)blocks, 256, 0, s>>>(parent_traj, n_parent, chk);
         e = cudaMemcpyAsync(h_chk, chk, sizeof h_chk, cudaMemcpyDeviceToHost, s);
     }

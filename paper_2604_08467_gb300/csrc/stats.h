@@ -12,6 +12,10 @@ enum KernelId {
     K_ALLOC, K_SAMPLE_PARENTS, K_EMIT, K_PACK, K_EXPVAL, K_MISC, K_HARVEST, K_CONTRACT_SMALL, K_CACHE, K_COUNT
 };
 
+// Counts n launches of kernel `kid` that no StatScope brackets (the launch
+// total then equals the number of kernels launched).
+void count_launches(int kid, int n = 1);
+
 // Path step the calling thread is launching (recorded with each timed launch).
 void set_step_tag(int block, int step);
 struct StepTag {

@@ -456,6 +456,8 @@ def main():
                     help="also run the 64-circuit mixed batch with this many concurrent circuits (0: skip)")
     ap.add_argument("--cache", type=int, default=1, choices=[0, 1],
                     help="intermediate caching across error sets (ptn_plan_opts.cache_intermediates)")
+    ap.add_argument("--keep-products", type=int, default=0, choices=[0, 1],
+                    help="1: materialise outer-product steps instead of forming them in the operand pack")
     ap.add_argument("--nonprop-traj", type=int, default=256,
                     help="trajectories of the non-proportional sub-lines on the paper's family (0: skip)")
     ap.add_argument("--nonprop-sizes", default="50x200,100x600,200x1000",
@@ -504,7 +506,7 @@ def main():
     t_plan = time.perf_counter()
     plan = ptn.ptn_plan_path(cfg["circuit"], cfg["block_sizes"], hypersamples=args.hypersamples,
                              est_traj=cfg["n_traj"], est_shots=cfg["total_shots"], mem_cap_bytes=args.mem_cap_gb * 1e9,
-                             cache_intermediates=bool(args.cache))
+                             cache_intermediates=bool(args.cache), keep_products=bool(args.keep_products))
     t_plan = time.perf_counter() - t_plan
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
@@ -742,7 +744,7 @@ def main():
                            "device_mem_used_gb": (total_b - free_b) / 1e9,
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)",
                            "nets_per_block": nets, "plan_seconds": t_plan,
-                           "cache_intermediates": bool(args.cache),
+                           "cache_intermediates": bool(args.cache), "keep_products": bool(args.keep_products),
                            "precision": f"{args.precision}: complex64 storage, tensor-core operands split hi/lo "
                                         f"({args.precision}), fp64 CDF / log-probabilities",
                            "error_vs_fp64": PRECISIONS[args.precision][1]},

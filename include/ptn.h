@@ -148,6 +148,10 @@ typedef struct {
                                   chunk's trajectories that agree on every variant column of its
                                   subtree, and read through a per-chunk representative table;
                                   results are bit-identical to 0 (no caching) */
+    int32_t  keep_products;    /* 0: an outer-product step (no summed bits) read only by a
+                                  tensor-core step is not launched; that step's operand pack forms
+                                  each element as the product of the two factors (the same
+                                  rounding, so the same results); 1: materialise it */
 } ptn_plan_opts;
 
 /* Network forms of the block marginals (Sec. II-B; the ket-only form gives the

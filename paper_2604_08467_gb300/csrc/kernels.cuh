@@ -163,8 +163,11 @@ struct GroupTable {
 };
 // precision: PTN_PREC_*.  pack_a / pack_b: packing scratch sized for 4-byte
 // elements plus 1/64 slack (the FP16 mode keeps its per-row exponents there).
+// prod_src: the (virt) outer-product step whose output is the operand st.prod - 1, formed
+// in the pack from its two factors (st.prod != 0), else null.
 ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
-                            int* err, const GroupTable& grp, int precision, cudaStream_t s);
+                            int* err, const GroupTable& grp, int precision, cudaStream_t s,
+                            const StepDesc* prod_src = nullptr);
 
 // ---- expectation values and gradients (kernels_expval.cu)
 struct ObsTerm {

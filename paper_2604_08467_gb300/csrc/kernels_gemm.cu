@@ -102,6 +102,11 @@ struct PackArgs {
                              // segment is stored scaled by 2^-e), else null
     int32_t seg_slots;       // FP16: complex slots per K segment (the GEMM's kSegKb k-blocks)
     const int32_t* inst_map; // cached step: packed instance i is local trajectory inst_map[i] (else i)
+    // Outer-product operand (StepDesc.prod): the element is op[o0] * op1[o1], and every
+    // stride above holds o0 in its low and o1 in its high 32 bits (sums stay carry-free,
+    // each factor having at most 2^31 elements per instance); xconj: conjugate the product
+    int32_t prod, xconj;
+    OperandDesc op1;
 };
 
 struct GemmArgs {
@@ -245,19 +250,45 @@ __device__ __forceinline__ void build_rtab(const PackArgs& a, int64_t* rtab) {
         rtab[i] = off;
     }
 }
-__device__ __forceinline__ const float2* pack_row_base(const PackArgs& a, const ChunkCtx& c, const int64_t* rtab,
-                                                      int64_t jr, int64_t& z, int64_t& row) {
+struct PackSrc {
+    const float2* b0;        // the operand's row (outer product: factor 0's)
+    const float2* b1;        // outer product: factor 1's, else unused
+};
+constexpr int64_t kLo32 = 0xffffffffll;
+__device__ __forceinline__ PackSrc pack_row_base(const PackArgs& a, const ChunkCtx& c, const int64_t* rtab,
+                                                 int64_t jr, int64_t& z, int64_t& row) {
     row = jr & (((int64_t)1 << a.n_rb) - 1);
     z = jr >> a.n_rb;
     const int64_t h = z & (((int64_t)1 << a.n_hb) - 1);
     const int64_t pi = a.inst_map ? (int64_t)a.inst_map[z >> a.n_hb] : z >> a.n_hb;
-    const float2* base = pack_operand_ptr(a.op, a.pcls, pi, c);
-    base += rtab[row & (kKTab - 1)] + rtab[kKTab + ((row >> 10) & (kKTab - 1))];
+    int64_t off = rtab[row & (kKTab - 1)] + rtab[kKTab + ((row >> 10) & (kKTab - 1))];
     for (int i = 20; i < a.n_rb; i++)
-        if ((row >> i) & 1) base += a.r_stride[i];
+        if ((row >> i) & 1) off += a.r_stride[i];
     for (int i = 0; i < a.n_hb; i++)
-        if ((h >> i) & 1) base += a.h_stride[i];
-    return base;
+        if ((h >> i) & 1) off += a.h_stride[i];
+    PackSrc src;
+    if (!a.prod) {
+        src.b0 = pack_operand_ptr(a.op, a.pcls, pi, c) + off;
+        src.b1 = nullptr;
+    } else {
+        src.b0 = pack_operand_ptr(a.op, a.pcls, pi, c) + (off & kLo32);
+        src.b1 = pack_operand_ptr(a.op1, a.pcls, pi, c) + (off >> 32);
+    }
+    return src;
+}
+// Element at K offset koff of a row: a plain read, or the product of the two
+// factors with the single-term multiply-add sequence of the SIMT contraction
+// kernels (so the packed values equal those of the materialised product).
+__device__ __forceinline__ float2 pack_load(const PackArgs& a, const PackSrc& src, int64_t koff) {
+    if (!a.prod) return src.b0[koff];
+    const float2 x = src.b0[koff & kLo32], y = src.b1[koff >> 32];
+    const float xi = a.op.conj ? -x.y : x.y, yi = a.op1.conj ? -y.y : y.y;
+    float2 r;
+    r.x = fmaf(x.x, y.x, 0.f);
+    r.x = fmaf(-xi, yi, r.x);
+    r.y = fmaf(x.x, yi, 0.f);
+    r.y = fmaf(xi, y.x, r.y);
+    return r;
 }
 template <int F>
 __device__ __forceinline__ void pack_store(const PackArgs& a, typename Fmt<F>::T* d0, int64_t rowlen, int64_t kc,
@@ -307,7 +338,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
     const int l0 = lk >= 5 ? lane : (lane & ((int)kcp - 1));
     const int64_t n_rows = a.n_pinst << (a.n_hb + a.n_rb);
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const float csign = a.op.conj ? -1.f : 1.f;
+    const float csign = (a.prod ? a.xconj : a.op.conj) ? -1.f : 1.f;
     if (F == FMT_FP16 && kc_real < 32) {
         // short FP16 rows (fewer real slots than a warp, padded to 32): g =
         // kc_real lanes per row, 32 / g rows per warp, the row maximum
@@ -320,10 +351,9 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
             const bool act = jr < n_rows;
             float2 v = make_float2(0.f, 0.f);
             int64_t z = 0, row = 0;
-            const float2* base = nullptr;
             if (act) {
-                base = pack_row_base(a, c, rtab, jr, z, row);
-                v = base[kofs(a, ktab, l0r)];
+                const PackSrc src = pack_row_base(a, c, rtab, jr, z, row);
+                v = pack_load(a, src, kofs(a, ktab, l0r));
             }
             float mx = fmaxf(fabsf(v.x), fabsf(v.y));
             for (int o = g >> 1; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -348,7 +378,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
         for (int64_t w = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < units; w += warps) {
             const int64_t jr = w >> (lk - lseg), sg = w & (nseg - 1);
             int64_t z, row;
-            const float2* base = pack_row_base(a, c, rtab, jr, z, row);
+            const PackSrc src = pack_row_base(a, c, rtab, jr, z, row);
             T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
             const int64_t kc0 = sg << lseg;
             float2 v[kPackRegRow / 32];
@@ -357,7 +387,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
             for (int i = 0; i < kPackRegRow / 32; i++) {
                 const int64_t kc = kc0 + lane + 32 * i;
                 v[i] = make_float2(0.f, 0.f);
-                if (lane + 32 * i < seg && kc < kc_real) v[i] = base[kofs(a, ktab, kc)];
+                if (lane + 32 * i < seg && kc < kc_real) v[i] = pack_load(a, src, kofs(a, ktab, kc));
                 mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
             }
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -375,13 +405,13 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackArgs a
         const int64_t jr = w * rpw + sub;                // (pi, h, row), row fastest
         if (jr >= n_rows) continue;
         int64_t z, row;
-        const float2* base = pack_row_base(a, c, rtab, jr, z, row);
+        const PackSrc src = pack_row_base(a, c, rtab, jr, z, row);
         T* d0 = a.role == 0 ? dst + jr * rowlen : dst + ((z << (a.n_rb + 1)) + 2 * row) * rowlen;
         {
             for (int64_t kc = l0; kc < kcp; kc += lstep) {
                 float re = 0.f, im = 0.f;
                 if (kc < kc_real) {
-                    const float2 v = base[kofs(a, ktab, kc)];
+                    const float2 v = pack_load(a, src, kofs(a, ktab, kc));
                     re = v.x;
                     im = csign * v.y;
                 }
@@ -945,7 +975,7 @@ unsigned grid_of(int64_t n) {
 
 template <int F>
 ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
-                    int* err, const GroupTable& grp, cudaStream_t s) {
+                    int* err, const GroupTable& grp, cudaStream_t s, const StepDesc* prod_src) {
     constexpr int kEB = Fmt<F>::kBytes;
     constexpr int kBK = kRowBytes / kEB;
     const CUtensorMapDataType dt = F == FMT_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -992,6 +1022,36 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
     pb.op = st.op[b];
     pa.pcls = pack_class(st.op[a], st.out_cls);
     pb.pcls = pack_class(st.op[b], st.out_cls);
+    if (st.prod) {
+        // the operand st.prod - 1 is prod_src's outer product: bit p of it (stride
+        // 2^p) is bit p of prod_src's output, at strides out_stride[0 / 1][p] of
+        // the two factors, packed into one word (low / high 32 bits)
+        if (!prod_src || st.prod < 1 || st.prod > 2)
+            return set_error(PTN_ERR_INVALID_ARG, "internal: outer-product operand without its step");
+        PackArgs& px = st.prod - 1 == a ? pa : pb;
+        bool ok = true;
+        auto packed = [&](int64_t v) -> int64_t {
+            if (v <= 0 || (v & (v - 1))) {
+                ok = false;
+                return 0;
+            }
+            const int p = __builtin_ctzll((unsigned long long)v);
+            if (p >= prod_src->n_out) {
+                ok = false;
+                return 0;
+            }
+            return prod_src->out_stride[0][p] | (prod_src->out_stride[1][p] << 32);
+        };
+        const int n_rb = st.prod - 1 == a ? nm : nn;
+        for (int i = 0; i < n_rb; i++) px.r_stride[i] = packed(px.r_stride[i]);
+        for (int i = 0; i < nh; i++) px.h_stride[i] = packed(px.h_stride[i]);
+        for (int i = 0; i < st.n_sum; i++) px.k_stride[i] = packed(px.k_stride[i]);
+        if (!ok) return set_error(PTN_ERR_INVALID_ARG, "internal: outer-product operand with a non-dense stride");
+        px.prod = 1;
+        px.xconj = st.op[st.prod - 1].conj;
+        px.op = prod_src->op[0];
+        px.op1 = prod_src->op[1];
+    }
     pa.role = 0;
     pb.role = 1;
     pa.n_rb = nm;
@@ -1110,7 +1170,7 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
 
 ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, void* pack_a, void* pack_b,
                             int* err, const GroupTable& grp, int precision,
-                            cudaStream_t s) {
+                            cudaStream_t s, const StepDesc* prod_src) {
     // Contractions of at most 16 complex terms run in TF32 hi/lo in every mode:
     // they fill one 128-byte K-block of TF32 exactly where a 16-bit K-block
     // would be half padding, and their time is the epilogue's (FP16 adds
@@ -1119,9 +1179,9 @@ ptn_status launch_gemm_step(const StepDesc& st, const ChunkCtx& ctx, int64_t n_i
         (precision == PTN_PREC_BF16X3 || precision == PTN_PREC_FP16X3))
         precision = PTN_PREC_FP32;
     switch (precision) {
-        case PTN_PREC_FP32: return run_gemm<FMT_TF32>(st, ctx, n_inst, pack_a, pack_b, err, grp, s);
-        case PTN_PREC_BF16X3: return run_gemm<FMT_BF16>(st, ctx, n_inst, pack_a, pack_b, err, grp, s);
-        case PTN_PREC_FP16X3: return run_gemm<FMT_FP16>(st, ctx, n_inst, pack_a, pack_b, err, grp, s);
+        case PTN_PREC_FP32: return run_gemm<FMT_TF32>(st, ctx, n_inst, pack_a, pack_b, err, grp, s, prod_src);
+        case PTN_PREC_BF16X3: return run_gemm<FMT_BF16>(st, ctx, n_inst, pack_a, pack_b, err, grp, s, prod_src);
+        case PTN_PREC_FP16X3: return run_gemm<FMT_FP16>(st, ctx, n_inst, pack_a, pack_b, err, grp, s, prod_src);
     }
     return set_error(PTN_ERR_UNSUPPORTED, "precision mode %d", precision);
 }

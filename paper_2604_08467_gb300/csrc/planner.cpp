@@ -630,6 +630,56 @@ static void assign_cache(const ptn_plan* plan, BlockPlan& bp) {
     read(bp.root.op, root);
 }
 
+// Outer products formed in the operand pack.  A direct step P with no summed
+// bits writes out[o] = f0[a0(o)] f1[a1(o)]; when its only reader is an operand
+// X of a tensor-core step G, G's pack can form each element of X from the two
+// factors instead of reading P's output, and P is not launched.  X reads P's
+// dense output bit by bit (stride 2^p for bit p), so every stride of X maps to
+// one stride per factor.  Conditions: P outside the fused runs, X without
+// projected bits, factors of at most 2^31 elements per instance (the pack keeps
+// both 32-bit offsets in one 64-bit word), and no step between P and G writing
+// into an arena range of either factor (their buffers were released after P).
+static void mark_pack_products(BlockPlan& bp, int fuse_max) {
+    const size_t n = bp.steps.size();
+    std::map<std::pair<int32_t, int64_t>, size_t> writer;
+    std::vector<std::array<int64_t, 2>> prod_of(n, {-1, -1});   // producer of each operand
+    for (size_t i = 0; i < n; i++) {
+        StepDesc& st = bp.steps[i];
+        st.virt = st.prod = st.prod_src = 0;
+        for (int x = 0; x < 2; x++) {
+            const OperandDesc& d = st.op[x];
+            if (d.mode != OP_BUF) continue;
+            auto it = writer.find({d.arena, d.arena_off});
+            if (it != writer.end()) prod_of[i][x] = (int64_t)it->second;
+        }
+        writer[{st.out_arena, st.out_off}] = i;
+    }
+    for (size_t g = 0; g < n; g++) {
+        StepDesc& G = bp.steps[g];
+        if (G.kind == STEP_DIRECT) continue;
+        for (int x = 0; x < 2 && !G.prod; x++) {
+            if (prod_of[g][x] < 0 || G.op[x].n_slice) continue;
+            const size_t k = (size_t)prod_of[g][x];
+            StepDesc& P = bp.steps[k];
+            const bool fused = fuse_max > 1 && small_step(P) && (P.fuse_prev || (k + 1 < n && bp.steps[k + 1].fuse_prev));
+            if (P.kind != STEP_DIRECT || P.n_sum != 0 || P.virt || fused) continue;
+            if (P.op[0].inst_size > (1ll << 31) || P.op[1].inst_size > (1ll << 31)) continue;
+            bool clash = false;
+            for (size_t s = k + 1; s < g && !clash; s++) {
+                const StepDesc& S = bp.steps[s];
+                for (const OperandDesc& f : P.op)
+                    if (f.mode == OP_BUF && f.arena == S.out_arena && f.arena_off < S.out_off + S.out_size &&
+                        S.out_off < f.arena_off + f.inst_size)
+                        clash = true;
+            }
+            if (clash) continue;
+            P.virt = 1;
+            G.prod = 1 + x;
+            G.prod_src = (int32_t)k;
+        }
+    }
+}
+
 // Lower a searched path to step descriptors.  expval: the network is the ket
 // state with every qubit open; the forward intermediates are kept (all of
 // them, or with checkpointing those crossing a segment boundary) and the
@@ -973,6 +1023,7 @@ static ptn_status lower_block(const ptn_plan* plan, const BlockNet& net, const S
     for (int k = 0; k < 3; k++) bp.arena_peak[k] = arenas[k].peak;
     if (!expval) {
         if (plan->opts.cache_intermediates) assign_cache(plan, bp);
+        if (!plan->opts.keep_products) mark_pack_products(bp, plan->opts.fuse_max);
         return PTN_OK;
     }
 
@@ -1350,6 +1401,8 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
     if (opts.fuse_max == 0) opts.fuse_max = 1024;
     if (opts.cache_intermediates < 0 || opts.cache_intermediates > 1)
         return set_error(PTN_ERR_INVALID_ARG, "cache_intermediates must be 0 or 1");
+    if (opts.keep_products < 0 || opts.keep_products > 1)
+        return set_error(PTN_ERR_INVALID_ARG, "keep_products must be 0 or 1");
     plan->opts = opts;
     plan->mem_cap = opts.mem_cap_bytes;
 
@@ -1766,9 +1819,10 @@ static void json_steps(std::string& s, const std::vector<StepDesc>& steps) {
         const StepDesc& st = steps[i];
         snprintf(buf, sizeof buf,
                  "%s{\"out_cls\":%d,\"n_out\":%d,\"n_sum\":%d,\"kind\":%d,\"gemm_a\":%d,\"out_arena\":%d,"
-                 "\"out_off\":%lld,\"fuse_prev\":%d,\"cache\":%d,\"ops\":[",
+                 "\"out_off\":%lld,\"fuse_prev\":%d,\"cache\":%d,\"virt\":%d,\"prod\":%d,\"prod_src\":%d,"
+                 "\"ops\":[",
                  i ? "," : "", st.out_cls, st.n_out, st.n_sum, st.kind, st.gemm_a, st.out_arena, (long long)st.out_off,
-                 st.fuse_prev, st.cache);
+                 st.fuse_prev, st.cache, st.virt, st.prod, st.prod_src);
         s += buf;
         json_op(s, st.op[0]);
         s += ",";

@@ -72,7 +72,11 @@ struct StepDesc {
                              // the trajectories that agree on every variant column of its subtree
                              // (intermediate caching across error sets, Sec. VI): it runs over the
                              // chunk's representative trajectories only; 0 = not cached
-    int32_t reserved_s[3];
+    int32_t virt;            // 1: an outer product (no summed bits) read only by a tensor-core step
+                             // that forms it in its operand pack; not launched
+    int32_t prod;            // tensor-core steps: 1 + the operand (0 / 1) formed in the pack as the
+                             // elementwise product of the factors of step prod_src (a virt step)
+    int32_t prod_src;
     int64_t out_size;        // 2^n_out
     int64_t out_off;         // offset of the output buffer in its arena (elements per instance)
     OperandDesc op[2];

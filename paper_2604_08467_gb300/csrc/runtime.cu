@@ -523,6 +523,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
         }
         for (size_t st = 0; st < bp.steps.size(); st++) {
             const StepDesc& h = bp.steps[st];
+            if (h.virt) continue;   // formed inside its consumer's operand pack
             StepTag tag(j, (int)st);
             if (small_step(h)) {   // a run of small trajectory-class steps: one fused launch
                 size_t en = st + 1;
@@ -537,7 +538,7 @@ ptn_status contract_level(const ptn_plan* plan, const ptn_traj* tr, int j, const
             if (ccnt && h.cache > 0) ni = ccnt[h.cache - 1];
             if (h.kind == STEP_GEMM || h.kind == STEP_GEMM_STACKED) {
                 e = launch_gemm_step(h, ctx, ni, ws->pack[0].p, ws->pack[1].p, ws->err.as<int>(), gt,
-                                     precision, ls);
+                                     precision, ls, h.prod ? &bp.steps[h.prod_src] : nullptr);
                 if (e) {
                     end_capture();
                     return e;
@@ -941,7 +942,7 @@ ptn_status ptn_tune_tiles(ptn_plan* plan, const ptn_traj* traj, int64_t n_probe,
                     continue;
                 }
             }
-            if (h.kind != STEP_DIRECT) continue;
+            if (h.kind != STEP_DIRECT || h.virt) continue;
             int ra_av = 0, rb_av = 0;
             for (int q = 0; q < h.n_out; q++) {
                 const bool va = h.out_stride[0][q] != 0, vb = h.out_stride[1][q] != 0;

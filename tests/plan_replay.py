@@ -104,6 +104,13 @@ def run_block(desc, j, kraus_rows, net_traj, net_prefix, schedule=None, cache=Fa
         v = arr[base:base + d["inst_size"]]
         return np.conj(v) if d["conj"] else v
 
+    def product(src, out_cls, inst):
+        """The outer product of a virt step's factors, read now (as the
+        consumer's operand pack forms it)."""
+        oa = _bits_offsets(src["out_stride"][0], src["n_out"])
+        ob = _bits_offsets(src["out_stride"][1], src["n_out"])
+        return operand(src["ops"][0], out_cls, inst)[oa] * operand(src["ops"][1], out_cls, inst)[ob]
+
     def one(st, inst):
         oa = _bits_offsets(st["out_stride"][0], st["n_out"])
         ob = _bits_offsets(st["out_stride"][1], st["n_out"])
@@ -111,12 +118,26 @@ def run_block(desc, j, kraus_rows, net_traj, net_prefix, schedule=None, cache=Fa
         kb = _bits_offsets(st["sum_stride"][1], st["n_sum"])
         size = 1 << st["n_out"]
         obase = st["out_off"] * inst_of[st["out_arena"]]
-        A = operand(st["ops"][0], st["out_cls"], inst)
-        B = operand(st["ops"][1], st["out_cls"], inst)
+        ops = [operand(st["ops"][x], st["out_cls"], inst) for x in range(2)]
+        if st.get("prod"):
+            x = st["prod"] - 1
+            ops[x] = product(blk["steps"][st["prod_src"]], st["out_cls"], inst)
+            if st["ops"][x]["conj"]:
+                ops[x] = np.conj(ops[x])
+        A, B = ops
         val = (A[oa[:, None] + ka[None, :]] * B[ob[:, None] + kb[None, :]]).sum(axis=1)
         arenas[st["out_arena"]][obase + inst * size: obase + (inst + 1) * size] = val
 
+    def skip(st):
+        """A virt step is not executed: its output is poisoned with NaN."""
+        size = 1 << st["n_out"]
+        obase = st["out_off"] * inst_of[st["out_arena"]]
+        arenas[st["out_arena"]][obase: obase + inst_of[st["out_cls"]] * size] = np.nan
+
     for run in _runs(blk["steps"], schedule):
+        if len(run) == 1 and run[0].get("virt"):
+            skip(run[0])
+            continue
         if len(run) == 1:
             st = run[0]
             k = st.get("cache", 0) if reps is not None else 0

@@ -56,9 +56,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # profiles/k_pack_c2_64traj.md: two GEMM and two pack launches of the middle
 # block); a class's roofline traffic per launch is this ratio times its
 # algorithmic bytes per launch in the timed run.  Classes without a capture
-# of the current kernel report null.
-TRAFFIC_RATIO = {"contract_gemm": (14.089 + 6.385) / (12.10 + 6.44),
-                 "gemm_pack": (6.792 + 12.834) / (6.84 + 12.88)}
+# of the current kernel report null: both kernels changed after those captures
+# (the GEMM epilogue's instance map for cached steps, the pack's outer-product
+# operands), so the ratios are kept for reference only.
+TRAFFIC_RATIO_CAPTURED = {"contract_gemm": (14.089 + 6.385) / (12.10 + 6.44),
+                          "gemm_pack": (6.792 + 12.834) / (6.84 + 12.88)}
+TRAFFIC_RATIO = {}
 
 
 def load_peaks():
@@ -715,9 +718,12 @@ def main():
             r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                  "peak_note": f"hbm copy ({peak_src})"}
         tr = TRAFFIC_RATIO.get(name)
+        old = TRAFFIC_RATIO_CAPTURED.get(name)
         r.update({"frac": r["achieved"] / r["peak"],
                   "traffic": tr * s["alg_bytes"] / max(s["timed_launches"], 1) if tr else None,
                   "traffic_unit": "bytes per launch (ncu DRAM/algorithmic ratio x algorithmic bytes)" if tr else None,
+                  "traffic_note": (f"null: the kernel changed after its last ncu DRAM capture (DRAM/algorithmic "
+                                   f"ratio then {old:.2f})") if (old and not tr) else None,
                   "launches_per_step": s["timed_launches"] / max(steps, 1),
                   "ms_per_step": s["ms"] / max(steps, 1),
                   "share_of_step": sec / max(step_seconds, 1e-12)})

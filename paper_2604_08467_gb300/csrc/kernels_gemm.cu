@@ -1104,7 +1104,14 @@ ptn_status run_gemm(const StepDesc& st, const ChunkCtx& ctx, int64_t n_inst, voi
         if (Kh / 2 < 32) return set_error(PTN_ERR_INVALID_ARG, "internal: FP16 rows shorter than a warp");
     }
     {
-        StatScope sc(K_PACK, s, 8.0 * (double)(tot_a + tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b, 0.0);
+        // algorithmic bytes: every operand element read once (an outer-product
+        // operand: its two factors per instance), the hi/lo rows written once
+        auto rd = [&](const PackArgs& pk, int64_t tot) {
+            return pk.prod ? 8.0 * (double)pk.n_pinst * (double)(pk.op.inst_size + pk.op1.inst_size)
+                           : 8.0 * (double)tot;
+        };
+        StatScope sc(K_PACK, s, rd(pa, tot_a) + rd(pb, tot_b) + 4.0 * kEB * (double)tot_a + 8.0 * kEB * (double)tot_b,
+                     0.0);
         // (grid_of sizes by complex slots; the kernels stride over rows)
         for (PackArgs* pk : {&pa, &pb}) {
             const int64_t tot = pk == &pa ? tot_a : tot_b;

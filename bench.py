@@ -388,7 +388,7 @@ REPLAN_FACTOR = 10       # circuits within this factor of the budget are planned
                          # the restarts
 
 
-def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers):
+def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers, replan=False):
     """Plans (untimed), pre-samples (untimed) and runs the mixed batch through
     ptn_sample_shots_batch, once with one circuit in flight and once with
     `workers`; circuits beyond the planner's limits or the memory cap count as
@@ -405,15 +405,15 @@ def run_mixed_batch(ptn, shard, torch, dist, rank, world, hypersamples, workers)
                                                  est_traj=c["n_traj"], est_shots=c["total_shots"])
         except ptn.PtnError as e:
             status[c["name"]] = f"plan: {ptn.STATUS_NAMES.get(e.status, e.status)}"
-    # a circuit whose modelled time is over the budget but within REPLAN_FACTOR of
-    # it is planned again with REPLAN_FACTOR times the greedy restarts (the
-    # randomised search keeps finding cheaper paths for the 6x5 grids)
+    # replan: a circuit whose modelled time is over the budget but within
+    # REPLAN_FACTOR of it is planned again with REPLAN_FACTOR times the greedy
+    # restarts (the randomised search keeps finding cheaper paths for the 6x5 grids)
     replanned = {}
     for c in cfgs:
         if c["name"] not in plans:
             continue
         est = sum(b["est_time"] for b in plans[c["name"]].describe()["blocks"])
-        if MIXED_MAX_EST_S < est <= REPLAN_FACTOR * MIXED_MAX_EST_S:
+        if replan and MIXED_MAX_EST_S < est <= REPLAN_FACTOR * MIXED_MAX_EST_S:
             p2 = ptn.ptn_plan_path(c["circuit"], c["block_sizes"], hypersamples=REPLAN_FACTOR * hypersamples,
                                    est_traj=c["n_traj"], est_shots=c["total_shots"])
             est2 = sum(b["est_time"] for b in p2.describe()["blocks"])
@@ -476,6 +476,9 @@ def main():
                     help="also run the 64-circuit mixed batch with this many concurrent circuits (0: skip)")
     ap.add_argument("--cache", type=int, default=1, choices=[0, 1],
                     help="intermediate caching across error sets (ptn_plan_opts.cache_intermediates)")
+    ap.add_argument("--replan", type=int, default=0, choices=[0, 1],
+                    help="mixed batch: plan circuits modelled within 10x of the time budget again with 10x the "
+                         "restarts")
     ap.add_argument("--keep-products", type=int, default=0, choices=[0, 1],
                     help="1: materialise outer-product steps instead of forming them in the operand pack")
     ap.add_argument("--nonprop-traj", type=int, default=256,
@@ -703,7 +706,7 @@ def main():
     mixed = None
     if args.mixed_batch > 0:
         del plan          # frees the brickwork workspace so the batch gets the device memory
-        mixed = run_mixed_batch(ptn, shard, torch, dist, rank, world, args.hypersamples, args.mixed_batch)
+        mixed = run_mixed_batch(ptn, shard, torch, dist, rank, world, args.hypersamples, args.mixed_batch, replan=bool(args.replan))
 
     # ---- rooflines.  Tensor-core GEMMs are charged their algorithmic complex
     # flops (8 per complex multiply-add) against the dense peak of their input

@@ -180,7 +180,11 @@ ptn_status ptn_plan_path(const ptn_circuit* circuit, const ptn_noise* noise,
  * class, arena sizes and modelled work.  detail = 1 adds every lowered step
  * (operand descriptors, stride tables), the block roots, the variant-selecting
  * sites of every merged-gate leaf and the complex64 variant table, so the
- * lowering can be inspected or replayed on the host; detail = 2 adds the
+ * lowering can be inspected or replayed on the host.  Each step also carries
+ * its cache slot ("cache", and per block "n_cache" and "cache_cols", the
+ * variant columns of every slot) and its outer-product marks ("virt": formed
+ * in its consumer's pack, "prod" / "prod_src": the operand formed and the
+ * step it comes from).  detail = 2 adds the
  * expectation-value plan of ptn_expval_grad (ket network of the whole circuit,
  * its forward steps, the reversed adjoint steps and the parametrised leaves),
  * building it if needed.  Writes at most cap bytes

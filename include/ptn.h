@@ -152,6 +152,10 @@ typedef struct {
                                   tensor-core step is not launched; that step's operand pack forms
                                   each element as the product of the two factors (the same
                                   rounding, so the same results); 1: materialise it */
+    int32_t  search_threads;   /* 0: the restarts of the path search draw from one random stream,
+                                  in order; n >= 1: restart h draws from its own stream (seeded
+                                  from seed and h) and the restarts run on n host threads; the plan
+                                  then does not depend on n (it differs from the one of 0) */
 } ptn_plan_opts;
 
 /* Network forms of the block marginals (Sec. II-B; the ket-only form gives the

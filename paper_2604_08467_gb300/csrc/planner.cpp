@@ -33,6 +33,7 @@
 #include <array>
 #include <functional>
 #include <map>
+#include <thread>
 #include <queue>
 #include <random>
 #include <unordered_map>
@@ -1300,15 +1301,65 @@ static ptn_status search_and_lower(ptn_plan* plan, BlockNet& net, int j, int sta
     Searcher best(net, cm), cur_s(net, cm);
     double best_time = INFINITY;
     std::uniform_real_distribution<double> U(0.0, 1.0);
-    for (int h = 0; h < opts.hypersamples; h++) {
-        double temp = h == 0 ? 0.0 : 0.02 + 1.0 * U(rng);
-        double costmod = h == 0 ? 1.0 : 0.5 + 1.5 * U(rng);
-        cur_s.run(temp, costmod, rng);
-        if (cur_s.root() < 0) continue;
-        if (cur_s.max_rank > kMaxOut) continue;
-        if (cur_s.time < best_time) {
-            best_time = cur_s.time;
-            best = cur_s;
+    if (opts.search_threads <= 0) {
+        // one random stream for all restarts, in order
+        for (int h = 0; h < opts.hypersamples; h++) {
+            double temp = h == 0 ? 0.0 : 0.02 + 1.0 * U(rng);
+            double costmod = h == 0 ? 1.0 : 0.5 + 1.5 * U(rng);
+            cur_s.run(temp, costmod, rng);
+            if (cur_s.root() < 0) continue;
+            if (cur_s.max_rank > kMaxOut) continue;
+            if (cur_s.time < best_time) {
+                best_time = cur_s.time;
+                best = cur_s;
+            }
+        }
+    } else {
+        // restart h draws from its own stream (seeded from one draw of the plan's
+        // stream and h); the best restart, ties to the lowest h, does not depend
+        // on how the restarts are spread over the threads
+        const uint64_t base = rng();
+        const int T = std::max(1, std::min(opts.search_threads, opts.hypersamples));
+        std::vector<Searcher> wbest(T, Searcher(net, cm));
+        std::vector<double> wtime(T, INFINITY);
+        std::vector<int> wh(T, -1);
+        std::vector<int> wfail(T, 0);
+        auto work = [&](int w) {
+            try {
+                Searcher cur(net, cm);
+                for (int h = w; h < opts.hypersamples; h += T) {
+                    uint64_t z = base + 0x9E3779B97F4A7C15ull * (uint64_t)(h + 1);   // splitmix64 step
+                    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+                    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+                    std::mt19937_64 r(z ^ (z >> 31));
+                    std::uniform_real_distribution<double> Uw(0.0, 1.0);
+                    const double temp = h == 0 ? 0.0 : 0.02 + 1.0 * Uw(r);
+                    const double costmod = h == 0 ? 1.0 : 0.5 + 1.5 * Uw(r);
+                    cur.run(temp, costmod, r);
+                    if (cur.root() < 0 || cur.max_rank > kMaxOut) continue;
+                    if (cur.time < wtime[w]) {   // h increases within a thread: ties keep the lower h
+                        wtime[w] = cur.time;
+                        wh[w] = h;
+                        wbest[w] = cur;
+                    }
+                }
+            } catch (...) {
+                wfail[w] = 1;
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int w = 1; w < T; w++) pool.emplace_back(work, w);
+        work(0);
+        for (auto& t : pool) t.join();
+        int pick = -1;
+        for (int w = 0; w < T; w++) {
+            if (wfail[w]) return set_error(PTN_ERR_OOM, "block %d: path search thread failed", j);
+            if (wh[w] < 0) continue;
+            if (pick < 0 || wtime[w] < wtime[pick] || (wtime[w] == wtime[pick] && wh[w] < wh[pick])) pick = w;
+        }
+        if (pick >= 0) {
+            best_time = wtime[pick];
+            best = wbest[pick];
         }
     }
     if (!std::isfinite(best_time))
@@ -1403,6 +1454,8 @@ ptn_status build_plan(const ptn_circuit* c, const ptn_noise* nz, const int32_t* 
         return set_error(PTN_ERR_INVALID_ARG, "cache_intermediates must be 0 or 1");
     if (opts.keep_products < 0 || opts.keep_products > 1)
         return set_error(PTN_ERR_INVALID_ARG, "keep_products must be 0 or 1");
+    if (opts.search_threads < 0 || opts.search_threads > 1024)
+        return set_error(PTN_ERR_INVALID_ARG, "search_threads must be in 0..1024");
     plan->opts = opts;
     plan->mem_cap = opts.mem_cap_bytes;
 

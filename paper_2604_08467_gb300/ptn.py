@@ -57,7 +57,8 @@ class ptn_plan_opts(C.Structure):
     _fields_ = [("hypersamples", C.c_int32), ("split_gates", C.c_int32), ("seed", C.c_uint64),
                 ("est_traj", C.c_double), ("est_shots", C.c_double), ("mem_cap_bytes", C.c_double),
                 ("simt_only", C.c_int32), ("grad_checkpoint", C.c_int32), ("network_form", C.c_int32),
-                ("fuse_max", C.c_int32), ("cache_intermediates", C.c_int32), ("keep_products", C.c_int32)]
+                ("fuse_max", C.c_int32), ("cache_intermediates", C.c_int32), ("keep_products", C.c_int32),
+                ("search_threads", C.c_int32)]
 
 
 class ptn_sample_opts(C.Structure):
@@ -335,7 +336,7 @@ class Shots:
 
 def ptn_plan_path(circ, block_sizes=None, hypersamples=100, split_gates=1, seed=1234, est_traj=1024,
                   est_shots=1e6, mem_cap_bytes=0.0, simt_only=False, grad_checkpoint=False, network_form=0,
-                  fuse_max=0, cache_intermediates=True, keep_products=False):
+                  fuse_max=0, cache_intermediates=True, keep_products=False, search_threads=0):
     """Plan a circuit (ptn_plan_opts in include/ptn.h).  Intermediate caching
     across error sets is on by default here (results are bit-identical with
     it off; the C structure's zero value is off)."""
@@ -347,7 +348,7 @@ def ptn_plan_path(circ, block_sizes=None, hypersamples=100, split_gates=1, seed=
     bs = (C.c_int32 * len(block_sizes))(*block_sizes)
     opts = ptn_plan_opts(hypersamples, split_gates, seed, float(est_traj), float(est_shots), float(mem_cap_bytes),
                          int(bool(simt_only)), int(bool(grad_checkpoint)), int(network_form), int(fuse_max),
-                         int(bool(cache_intermediates)), int(bool(keep_products)))
+                         int(bool(cache_intermediates)), int(bool(keep_products)), int(search_threads))
     h = C.c_void_p()
     _check(lib().ptn_plan_path(C.byref(c), C.byref(nz), bs, len(block_sizes), C.byref(opts), C.byref(h)))
     del keep

@@ -204,6 +204,7 @@ struct Searcher {
     std::vector<Move> moves;
     double time = 0, macs[3] = {0, 0, 0}, bytes[3] = {0, 0, 0};
     int64_t max_rank = 0;
+    int64_t max_sum = 0;     // most summed bits of a step, counted as the lowering counts them
 
     Searcher(const BlockNet& n, const CostModel& c) : net(&n), cm(&c) {}
 
@@ -217,6 +218,7 @@ struct Searcher {
         time = 0;
         for (int k = 0; k < 3; k++) macs[k] = bytes[k] = 0;
         max_rank = 0;
+        max_sum = 0;
         int nl = net->n_leaf_tensors;
         for (size_t i = 0; i < net->tidx.size(); i++) {
             GT g;
@@ -341,6 +343,23 @@ struct Searcher {
         std::vector<int32_t> out;
         int32_t nsum, cls, nslice;
         result(a, b, out, nsum, cls, nslice);
+        {
+            // a prefix-projected index the two share is fixed per network, not
+            // summed, when the step is lowered
+            int32_t fixed = 0;
+            const GT &A = t[a], &B = t[b];
+            for (size_t i = 0, j = 0; i < A.idx.size() && j < B.idx.size();) {
+                if (A.idx[i] < B.idx[j]) i++;
+                else if (B.idx[j] < A.idx[i]) j++;
+                else {
+                    const int32_t x = A.idx[i];
+                    if (is_slice(x) && occ[x].size() == 2) fixed++;
+                    i++;
+                    j++;
+                }
+            }
+            max_sum = std::max<int64_t>(max_sum, nsum - fixed);
+        }
         if (count) account(cls, out, nsum, t[a], t[b]);
         GT g;
         g.idx = std::move(out);
@@ -1308,7 +1327,7 @@ static ptn_status search_and_lower(ptn_plan* plan, BlockNet& net, int j, int sta
             double costmod = h == 0 ? 1.0 : 0.5 + 1.5 * U(rng);
             cur_s.run(temp, costmod, rng);
             if (cur_s.root() < 0) continue;
-            if (cur_s.max_rank > kMaxOut) continue;
+            if (cur_s.max_rank > kMaxOut || cur_s.max_sum > kMaxSum) continue;
             if (cur_s.time < best_time) {
                 best_time = cur_s.time;
                 best = cur_s;
@@ -1336,7 +1355,7 @@ static ptn_status search_and_lower(ptn_plan* plan, BlockNet& net, int j, int sta
                     const double temp = h == 0 ? 0.0 : 0.02 + 1.0 * Uw(r);
                     const double costmod = h == 0 ? 1.0 : 0.5 + 1.5 * Uw(r);
                     cur.run(temp, costmod, r);
-                    if (cur.root() < 0 || cur.max_rank > kMaxOut) continue;
+                    if (cur.root() < 0 || cur.max_rank > kMaxOut || cur.max_sum > kMaxSum) continue;
                     if (cur.time < wtime[w]) {   // h increases within a thread: ties keep the lower h
                         wtime[w] = cur.time;
                         wh[w] = h;
@@ -1363,7 +1382,8 @@ static ptn_status search_and_lower(ptn_plan* plan, BlockNet& net, int j, int sta
         }
     }
     if (!std::isfinite(best_time))
-        return set_error(PTN_ERR_TOO_LARGE, "block %d: no path with at most %d open bits per tensor", j, kMaxOut);
+        return set_error(PTN_ERR_TOO_LARGE, "block %d: no path with at most %d open and %d summed bits per step", j,
+                         kMaxOut, kMaxSum);
     bp.start = start;
     bp.b = b;
     for (int k = 0; k < 3; k++) {

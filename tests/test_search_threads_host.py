@@ -47,3 +47,15 @@ def test_negative_thread_count_rejected():
     c1 = W.config_c1()
     with pytest.raises(ptn.PtnError):
         ptn.ptn_plan_path(c1["circuit"], c1["block_sizes"], hypersamples=4, search_threads=-1)
+
+
+def test_search_keeps_only_lowerable_paths():
+    """Paths with a step summing more bits than a step may (24) are skipped by
+    the search rather than chosen and rejected at lowering: the ket-only form of
+    a 6x5-grid block whose cheapest ket-only path exceeds the limit still plans,
+    and every lowered step stays within it."""
+    c = {x["name"]: x for x in W.config_c3()}["c3_55_grid6x5_d13"]
+    plan = ptn.ptn_plan_path(c["circuit"], c["block_sizes"], hypersamples=100, est_traj=c["n_traj"],
+                             est_shots=c["total_shots"], network_form=2)
+    d = plan.describe(detail=1)
+    assert all(st["n_sum"] <= 24 and st["n_out"] <= 40 for b in d["blocks"] for st in b["steps"])
